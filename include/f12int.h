@@ -1,0 +1,145 @@
+/*
+ * f12int.h -- C ABI of the GB300 library for the two-electron integrals that
+ * explicitly correlated (F12) methods need with the range-separated
+ * correlation factor of Silkowski, Lesiuk and Moszynski (arXiv:1412.5070).
+ *
+ * Conventions shared by every entry point
+ *   - Every call returns an f12int_status; nothing throws across the ABI.
+ *   - Host arrays passed in are borrowed for the duration of the call and
+ *     copied; the caller keeps ownership.
+ *   - Device pointers (suffix _dev) are owned by the caller, must be
+ *     allocated on the context's device and must stay valid until the work
+ *     queued on the given stream has finished.
+ *   - Streams are raw cudaStream_t values passed as void*; NULL means the
+ *     context's own stream.
+ *   - Units are bohr.  Primitives are the unnormalised Cartesian Gaussians
+ *     x_A^i y_A^k z_A^m exp(-a r_A^2) of Sec. 2.1 (Eq. basis); contraction
+ *     coefficients multiply them as given.
+ *   - Cartesian components of a shell of angular momentum l are ordered
+ *     lexicographically: for l = 2 xx, xy, xz, yy, yz, zz; for l = 3 xxx,
+ *     xxy, xxz, xyy, xyz, xzz, yyy, yyz, yzz, zzz.
+ *   - A block of a shell quartet (ab|cd) is dense FP64, row-major
+ *     [a][b][c][d] over those components.
+ */
+#ifndef F12INT_H
+#define F12INT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct f12int_ctx f12int_ctx;
+
+typedef enum {
+  F12INT_OK = 0,
+  F12INT_EINVAL = -1,    /* an argument is out of range or inconsistent        */
+  F12INT_ENOMEM = -2,    /* device memory beyond the context's HBM budget       */
+  F12INT_EDOMAIN = -3,   /* correlation-factor parameters outside the domain    */
+  F12INT_ENOTREADY = -4, /* a basis or factor was not set before use            */
+  F12INT_ETIMEOUT = -5,  /* a bounded wait ran out                              */
+  F12INT_ECUDA = -6,     /* a CUDA runtime call failed                          */
+  F12INT_EDEVICE = -7    /* a device-side check failed (status word)            */
+} f12int_status;
+
+/* Integral classes of Sec. 2.1: I1 (ab|1/r12|cd), Eq. I1; I2 (ab|f/r12|cd),
+ * Eq. I2; I3 (ab|f|cd), Eq. I3; I4 (ab|f f'|cd), Eq. I4; I5 (ab|[f,T1]|cd),
+ * Eq. I5, evaluated as 1/2 (lap_A - lap_B) I3 (Eq. I5_); I6 (ab|[[f,T1],f']|cd)
+ * = (ab|f_r f'_r|cd), Eq. I6_. */
+typedef enum { F12INT_I1 = 1, F12INT_I2, F12INT_I3, F12INT_I4, F12INT_I5, F12INT_I6 } f12int_class;
+
+/* Range-separated correlation factor, Sec. 3.1, Eq. rs12 with the
+ * Tang-Toennies damping of Eq. ttdamp:
+ *   f(r) = (1 + r/2) exp(-mu r^2) + S_n(mu r^2) c0 r^rho exp(B r). */
+typedef struct {
+  double c0, rho, B, mu;
+  int n;
+} f12int_factor;
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes caps the
+ * device memory the context allocates (0 = no cap).  cuda_stream is the
+ * default stream for the context (NULL = the legacy default stream).
+ * On success *ctx receives a new context the caller must f12int_destroy. */
+int f12int_create(f12int_ctx **ctx, int device, size_t hbm_budget_bytes, void *cuda_stream);
+
+/* Release every device and host resource of the context. */
+int f12int_destroy(f12int_ctx *ctx);
+
+/* Upload a basis and build its shell-pair data on the device (Sec. 2.2,
+ * Eqs. AB, Lambda, Erec0-Erect and the F = dE/dAB recursions).
+ *   nshell        number of shells
+ *   centers[3n]   shell centres (bohr)
+ *   l[n]          angular momentum, 0..3
+ *   nprim[n]      primitives per shell, >= 1
+ *   exps[], coefs[]  primitive exponents (> 0) and contraction coefficients,
+ *                 shell after shell (sum nprim entries each)
+ * The pair data stays resident in device memory until the context is
+ * destroyed.  *basis_id receives the handle used by the other calls.
+ * Errors: F12INT_EINVAL for out-of-range input, F12INT_ENOMEM when the pair
+ * data would exceed the budget. */
+int f12int_set_basis(f12int_ctx *ctx, int nshell, const double *centers, const int *l,
+                     const int *nprim, const double *exps, const double *coefs, int *basis_id);
+
+/* Set the correlation factors f and f' (Eq. rs12; fprime = NULL means
+ * f' = f).  Builds, on the host, the term lists of the kernels k1..k6
+ * (Eqs. k1-k6) as sums of c x^a exp(b x - g x^2) and their radial
+ * derivatives, and copies them to the device.
+ * Errors: F12INT_EDOMAIN when mu <= 0, c0 < 0, B < 0, a value is not
+ * finite, n < 0, or rho + 2n + 2 <= 0 (the damped long-range term must be
+ * integrable at r = 0, Sec. 3.1). */
+int f12int_set_factor(f12int_ctx *ctx, const f12int_factor *f, const f12int_factor *fprime);
+
+/* Schwarz-type screening for class cls: bound(ab) = sqrt(max |(ab|k|ab)|)
+ * over the diagonal block (the I3 diagonal for I5).  Writes the canonical
+ * shell quartets whose bound product is >= thresh into quartets_out[4*i]
+ * (host memory, room for cap quartets) and their count into *n_out.
+ * Canonical means a >= b, c >= d and (ab) >= (cd) for I1-I4 and I6; for I5
+ * (no bra-ket symmetry, antisymmetric in a <-> b) it means a >= b, c >= d
+ * with every (ab), (cd) combination.  If more than cap quartets survive,
+ * *n_out holds the full count and nothing beyond cap is written.
+ * The bound is rigorous only for positive-definite kernels; for the F12
+ * kernels it is a heuristic. */
+int f12int_screen(f12int_ctx *ctx, int basis_id, int cls, double thresh, int32_t *quartets_out,
+                  int64_t cap, int64_t *n_out);
+
+/* Compute the contracted blocks of class cls (Eq. ii for I1-I4 and I6,
+ * Eq. I5byI3_ for I5) for n shell quartets.
+ *   quartets_dev[4n]  shell indices (a, b, c, d), device memory
+ *   offsets_dev[n]    element offset of each block in out_dev, device memory
+ *   out_dev           output, device memory, FP64
+ * The work is queued on cuda_stream; the call returns once it is queued.
+ * Scratch memory is allocated by the context (bounded by its budget).
+ * Errors: F12INT_ENOTREADY without basis or factor, F12INT_EINVAL for bad
+ * arguments, F12INT_ENOMEM when scratch would exceed the budget. */
+int f12int_compute_class(f12int_ctx *ctx, int basis_id, int cls, const int32_t *quartets_dev,
+                         int64_t n, double *out_dev, const int64_t *offsets_dev, void *cuda_stream);
+
+/* Radial derivatives g_n = (Q^-1 d/dQ)^n B_i of the basic integral of
+ * class cls at given xi = pq/(p+q) and D = |P - Q| (Sec. 2.3, Eq. bfinal;
+ * Sec. 2.5), without the prefactor sqrt(pi^5/(p+q))/(pq):
+ *   out_dev[i*(nmax+1) + n] = int_0^inf k(r) r (Q^-1 d/dQ)^n
+ *                              [(e^{-xi (r-D)^2} - e^{-xi (r+D)^2}) / D] dr
+ * for i < npts, n <= nmax (nmax <= 14).  xi_dev, D_dev, out_dev are
+ * device arrays.  This is the auxiliary-function stage of compute_class,
+ * exposed for testing. */
+int f12int_aux(f12int_ctx *ctx, int cls, int64_t npts, const double *xi_dev, const double *D_dev,
+               int nmax, double *out_dev, void *cuda_stream);
+
+/* Number of kernel launches the context has issued so far (monotonic). */
+int64_t f12int_launch_count(const f12int_ctx *ctx);
+
+/* Read and clear the device status word (a device-side check failing sets
+ * it).  Synchronises the context's stream.  Returns F12INT_OK or
+ * F12INT_EDEVICE. */
+int f12int_device_status(f12int_ctx *ctx);
+
+/* Human-readable message for a status code (static storage). */
+const char *f12int_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* F12INT_H */

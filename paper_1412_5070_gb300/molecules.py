@@ -1,0 +1,126 @@
+"""Seeded synthetic molecules and Cartesian Gaussian basis sets.
+
+This module only draws inputs; it holds none of the integral arithmetic.
+Both the CUDA path and the CPU oracle read the arrays it returns.
+
+Draw order (numpy ``default_rng(seed)``, PCG64):
+  1. atom positions by rejection sampling against the minimum separation;
+  2. for each atom, its shells in s, p, d, f order;
+  3. for each shell: the primitive count (uniform integer), then the
+     exponents (log-uniform, sorted in descending order), then the
+     contraction coefficients (uniform).
+
+Primitives are unnormalised (Sec. 2.1, Eq. basis of arXiv:1412.5070);
+coefficients multiply them as given.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class Basis:
+    centers: np.ndarray          # [nshell, 3] bohr
+    l: np.ndarray                # [nshell] int32
+    nprim: np.ndarray            # [nshell] int32
+    exps: np.ndarray             # [sum nprim]
+    coefs: np.ndarray            # [sum nprim]
+    atom_of_shell: np.ndarray = field(default=None)
+    name: str = ""
+
+    @property
+    def nshell(self) -> int:
+        return int(len(self.l))
+
+    @property
+    def prim_off(self) -> np.ndarray:
+        return np.concatenate([[0], np.cumsum(self.nprim)[:-1]]).astype(np.int32)
+
+    def nfunc(self) -> int:
+        return int(sum((l + 1) * (l + 2) // 2 for l in self.l))
+
+
+def _place_atoms(rng, natom, box, min_sep, max_tries=100000):
+    pos = []
+    tries = 0
+    while len(pos) < natom:
+        tries += 1
+        if tries > max_tries:
+            raise RuntimeError("could not place %d atoms in a %g box" % (natom, box))
+        x = rng.uniform(0.0, box, size=3)
+        if all(np.linalg.norm(x - y) >= min_sep for y in pos):
+            pos.append(x)
+    return np.array(pos)
+
+
+def random_molecule(seed, natom, box, min_sep, shells_per_l, nprim_range, exp_range, coef_range=(0.1, 1.0),
+                    name=""):
+    """Seeded molecule; ``shells_per_l`` = counts of s, p, d, f shells per atom."""
+    rng = np.random.default_rng(seed)
+    pos = _place_atoms(rng, natom, box, min_sep)
+    centers, ls, nprims, exps, coefs, atoms = [], [], [], [], [], []
+    lo, hi = np.log(exp_range[0]), np.log(exp_range[1])
+    for ia in range(natom):
+        for l, cnt in enumerate(shells_per_l):
+            for _ in range(cnt):
+                npr = int(rng.integers(nprim_range[0], nprim_range[1] + 1))
+                e = np.sort(np.exp(rng.uniform(lo, hi, size=npr)))[::-1]
+                c = rng.uniform(coef_range[0], coef_range[1], size=npr)
+                centers.append(pos[ia]); ls.append(l); nprims.append(npr)
+                exps.extend(e.tolist()); coefs.extend(c.tolist()); atoms.append(ia)
+    return Basis(np.array(centers, dtype=np.float64), np.array(ls, dtype=np.int32),
+                 np.array(nprims, dtype=np.int32), np.array(exps), np.array(coefs),
+                 np.array(atoms, dtype=np.int32), name)
+
+
+def two_centre_sp() -> Basis:
+    """Two centres 5.6 bohr apart on z; on each, uncontracted s shells with
+    exponents 0.1, 0.3, 0.9, 2.7 and p shells with exponents 0.3, 0.9
+    (6 shells per centre, coefficient 1)."""
+    centers, ls, exps = [], [], []
+    for z in (0.0, 5.6):
+        for e in (0.1, 0.3, 0.9, 2.7):
+            centers.append((0.0, 0.0, z)); ls.append(0); exps.append(e)
+        for e in (0.3, 0.9):
+            centers.append((0.0, 0.0, z)); ls.append(1); exps.append(e)
+    n = len(ls)
+    return Basis(np.array(centers, dtype=np.float64), np.array(ls, dtype=np.int32), np.ones(n, dtype=np.int32),
+                 np.array(exps), np.ones(n), np.array([0] * 6 + [1] * 6, dtype=np.int32), "two-centre s4p2")
+
+
+def twelve_atom_spd(seed: int = 2) -> Basis:
+    """12 atoms in a 12 bohr cube (minimum separation 1.8 bohr), each with
+    3s2p1d contracted shells of 3 primitives, exponents log-uniform in
+    [0.05, 50], coefficients uniform in [0.1, 1]."""
+    return random_molecule(seed, 12, 12.0, 1.8, (3, 2, 1, 0), (3, 3), (0.05, 50.0), name="12-atom 3s2p1d")
+
+
+def canonical_quartets(basis: Basis, cls: int) -> np.ndarray:
+    """All canonical shell quartets: a >= b, c >= d and (ab) >= (cd) for the
+    classes with 8-fold symmetry; a >= b, c >= d with every (ab), (cd)
+    combination for I5 (antisymmetric in a <-> b, no bra-ket symmetry)."""
+    n = basis.nshell
+    pairs = [(a, b) for a in range(n) for b in range(a + 1)]
+    out = []
+    if cls == 5:
+        for ab in pairs:
+            for cd in pairs:
+                out.append(ab + cd)
+    else:
+        for i, ab in enumerate(pairs):
+            for cd in pairs[: i + 1]:
+                out.append(ab + cd)
+    return np.array(out, dtype=np.int32).reshape(-1, 4)
+
+
+def block_offsets(basis: Basis, quartets: np.ndarray) -> np.ndarray:
+    nc = (basis.l + 1) * (basis.l + 2) // 2
+    q = np.asarray(quartets).reshape(-1, 4)
+    sizes = nc[q[:, 0]] * nc[q[:, 1]] * nc[q[:, 2]] * nc[q[:, 3]]
+    return np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+
+
+# factor parameter set used throughout: f' = f
+P0 = dict(c0=0.5, rho=-0.5, B=0.5, mu=1.0, n=0)

@@ -1,0 +1,392 @@
+"""Pins for the CPU oracle (no GPU).
+
+Each test checks the oracle against something other than itself: closed
+forms (Boys function, Gaussian geminal, overlap), brute-force quadrature in
+two dimensions, permutational and translational symmetry, and
+finite-difference centre derivatives.  References are to arXiv:1412.5070.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate, special
+
+from oracle import oracle as O
+from paper_1412_5070_gb300 import molecules as M
+
+P0 = M.P0
+
+
+def boys(n, T):
+    """Boys function F_n(T) = int_0^1 t^{2n} e^{-T t^2} dt (textbook definition)."""
+    if T < 1e-12:
+        return 1.0 / (2 * n + 1)
+    a = n + 0.5
+    return special.gamma(a) * special.gammainc(a, T) / (2.0 * T ** a)
+
+
+# ------------------------------------------------------------------ radial --
+
+@pytest.mark.parametrize("xi,D", [(0.7, 0.3), (2.0, 3.0), (0.05, 10.0), (50.0, 0.01), (50.0, 5.0),
+                                  (1.3, 0.0), (10.0, 1.3)])
+def test_radial_coulomb_is_boys(xi, D):
+    """k = 1/r: the basic integral of Eq. bfinal reduces to the Boys function,
+    hat g_n = 2 (-2 xi)^n F_n(xi D^2)."""
+    g = O.radial(O.test_kernel(O.K_COULOMB), 3, xi, D, 12)
+    T = xi * D * D
+    ref = np.array([2 * (-2 * xi) ** n * boys(n, T) for n in range(13)])
+    np.testing.assert_allclose(g, ref, rtol=2e-13, atol=0)
+
+
+@pytest.mark.parametrize("gam", [0.3, 1.0, 4.0])
+@pytest.mark.parametrize("xi,D", [(0.5, 0.0), (0.5, 1.7), (3.0, 2.2), (20.0, 0.4)])
+def test_radial_gaussian_closed_form(gam, xi, D):
+    """k = exp(-gam r^2): B is a Gaussian in D with exponent w = xi gam/(xi+gam),
+    so hat g_n = (-2w)^n hat g_0 with hat g_0 = sqrt(pi/xi) xi^{3/2} ... written out:
+    hat g_0 = (pi/(xi+gam))^{3/2} * xi^{3/2} / pi^{3/2} * 2 sqrt(pi) / sqrt(xi) ... (see below)."""
+    # (ss|k|ss)/(K_ab K_cd) = (pi/(p+q))^{3/2} (pi/(xi+gam))^{3/2} e^{-w D^2}; and
+    # (ss|k|ss)/(K_ab K_cd) = sqrt(pi^5/(p+q))/(pq) hat g_0 with pq/(p+q) = xi, so
+    # hat g_0 = (pi/(p+q))^{3/2} (pi/(xi+gam))^{3/2} e^{-wD^2} pq / sqrt(pi^5/(p+q))
+    #         = pi^{1/2} xi (xi+gam)^{-3/2} e^{-wD^2}.
+    w = xi * gam / (xi + gam)
+    g = O.radial(O.test_kernel(O.K_GAUSS, gam), 3, xi, D, 10)
+    g0 = math.sqrt(math.pi) * xi * (xi + gam) ** -1.5 * math.exp(-w * D * D)
+    ref = np.array([(-2 * w) ** n * g0 for n in range(11)])
+    np.testing.assert_allclose(g, ref, rtol=2e-13, atol=0)
+
+
+@pytest.mark.parametrize("cls", [2, 3, 4, 6])
+@pytest.mark.parametrize("xi,D", [(0.3, 13.0), (2.0, 2.9), (8.0, 1.5), (0.9, 5.0)])
+def test_radial_two_forms_agree(cls, xi, D):
+    """The oracle evaluates D_Q^n of the bracket of Eq. bfinal in two forms
+    (Bessel form and separated exponentials); they must agree wherever both
+    are accurate (around the switch T = 16)."""
+    K = O.factor_kernel(P0)
+    a = O.radial_mode(K, cls, xi, D, 10, 0)
+    b = O.radial_mode(K, cls, xi, D, 10, 1)
+    scale = np.maximum(np.abs(a), np.abs(b))
+    assert np.all(np.abs(a - b) <= 1e-13 * scale + 1e-300), (a, b)
+
+
+def test_jhat_switch_continuity():
+    """e^{-z} j_m(z) from the series and from the closed forms meet at the switch."""
+    N = 10
+    z0 = 40 + 2 * N
+    lo = O.jhat(z0 * (1 - 1e-12), N)
+    hi = O.jhat(z0 * (1 + 1e-12), N)
+    # the two evaluation points differ by 2e-12 in z; a wrong branch would differ by far more
+    np.testing.assert_allclose(lo, hi, rtol=1e-10)
+    # spot values against the elementary closed forms
+    z = 2.5
+    np.testing.assert_allclose(O.jhat(z, 1)[0], math.exp(-z) * math.sinh(z) / z, rtol=1e-15)
+    j1 = (math.cosh(z) / z - math.sinh(z) / z ** 2) / z
+    np.testing.assert_allclose(O.jhat(z, 1)[1], math.exp(-z) * j1, rtol=1e-14)
+
+
+# ----------------------------------------------------- kernels (pointwise) --
+
+def f_rs(r, c0, rho, B, mu, n):
+    """Eq. rs12 with Eq. ttdamp, written independently for the tests."""
+    x = mu * r * r
+    Sn = 1.0 - math.exp(-x) * sum(x ** k / math.factorial(k) for k in range(n + 1))
+    return (1 + r / 2) * math.exp(-mu * r * r) + Sn * c0 * r ** rho * math.exp(B * r)
+
+
+@pytest.mark.parametrize("r", [0.05, 0.4, 1.0, 2.7, 6.0])
+def test_kernel_derivative_by_finite_differences(r):
+    """k6 = f_r f'_r (Eq. I6_): the oracle's f_r agrees with a finite-difference
+    derivative of Eq. rs12."""
+    h = 1e-5 * max(r, 0.1)
+    f = lambda x: f_rs(x, **P0)
+    fr = (f(r - 2 * h) - 8 * f(r - h) + 8 * f(r + h) - f(r + 2 * h)) / (12 * h)
+    K = O.factor_kernel(P0)
+    np.testing.assert_allclose(O.kernel_value(K, 6, r), fr * fr, rtol=1e-9)
+    np.testing.assert_allclose(O.kernel_value(K, 3, r), f(r), rtol=1e-14)
+    np.testing.assert_allclose(O.kernel_value(K, 2, r), f(r) / r, rtol=1e-14)
+    np.testing.assert_allclose(O.kernel_value(K, 4, r), f(r) ** 2, rtol=1e-14)
+
+
+def test_kernel_cusp_values():
+    """f(0) = 1 and f_r(0) = 1/2 for the default parameters (cusp condition).
+    With rho = -1/2 the damped long-range term adds O(r^{3/2}) to f and
+    O(r^{1/2}) to f_r, hence the tolerances at r = 1e-12."""
+    K = O.factor_kernel(P0)
+    assert abs(O.kernel_value(K, 3, 1e-12) - 1.0) < 1e-11
+    assert abs(O.kernel_value(K, 6, 1e-12) - 0.25) < 2e-6
+
+
+# ----------------------------------------------------- s-type brute force --
+
+def brute_ss(kfun, a, A, b, B_, c, C, d, D_):
+    """(ss|k|ss) by two-dimensional quadrature of
+    K_ab K_cd (pi/(p+q))^{3/2} int d^3s k(s) exp(-xi |s - R|^2)
+    over s in [0, inf) and cos(theta) in [-1, 1] (Gauss-Legendre, 128 nodes)."""
+    A, B_, C, D_ = map(np.asarray, (A, B_, C, D_))
+    p, q = a + b, c + d
+    P = (a * A + b * B_) / p
+    Q = (c * C + d * D_) / q
+    Kab = math.exp(-a * b / p * np.dot(A - B_, A - B_))
+    Kcd = math.exp(-c * d / q * np.dot(C - D_, C - D_))
+    xi = p * q / (p + q)
+    R = float(np.linalg.norm(P - Q))
+    xc, wc = np.polynomial.legendre.leggauss(128)
+
+    def inner(s):
+        return 2 * math.pi * s * s * kfun(s) * float(np.dot(wc, np.exp(-xi * (s * s + R * R - 2 * s * R * xc))))
+
+    top = R + 3.0 + 14.0 / math.sqrt(xi)
+    pts = sorted({0.0, 0.5, 1.0, 2.0, max(R - 4 / math.sqrt(xi), 0.0), R, R + 4 / math.sqrt(xi), top})
+    tot = 0.0
+    for lo, hi in zip(pts[:-1], pts[1:]):
+        if hi > lo:
+            val, _ = integrate.quad(inner, lo, hi, epsabs=0, epsrel=2e-14, limit=400)
+            tot += val
+    return Kab * Kcd * (math.pi / (p + q)) ** 1.5 * tot
+
+
+def fr_rs(r, c0, rho, B, mu, n):
+    h = 1e-6 * max(r, 1e-3)
+    return (f_rs(r + h, c0, rho, B, mu, n) - f_rs(r - h, c0, rho, B, mu, n)) / (2 * h)
+
+
+SS_CASES = [
+    (0.9, (0, 0, 0), 0.3, (0, 0, 0), 2.7, (0, 0, 5.6), 0.1, (0, 0, 5.6)),
+    (0.1, (0, 0, 0), 0.1, (0, 0, 5.6), 0.3, (0, 0, 0), 0.9, (0, 0, 0)),
+    (1.7, (0.3, -0.2, 0.1), 0.6, (1.1, 0.4, -0.5), 0.25, (-0.7, 1.3, 0.9), 3.0, (0.2, 0.1, 2.4)),
+]
+
+
+@pytest.mark.parametrize("case", SS_CASES)
+@pytest.mark.parametrize("cls", [2, 3, 4])
+def test_ss_brute_force(case, cls):
+    """s-type quartets against 2-D brute-force quadrature (pins the prefactor
+    of Eq. bfinal and the kernels of Eqs. k2-k4)."""
+    a, A, b, B_, c, C, d, D_ = case
+    f = lambda s: f_rs(s, **P0)
+    kf = {2: lambda s: f(s) / s, 3: f, 4: lambda s: f(s) ** 2}[cls]
+    ref = brute_ss(kf, a, A, b, B_, c, C, d, D_)
+    got = O.prim_block(O.factor_kernel(P0), cls, [0, 0, 0, 0], [a, b, c, d], [A, B_, C, D_])[0, 0, 0, 0]
+    assert abs(got - ref) <= 1e-10 * abs(ref), (got, ref)
+
+
+@pytest.mark.parametrize("case", SS_CASES[:2])
+def test_ss_brute_force_k6(case):
+    """I6 kernel f_r^2 (Eq. I6_) against brute force with a finite-difference f_r."""
+    a, A, b, B_, c, C, d, D_ = case
+    kf = lambda s: fr_rs(s, **P0) ** 2
+    ref = brute_ss(kf, a, A, b, B_, c, C, d, D_)
+    got = O.prim_block(O.factor_kernel(P0), 6, [0, 0, 0, 0], [a, b, c, d], [A, B_, C, D_])[0, 0, 0, 0]
+    assert abs(got - ref) <= 1e-8 * abs(ref), (got, ref)
+
+
+# ------------------------------------- separable kernels: full angular momentum --
+
+def cart(l):
+    return [(i, j, l - i - j) for i in range(l, -1, -1) for j in range(l - i, -1, -1)]
+
+
+def geminal_block_ref(ls, ex, cen, gam):
+    """(ab|exp(-gam r12^2)|cd) for Cartesian GTOs by a product of 2-D
+    Gauss-Hermite quadratures, one per Cartesian direction (the kernel is
+    separable).  gam = 0 gives the overlap product S_ab S_cd."""
+    a, b, c, d = ex
+    p, q = a + b, c + d
+    t, w = np.polynomial.hermite.hermgauss(60)
+    blocks = []
+    comps = [cart(l) for l in ls]
+    out = np.zeros([len(x) for x in comps])
+    cen = np.asarray(cen, dtype=float).reshape(4, 3)
+    per_dim = []
+    for k in range(3):
+        A, B_, C, D_ = cen[:, k]
+        P = (a * A + b * B_) / p
+        Q = (c * C + d * D_) / q
+        Kab = math.exp(-a * b / p * (A - B_) ** 2)
+        Kcd = math.exp(-c * d / q * (C - D_) ** 2)
+        x1 = P + t / math.sqrt(p)
+        x2 = Q + t / math.sqrt(q)
+        X1, X2 = np.meshgrid(x1, x2, indexing="ij")
+        W = np.outer(w, w) / math.sqrt(p * q) * Kab * Kcd * np.exp(-gam * (X1 - X2) ** 2)
+        tab = {}
+        for ia in range(ls[0] + 1):
+            for ib in range(ls[1] + 1):
+                for ic in range(ls[2] + 1):
+                    for id_ in range(ls[3] + 1):
+                        tab[(ia, ib, ic, id_)] = float(np.sum(W * (X1 - A) ** ia * (X1 - B_) ** ib *
+                                                              (X2 - C) ** ic * (X2 - D_) ** id_))
+        per_dim.append(tab)
+    for i0, ca in enumerate(comps[0]):
+        for i1, cb in enumerate(comps[1]):
+            for i2, cc in enumerate(comps[2]):
+                for i3, cd in enumerate(comps[3]):
+                    v = 1.0
+                    for k in range(3):
+                        v *= per_dim[k][(ca[k], cb[k], cc[k], cd[k])]
+                    out[i0, i1, i2, i3] = v
+    return out
+
+
+GEOM = [(0.3, -0.2, 0.1), (1.1, 0.4, -0.5), (-0.7, 1.3, 0.9), (0.2, 0.1, 1.4)]
+
+
+@pytest.mark.parametrize("ls", [(0, 0, 0, 0), (1, 0, 0, 0), (1, 1, 0, 0), (1, 0, 1, 0), (2, 1, 1, 0),
+                                (2, 2, 1, 1), (3, 1, 2, 0), (3, 3, 0, 0), (2, 2, 2, 2)])
+@pytest.mark.parametrize("gam", [0.0, 0.8])
+def test_separable_kernels_all_l(ls, gam):
+    """k = 1 (overlap product) and k = exp(-gam r12^2) (Gaussian geminal) for
+    Cartesian shells up to f: pins the E coefficients (Eq. AB), the Hermite
+    recursion for R (Eq. ri), the contraction of Eq. ii and the component
+    order, independently of the McMurchie-Davidson machinery."""
+    ex = [1.3, 0.7, 0.9, 2.1]
+    kern = O.test_kernel(O.K_ONE) if gam == 0.0 else O.test_kernel(O.K_GAUSS, gam)
+    got = O.prim_block(kern, 3, list(ls), ex, GEOM)
+    ref = geminal_block_ref(ls, ex, GEOM, gam)
+    scale = np.max(np.abs(ref))
+    np.testing.assert_allclose(got, ref, rtol=1e-11, atol=1e-12 * scale)
+
+
+# --------------------------------------------------- symmetry / invariance --
+
+def test_permutational_symmetry():
+    """8-fold symmetry of I1-I4 and I6 (real orbitals, symmetric kernel)."""
+    ex = [1.3, 0.7, 0.9, 2.1]
+    ls = [2, 1, 1, 0]
+    K = O.factor_kernel(P0)
+    for cls in (1, 2, 3, 4, 6):
+        base = O.prim_block(K, cls, ls, ex, GEOM)
+        # a <-> b
+        sw = O.prim_block(K, cls, [ls[1], ls[0], ls[2], ls[3]], [ex[1], ex[0], ex[2], ex[3]],
+                          [GEOM[1], GEOM[0], GEOM[2], GEOM[3]])
+        np.testing.assert_allclose(sw.transpose(1, 0, 2, 3), base, rtol=1e-12, atol=1e-14)
+        # bra <-> ket
+        bk = O.prim_block(K, cls, [ls[2], ls[3], ls[0], ls[1]], [ex[2], ex[3], ex[0], ex[1]],
+                          [GEOM[2], GEOM[3], GEOM[0], GEOM[1]])
+        np.testing.assert_allclose(bk.transpose(2, 3, 0, 1), base, rtol=1e-12, atol=1e-14)
+
+
+def test_i5_symmetries():
+    """I5 is antisymmetric under a <-> b (Eq. I5_) and symmetric under c <-> d."""
+    ex = [1.3, 0.7, 0.9, 2.1]
+    ls = [1, 1, 1, 0]
+    K = O.factor_kernel(P0)
+    base = O.prim_block(K, 5, ls, ex, GEOM)
+    sw = O.prim_block(K, 5, [ls[1], ls[0], ls[2], ls[3]], [ex[1], ex[0], ex[2], ex[3]],
+                      [GEOM[1], GEOM[0], GEOM[2], GEOM[3]])
+    np.testing.assert_allclose(sw.transpose(1, 0, 2, 3), -base, rtol=1e-11, atol=1e-14)
+    cd = O.prim_block(K, 5, [ls[0], ls[1], ls[3], ls[2]], [ex[0], ex[1], ex[3], ex[2]],
+                      [GEOM[0], GEOM[1], GEOM[3], GEOM[2]])
+    np.testing.assert_allclose(cd.transpose(0, 1, 3, 2), base, rtol=1e-11, atol=1e-14)
+
+
+def test_translation_invariance():
+    ex = [1.3, 0.7, 0.9, 2.1]
+    ls = [1, 1, 0, 1]
+    K = O.factor_kernel(P0)
+    shift = np.array([0.37, -1.1, 2.3])
+    for cls in (2, 5, 6):
+        a = O.prim_block(K, cls, ls, ex, GEOM)
+        b = O.prim_block(K, cls, ls, ex, [np.asarray(g) + shift for g in GEOM])
+        np.testing.assert_allclose(a, b, rtol=1e-11, atol=1e-13 * np.max(np.abs(a)))
+
+
+# --------------------------------------------------- finite differences --
+
+def test_centre_derivative_raises_angular_momentum():
+    """d/dA_x [x_A^i e^{-a r_A^2}] = 2a x_A^{i+1} e - i x_A^{i-1} e ties the
+    l+1 components to derivatives of the l components (checked for p <- s and
+    d <- p, every class)."""
+    ex = [1.1, 0.8, 0.6, 1.9]
+    K = O.factor_kernel(P0)
+    h = 1e-3
+    for cls in (1, 2, 3, 4, 6):
+        for l_lo in (0, 1):
+            ls_lo = [l_lo, 1, 0, 1]
+            ls_hi = [l_lo + 1, 1, 0, 1]
+            hi = O.prim_block(K, cls, ls_hi, ex, GEOM)
+            comps_lo, comps_hi = cart(l_lo), cart(l_lo + 1)
+            for k in range(3):
+                def blk(dx):
+                    g = [np.array(x, dtype=float) for x in GEOM]
+                    g[0][k] += dx
+                    return O.prim_block(K, cls, ls_lo, ex, g)
+                deriv = (blk(-2 * h) - 8 * blk(-h) + 8 * blk(h) - blk(2 * h)) / (12 * h)
+                lower = O.prim_block(K, cls, [max(l_lo - 1, 0), 1, 0, 1], ex, GEOM) if l_lo > 0 else None
+                for i_lo, c in enumerate(comps_lo):
+                    up = list(c)
+                    up[k] += 1
+                    i_hi = comps_hi.index(tuple(up))
+                    rhs = deriv[i_lo].copy()
+                    if c[k] > 0:
+                        dn = list(c)
+                        dn[k] -= 1
+                        rhs += c[k] * lower[cart(l_lo - 1).index(tuple(dn))]
+                    rhs /= 2 * ex[0]
+                    scale = np.max(np.abs(hi)) + 1e-300
+                    np.testing.assert_allclose(hi[i_hi], rhs, rtol=0, atol=2e-9 * scale)
+
+
+def test_i5_equals_laplacian_difference_of_i3():
+    """Eq. I5_: I5 = 1/2 (lap_A - lap_B) I3, with the Laplacians taken by
+    finite differences of I3 in the centres A and B."""
+    ex = [1.1, 0.8, 0.6, 1.9]
+    ls = [1, 0, 1, 0]
+    K = O.factor_kernel(P0)
+    h = 2e-3
+
+    def i3(dA, dB):
+        g = [np.array(x, dtype=float) for x in GEOM]
+        g[0] += dA
+        g[1] += dB
+        return O.prim_block(K, 3, ls, ex, g)
+
+    base = i3(np.zeros(3), np.zeros(3))
+    lapA = np.zeros_like(base)
+    lapB = np.zeros_like(base)
+    for k in range(3):
+        e = np.zeros(3)
+        e[k] = h
+        for which, acc in ((0, lapA), (1, lapB)):
+            f = lambda s: i3(s * e, 0 * e) if which == 0 else i3(0 * e, s * e)
+            acc += (-f(2) + 16 * f(1) - 30 * base + 16 * f(-1) - f(-2)) / (12 * h * h)
+    ref = 0.5 * (lapA - lapB)
+    got = O.prim_block(K, 5, ls, ex, GEOM)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=2e-7 * np.max(np.abs(ref)))
+
+
+def test_i5_vanishes_for_constant_factor():
+    """[f, T1] = 0 for constant f, so I5 = 0 (Eq. I5)."""
+    ex = [1.1, 0.8, 0.6, 1.9]
+    got = O.prim_block(O.test_kernel(O.K_ONE), 5, [2, 1, 1, 0], ex, GEOM)
+    ref_scale = np.max(np.abs(O.prim_block(O.test_kernel(O.K_ONE), 3, [2, 1, 1, 0], ex, GEOM)))
+    assert np.max(np.abs(got)) <= 1e-13 * ref_scale * max(ex) ** 2
+
+
+def test_coulomb_ss_closed_form():
+    """I1 for s functions: 2 pi^{5/2} / (p q sqrt(p+q)) K_ab K_cd F_0(T)."""
+    a, b, c, d = 0.9, 0.3, 2.7, 0.1
+    A, B_, C, D_ = map(np.array, [(0, 0, 0), (0, 0, 0), (0, 0, 5.6), (0, 0, 5.6)])
+    p, q = a + b, c + d
+    T = p * q / (p + q) * 5.6 ** 2
+    ref = 2 * math.pi ** 2.5 / (p * q * math.sqrt(p + q)) * boys(0, T)
+    got = O.prim_block(O.factor_kernel(P0), 1, [0, 0, 0, 0], [a, b, c, d], [A, B_, C, D_])[0, 0, 0, 0]
+    assert abs(got - ref) <= 1e-14 * ref
+
+
+def test_contracted_blocks_sum_primitives():
+    """Contracted blocks are the coefficient-weighted sums of primitive blocks."""
+    basis = M.twelve_atom_spd(2)
+    q = np.array([[5, 3, 1, 0]], dtype=np.int32)
+    K = O.factor_kernel(P0)
+    out, off = O.shell_blocks(K, 3, basis, q)
+    po = basis.prim_off
+    ls = [int(basis.l[s]) for s in q[0]]
+    acc = 0
+    for i0 in range(3):
+        for i1 in range(3):
+            for i2 in range(3):
+                for i3 in range(3):
+                    idx = [po[q[0][0]] + i0, po[q[0][1]] + i1, po[q[0][2]] + i2, po[q[0][3]] + i3]
+                    co = np.prod([basis.coefs[i] for i in idx])
+                    acc = acc + co * O.prim_block(K, 3, ls, [basis.exps[i] for i in idx],
+                                                  [basis.centers[s] for s in q[0]])
+    np.testing.assert_allclose(out.reshape(acc.shape), acc, rtol=1e-13, atol=0)
