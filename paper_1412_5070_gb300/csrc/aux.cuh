@@ -1,0 +1,276 @@
+// aux.cuh -- device evaluation of the radial derivatives of the basic
+// integrals (the auxiliary-function stage).
+//
+// For a kernel k(r) the quantity needed per primitive quartet is, for
+// l = 0..L (Sec. 2.4-2.5, Eq. DQ),
+//
+//   hat g_l(xi, D) = int_0^inf k(r) r D_Q^l [(e^{-xi(r-D)^2} - e^{-xi(r+D)^2}) / D] dr,
+//
+// D_Q = D^-1 d/dD, so that g_l = sqrt(pi^5/(p+q))/(pq) hat g_l (Eq. bfinal).
+// Moving the l derivatives from the Gaussian onto the kernel (integration
+// by parts, Hobson's operator identity in 2l+3 dimensions) gives the form
+// evaluated here,
+//
+//   hat g_l = 4 xi (2 xi)^l e^{-xi D^2} int_0^inf F_l(x) e^{-xi x^2} j_l(2 xi D x) dx,
+//   F_l(x)  = x^{2l+2} (D_r^l k)(x),  D_r = x^-1 d/dx,
+//   j_l(z)  = (z^-1 d/dz)^l (sinh z / z) = sum_k 2^l (k+l)!/(k!(2k+2l+1)!) z^{2k},
+//
+// whose integrand carries no cancelling alternating terms.  Each family
+// (b, g, alpha_0 + j) of F_l contributes through the generating integrals
+// S(alpha, beta, gamma) = int_0^inf x^alpha e^{beta x - gamma x^2} dx of
+// Eq. sila with gamma = g + xi:
+//
+//  * z = (b + 2 xi D)^2 / (4 gamma) below a threshold that grows with l:
+//    the small-Q series (Sec. 2.5.1, Eq. bidersmall, here with j_l in place
+//    of the alternating D_Q expansion)
+//      sum_j P_lj sum_k c_lk (2 xi D)^{2k} S(alpha_0 + j + 2k, b, gamma),
+//    S on one alpha_0 + N family from two start values by the recursion of
+//    Eq. Srec1 (upward in alpha; every term positive for beta >= 0), the
+//    start values from Kummer's M (App. B, Eq. msmallz) in the form valid
+//    for beta >= 0, and the finite part S(-1, beta, gamma) for the integer
+//    family of the f_r f'_r kernel (Sec. 3.3.2);
+//  * above it, Gauss-Hermite quadrature of the same integral about the
+//    peak x* = (b + 2 xi D)/(2 gamma) of e^{(b + 2 xi D) x - gamma x^2}
+//    (the moderate/large-Q case of Sec. 2.5.2; the r12 -> 0 end contributes
+//    below double precision there).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace f12dev {
+
+constexpr int LAUX = 14;     // highest radial order (f shells, I5: 3+3+3+3+2)
+constexpr int JMAX = 48;     // longest family polynomial
+constexpr int WIN = 64;      // circular window over the S sequence (> JMAX + 2)
+constexpr int KMAX = 1500;   // series length cap
+constexpr int NGH = 48;      // Gauss-Hermite nodes
+constexpr int MAXFAM = 24;   // families per kernel
+constexpr int NCLASS = 7;    // index by class 1..6
+
+struct FamDev {
+  double b, g;
+  double alpha0;              // lowest power of F_l (a0 + 2)
+  double gam_tab[JMAX];       // Gamma((alpha0 + 1 + j)/2); unused entry for alpha0 + 1 + j == 0
+  double rho_start;           // Gamma((as+2)/2) / Gamma((as+1)/2), as = first regular alpha
+  int fp_minus1;              // alpha0 == -1: the j = 0 term needs the finite part S(-1,...)
+  int span[LAUX + 1];
+  int coff[LAUX + 1];         // offset of P_l in the coefficient pool
+};
+
+struct Tables {
+  int nfam[NCLASS];
+  int fam0[NCLASS];
+  const FamDev *fam;
+  const double *coef;
+};
+
+__constant__ double c_gh_x[NGH];
+__constant__ double c_gh_w[NGH];
+
+__device__ __forceinline__ double threshold_z(int l) { return 36.0 + 4.5 * l; }
+
+// e^{-z} j_l(z) for l = 0..N (N <= LAUX): power series for the top two orders
+// and the stable downward recurrence j_{l-1} = z^2 j_{l+1} + (2l+1) j_l for
+// small z; closed forms of j_0, j_1 and the upward recurrence for large z.
+__device__ inline void jhat_all(double z, int N, double *jh) {
+  if (z > 2.0 * N + 30.0) {
+    double e2 = exp(-2.0 * z), iz = 1.0 / z;
+    jh[0] = 0.5 * (1.0 - e2) * iz;
+    if (N >= 1) jh[1] = 0.5 * ((1.0 - iz) + e2 * (1.0 + iz)) * iz * iz;
+    for (int m = 1; m < N; ++m) jh[m + 1] = (jh[m - 1] - (2 * m + 1) * jh[m]) * iz * iz;
+    return;
+  }
+  double z2 = z * z, ez = exp(-z);
+  int mlo = N > 0 ? N - 1 : 0;
+  for (int m = N; m >= mlo; --m) {
+    double c = 1.0;
+    for (int j = 1; j <= m; ++j) c /= (2 * j + 1);
+    double term = c, s = 0.0;
+    for (int k = 0; k < 400; ++k) {
+      s += term;
+      term *= z2 * (k + m + 1) / ((double)(k + 1) * (2 * k + 2 * m + 2) * (2 * k + 2 * m + 3));
+      if (term <= 1e-18 * s && k > 1) break;
+    }
+    jh[m] = ez * s;
+  }
+  for (int m = N - 1; m >= 1; --m) jh[m - 1] = z2 * jh[m + 1] + (2 * m + 1) * jh[m];
+}
+
+// Kummer M(a, b, z), z >= 0, a, b > 0 (App. B, Eq. msmallz).
+__device__ inline double kummer_m(double a, double b, double z, int *bad) {
+  double t = 1.0, s = 1.0;
+  for (int n = 0; n < 4000; ++n) {
+    t *= (a + n) * z / ((b + n) * (n + 1));
+    s += t;
+    if (t <= 1e-18 * s) return s;
+  }
+  *bad = 1;
+  return s;
+}
+
+// Normalised scaled generating integral
+//   Jh_alpha(y) = [int_0^inf t^alpha e^{y t - t^2} dt] / Gamma((alpha+1)/2),  y >= 0,
+// from the Kummer form  J = 1/2 [Gamma((a+1)/2) M((a+1)/2, 1/2, y^2/4)
+//                               + y Gamma((a+2)/2) M((a+2)/2, 3/2, y^2/4)].
+// rho = Gamma((alpha+2)/2)/Gamma((alpha+1)/2).
+__device__ inline double jhat_start(double alpha, double rho, double y, int *bad) {
+  double z = 0.25 * y * y;
+  return 0.5 * (kummer_m(0.5 * (alpha + 1.0), 0.5, z, bad) + y * rho * kummer_m(0.5 * (alpha + 2.0), 1.5, z, bad));
+}
+
+// Finite part S(-1, b, gamma) (Sec. 3.3.2, integer alpha; Eq. sila):
+//   = -gamma_E/2 - log(gamma)/2 + 1/2 sum_{m>=1} y^m Gamma(m/2)/m!,  y = b/sqrt(gamma) >= 0.
+__device__ inline double s_minus1(double b, double gam, int *bad) {
+  const double euler = 0.57721566490153286061;
+  double y = b / sqrt(gam);
+  double s = -0.5 * euler - 0.5 * log(gam);
+  if (y > 0.0) {
+    // t_m = y^m Gamma(m/2) / (2 m!);  t_1 = y sqrt(pi)/2
+    double r = 0.56418958354775628695;  // Gamma(1/2)/Gamma(1)... ratio Gamma((m+1)/2)/Gamma(m/2) at m=1 is 1/sqrt(pi)
+    double t = 0.5 * y * 1.77245385090551602730;
+    double acc = 0.0;
+    for (int m = 1; m < 4000; ++m) {
+      acc += t;
+      // t_{m+1}/t_m = y Gamma((m+1)/2) / (Gamma(m/2) (m+1))
+      t *= y * r / (m + 1);
+      r = 0.5 * m / r;
+      if (t <= 1e-18 * acc && m > 2) {
+        s += acc;
+        return s;
+      }
+    }
+    *bad = 1;
+    s += acc;
+  }
+  return s;
+}
+
+// hat g_l for l = 0..L of the kernel with families fam[0..nf).
+// Returns nonzero if a series did not converge within KMAX terms.
+__device__ inline int aux_eval(const Tables &T, int kcls, double xi, double D, int L, double *out) {
+  for (int l = 0; l <= L; ++l) out[l] = 0.0;
+  int bad = 0;
+  const int nf = T.nfam[kcls];
+  const FamDev *fams = T.fam + T.fam0[kcls];
+  const double T2 = xi * D * D;
+  const double w2 = 4.0 * xi * xi * D * D;  // (2 xi D)^2
+  for (int f = 0; f < nf; ++f) {
+    const FamDev &F = fams[f];
+    const double gam = F.g + xi;
+    const double beta = F.b + 2.0 * xi * D;
+    const double z = beta * beta / (4.0 * gam);
+    // orders l < ls use the quadrature about the peak, l >= ls the series
+    int ls = 0;
+    while (ls <= L && z >= threshold_z(ls)) ++ls;
+
+    if (ls > 0) {
+      const double sg = sqrt(gam);
+      const double xs = beta / (2.0 * gam);
+      const double estar = (F.b * F.b + 4.0 * F.b * xi * D - 4.0 * F.g * xi * D * D) / (4.0 * gam);
+      const double pre = exp(estar) / sg;
+      double acc[LAUX + 1];
+      for (int l = 0; l < ls; ++l) acc[l] = 0.0;
+      double jh[LAUX + 2];
+      for (int i = 0; i < NGH; ++i) {
+        double x = xs + c_gh_x[i] / sg;
+        if (x <= 0.0) continue;
+        jhat_all(2.0 * xi * D * x, ls - 1, jh);
+        double xa = pow(x, F.alpha0) * c_gh_w[i];
+        for (int l = 0; l < ls; ++l) {
+          const double *P = T.coef + F.coff[l];
+          int sp = F.span[l];
+          double h = 0.0;
+          for (int j = sp - 1; j >= 0; --j) h = h * x + P[j];
+          acc[l] += xa * jh[l] * h;
+        }
+      }
+      for (int l = 0; l < ls; ++l) out[l] += pre * acc[l];
+    }
+
+    if (ls <= L) {
+      const double y = F.b / sqrt(gam);
+      const double v = w2 / gam;
+      const double eT = exp(-T2);
+      const double rgam = 1.0 / sqrt(gam);
+      // start values of the normalised sequence Jh_{alpha_s}, Jh_{alpha_s + 1}
+      const int m0 = F.fp_minus1 ? 1 : 0;      // first regular index
+      const double as = F.alpha0 + m0;
+      const double j0 = jhat_start(as, F.rho_start, y, &bad);
+      // rho at alpha_s + 1: Gamma((as+3)/2)/Gamma((as+2)/2) = ((as+1)/2)/rho_start
+      const double rho1 = 0.5 * (as + 1.0) / F.rho_start;
+      const double j1 = jhat_start(as + 1.0, rho1, y, &bad);
+      const double sm1 = F.fp_minus1 ? s_minus1(F.b, gam, &bad) : 0.0;
+      const double gpow0 = pow(gam, -0.5 * (F.alpha0 + 1.0));
+
+      for (int l = ls; l <= L; ++l) {
+        const double *P = T.coef + F.coff[l];
+        const int sp = F.span[l];
+        double q[JMAX], t[JMAX];
+        // c_{l,0} = 2^l l! / (2l+1)! = 1/(2l+1)!!
+        double cl0 = 1.0;
+        for (int j = 1; j <= l; ++j) cl0 /= (2 * j + 1);
+        double gp = gpow0;
+        for (int j = 0; j < sp; ++j) {
+          q[j] = P[j] * gp;
+          gp *= rgam;
+          t[j] = cl0 * F.gam_tab[j] * eT;
+        }
+        double sum = 0.0;
+        if (F.fp_minus1) {
+          sum += q[0] * cl0 * eT * sm1;
+          t[0] = cl0 * eT;   // becomes c_{l,1} v Gamma(1) after the first update (see below)
+        }
+        // circular window over Jh_m, m = index relative to alpha0
+        double win[WIN];
+        int mfill;  // next index to fill
+        win[m0 & (WIN - 1)] = j0;
+        win[(m0 + 1) & (WIN - 1)] = j1;
+        mfill = m0 + 2;
+        // Recurrence in alpha (Eq. Srec1 in normalised form):
+        //   Jh_{a+1} = Jh_{a-1} + (y rho_a / a) Jh_a,   rho_{a+1} = a / (2 rho_a),
+        // rho_a = Gamma((a+1)/2)/Gamma(a/2); the first step is at a = as + 1,
+        // where rho = Gamma((as+2)/2)/Gamma((as+1)/2) = rho_start.
+        double rho = F.rho_start;
+        double abs_total = 0.0;
+        double prev_mag = 0.0;
+        int k;
+        for (k = 0; k < KMAX; ++k) {
+          int need = sp - 1 + 2 * k;  // highest index used at this k
+          while (mfill <= need) {
+            double a = F.alpha0 + (mfill - 1);
+            double jn = win[(mfill - 2) & (WIN - 1)] + y * rho / a * win[(mfill - 1) & (WIN - 1)];
+            rho = a / (2.0 * rho);
+            win[mfill & (WIN - 1)] = jn;
+            ++mfill;
+          }
+          double contrib = 0.0, mag = 0.0;
+          int jlo = (F.fp_minus1 && k == 0) ? 1 : 0;
+          for (int j = jlo; j < sp; ++j) {
+            double term = q[j] * t[j] * win[(j + 2 * k) & (WIN - 1)];
+            contrib += term;
+            mag += fabs(term);
+          }
+          sum += contrib;
+          abs_total += mag;
+          if (k > 2 && mag <= 1e-18 * abs_total && mag <= prev_mag) break;
+          prev_mag = mag;
+          // advance the coefficients: t_{j,k+1} = t_{j,k} v c_{l,k+1}/c_{l,k} (k + (alpha_j+1)/2)
+          double ratio = v * (double)(k + l + 1) / ((double)(k + 1) * (2.0 * k + 2.0 * l + 2.0) * (2.0 * k + 2.0 * l + 3.0));
+          for (int j = 0; j < sp; ++j) t[j] *= ratio * (k + 0.5 * (F.alpha0 + 1.0 + j));
+          if (F.fp_minus1 && k == 0) t[0] = cl0 * eT * ratio;  // (alpha_0+1)/2 = 0: Gamma(k) from k = 1
+        }
+        if (k == KMAX) bad = 1;
+        out[l] += sum;
+      }
+    }
+  }
+  // common factor 4 xi (2 xi)^l
+  double fct = 4.0 * xi;
+  for (int l = 0; l <= L; ++l) {
+    out[l] *= fct;
+    fct *= 2.0 * xi;
+  }
+  return bad;
+}
+
+}  // namespace f12dev

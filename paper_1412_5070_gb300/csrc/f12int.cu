@@ -1,0 +1,954 @@
+// f12int.cu -- CUDA kernels and C ABI of the F12 integral library (sm_103a).
+//
+// Stages (arXiv:1412.5070, Sec. 2):
+//   1. shell-pair data: p, P, and the Hermite expansion coefficients
+//      E_t^{ij} (Eq. AB, Eqs. Erec0-Erect) with their AB derivatives
+//      F_t^{ij} = dE_t^{ij}/dAB_x for I5, one thread per primitive pair,
+//      resident in device memory for the life of the basis;
+//   2. auxiliary functions g_n = D_Q^n B_i per primitive quartet (aux.cuh);
+//   3. the Hermite integrals R_tuv = d^t/dQx^t d^u/dQy^u d^v/dQz^v B_i
+//      (Eq. ri) by the Cartesian recursion for a radial function
+//        R^(n)_{t+1,u,v} = t R^(n+1)_{t-1,u,v} + X_QP R^(n+1)_{t,u,v},
+//      which holds because d/dQx D_Q^n B = X_QP D_Q^{n+1} B;
+//   4. the contraction of Eq. ii (inner ket sum, then bra sum) and for I5 the
+//      combination of Eq. I5byI3_, accumulated over primitive quartets.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/f12int.h"
+#include "aux.cuh"
+#include "termlist.h"
+
+using namespace f12dev;
+
+namespace {
+
+constexpr int LSH = 3;                 // highest shell angular momentum
+constexpr int NHMAX = 680;             // Hermite indices with t+u+v <= 14
+constexpr int BLOCK_CONTRACT = 128;
+constexpr int BLOCK_AUX = 64;
+
+__constant__ unsigned char c_tuv[NHMAX][3];   // Hermite index -> (t, u, v)
+__constant__ unsigned char c_cart[LSH + 3][28][3];  // shell l (<= 5) -> component exponents
+
+__host__ __device__ __forceinline__ int nh_count(int L) { return (L + 1) * (L + 2) * (L + 3) / 6; }
+__host__ __device__ __forceinline__ int ncart(int l) { return (l + 1) * (l + 2) / 2; }
+__host__ __device__ __forceinline__ int hidx(int t, int u, int v) {
+  int s = t + u + v, w = s - t;
+  return s * (s + 1) * (s + 2) / 6 + w * (w + 1) / 2 + v;
+}
+
+// ---------------------------------------------------------------------------
+// device status word bits: 1 = an auxiliary series hit its length cap,
+// 4 = a quartet needs a radial order above LAUX
+
+struct PairView {
+  const int *pair_start;     // [nshell*nshell + 1] first primitive pair of shell pair (i,j)
+  const double *pp_p;        // exponent sum p
+  const double *pp_P;        // [3*npp] centre P
+  const double *pp_ab;       // [2*npp] exponents a, b
+  const int64_t *pp_eoff;    // offset into epool of this primitive pair's tables
+  const double *epool;       // E (3 dims) then F (3 dims), each (la+1)(lb+1)(la+lb+1)
+  const int *shell_l;
+  int nshell;
+};
+
+// ------------------------------------------------------------ pair builder --
+// E_0^{00} = exp(-(ab/p) X_AB^2)  (Eq. Erec0); upward in i and j with
+//   E_t^{i+1,j} = E_{t-1}^{ij}/(2p) + X_PA E_t^{ij} + (t+1) E_{t+1}^{ij}
+//   E_t^{i,j+1} = E_{t-1}^{ij}/(2p) + X_PB E_t^{ij} + (t+1) E_{t+1}^{ij}
+// (the standard McMurchie-Davidson form equivalent to Eqs. Ereci-Erect, whose
+// printed j-recursion carries a stray factor).  F = dE/dAB_x follows by
+// differentiating every step: dX_PA/dAB = -b/p, dX_PB/dAB = a/p,
+// dE_0^{00}/dAB = -(2ab/p) X_AB E_0^{00}.
+__global__ void k_build_pairs(int npp, const int *pp_shell_a, const int *pp_shell_b, const int *pp_prim_a,
+                              const int *pp_prim_b, const double *centers, const int *shell_l,
+                              const double *exps, const double *coefs, double *pp_p, double *pp_P,
+                              double *pp_ab, const int64_t *pp_eoff, double *epool) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npp) return;
+  int sa = pp_shell_a[i], sb = pp_shell_b[i];
+  int la = shell_l[sa], lb = shell_l[sb];
+  double a = exps[pp_prim_a[i]], b = exps[pp_prim_b[i]];
+  double da = coefs[pp_prim_a[i]], db = coefs[pp_prim_b[i]];
+  double p = a + b;
+  pp_p[i] = p;
+  pp_ab[2 * i] = a;
+  pp_ab[2 * i + 1] = b;
+  const int nt = la + lb + 1;
+  const int n1 = (la + 1) * (lb + 1) * nt;
+  double *E = epool + pp_eoff[i];
+  double *F = E + 3 * n1;
+  for (int k = 0; k < 3; ++k) {
+    double A = centers[3 * sa + k], B = centers[3 * sb + k];
+    double P = (a * A + b * B) / p;
+    pp_P[3 * i + k] = P;
+    double XAB = A - B, XPA = P - A, XPB = P - B;
+    double K = exp(-a * b / p * XAB * XAB);
+    double scale = (k == 0) ? da * db : 1.0;
+    double *Ek = E + k * n1, *Fk = F + k * n1;
+    for (int j = 0; j < n1; ++j) Ek[j] = Fk[j] = 0.0;
+#define EI(ii, jj, t) Ek[((ii) * (lb + 1) + (jj)) * nt + (t)]
+#define FI(ii, jj, t) Fk[((ii) * (lb + 1) + (jj)) * nt + (t)]
+    EI(0, 0, 0) = K;
+    FI(0, 0, 0) = -2.0 * a * b / p * XAB * K;
+    const double h = 0.5 / p;
+    for (int ii = 0; ii <= la; ++ii) {
+      if (ii > 0) {
+        for (int t = 0; t <= ii; ++t) {
+          double e = XPA * EI(ii - 1, 0, t), f = XPA * FI(ii - 1, 0, t) - b / p * EI(ii - 1, 0, t);
+          if (t > 0) {
+            e += h * EI(ii - 1, 0, t - 1);
+            f += h * FI(ii - 1, 0, t - 1);
+          }
+          if (t + 1 <= ii - 1) {
+            e += (t + 1) * EI(ii - 1, 0, t + 1);
+            f += (t + 1) * FI(ii - 1, 0, t + 1);
+          }
+          EI(ii, 0, t) = e;
+          FI(ii, 0, t) = f;
+        }
+      }
+      for (int jj = 1; jj <= lb; ++jj) {
+        for (int t = 0; t <= ii + jj; ++t) {
+          double e = XPB * EI(ii, jj - 1, t), f = XPB * FI(ii, jj - 1, t) + a / p * EI(ii, jj - 1, t);
+          if (t > 0) {
+            e += h * EI(ii, jj - 1, t - 1);
+            f += h * FI(ii, jj - 1, t - 1);
+          }
+          if (t + 1 <= ii + jj - 1) {
+            e += (t + 1) * EI(ii, jj - 1, t + 1);
+            f += (t + 1) * FI(ii, jj - 1, t + 1);
+          }
+          EI(ii, jj, t) = e;
+          FI(ii, jj, t) = f;
+        }
+      }
+    }
+#undef EI
+#undef FI
+    for (int j = 0; j < n1; ++j) {
+      Ek[j] *= scale;
+      Fk[j] *= scale;
+    }
+  }
+}
+
+// ------------------------------------------------------------------- aux --
+struct QuartetView {
+  const int32_t *quartets;   // [n][4]
+  const int64_t *pq_off;     // [n+1] first primitive quartet of each shell quartet
+  int64_t n;
+};
+
+__device__ __forceinline__ int64_t find_quartet(const int64_t *off, int64_t n, int64_t pq) {
+  int64_t lo = 0, hi = n - 1;
+  while (lo < hi) {
+    int64_t mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= pq) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// g_n (with the prefactor sqrt(pi^5/(p+q))/(pq) of Eq. bfinal) for every
+// primitive quartet of the batch, into scratch[pq*(LAUX+1) + n].
+__global__ void k_aux_quartets(Tables T, PairView PV, QuartetView QV, int cls, int64_t npq, double *scratch,
+                               unsigned int *status) {
+  int64_t pq = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (pq >= npq) return;
+  int64_t q = find_quartet(QV.pq_off, QV.n, pq);
+  const int32_t *s = QV.quartets + 4 * q;
+  const int ns = PV.nshell;
+  int ab = s[0] * ns + s[1], cd = s[2] * ns + s[3];
+  int npcd = PV.pair_start[cd + 1] - PV.pair_start[cd];
+  int64_t r = pq - QV.pq_off[q];
+  int iab = PV.pair_start[ab] + (int)(r / npcd);
+  int icd = PV.pair_start[cd] + (int)(r % npcd);
+  int L = PV.shell_l[s[0]] + PV.shell_l[s[1]] + PV.shell_l[s[2]] + PV.shell_l[s[3]] + (cls == 5 ? 2 : 0);
+  double p = PV.pp_p[iab], qq = PV.pp_p[icd];
+  double X = PV.pp_P[3 * icd] - PV.pp_P[3 * iab];
+  double Y = PV.pp_P[3 * icd + 1] - PV.pp_P[3 * iab + 1];
+  double Z = PV.pp_P[3 * icd + 2] - PV.pp_P[3 * iab + 2];
+  double D = sqrt(X * X + Y * Y + Z * Z);
+  double xi = p * qq / (p + qq);
+  double g[LAUX + 1];
+  if (L > LAUX) {
+    atomicOr(status, 4u);
+    return;
+  }
+  int bad = aux_eval(T, cls == 5 ? 3 : cls, xi, D, L, g);
+  if (bad) atomicOr(status, 1u);
+  // sqrt(pi^5/(p+q)) / (p q)
+  const double pi52 = 17.493418327624862846;  // pi^{5/2}
+  double pref = pi52 / (sqrt(p + qq) * p * qq);
+  double *o = scratch + pq * (LAUX + 1);
+  for (int n = 0; n <= L; ++n) o[n] = pref * g[n];
+}
+
+// hat g_n at given (xi, D) points (no prefactor), for the aux-stage tests.
+__global__ void k_aux_points(Tables T, int cls, int64_t npts, const double *xi, const double *D, int nmax,
+                             double *out, unsigned int *status) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= npts) return;
+  double g[LAUX + 1];
+  int bad = aux_eval(T, cls == 5 ? 3 : cls, xi[i], D[i], nmax, g);
+  if (bad) atomicOr(status, 1u);
+  for (int n = 0; n <= nmax; ++n) out[i * (nmax + 1) + n] = g[n];
+}
+
+// -------------------------------------------------------------- contract --
+// One block per shell quartet.  Shared memory:
+//   R0, R1   two levels of the Hermite recursion        2 * nh(L)
+//   W        ket-contracted integrals, summed over the
+//            ket primitive pairs, bra order <= lab(+2)    nh(Lb) * ncd
+//   O        output accumulator                           nab * ncd
+__global__ void __launch_bounds__(BLOCK_CONTRACT)
+k_contract(PairView PV, QuartetView QV, int cls, const double *scratch, double *out, const int64_t *offsets,
+           unsigned int *status) {
+  extern __shared__ double smem[];
+  const int64_t q = blockIdx.x;
+  if (q >= QV.n) return;
+  const int32_t *s = QV.quartets + 4 * q;
+  const int ns = PV.nshell;
+  const int la = PV.shell_l[s[0]], lb = PV.shell_l[s[1]], lc = PV.shell_l[s[2]], ld = PV.shell_l[s[3]];
+  const int ext = cls == 5 ? 2 : 0;
+  const int lab = la + lb, lcd = lc + ld;
+  const int L = lab + lcd + ext;
+  const int Lb = lab + ext;
+  const int na = ncart(la), nb = ncart(lb), nc = ncart(lc), nd = ncart(ld);
+  const int ncd = nc * nd, nab = na * nb;
+  const int nhL = nh_count(L), nhB = nh_count(Lb);
+  double *R0 = smem;
+  double *R1 = R0 + nhL;
+  double *W = R1 + nhL;
+  double *Oacc = W + (size_t)nhB * ncd;
+  const int ab = s[0] * ns + s[1], cd = s[2] * ns + s[3];
+  const int ab0 = PV.pair_start[ab], npab = PV.pair_start[ab + 1] - ab0;
+  const int cd0 = PV.pair_start[cd], npcd = PV.pair_start[cd + 1] - cd0;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int ntab = lab + 1, ntcd = lcd + 1;
+  const int n1ab = na > 0 ? (la + 1) * (lb + 1) * ntab : 0;
+  const int n1cd = (lc + 1) * (ld + 1) * ntcd;
+
+  for (int i = tid; i < nab * ncd; i += nthr) Oacc[i] = 0.0;
+
+  for (int iab = 0; iab < npab; ++iab) {
+    const int pab = ab0 + iab;
+    for (int i = tid; i < nhB * ncd; i += nthr) W[i] = 0.0;
+    __syncthreads();
+    for (int icd = 0; icd < npcd; ++icd) {
+      const int pcd = cd0 + icd;
+      const double *g = scratch + (QV.pq_off[q] + (int64_t)iab * npcd + icd) * (LAUX + 1);
+      const double X = PV.pp_P[3 * pcd] - PV.pp_P[3 * pab];
+      const double Y = PV.pp_P[3 * pcd + 1] - PV.pp_P[3 * pab + 1];
+      const double Z = PV.pp_P[3 * pcd + 2] - PV.pp_P[3 * pab + 2];
+      // Hermite recursion from level n = L down to 0, ping-pong between R0/R1
+      double *cur = R0, *nxt = R1;
+      if (tid == 0) cur[0] = g[L];
+      __syncthreads();
+      for (int n = L - 1; n >= 0; --n) {
+        const int cnt = nh_count(L - n);
+        for (int idx = tid; idx < cnt; idx += nthr) {
+          const int t = c_tuv[idx][0], u = c_tuv[idx][1], v = c_tuv[idx][2];
+          double val;
+          if (idx == 0) {
+            val = g[n];
+          } else if (t > 0) {
+            val = X * cur[hidx(t - 1, u, v)];
+            if (t > 1) val += (t - 1) * cur[hidx(t - 2, u, v)];
+          } else if (u > 0) {
+            val = Y * cur[hidx(t, u - 1, v)];
+            if (u > 1) val += (u - 1) * cur[hidx(t, u - 2, v)];
+          } else {
+            val = Z * cur[hidx(t, u, v - 1)];
+            if (v > 1) val += (v - 1) * cur[hidx(t, u, v - 2)];
+          }
+          nxt[idx] = val;
+        }
+        __syncthreads();
+        double *tmp = cur;
+        cur = nxt;
+        nxt = tmp;
+      }
+      // inner (ket) sum of Eq. ii:  W[tuv][cd] += sum E^{cd}_{t'u'v'} R_{t+t',u+u',v+v'}
+      const double *Ecd = PV.epool + PV.pp_eoff[pcd];
+      for (int i = tid; i < nhB * ncd; i += nthr) {
+        const int bi = i / ncd, j = i - bi * ncd;
+        const int ic = j / nd, id = j - ic * nd;
+        const int t = c_tuv[bi][0], u = c_tuv[bi][1], v = c_tuv[bi][2];
+        const unsigned char *ec = c_cart[lc][ic], *ed = c_cart[ld][id];
+        const double *ex = Ecd + (ec[0] * (ld + 1) + ed[0]) * ntcd;
+        const double *ey = Ecd + n1cd + (ec[1] * (ld + 1) + ed[1]) * ntcd;
+        const double *ez = Ecd + 2 * n1cd + (ec[2] * (ld + 1) + ed[2]) * ntcd;
+        const int tx = ec[0] + ed[0], ty = ec[1] + ed[1], tz = ec[2] + ed[2];
+        double acc = 0.0;
+        for (int t2 = 0; t2 <= tx; ++t2)
+          for (int u2 = 0; u2 <= ty; ++u2) {
+            const double exy = ex[t2] * ey[u2];
+            for (int v2 = 0; v2 <= tz; ++v2) acc += exy * ez[v2] * cur[hidx(t + t2, u + u2, v + v2)];
+          }
+        W[i] += acc;
+      }
+      __syncthreads();
+    }
+    // outer (bra) sum
+    const double *Eab = PV.epool + PV.pp_eoff[pab];
+    const double *Fab = Eab + 3 * n1ab;
+    const double a = PV.pp_ab[2 * pab], b = PV.pp_ab[2 * pab + 1];
+    const double c5 = (a - b) / (2.0 * (a + b));
+    for (int i = tid; i < nab * ncd; i += nthr) {
+      const int iabc = i / ncd, j = i - iabc * ncd;
+      const int ia = iabc / nb, ib = iabc - ia * nb;
+      const unsigned char *ea = c_cart[la][ia], *eb = c_cart[lb][ib];
+      const int ox = (ea[0] * (lb + 1) + eb[0]) * ntab;
+      const int oy = n1ab + (ea[1] * (lb + 1) + eb[1]) * ntab;
+      const int oz = 2 * n1ab + (ea[2] * (lb + 1) + eb[2]) * ntab;
+      const int tx = ea[0] + eb[0], ty = ea[1] + eb[1], tz = ea[2] + eb[2];
+      double acc = 0.0;
+      for (int t = 0; t <= tx; ++t)
+        for (int u = 0; u <= ty; ++u)
+          for (int v = 0; v <= tz; ++v) {
+            const double sgn = ((t + u + v) & 1) ? -1.0 : 1.0;
+            if (cls != 5) {
+              acc += sgn * Eab[ox + t] * Eab[oy + u] * Eab[oz + v] * W[hidx(t, u, v) * ncd + j];
+            } else {
+              // Eq. I5byI3_ with the second coefficient -1 (see the derivation note below)
+              const double e = Eab[ox + t] * Eab[oy + u] * Eab[oz + v];
+              const double lap = W[hidx(t + 2, u, v) * ncd + j] + W[hidx(t, u + 2, v) * ncd + j] +
+                                 W[hidx(t, u, v + 2) * ncd + j];
+              const double grad = Fab[ox + t] * Eab[oy + u] * Eab[oz + v] * W[hidx(t + 1, u, v) * ncd + j] +
+                                  Eab[ox + t] * Fab[oy + u] * Eab[oz + v] * W[hidx(t, u + 1, v) * ncd + j] +
+                                  Eab[ox + t] * Eab[oy + u] * Fab[oz + v] * W[hidx(t, u, v + 1) * ncd + j];
+              acc += sgn * (c5 * e * lap - grad);
+            }
+          }
+      Oacc[i] += acc;
+    }
+    __syncthreads();
+  }
+  double *o = out + offsets[q];
+  for (int i = tid; i < nab * ncd; i += nthr) o[i] = Oacc[i];
+}
+// Derivation note for I5: with d/dA_x = (a/p) d/dP_x + d/dAB_x and
+// d/dB_x = (b/p) d/dP_x - d/dAB_x (E depends on AB only, R on P only),
+//   1/2 (lap_A - lap_B) = sum_x [ (a-b)/(2p) d^2/dP_x^2 + d/dP_x d/dAB_x ],
+// and d/dP_x = -d/dQ_x on R; hence the coefficient of the gradient term is
+// -(a+b)/p = -1.
+
+}  // namespace
+
+// ================================================================ host API ==
+
+struct f12int_ctx {
+  int device = 0;
+  size_t budget = 0;
+  size_t used = 0;
+  cudaStream_t stream = nullptr;
+  int64_t launches = 0;
+  unsigned int *d_status = nullptr;
+  // factor tables
+  bool factor_ready = false;
+  FamDev *d_fam = nullptr;
+  double *d_coef = nullptr;
+  Tables tables{};
+  size_t fam_bytes = 0, coef_bytes = 0;
+  // basis
+  struct BasisData {
+    int nshell = 0;
+    int *d_shell_l = nullptr;
+    double *d_centers = nullptr;
+    int *d_pair_start = nullptr;
+    double *d_pp_p = nullptr, *d_pp_P = nullptr, *d_pp_ab = nullptr, *d_epool = nullptr;
+    int64_t *d_pp_eoff = nullptr;
+    std::vector<int> l, nprim, pair_start;
+    std::vector<double> centers;
+    size_t bytes = 0;
+  };
+  std::vector<BasisData> bases;
+  // scratch for compute_class
+  double *d_scratch = nullptr;
+  size_t scratch_bytes = 0;
+  int32_t *d_qbuf = nullptr;
+  int64_t *d_pqoff = nullptr;
+  size_t qbuf_cap = 0, pqoff_cap = 0;
+  std::mutex mu;
+};
+
+namespace {
+
+int cuda_fail(cudaError_t e) {
+  if (e == cudaErrorMemoryAllocation) return F12INT_ENOMEM;
+  return F12INT_ECUDA;
+}
+
+#define CK(call)                                    \
+  do {                                              \
+    cudaError_t e_ = (call);                        \
+    if (e_ != cudaSuccess) return cuda_fail(e_);    \
+  } while (0)
+
+template <class T>
+int dalloc(f12int_ctx *ctx, T **p, size_t bytes) {
+  if (bytes == 0) bytes = 8;
+  if (ctx->budget && ctx->used + bytes > ctx->budget) return F12INT_ENOMEM;
+  cudaError_t e = cudaMalloc((void **)p, bytes);
+  if (e != cudaSuccess) return cuda_fail(e);
+  ctx->used += bytes;
+  return F12INT_OK;
+}
+
+template <class T>
+void dfree(f12int_ctx *ctx, T *&p, size_t bytes) {
+  if (p) {
+    cudaFree(p);
+    ctx->used -= std::min(ctx->used, bytes ? bytes : (size_t)8);
+    p = nullptr;
+  }
+}
+
+cudaStream_t pick_stream(f12int_ctx *ctx, void *s) { return s ? (cudaStream_t)s : ctx->stream; }
+
+// Gauss-Hermite nodes and weights (weight e^{-t^2}) from the orthonormal
+// Hermite recurrence: sign changes on a fine grid, then Newton.
+void gauss_hermite(int n, double *x, double *w) {
+  auto eval = [n](double t, double &pn, double &pn1) {
+    double p0 = 0.0, p1 = std::pow(M_PI, -0.25);
+    for (int k = 0; k < n; ++k) {
+      double p2 = t * std::sqrt(2.0 / (k + 1)) * p1 - std::sqrt((double)k / (k + 1)) * p0;
+      p0 = p1;
+      p1 = p2;
+    }
+    pn = p1;
+    pn1 = p0;
+  };
+  double lim = std::sqrt(2.0 * n + 1.0) + 1.0;
+  int found = 0;
+  const int grid = 200000;
+  double tprev = -lim, pprev, dummy;
+  eval(tprev, pprev, dummy);
+  for (int i = 1; i <= grid && found < n; ++i) {
+    double t = -lim + 2.0 * lim * i / grid, pc;
+    eval(t, pc, dummy);
+    if ((pc < 0) != (pprev < 0)) {
+      double r = 0.5 * (t + tprev);
+      for (int it = 0; it < 100; ++it) {
+        double pn, pn1;
+        eval(r, pn, pn1);
+        double dp = std::sqrt(2.0 * n) * pn1;
+        double dr = pn / dp;
+        r -= dr;
+        if (std::fabs(dr) < 1e-15 * (1.0 + std::fabs(r))) break;
+      }
+      double pn, pn1;
+      eval(r, pn, pn1);
+      x[found] = r;
+      w[found] = 1.0 / (n * pn1 * pn1);
+      ++found;
+    }
+    tprev = t;
+    pprev = pc;
+  }
+}
+
+bool g_const_ready = false;
+std::mutex g_const_mu;
+
+int upload_constants() {
+  std::lock_guard<std::mutex> lk(g_const_mu);
+  if (g_const_ready) return F12INT_OK;
+  unsigned char tuv[NHMAX][3];
+  for (int s = 0; s <= 14; ++s)
+    for (int t = s; t >= 0; --t)
+      for (int v = 0; v <= s - t; ++v) {
+        int u = s - t - v;
+        int i = hidx(t, u, v);
+        tuv[i][0] = (unsigned char)t;
+        tuv[i][1] = (unsigned char)u;
+        tuv[i][2] = (unsigned char)v;
+      }
+  unsigned char cart[LSH + 3][28][3];
+  std::memset(cart, 0, sizeof(cart));
+  for (int l = 0; l < LSH + 3; ++l) {
+    int k = 0;
+    for (int i = l; i >= 0; --i)
+      for (int j = l - i; j >= 0; --j) {
+        cart[l][k][0] = (unsigned char)i;
+        cart[l][k][1] = (unsigned char)j;
+        cart[l][k][2] = (unsigned char)(l - i - j);
+        ++k;
+      }
+  }
+  double gx[NGH], gw[NGH];
+  gauss_hermite(NGH, gx, gw);
+  CK(cudaMemcpyToSymbol(c_tuv, tuv, sizeof(tuv)));
+  CK(cudaMemcpyToSymbol(c_cart, cart, sizeof(cart)));
+  CK(cudaMemcpyToSymbol(c_gh_x, gx, sizeof(gx)));
+  CK(cudaMemcpyToSymbol(c_gh_w, gw, sizeof(gw)));
+  g_const_ready = true;
+  return F12INT_OK;
+}
+
+bool finite_factor(const f12int_factor &f) {
+  return std::isfinite(f.c0) && std::isfinite(f.rho) && std::isfinite(f.B) && std::isfinite(f.mu);
+}
+
+int check_factor(const f12int_factor &f) {
+  if (!finite_factor(f)) return F12INT_EDOMAIN;
+  if (!(f.mu > 0.0) || f.c0 < 0.0 || f.B < 0.0 || f.n < 0 || f.n > 20) return F12INT_EDOMAIN;
+  if (f.c0 > 0.0 && !(f.rho + 2.0 * f.n + 2.0 > 0.0)) return F12INT_EDOMAIN;
+  return F12INT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *f12int_strerror(int status) {
+  switch (status) {
+    case F12INT_OK: return "ok";
+    case F12INT_EINVAL: return "invalid argument";
+    case F12INT_ENOMEM: return "device memory budget exceeded";
+    case F12INT_EDOMAIN: return "correlation-factor parameters outside the supported domain";
+    case F12INT_ENOTREADY: return "basis or correlation factor not set";
+    case F12INT_ETIMEOUT: return "timed out";
+    case F12INT_ECUDA: return "CUDA runtime error";
+    case F12INT_EDEVICE: return "device-side check failed";
+    default: return "unknown status";
+  }
+}
+
+int f12int_create(f12int_ctx **out, int device, size_t hbm_budget_bytes, void *cuda_stream) {
+  if (!out) return F12INT_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  CK(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return F12INT_EINVAL;
+  CK(cudaSetDevice(device));
+  f12int_ctx *ctx = new (std::nothrow) f12int_ctx();
+  if (!ctx) return F12INT_ENOMEM;
+  ctx->device = device;
+  ctx->budget = hbm_budget_bytes;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  int rc = upload_constants();
+  if (rc == F12INT_OK) rc = dalloc(ctx, &ctx->d_status, sizeof(unsigned int));
+  if (rc == F12INT_OK && cudaMemset(ctx->d_status, 0, sizeof(unsigned int)) != cudaSuccess) rc = F12INT_ECUDA;
+  if (rc != F12INT_OK) {
+    f12int_destroy(ctx);
+    return rc;
+  }
+  *out = ctx;
+  return F12INT_OK;
+}
+
+int f12int_destroy(f12int_ctx *ctx) {
+  if (!ctx) return F12INT_EINVAL;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  for (auto &b : ctx->bases) {
+    cudaFree(b.d_shell_l);
+    cudaFree(b.d_centers);
+    cudaFree(b.d_pair_start);
+    cudaFree(b.d_pp_p);
+    cudaFree(b.d_pp_P);
+    cudaFree(b.d_pp_ab);
+    cudaFree(b.d_epool);
+    cudaFree(b.d_pp_eoff);
+  }
+  cudaFree(ctx->d_fam);
+  cudaFree(ctx->d_coef);
+  cudaFree(ctx->d_scratch);
+  cudaFree(ctx->d_qbuf);
+  cudaFree(ctx->d_pqoff);
+  cudaFree(ctx->d_status);
+  delete ctx;
+  return F12INT_OK;
+}
+
+int64_t f12int_launch_count(const f12int_ctx *ctx) { return ctx ? ctx->launches : -1; }
+
+int f12int_device_status(f12int_ctx *ctx) {
+  if (!ctx) return F12INT_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  CK(cudaSetDevice(ctx->device));
+  unsigned int h = 0;
+  CK(cudaMemcpyAsync(&h, ctx->d_status, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned int), ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return h ? F12INT_EDEVICE : F12INT_OK;
+}
+
+int f12int_set_factor(f12int_ctx *ctx, const f12int_factor *f, const f12int_factor *fprime) {
+  if (!ctx || !f) return F12INT_EINVAL;
+  const f12int_factor &fp = fprime ? *fprime : *f;
+  int rc = check_factor(*f);
+  if (rc == F12INT_OK) rc = check_factor(fp);
+  if (rc != F12INT_OK) return rc;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  CK(cudaSetDevice(ctx->device));
+  f12::Factor F1{f->c0, f->rho, f->B, f->mu, f->n}, F2{fp.c0, fp.rho, fp.B, fp.mu, fp.n};
+  std::vector<FamDev> fams;
+  std::vector<double> coef;
+  Tables T{};
+  for (int cls = 1; cls <= 6; ++cls) {
+    T.fam0[cls] = (int)fams.size();
+    T.nfam[cls] = 0;
+    if (cls == 5) {
+      T.fam0[cls] = T.fam0[3];
+      T.nfam[cls] = T.nfam[3];
+      continue;
+    }
+    f12::TermList kt = f12::kernel_terms(cls, F1, F2);
+    std::vector<f12::Family> fl = f12::families(kt);
+    if ((int)fl.size() > MAXFAM) return F12INT_EDOMAIN;
+    for (const f12::Family &fam0 : fl) {
+      FamDev d{};
+      d.b = fam0.b;
+      d.g = fam0.g;
+      d.alpha0 = fam0.a0 + 2.0;   // F_l = x^{2l+2} D_r^l k: lowest power a0 + 2 for every l
+      if (d.alpha0 < -1.0 - 1e-9) return F12INT_EDOMAIN;       // not integrable even as finite part here
+      d.fp_minus1 = std::fabs(d.alpha0 + 1.0) < 1e-9 ? 1 : 0;
+      if (!d.fp_minus1 && d.alpha0 <= -1.0) return F12INT_EDOMAIN;
+      if (d.fp_minus1) d.alpha0 = -1.0;
+      for (int j = 0; j < JMAX; ++j) {
+        double arg = 0.5 * (d.alpha0 + 1.0 + j);
+        d.gam_tab[j] = arg > 0.0 ? std::tgamma(arg) : 0.0;
+      }
+      double as = d.fp_minus1 ? 0.0 : d.alpha0;
+      d.rho_start = std::exp(std::lgamma(0.5 * (as + 2.0)) - std::lgamma(0.5 * (as + 1.0)));
+      f12::Family cur = fam0;
+      for (int l = 0; l <= LAUX; ++l) {
+        if ((int)cur.poly.size() > JMAX) return F12INT_EDOMAIN;
+        d.coff[l] = (int)coef.size();
+        d.span[l] = (int)cur.poly.size();
+        coef.insert(coef.end(), cur.poly.begin(), cur.poly.end());
+        cur = f12::radial_derivative(cur);
+      }
+      fams.push_back(d);
+    }
+    T.nfam[cls] = (int)fl.size();
+  }
+  // upload
+  dfree(ctx, ctx->d_fam, ctx->fam_bytes);
+  dfree(ctx, ctx->d_coef, ctx->coef_bytes);
+  ctx->fam_bytes = fams.size() * sizeof(FamDev);
+  ctx->coef_bytes = coef.size() * sizeof(double);
+  rc = dalloc(ctx, &ctx->d_fam, ctx->fam_bytes);
+  if (rc == F12INT_OK) rc = dalloc(ctx, &ctx->d_coef, ctx->coef_bytes);
+  if (rc != F12INT_OK) return rc;
+  CK(cudaMemcpy(ctx->d_fam, fams.data(), ctx->fam_bytes, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->d_coef, coef.data(), ctx->coef_bytes, cudaMemcpyHostToDevice));
+  T.fam = ctx->d_fam;
+  T.coef = ctx->d_coef;
+  ctx->tables = T;
+  ctx->factor_ready = true;
+  return F12INT_OK;
+}
+
+int f12int_set_basis(f12int_ctx *ctx, int nshell, const double *centers, const int *l, const int *nprim,
+                     const double *exps, const double *coefs, int *basis_id) {
+  if (!ctx || nshell <= 0 || !centers || !l || !nprim || !exps || !coefs || !basis_id) return F12INT_EINVAL;
+  int nptot = 0;
+  for (int i = 0; i < nshell; ++i) {
+    if (l[i] < 0 || l[i] > LSH || nprim[i] < 1) return F12INT_EINVAL;
+    for (int k = 0; k < 3; ++k)
+      if (!std::isfinite(centers[3 * i + k])) return F12INT_EINVAL;
+    nptot += nprim[i];
+  }
+  for (int i = 0; i < nptot; ++i)
+    if (!(exps[i] > 0.0) || !std::isfinite(exps[i]) || !std::isfinite(coefs[i])) return F12INT_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  CK(cudaSetDevice(ctx->device));
+  f12int_ctx::BasisData B;
+  B.nshell = nshell;
+  B.l.assign(l, l + nshell);
+  B.nprim.assign(nprim, nprim + nshell);
+  B.centers.assign(centers, centers + 3 * nshell);
+  std::vector<int> poff(nshell);
+  for (int i = 0, o = 0; i < nshell; ++i) {
+    poff[i] = o;
+    o += nprim[i];
+  }
+  // primitive pairs of every ordered shell pair (i, j), i outer
+  std::vector<int> sa, sb, pa, pb;
+  std::vector<int64_t> eoff;
+  B.pair_start.assign((size_t)nshell * nshell + 1, 0);
+  int64_t epos = 0;
+  for (int i = 0; i < nshell; ++i)
+    for (int j = 0; j < nshell; ++j) {
+      B.pair_start[(size_t)i * nshell + j] = (int)sa.size();
+      int n1 = (l[i] + 1) * (l[j] + 1) * (l[i] + l[j] + 1);
+      for (int x = 0; x < nprim[i]; ++x)
+        for (int y = 0; y < nprim[j]; ++y) {
+          sa.push_back(i);
+          sb.push_back(j);
+          pa.push_back(poff[i] + x);
+          pb.push_back(poff[j] + y);
+          eoff.push_back(epos);
+          epos += 6 * n1;
+        }
+    }
+  B.pair_start[(size_t)nshell * nshell] = (int)sa.size();
+  const int npp = (int)sa.size();
+  // device buffers
+  int *d_sa = nullptr, *d_sb = nullptr, *d_pa = nullptr, *d_pb = nullptr;
+  double *d_exps = nullptr, *d_coefs = nullptr;
+  int rc = F12INT_OK;
+  size_t bytes = 0;
+  auto A = [&](auto **p, size_t n) {
+    if (rc != F12INT_OK) return;
+    rc = dalloc(ctx, p, n);
+    bytes += n;
+  };
+  A(&B.d_shell_l, sizeof(int) * nshell);
+  A(&B.d_centers, sizeof(double) * 3 * nshell);
+  A(&B.d_pair_start, sizeof(int) * B.pair_start.size());
+  A(&B.d_pp_p, sizeof(double) * npp);
+  A(&B.d_pp_P, sizeof(double) * 3 * npp);
+  A(&B.d_pp_ab, sizeof(double) * 2 * npp);
+  A(&B.d_pp_eoff, sizeof(int64_t) * npp);
+  A(&B.d_epool, sizeof(double) * std::max<int64_t>(epos, 1));
+  B.bytes = bytes;
+  size_t tmpb = 0;
+  auto At = [&](auto **p, size_t n) {
+    if (rc != F12INT_OK) return;
+    rc = dalloc(ctx, p, n);
+    tmpb += n;
+  };
+  At(&d_sa, sizeof(int) * npp);
+  At(&d_sb, sizeof(int) * npp);
+  At(&d_pa, sizeof(int) * npp);
+  At(&d_pb, sizeof(int) * npp);
+  At(&d_exps, sizeof(double) * nptot);
+  At(&d_coefs, sizeof(double) * nptot);
+  if (rc == F12INT_OK) {
+    cudaStream_t st = ctx->stream;
+    cudaMemcpyAsync(B.d_shell_l, l, sizeof(int) * nshell, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(B.d_centers, centers, sizeof(double) * 3 * nshell, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(B.d_pair_start, B.pair_start.data(), sizeof(int) * B.pair_start.size(), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(B.d_pp_eoff, eoff.data(), sizeof(int64_t) * npp, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(d_sa, sa.data(), sizeof(int) * npp, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(d_sb, sb.data(), sizeof(int) * npp, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(d_pa, pa.data(), sizeof(int) * npp, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(d_pb, pb.data(), sizeof(int) * npp, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(d_exps, exps, sizeof(double) * nptot, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(d_coefs, coefs, sizeof(double) * nptot, cudaMemcpyHostToDevice, st);
+    int nb = (npp + 127) / 128;
+    k_build_pairs<<<nb, 128, 0, st>>>(npp, d_sa, d_sb, d_pa, d_pb, B.d_centers, B.d_shell_l, d_exps, d_coefs,
+                                      B.d_pp_p, B.d_pp_P, B.d_pp_ab, B.d_pp_eoff, B.d_epool);
+    ctx->launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = cuda_fail(e);
+  }
+  dfree(ctx, d_sa, sizeof(int) * npp);
+  dfree(ctx, d_sb, sizeof(int) * npp);
+  dfree(ctx, d_pa, sizeof(int) * npp);
+  dfree(ctx, d_pb, sizeof(int) * npp);
+  dfree(ctx, d_exps, sizeof(double) * nptot);
+  dfree(ctx, d_coefs, sizeof(double) * nptot);
+  if (rc != F12INT_OK) {
+    cudaFree(B.d_shell_l);
+    cudaFree(B.d_centers);
+    cudaFree(B.d_pair_start);
+    cudaFree(B.d_pp_p);
+    cudaFree(B.d_pp_P);
+    cudaFree(B.d_pp_ab);
+    cudaFree(B.d_pp_eoff);
+    cudaFree(B.d_epool);
+    ctx->used -= std::min(ctx->used, B.bytes);
+    return rc;
+  }
+  ctx->bases.push_back(std::move(B));
+  *basis_id = (int)ctx->bases.size() - 1;
+  return F12INT_OK;
+}
+
+static int ensure_scratch(f12int_ctx *ctx, size_t bytes) {
+  if (ctx->scratch_bytes >= bytes) return F12INT_OK;
+  dfree(ctx, ctx->d_scratch, ctx->scratch_bytes);
+  ctx->scratch_bytes = 0;
+  size_t want = std::max(bytes, (size_t)1 << 20);
+  int rc = dalloc(ctx, &ctx->d_scratch, want);
+  if (rc == F12INT_OK) ctx->scratch_bytes = want;
+  return rc;
+}
+
+static size_t contract_smem(int la, int lb, int lc, int ld, int cls) {
+  int ext = cls == 5 ? 2 : 0;
+  int L = la + lb + lc + ld + ext;
+  int nhL = nh_count(L), nhB = nh_count(la + lb + ext);
+  int ncd = ncart(lc) * ncart(ld), nab = ncart(la) * ncart(lb);
+  return sizeof(double) * ((size_t)2 * nhL + (size_t)nhB * ncd + (size_t)nab * ncd);
+}
+
+// Queue aux + contraction for quartets already on the device.
+static int launch_batch(f12int_ctx *ctx, const f12int_ctx::BasisData &B, int cls, const int32_t *d_quartets,
+                        const int64_t *d_pqoff, int64_t n, int64_t npq, size_t smem, double *out_dev,
+                        const int64_t *offsets_dev, cudaStream_t st) {
+  PairView PV{B.d_pair_start, B.d_pp_p, B.d_pp_P, B.d_pp_ab, B.d_pp_eoff, B.d_epool, B.d_shell_l, B.nshell};
+  QuartetView QV{d_quartets, d_pqoff, n};
+  if (npq > 0) {
+    int64_t nb = (npq + BLOCK_AUX - 1) / BLOCK_AUX;
+    k_aux_quartets<<<(unsigned)nb, BLOCK_AUX, 0, st>>>(ctx->tables, PV, QV, cls, npq, ctx->d_scratch,
+                                                       ctx->d_status);
+    ctx->launches++;
+    CK(cudaGetLastError());
+  }
+  if (smem > 48 * 1024) CK(cudaFuncSetAttribute(k_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_contract<<<(unsigned)n, BLOCK_CONTRACT, smem, st>>>(PV, QV, cls, ctx->d_scratch, out_dev, offsets_dev,
+                                                         ctx->d_status);
+  ctx->launches++;
+  CK(cudaGetLastError());
+  return F12INT_OK;
+}
+
+int f12int_compute_class(f12int_ctx *ctx, int basis_id, int cls, const int32_t *quartets_dev, int64_t n,
+                         double *out_dev, const int64_t *offsets_dev, void *cuda_stream) {
+  if (!ctx) return F12INT_EINVAL;
+  if (cls < 1 || cls > 6 || n < 0) return F12INT_EINVAL;
+  if (basis_id < 0 || basis_id >= (int)ctx->bases.size()) return F12INT_ENOTREADY;
+  if (!ctx->factor_ready) return F12INT_ENOTREADY;
+  if (n == 0) return F12INT_OK;
+  if (!quartets_dev || !out_dev || !offsets_dev) return F12INT_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  CK(cudaSetDevice(ctx->device));
+  const f12int_ctx::BasisData &B = ctx->bases[basis_id];
+  cudaStream_t st = pick_stream(ctx, cuda_stream);
+  // quartet metadata: primitive-quartet offsets and shared-memory need
+  std::vector<int32_t> hq((size_t)4 * n);
+  CK(cudaMemcpyAsync(hq.data(), quartets_dev, sizeof(int32_t) * 4 * n, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  std::vector<int64_t> pqoff((size_t)n + 1);
+  int64_t npq = 0;
+  size_t smem = 0;
+  const int ns = B.nshell;
+  for (int64_t i = 0; i < n; ++i) {
+    const int32_t *s = &hq[4 * i];
+    for (int k = 0; k < 4; ++k)
+      if (s[k] < 0 || s[k] >= ns) return F12INT_EINVAL;
+    pqoff[i] = npq;
+    npq += (int64_t)B.nprim[s[0]] * B.nprim[s[1]] * B.nprim[s[2]] * B.nprim[s[3]];
+    smem = std::max(smem, contract_smem(B.l[s[0]], B.l[s[1]], B.l[s[2]], B.l[s[3]], cls));
+  }
+  pqoff[n] = npq;
+  if (smem > 227 * 1024) return F12INT_EINVAL;
+  int rc = ensure_scratch(ctx, sizeof(double) * (size_t)npq * (LAUX + 1));
+  if (rc != F12INT_OK) return rc;
+  if (ctx->pqoff_cap < (size_t)n + 1) {
+    dfree(ctx, ctx->d_pqoff, ctx->pqoff_cap * sizeof(int64_t));
+    ctx->pqoff_cap = 0;
+    rc = dalloc(ctx, &ctx->d_pqoff, sizeof(int64_t) * ((size_t)n + 1));
+    if (rc != F12INT_OK) return rc;
+    ctx->pqoff_cap = (size_t)n + 1;
+  }
+  CK(cudaMemcpyAsync(ctx->d_pqoff, pqoff.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, st));
+  rc = launch_batch(ctx, B, cls, quartets_dev, ctx->d_pqoff, n, npq, smem, out_dev, offsets_dev, st);
+  if (rc != F12INT_OK) return rc;
+  // keep the host buffer alive until the copy has been consumed
+  CK(cudaStreamSynchronize(st));
+  return F12INT_OK;
+}
+
+int f12int_aux(f12int_ctx *ctx, int cls, int64_t npts, const double *xi_dev, const double *D_dev, int nmax,
+               double *out_dev, void *cuda_stream) {
+  if (!ctx || cls < 1 || cls > 6 || npts < 0 || nmax < 0 || nmax > LAUX) return F12INT_EINVAL;
+  if (!ctx->factor_ready) return F12INT_ENOTREADY;
+  if (npts == 0) return F12INT_OK;
+  if (!xi_dev || !D_dev || !out_dev) return F12INT_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = pick_stream(ctx, cuda_stream);
+  int64_t nb = (npts + BLOCK_AUX - 1) / BLOCK_AUX;
+  k_aux_points<<<(unsigned)nb, BLOCK_AUX, 0, st>>>(ctx->tables, cls, npts, xi_dev, D_dev, nmax, out_dev,
+                                                   ctx->d_status);
+  ctx->launches++;
+  CK(cudaGetLastError());
+  return F12INT_OK;
+}
+
+int f12int_screen(f12int_ctx *ctx, int basis_id, int cls, double thresh, int32_t *quartets_out, int64_t cap,
+                  int64_t *n_out) {
+  if (!ctx || cls < 1 || cls > 6 || !n_out || cap < 0 || (cap > 0 && !quartets_out)) return F12INT_EINVAL;
+  if (basis_id < 0 || basis_id >= (int)ctx->bases.size() || !ctx->factor_ready) return F12INT_ENOTREADY;
+  if (!(thresh >= 0.0)) return F12INT_EINVAL;
+  const f12int_ctx::BasisData &B = ctx->bases[basis_id];
+  const int ns = B.nshell;
+  const int dcls = cls == 5 ? 3 : cls;
+  // diagonal blocks (ab|ab) for a >= b
+  std::vector<int32_t> hq;
+  std::vector<int64_t> off;
+  int64_t tot = 0;
+  for (int a = 0; a < ns; ++a)
+    for (int b = 0; b <= a; ++b) {
+      hq.insert(hq.end(), {a, b, a, b});
+      off.push_back(tot);
+      int nab = ncart(B.l[a]) * ncart(B.l[b]);
+      tot += (int64_t)nab * nab;
+    }
+  const int64_t nq = (int64_t)off.size();
+  int32_t *dq = nullptr;
+  int64_t *doff = nullptr;
+  double *dout = nullptr;
+  int rc = dalloc(ctx, &dq, sizeof(int32_t) * hq.size());
+  if (rc == F12INT_OK) rc = dalloc(ctx, &doff, sizeof(int64_t) * nq);
+  if (rc == F12INT_OK) rc = dalloc(ctx, &dout, sizeof(double) * tot);
+  std::vector<double> hout((size_t)tot);
+  if (rc == F12INT_OK) {
+    cudaStream_t st = ctx->stream;
+    if (cudaMemcpyAsync(dq, hq.data(), sizeof(int32_t) * hq.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(doff, off.data(), sizeof(int64_t) * nq, cudaMemcpyHostToDevice, st) != cudaSuccess)
+      rc = F12INT_ECUDA;
+    if (rc == F12INT_OK) rc = f12int_compute_class(ctx, basis_id, dcls, dq, nq, dout, doff, st);
+    if (rc == F12INT_OK &&
+        (cudaMemcpyAsync(hout.data(), dout, sizeof(double) * tot, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+         cudaStreamSynchronize(st) != cudaSuccess))
+      rc = F12INT_ECUDA;
+  }
+  dfree(ctx, dq, sizeof(int32_t) * hq.size());
+  dfree(ctx, doff, sizeof(int64_t) * nq);
+  dfree(ctx, dout, sizeof(double) * tot);
+  if (rc != F12INT_OK) return rc;
+  // bound(ab) = sqrt(max |(ab|k|ab)|)
+  std::vector<double> bound((size_t)ns * ns, 0.0);
+  int64_t k = 0;
+  for (int a = 0; a < ns; ++a)
+    for (int b = 0; b <= a; ++b, ++k) {
+      int nab = ncart(B.l[a]) * ncart(B.l[b]);
+      double m = 0.0;
+      for (int64_t i = 0; i < (int64_t)nab * nab; ++i) m = std::max(m, std::fabs(hout[off[k] + i]));
+      bound[(size_t)a * ns + b] = bound[(size_t)b * ns + a] = std::sqrt(m);
+    }
+  std::vector<std::pair<int, int>> pairs;
+  for (int a = 0; a < ns; ++a)
+    for (int b = 0; b <= a; ++b) pairs.emplace_back(a, b);
+  int64_t cnt = 0;
+  for (size_t i = 0; i < pairs.size(); ++i) {
+    size_t jend = (cls == 5) ? pairs.size() : i + 1;
+    double bi = bound[(size_t)pairs[i].first * ns + pairs[i].second];
+    for (size_t j = 0; j < jend; ++j) {
+      double bj = bound[(size_t)pairs[j].first * ns + pairs[j].second];
+      if (bi * bj >= thresh) {
+        if (cnt < cap) {
+          quartets_out[4 * cnt] = pairs[i].first;
+          quartets_out[4 * cnt + 1] = pairs[i].second;
+          quartets_out[4 * cnt + 2] = pairs[j].first;
+          quartets_out[4 * cnt + 3] = pairs[j].second;
+        }
+        ++cnt;
+      }
+    }
+  }
+  *n_out = cnt;
+  return F12INT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,167 @@
+"""Thin Python binding of the C ABI in include/f12int.h.
+
+Argument marshalling only: every step of the integral path runs in the CUDA
+library ``_build/libf12int.so``.  PyTorch supplies device memory and
+streams (tensors' ``data_ptr()`` and ``torch.cuda.Stream.cuda_stream``).
+The functions carry the C names; a nonzero status raises F12IntError.
+Importing this module does not need a GPU; loading the library does need
+the library to have been built (``paper_1412_5070_gb300.build``) and fails
+loudly otherwise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+F12INT_I1, F12INT_I2, F12INT_I3, F12INT_I4, F12INT_I5, F12INT_I6 = 1, 2, 3, 4, 5, 6
+STATUS = {0: "F12INT_OK", -1: "F12INT_EINVAL", -2: "F12INT_ENOMEM", -3: "F12INT_EDOMAIN",
+          -4: "F12INT_ENOTREADY", -5: "F12INT_ETIMEOUT", -6: "F12INT_ECUDA", -7: "F12INT_EDEVICE"}
+
+# every entry point declared in include/f12int.h
+EXPORTS = ("f12int_create", "f12int_destroy", "f12int_set_basis", "f12int_set_factor", "f12int_screen",
+           "f12int_compute_class", "f12int_aux", "f12int_launch_count", "f12int_device_status",
+           "f12int_strerror")
+
+
+class F12IntError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = _lib.f12int_strerror(status).decode() if _lib is not None else STATUS.get(status, "?")
+        super().__init__("%s failed: %s (%s)" % (where, STATUS.get(status, status), msg))
+
+
+class Factor(ctypes.Structure):
+    _fields_ = [("c0", ctypes.c_double), ("rho", ctypes.c_double), ("B", ctypes.c_double),
+                ("mu", ctypes.c_double), ("n", ctypes.c_int)]
+
+    @classmethod
+    def of(cls, d):
+        return cls(float(d["c0"]), float(d["rho"]), float(d["B"]), float(d["mu"]), int(d["n"]))
+
+
+_lib = None
+_vp, _dp, _ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load the compiled library; raise if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise ImportError("CUDA library %s is missing: run paper_1412_5070_gb300.build.build() first" % path)
+    L = ctypes.CDLL(path)
+    L.f12int_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_size_t, _vp]
+    L.f12int_destroy.argtypes = [_vp]
+    L.f12int_set_basis.argtypes = [_vp, ctypes.c_int, _dp, _ip, _ip, _dp, _dp, _ip]
+    L.f12int_set_factor.argtypes = [_vp, ctypes.POINTER(Factor), ctypes.POINTER(Factor)]
+    L.f12int_screen.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                ctypes.POINTER(ctypes.c_int32), ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
+    L.f12int_compute_class.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int64, _vp, _vp, _vp]
+    L.f12int_aux.argtypes = [_vp, ctypes.c_int, ctypes.c_int64, _vp, _vp, ctypes.c_int, _vp, _vp]
+    L.f12int_launch_count.argtypes = [_vp]
+    L.f12int_launch_count.restype = ctypes.c_int64
+    L.f12int_device_status.argtypes = [_vp]
+    L.f12int_strerror.argtypes = [ctypes.c_int]
+    L.f12int_strerror.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name not in ("f12int_launch_count", "f12int_strerror"):
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(rc: int, where: str):
+    if rc != 0:
+        raise F12IntError(rc, where)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def _ptr(t):
+    """Device pointer of a torch tensor (must be contiguous and on CUDA)."""
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+def f12int_strerror(status: int) -> str:
+    return load().f12int_strerror(int(status)).decode()
+
+
+def f12int_create(device: int = 0, hbm_budget_bytes: int = 0, stream=None):
+    L = load()
+    h = _vp()
+    _check(L.f12int_create(ctypes.byref(h), int(device), int(hbm_budget_bytes), _stream_ptr(stream)),
+           "f12int_create")
+    return h
+
+
+def f12int_destroy(ctx) -> None:
+    _check(load().f12int_destroy(ctx), "f12int_destroy")
+
+
+def f12int_set_basis(ctx, basis) -> int:
+    c = np.ascontiguousarray(basis.centers, dtype=np.float64)
+    l = np.ascontiguousarray(basis.l, dtype=np.int32)
+    npr = np.ascontiguousarray(basis.nprim, dtype=np.int32)
+    e = np.ascontiguousarray(basis.exps, dtype=np.float64)
+    co = np.ascontiguousarray(basis.coefs, dtype=np.float64)
+    bid = ctypes.c_int(-1)
+    _check(load().f12int_set_basis(ctx, len(l), c.ctypes.data_as(_dp), l.ctypes.data_as(_ip),
+                                   npr.ctypes.data_as(_ip), e.ctypes.data_as(_dp), co.ctypes.data_as(_dp),
+                                   ctypes.byref(bid)), "f12int_set_basis")
+    return bid.value
+
+
+def f12int_set_factor(ctx, f, fprime=None) -> None:
+    F = Factor.of(f)
+    Fp = Factor.of(fprime) if fprime is not None else None
+    _check(load().f12int_set_factor(ctx, ctypes.byref(F), ctypes.byref(Fp) if Fp is not None else None),
+           "f12int_set_factor")
+
+
+def f12int_screen(ctx, basis_id: int, cls: int, thresh: float, cap: int = 0) -> np.ndarray:
+    """Canonical quartets surviving the Schwarz-type screen (host int32 [n, 4])."""
+    L = load()
+    n = ctypes.c_int64(0)
+    _check(L.f12int_screen(ctx, int(basis_id), int(cls), float(thresh), None, 0, ctypes.byref(n)), "f12int_screen")
+    out = np.zeros((max(n.value, 1), 4), dtype=np.int32)
+    _check(L.f12int_screen(ctx, int(basis_id), int(cls), float(thresh),
+                           out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), n.value, ctypes.byref(n)),
+           "f12int_screen")
+    return out[: n.value]
+
+
+def f12int_compute_class(ctx, basis_id: int, cls: int, quartets_dev, out_dev, offsets_dev, stream=None) -> None:
+    n = quartets_dev.numel() // 4
+    _check(load().f12int_compute_class(ctx, int(basis_id), int(cls), _ptr(quartets_dev), n, _ptr(out_dev),
+                                       _ptr(offsets_dev), _stream_ptr(stream)), "f12int_compute_class")
+
+
+def f12int_aux(ctx, cls: int, xi_dev, D_dev, nmax: int, out_dev, stream=None) -> None:
+    _check(load().f12int_aux(ctx, int(cls), xi_dev.numel(), _ptr(xi_dev), _ptr(D_dev), int(nmax), _ptr(out_dev),
+                             _stream_ptr(stream)), "f12int_aux")
+
+
+def f12int_launch_count(ctx) -> int:
+    return int(load().f12int_launch_count(ctx))
+
+
+def f12int_device_status(ctx) -> None:
+    _check(load().f12int_device_status(ctx), "f12int_device_status")

@@ -1,0 +1,123 @@
+"""Parity of the CUDA path with the CPU oracle (needs a GPU).
+
+Every comparison goes through the C ABI (paper_1412_5070_gb300.f12int) and
+the oracle (oracle/oracle.py) on the same seeded inputs.
+
+Tolerance (FP64 path): relative 1e-10 where |I_ref| > 1e-12, absolute 1e-12
+elsewhere.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import oracle as O
+from paper_1412_5070_gb300 import build as B
+from paper_1412_5070_gb300 import f12int as F
+from paper_1412_5070_gb300 import molecules as M
+
+RTOL, ATOL_SMALL, SMALL = 1e-10, 1e-12, 1e-12
+
+
+def close(got, ref):
+    """Mask of elements outside the FP64 tolerance."""
+    big = np.abs(ref) > SMALL
+    bad = np.zeros(ref.shape, dtype=bool)
+    bad[big] = np.abs(got[big] - ref[big]) > RTOL * np.abs(ref[big])
+    bad[~big] = np.abs(got[~big] - ref[~big]) > ATOL_SMALL
+    return bad
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    B.build()
+    c = F.f12int_create(0, 0, None)
+    F.f12int_set_factor(c, M.P0)
+    yield c
+    F.f12int_destroy(c)
+
+
+def gpu_blocks(ctx, bid, cls, basis, quartets):
+    q = np.ascontiguousarray(quartets, dtype=np.int32)
+    off = M.block_offsets(basis, q)
+    dq = torch.from_numpy(q).cuda()
+    doff = torch.from_numpy(off[:-1].copy()).cuda()
+    out = torch.full((int(off[-1]),), float("nan"), dtype=torch.float64, device="cuda")
+    F.f12int_compute_class(ctx, bid, cls, dq, out, doff)
+    torch.cuda.synchronize()
+    F.f12int_device_status(ctx)
+    return out.cpu().numpy(), off
+
+
+XI_D_GRID = [(xi, D) for xi in (0.025, 0.1, 0.5, 2.0, 10.0, 50.0) for D in (0.0, 0.05, 0.3, 1.0, 2.5, 5.0, 7.0,
+                                                                            10.0, 20.0)]
+
+
+@pytest.mark.parametrize("cls", [1, 2, 3, 4, 6])
+def test_aux_stage_against_oracle(ctx, cls):
+    """hat g_n (n <= 10) from the auxiliary-function kernel against the
+    oracle's quadrature of Eq. bfinal."""
+    nmax = 10
+    xi = torch.tensor([p[0] for p in XI_D_GRID], dtype=torch.float64, device="cuda")
+    D = torch.tensor([p[1] for p in XI_D_GRID], dtype=torch.float64, device="cuda")
+    out = torch.zeros(len(XI_D_GRID) * (nmax + 1), dtype=torch.float64, device="cuda")
+    F.f12int_aux(ctx, cls, xi, D, nmax, out)
+    torch.cuda.synchronize()
+    F.f12int_device_status(ctx)
+    got = out.cpu().numpy().reshape(len(XI_D_GRID), nmax + 1)
+    K = O.factor_kernel(M.P0)
+    worst = 0.0
+    for i, (x, d) in enumerate(XI_D_GRID):
+        ref = O.radial(K, cls, x, d, nmax)
+        rel = np.abs(got[i] - ref) / np.abs(ref)
+        worst = max(worst, float(rel.max()))
+    print("class %d worst relative error of hat g_n: %.3g" % (cls, worst))
+    assert worst < 1e-8
+
+
+@pytest.mark.parametrize("cls", [1, 2, 3, 4, 5, 6])
+def test_two_centre_sp_all_classes(ctx, cls):
+    """Two centres 5.6 bohr apart, uncontracted s/p shells: a quarter of the
+    canonical quartets (every (la,lb,lc,ld) combination present) against
+    the oracle, element by element."""
+    basis = M.two_centre_sp()
+    bid = F.f12int_set_basis(ctx, basis)
+    q = M.canonical_quartets(basis, cls)
+    sel = q[::4]
+    got, off = gpu_blocks(ctx, bid, cls, basis, sel)
+    ref, _ = O.shell_blocks(O.factor_kernel(M.P0), cls, basis, sel)
+    bad = close(got, ref)
+    assert not np.isnan(got).any()
+    assert not bad.any(), "mismatches: %d of %d; worst rel %.3g" % (
+        bad.sum(), bad.size, np.max(np.abs(got - ref)[bad] / np.maximum(np.abs(ref[bad]), 1e-300)))
+
+
+def stratified(basis, cls, per_class, seed):
+    """A few canonical quartets of every (la, lb, lc, ld) combination."""
+    q = M.canonical_quartets(basis, cls)
+    ls = basis.l[q]
+    key = ls[:, 0] * 64 + ls[:, 1] * 16 + ls[:, 2] * 4 + ls[:, 3]
+    rng = np.random.default_rng(seed)
+    pick = []
+    for k in np.unique(key):
+        idx = np.nonzero(key == k)[0]
+        pick.extend(rng.choice(idx, size=min(per_class, len(idx)), replace=False).tolist())
+    return q[np.sort(np.array(pick))]
+
+
+@pytest.mark.parametrize("cls", [1, 2, 3, 4, 5, 6])
+def test_twelve_atom_spd_stratified(ctx, cls):
+    """12-atom 3s2p1d molecule (3 primitives per shell, seed 2): one quartet
+    of every angular-momentum combination (s, p, d) against the oracle."""
+    basis = M.twelve_atom_spd(2)
+    bid = F.f12int_set_basis(ctx, basis)
+    sel = stratified(basis, cls, 1, 20 + cls)
+    got, off = gpu_blocks(ctx, bid, cls, basis, sel)
+    ref, _ = O.shell_blocks(O.factor_kernel(M.P0), cls, basis, sel)
+    bad = close(got, ref)
+    assert not np.isnan(got).any()
+    assert not bad.any(), "mismatches: %d of %d; worst rel %.3g" % (
+        bad.sum(), bad.size, np.max(np.abs(got - ref)[bad] / np.maximum(np.abs(ref[bad]), 1e-300)))
