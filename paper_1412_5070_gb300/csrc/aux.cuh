@@ -53,6 +53,8 @@ struct FamDev {
   double gam_tab[JMAX];       // Gamma((alpha0 + 1 + j)/2); unused entry for alpha0 + 1 + j == 0
   double rho_start;           // Gamma((as+2)/2) / Gamma((as+1)/2), as = first regular alpha
   int fp_minus1;              // alpha0 == -1: the j = 0 term needs the finite part S(-1,...)
+  int pow_kind;               // x^alpha0: 1 integer, 2 half-integer, 0 general
+  int pow_int;                // integer part for pow_kind 1 and 2
   int span[LAUX + 1];
   int coff[LAUX + 1];         // offset of P_l in the coefficient pool
 };
@@ -145,132 +147,160 @@ __device__ inline double s_minus1(double b, double gam, int *bad) {
   return s;
 }
 
-// hat g_l for l = 0..L of the kernel with families fam[0..nf).
-// Returns nonzero if a series did not converge within KMAX terms.
+// Contribution of one family to hat g_l, l = 0..L, added into out[] with the
+// common factor 4 xi (2 xi)^l applied.  Returns nonzero if a series did not
+// converge within KMAX terms.
+__device__ inline int family_eval(const Tables &T, const FamDev &F, double xi, double D, int L, double *out) {
+  int bad = 0;
+  const double gam = F.g + xi;
+  const double beta = F.b + 2.0 * xi * D;
+  const double z = beta * beta / (4.0 * gam);
+  // orders l < ls use the quadrature about the peak, l >= ls the series
+  int ls = 0;
+  while (ls <= L && z >= threshold_z(ls)) ++ls;
+  double fct[LAUX + 1];
+  fct[0] = 4.0 * xi;
+  for (int l = 1; l <= L; ++l) fct[l] = fct[l - 1] * 2.0 * xi;
+
+  if (ls > 0) {
+    const double sg = sqrt(gam), isg = 1.0 / sg;
+    const double xs = beta / (2.0 * gam);
+    const double estar = (F.b * F.b + 4.0 * F.b * xi * D - 4.0 * F.g * xi * D * D) / (4.0 * gam);
+    const double pre = exp(estar) * isg;
+    double acc[LAUX + 1];
+    for (int l = 0; l < ls; ++l) acc[l] = 0.0;
+    double jh[LAUX + 2];
+    const double twoxd = 2.0 * xi * D;
+    for (int i = 0; i < NGH; ++i) {
+      const double x = xs + c_gh_x[i] * isg;
+      if (x <= 0.0) continue;
+      jhat_all(twoxd * x, ls - 1, jh);
+      double xa;
+      if (F.pow_kind == 1) {          // alpha0 = integer n0
+        xa = 1.0;
+        for (int k = 0; k < F.pow_int; ++k) xa *= x;
+        if (F.pow_int < 0) xa = 1.0 / x;  // only alpha0 = -1 occurs
+      } else if (F.pow_kind == 2) {   // alpha0 = n0 + 1/2
+        xa = sqrt(x);
+        for (int k = 0; k < F.pow_int; ++k) xa *= x;
+        if (F.pow_int < 0) xa /= x;     // alpha0 = -1/2
+      } else {
+        xa = pow(x, F.alpha0);
+      }
+      xa *= c_gh_w[i];
+      for (int l = 0; l < ls; ++l) {
+        const double *P = T.coef + F.coff[l];
+        const int sp = F.span[l];
+        double h = 0.0;
+        for (int j = sp - 1; j >= 0; --j) h = fma(h, x, P[j]);
+        acc[l] = fma(xa * jh[l], h, acc[l]);
+      }
+    }
+    for (int l = 0; l < ls; ++l) out[l] += fct[l] * pre * acc[l];
+  }
+
+  if (ls <= L) {
+    const double y = F.b * rsqrt(gam);
+    const double v = 4.0 * xi * xi * D * D / gam;
+    const double eT = exp(-xi * D * D);
+    const double rgam = rsqrt(gam);
+    const int m0 = F.fp_minus1 ? 1 : 0;      // first regular index of the S family
+    const double as = F.alpha0 + m0;
+    // unnormalised start values J_{as}, J_{as+1} (J_alpha = int t^alpha e^{yt - t^2} dt)
+    const double rho1 = 0.5 * (as + 1.0) / F.rho_start;
+    const double J0 = jhat_start(as, F.rho_start, y, &bad) * F.gam_tab[m0];
+    const double J1 = jhat_start(as + 1.0, rho1, y, &bad) * F.gam_tab[m0 + 1];
+    const double sm1 = F.fp_minus1 ? s_minus1(F.b, gam, &bad) : 0.0;
+    const double gpow0 = pow(gam, -0.5 * (F.alpha0 + 1.0));
+    const double TWO600 = 4.149515568880993e+180, MTWO600 = 2.409919865102884e-181;
+
+    for (int l = ls; l <= L; ++l) {
+      const double *P = T.coef + F.coff[l];
+      const int sp = F.span[l];
+      double q[JMAX];
+      double qabs = 0.0, gp = gpow0;
+      for (int j = 0; j < sp; ++j) {
+        q[j] = P[j] * gp;
+        qabs += fabs(q[j]);
+        gp *= rgam;
+      }
+      // c_{l,0} = 1/(2l+1)!!
+      double cl0 = 1.0;
+      for (int j = 1; j <= l; ++j) cl0 /= (2 * j + 1);
+      double common = cl0 * eT;   // c_{l,k} v^k e^{-xi D^2}, times the window's scale
+      double sum = 0.0;
+      if (F.fp_minus1) sum = q[0] * common * sm1;
+      double win[WIN];
+      win[m0 & (WIN - 1)] = J0;
+      win[(m0 + 1) & (WIN - 1)] = J1;
+      int mfill = m0 + 2;
+      double abs_total = 0.0, prev_mag = 0.0;
+      int k;
+      for (k = 0; k < KMAX; ++k) {
+        const int need = sp - 1 + 2 * k;
+        while (mfill <= need) {
+          const double a = F.alpha0 + (mfill - 1);
+          double jn = 0.5 * fma(y, win[(mfill - 1) & (WIN - 1)], a * win[(mfill - 2) & (WIN - 1)]);
+          win[mfill & (WIN - 1)] = jn;
+          ++mfill;
+          if (fabs(jn) > TWO600) {   // keep the window in range; exact power-of-two rescale
+            for (int r = mfill - WIN; r < mfill; ++r)
+              if (r >= 0) win[r & (WIN - 1)] *= MTWO600;
+            common *= TWO600;
+          }
+        }
+        const int jlo = (F.fp_minus1 && k == 0) ? 1 : 0;
+        double part = 0.0;
+        for (int j = jlo; j < sp; ++j) part = fma(q[j], win[(j + 2 * k) & (WIN - 1)], part);
+        sum = fma(common, part, sum);
+        const double mag = fabs(common) * qabs *
+                           fmax(fabs(win[max(2 * k, m0) & (WIN - 1)]), fabs(win[(2 * k + sp - 1) & (WIN - 1)]));
+        abs_total += mag;
+        if (k > 2 && mag <= 1e-17 * abs_total && mag <= prev_mag) break;
+        prev_mag = mag;
+        // c_{l,k+1}/c_{l,k} v
+        common *= v * (double)(k + l + 1) / ((double)(k + 1) * (2.0 * k + 2.0 * l + 2.0) * (2.0 * k + 2.0 * l + 3.0));
+        if (common != 0.0 && fabs(common) < MTWO600 && mfill > 0) {
+          // move scale from the coefficient back into the window when it underflows
+          bool ok = true;
+          for (int r = mfill - WIN; r < mfill; ++r)
+            if (r >= 0 && fabs(win[r & (WIN - 1)]) > MTWO600 * 1e100) ok = false;
+          if (ok) {
+            for (int r = mfill - WIN; r < mfill; ++r)
+              if (r >= 0) win[r & (WIN - 1)] *= TWO600;
+            common *= MTWO600;
+          }
+        }
+      }
+      if (k == KMAX) bad = 1;
+      out[l] += fct[l] * sum;
+    }
+  }
+  return bad;
+}
+
+// hat g_l for l = 0..L of the kernel of class kcls (sum over its families).
 __device__ inline int aux_eval(const Tables &T, int kcls, double xi, double D, int L, double *out) {
   for (int l = 0; l <= L; ++l) out[l] = 0.0;
   int bad = 0;
   const int nf = T.nfam[kcls];
   const FamDev *fams = T.fam + T.fam0[kcls];
-  const double T2 = xi * D * D;
-  const double w2 = 4.0 * xi * xi * D * D;  // (2 xi D)^2
-  for (int f = 0; f < nf; ++f) {
-    const FamDev &F = fams[f];
-    const double gam = F.g + xi;
-    const double beta = F.b + 2.0 * xi * D;
-    const double z = beta * beta / (4.0 * gam);
-    // orders l < ls use the quadrature about the peak, l >= ls the series
-    int ls = 0;
-    while (ls <= L && z >= threshold_z(ls)) ++ls;
-
-    if (ls > 0) {
-      const double sg = sqrt(gam);
-      const double xs = beta / (2.0 * gam);
-      const double estar = (F.b * F.b + 4.0 * F.b * xi * D - 4.0 * F.g * xi * D * D) / (4.0 * gam);
-      const double pre = exp(estar) / sg;
-      double acc[LAUX + 1];
-      for (int l = 0; l < ls; ++l) acc[l] = 0.0;
-      double jh[LAUX + 2];
-      for (int i = 0; i < NGH; ++i) {
-        double x = xs + c_gh_x[i] / sg;
-        if (x <= 0.0) continue;
-        jhat_all(2.0 * xi * D * x, ls - 1, jh);
-        double xa = pow(x, F.alpha0) * c_gh_w[i];
-        for (int l = 0; l < ls; ++l) {
-          const double *P = T.coef + F.coff[l];
-          int sp = F.span[l];
-          double h = 0.0;
-          for (int j = sp - 1; j >= 0; --j) h = h * x + P[j];
-          acc[l] += xa * jh[l] * h;
-        }
-      }
-      for (int l = 0; l < ls; ++l) out[l] += pre * acc[l];
-    }
-
-    if (ls <= L) {
-      const double y = F.b / sqrt(gam);
-      const double v = w2 / gam;
-      const double eT = exp(-T2);
-      const double rgam = 1.0 / sqrt(gam);
-      // start values of the normalised sequence Jh_{alpha_s}, Jh_{alpha_s + 1}
-      const int m0 = F.fp_minus1 ? 1 : 0;      // first regular index
-      const double as = F.alpha0 + m0;
-      const double j0 = jhat_start(as, F.rho_start, y, &bad);
-      // rho at alpha_s + 1: Gamma((as+3)/2)/Gamma((as+2)/2) = ((as+1)/2)/rho_start
-      const double rho1 = 0.5 * (as + 1.0) / F.rho_start;
-      const double j1 = jhat_start(as + 1.0, rho1, y, &bad);
-      const double sm1 = F.fp_minus1 ? s_minus1(F.b, gam, &bad) : 0.0;
-      const double gpow0 = pow(gam, -0.5 * (F.alpha0 + 1.0));
-
-      for (int l = ls; l <= L; ++l) {
-        const double *P = T.coef + F.coff[l];
-        const int sp = F.span[l];
-        double q[JMAX], t[JMAX];
-        // c_{l,0} = 2^l l! / (2l+1)! = 1/(2l+1)!!
-        double cl0 = 1.0;
-        for (int j = 1; j <= l; ++j) cl0 /= (2 * j + 1);
-        double gp = gpow0;
-        for (int j = 0; j < sp; ++j) {
-          q[j] = P[j] * gp;
-          gp *= rgam;
-          t[j] = cl0 * F.gam_tab[j] * eT;
-        }
-        double sum = 0.0;
-        if (F.fp_minus1) {
-          sum += q[0] * cl0 * eT * sm1;
-          t[0] = cl0 * eT;   // becomes c_{l,1} v Gamma(1) after the first update (see below)
-        }
-        // circular window over Jh_m, m = index relative to alpha0
-        double win[WIN];
-        int mfill;  // next index to fill
-        win[m0 & (WIN - 1)] = j0;
-        win[(m0 + 1) & (WIN - 1)] = j1;
-        mfill = m0 + 2;
-        // Recurrence in alpha (Eq. Srec1 in normalised form):
-        //   Jh_{a+1} = Jh_{a-1} + (y rho_a / a) Jh_a,   rho_{a+1} = a / (2 rho_a),
-        // rho_a = Gamma((a+1)/2)/Gamma(a/2); the first step is at a = as + 1,
-        // where rho = Gamma((as+2)/2)/Gamma((as+1)/2) = rho_start.
-        double rho = F.rho_start;
-        double abs_total = 0.0;
-        double prev_mag = 0.0;
-        int k;
-        for (k = 0; k < KMAX; ++k) {
-          int need = sp - 1 + 2 * k;  // highest index used at this k
-          while (mfill <= need) {
-            double a = F.alpha0 + (mfill - 1);
-            double jn = win[(mfill - 2) & (WIN - 1)] + y * rho / a * win[(mfill - 1) & (WIN - 1)];
-            rho = a / (2.0 * rho);
-            win[mfill & (WIN - 1)] = jn;
-            ++mfill;
-          }
-          double contrib = 0.0, mag = 0.0;
-          int jlo = (F.fp_minus1 && k == 0) ? 1 : 0;
-          for (int j = jlo; j < sp; ++j) {
-            double term = q[j] * t[j] * win[(j + 2 * k) & (WIN - 1)];
-            contrib += term;
-            mag += fabs(term);
-          }
-          sum += contrib;
-          abs_total += mag;
-          if (k > 2 && mag <= 1e-18 * abs_total && mag <= prev_mag) break;
-          prev_mag = mag;
-          // advance the coefficients: t_{j,k+1} = t_{j,k} v c_{l,k+1}/c_{l,k} (k + (alpha_j+1)/2)
-          double ratio = v * (double)(k + l + 1) / ((double)(k + 1) * (2.0 * k + 2.0 * l + 2.0) * (2.0 * k + 2.0 * l + 3.0));
-          for (int j = 0; j < sp; ++j) t[j] *= ratio * (k + 0.5 * (F.alpha0 + 1.0 + j));
-          if (F.fp_minus1 && k == 0) t[0] = cl0 * eT * ratio;  // (alpha_0+1)/2 = 0: Gamma(k) from k = 1
-        }
-        if (k == KMAX) bad = 1;
-        out[l] += sum;
-      }
-    }
-  }
-  // common factor 4 xi (2 xi)^l
-  double fct = 4.0 * xi;
-  for (int l = 0; l <= L; ++l) {
-    out[l] *= fct;
-    fct *= 2.0 * xi;
-  }
+  for (int f = 0; f < nf; ++f) bad |= family_eval(T, fams[f], xi, D, L, out);
   return bad;
 }
+
+// Work-item key used to order (primitive quartet, family) items so that a
+// warp runs the same branch with a similar series length: family, total
+// order L, and a bin of z (series by z/2, then the quadrature/series split).
+__device__ __forceinline__ int item_bin(const FamDev &F, double xi, double D, int L) {
+  const double gam = F.g + xi;
+  const double beta = F.b + 2.0 * xi * D;
+  const double z = beta * beta / (4.0 * gam);
+  if (z < threshold_z(0)) return (int)(0.5 * z);            // 0..17
+  int ls = 0;
+  while (ls <= L && z >= threshold_z(ls)) ++ls;
+  return 18 + ls;                                             // 19..33
+}
+constexpr int NZBIN = 34;
 
 }  // namespace f12dev

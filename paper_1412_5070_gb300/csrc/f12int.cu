@@ -158,12 +158,13 @@ __device__ __forceinline__ int64_t find_quartet(const int64_t *off, int64_t n, i
   return lo;
 }
 
-// g_n (with the prefactor sqrt(pi^5/(p+q))/(pq) of Eq. bfinal) for every
-// primitive quartet of the batch, into scratch[pq*(LAUX+1) + n].
-__global__ void k_aux_quartets(Tables T, PairView PV, QuartetView QV, int cls, int64_t npq, double *scratch,
-                               unsigned int *status) {
-  int64_t pq = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (pq >= npq) return;
+// Work items of the auxiliary stage: item = (primitive quartet of the chunk) * nf + family.
+struct ItemGeom {
+  double xi, D;
+  int L;
+};
+
+__device__ __forceinline__ ItemGeom item_geometry(const PairView &PV, const QuartetView &QV, int cls, int64_t pq) {
   int64_t q = find_quartet(QV.pq_off, QV.n, pq);
   const int32_t *s = QV.quartets + 4 * q;
   const int ns = PV.nshell;
@@ -172,25 +173,92 @@ __global__ void k_aux_quartets(Tables T, PairView PV, QuartetView QV, int cls, i
   int64_t r = pq - QV.pq_off[q];
   int iab = PV.pair_start[ab] + (int)(r / npcd);
   int icd = PV.pair_start[cd] + (int)(r % npcd);
-  int L = PV.shell_l[s[0]] + PV.shell_l[s[1]] + PV.shell_l[s[2]] + PV.shell_l[s[3]] + (cls == 5 ? 2 : 0);
+  ItemGeom g;
+  g.L = PV.shell_l[s[0]] + PV.shell_l[s[1]] + PV.shell_l[s[2]] + PV.shell_l[s[3]] + (cls == 5 ? 2 : 0);
   double p = PV.pp_p[iab], qq = PV.pp_p[icd];
   double X = PV.pp_P[3 * icd] - PV.pp_P[3 * iab];
   double Y = PV.pp_P[3 * icd + 1] - PV.pp_P[3 * iab + 1];
   double Z = PV.pp_P[3 * icd + 2] - PV.pp_P[3 * iab + 2];
-  double D = sqrt(X * X + Y * Y + Z * Z);
-  double xi = p * qq / (p + qq);
-  double g[LAUX + 1];
-  if (L > LAUX) {
+  g.D = sqrt(X * X + Y * Y + Z * Z);
+  g.xi = p * qq / (p + qq);
+  return g;
+}
+
+__device__ __forceinline__ int item_key(int f, int L, int bin) { return (f * (LAUX + 1) + L) * NZBIN + bin; }
+
+// Pass 1: key of every item and a histogram of the keys.
+__global__ void k_items_classify(Tables T, PairView PV, QuartetView QV, int cls, int64_t pq0, int64_t nitems,
+                                 int *keys, unsigned int *hist) {
+  int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (it >= nitems) return;
+  const int kcls = cls == 5 ? 3 : cls;
+  const int nf = T.nfam[kcls];
+  const int64_t pq = pq0 + it / nf;
+  const int f = (int)(it % nf);
+  ItemGeom g = item_geometry(PV, QV, cls, pq);
+  const FamDev &F = T.fam[T.fam0[kcls] + f];
+  int key = item_key(f, min(g.L, LAUX), item_bin(F, g.xi, g.D, g.L));
+  keys[it] = key;
+  atomicAdd(&hist[key], 1u);
+}
+
+// Pass 2: exclusive scan of the histogram (one block).
+__global__ void k_items_scan(unsigned int *hist, int nkeys) {
+  __shared__ unsigned int part[1024];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int per = (nkeys + nt - 1) / nt;
+  unsigned int s = 0;
+  for (int i = tid * per; i < min(nkeys, (tid + 1) * per); ++i) s += hist[i];
+  part[tid] = s;
+  __syncthreads();
+  if (tid == 0) {
+    unsigned int run = 0;
+    for (int i = 0; i < nt; ++i) {
+      unsigned int v = part[i];
+      part[i] = run;
+      run += v;
+    }
+  }
+  __syncthreads();
+  unsigned int run = part[tid];
+  for (int i = tid * per; i < min(nkeys, (tid + 1) * per); ++i) {
+    unsigned int v = hist[i];
+    hist[i] = run;
+    run += v;
+  }
+}
+
+// Pass 3: scatter item indices into key order (order inside a key is free:
+// every item is evaluated independently, so results do not depend on it).
+__global__ void k_items_scatter(const int *keys, unsigned int *cursor, int64_t nitems, unsigned int *order) {
+  int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (it >= nitems) return;
+  unsigned int pos = atomicAdd(&cursor[keys[it]], 1u);
+  order[pos] = (unsigned int)it;
+}
+
+// Pass 4: one family's contribution to hat g_l (l <= L) per item, into
+// part[item * (LAUX+1) + l], in key order.
+__global__ void k_items_eval(Tables T, PairView PV, QuartetView QV, int cls, int64_t pq0, int64_t nitems,
+                             const unsigned int *order, double *part, unsigned int *status) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nitems) return;
+  const int64_t it = order[t];
+  const int kcls = cls == 5 ? 3 : cls;
+  const int nf = T.nfam[kcls];
+  const int64_t pq = pq0 + it / nf;
+  const int f = (int)(it % nf);
+  ItemGeom g = item_geometry(PV, QV, cls, pq);
+  if (g.L > LAUX) {
     atomicOr(status, 4u);
     return;
   }
-  int bad = aux_eval(T, cls == 5 ? 3 : cls, xi, D, L, g);
+  double out[LAUX + 1];
+  for (int l = 0; l <= g.L; ++l) out[l] = 0.0;
+  int bad = family_eval(T, T.fam[T.fam0[kcls] + f], g.xi, g.D, g.L, out);
   if (bad) atomicOr(status, 1u);
-  // sqrt(pi^5/(p+q)) / (p q)
-  const double pi52 = 17.493418327624862846;  // pi^{5/2}
-  double pref = pi52 / (sqrt(p + qq) * p * qq);
-  double *o = scratch + pq * (LAUX + 1);
-  for (int n = 0; n <= L; ++n) o[n] = pref * g[n];
+  double *o = part + it * (LAUX + 1);
+  for (int l = 0; l <= g.L; ++l) o[l] = out[l];
 }
 
 // hat g_n at given (xi, D) points (no prefactor), for the aux-stage tests.
@@ -211,11 +279,12 @@ __global__ void k_aux_points(Tables T, int cls, int64_t npts, const double *xi, 
 //            ket primitive pairs, bra order <= lab(+2)    nh(Lb) * ncd
 //   O        output accumulator                           nab * ncd
 __global__ void __launch_bounds__(BLOCK_CONTRACT)
-k_contract(PairView PV, QuartetView QV, int cls, const double *scratch, double *out, const int64_t *offsets,
-           unsigned int *status) {
+k_contract(PairView PV, QuartetView QV, int cls, int nf, int64_t pq0, int64_t q0, const double *part,
+           double *out, const int64_t *offsets, unsigned int *status) {
   extern __shared__ double smem[];
-  const int64_t q = blockIdx.x;
+  const int64_t q = q0 + blockIdx.x;
   if (q >= QV.n) return;
+  __shared__ double gsh[LAUX + 1];
   const int32_t *s = QV.quartets + 4 * q;
   const int ns = PV.nshell;
   const int la = PV.shell_l[s[0]], lb = PV.shell_l[s[1]], lc = PV.shell_l[s[2]], ld = PV.shell_l[s[3]];
@@ -246,10 +315,20 @@ k_contract(PairView PV, QuartetView QV, int cls, const double *scratch, double *
     __syncthreads();
     for (int icd = 0; icd < npcd; ++icd) {
       const int pcd = cd0 + icd;
-      const double *g = scratch + (QV.pq_off[q] + (int64_t)iab * npcd + icd) * (LAUX + 1);
+      const int64_t pq = QV.pq_off[q] + (int64_t)iab * npcd + icd - pq0;
       const double X = PV.pp_P[3 * pcd] - PV.pp_P[3 * pab];
       const double Y = PV.pp_P[3 * pcd + 1] - PV.pp_P[3 * pab + 1];
       const double Z = PV.pp_P[3 * pcd + 2] - PV.pp_P[3 * pab + 2];
+      // g_n = sqrt(pi^5/(p+q))/(pq) * sum over families, summed in a fixed order
+      if (tid <= L) {
+        const double p = PV.pp_p[pab], qq = PV.pp_p[pcd];
+        const double pi52 = 17.493418327624862846;  // pi^{5/2}
+        double acc = 0.0;
+        for (int fm = 0; fm < nf; ++fm) acc += part[(pq * nf + fm) * (LAUX + 1) + tid];
+        gsh[tid] = pi52 / (sqrt(p + qq) * p * qq) * acc;
+      }
+      __syncthreads();
+      const double *g = gsh;
       // Hermite recursion from level n = L down to 0, ping-pong between R0/R1
       double *cur = R0, *nxt = R1;
       if (tid == 0) cur[0] = g[L];
@@ -373,12 +452,12 @@ struct f12int_ctx {
     size_t bytes = 0;
   };
   std::vector<BasisData> bases;
-  // scratch for compute_class
-  double *d_scratch = nullptr;
-  size_t scratch_bytes = 0;
-  int32_t *d_qbuf = nullptr;
+  // scratch of compute_class (grown on demand, bounded by the budget)
   int64_t *d_pqoff = nullptr;
-  size_t qbuf_cap = 0, pqoff_cap = 0;
+  int *d_keys = nullptr;
+  unsigned *d_order = nullptr, *d_hist = nullptr;
+  double *d_part = nullptr;
+  size_t pqoff_cap = 0, keys_cap = 0, order_cap = 0, hist_cap = 0, part_cap = 0;
   std::mutex mu;
 };
 
@@ -564,9 +643,11 @@ int f12int_destroy(f12int_ctx *ctx) {
   }
   cudaFree(ctx->d_fam);
   cudaFree(ctx->d_coef);
-  cudaFree(ctx->d_scratch);
-  cudaFree(ctx->d_qbuf);
   cudaFree(ctx->d_pqoff);
+  cudaFree(ctx->d_keys);
+  cudaFree(ctx->d_order);
+  cudaFree(ctx->d_hist);
+  cudaFree(ctx->d_part);
   cudaFree(ctx->d_status);
   delete ctx;
   return F12INT_OK;
@@ -621,6 +702,13 @@ int f12int_set_factor(f12int_ctx *ctx, const f12int_factor *f, const f12int_fact
       for (int j = 0; j < JMAX; ++j) {
         double arg = 0.5 * (d.alpha0 + 1.0 + j);
         d.gam_tab[j] = arg > 0.0 ? std::tgamma(arg) : 0.0;
+      }
+      {
+        double fl = std::floor(d.alpha0 + 1e-9);
+        double fr = d.alpha0 - fl;
+        d.pow_int = (int)fl;
+        d.pow_kind = (std::fabs(fr) < 1e-9) ? 1 : (std::fabs(fr - 0.5) < 1e-9 ? 2 : 0);
+        if (d.pow_kind == 1 && d.pow_int < -1) d.pow_kind = 0;
       }
       double as = d.fp_minus1 ? 0.0 : d.alpha0;
       d.rho_start = std::exp(std::lgamma(0.5 * (as + 2.0)) - std::lgamma(0.5 * (as + 1.0)));
@@ -772,13 +860,17 @@ int f12int_set_basis(f12int_ctx *ctx, int nshell, const double *centers, const i
   return F12INT_OK;
 }
 
-static int ensure_scratch(f12int_ctx *ctx, size_t bytes) {
-  if (ctx->scratch_bytes >= bytes) return F12INT_OK;
-  dfree(ctx, ctx->d_scratch, ctx->scratch_bytes);
-  ctx->scratch_bytes = 0;
-  size_t want = std::max(bytes, (size_t)1 << 20);
-  int rc = dalloc(ctx, &ctx->d_scratch, want);
-  if (rc == F12INT_OK) ctx->scratch_bytes = want;
+static int ensure_buf(f12int_ctx *ctx, void **p, size_t *cap, size_t bytes) {
+  if (*cap >= bytes) return F12INT_OK;
+  if (*p) {
+    cudaFree(*p);
+    ctx->used -= std::min(ctx->used, *cap);
+    *p = nullptr;
+    *cap = 0;
+  }
+  size_t want = std::max(bytes, (size_t)1 << 16);
+  int rc = dalloc(ctx, (char **)p, want);
+  if (rc == F12INT_OK) *cap = want;
   return rc;
 }
 
@@ -790,22 +882,39 @@ static size_t contract_smem(int la, int lb, int lc, int ld, int cls) {
   return sizeof(double) * ((size_t)2 * nhL + (size_t)nhB * ncd + (size_t)nab * ncd);
 }
 
-// Queue aux + contraction for quartets already on the device.
-static int launch_batch(f12int_ctx *ctx, const f12int_ctx::BasisData &B, int cls, const int32_t *d_quartets,
-                        const int64_t *d_pqoff, int64_t n, int64_t npq, size_t smem, double *out_dev,
-                        const int64_t *offsets_dev, cudaStream_t st) {
+// items of the auxiliary stage per chunk (bounds the scratch memory)
+static const int64_t kItemChunk = (int64_t)8 << 20;
+static const int kNKeys = MAXFAM * (LAUX + 1) * NZBIN;
+
+// Queue the auxiliary stage (classify, scan, scatter, evaluate) and the
+// contraction for quartets [qa, qb) of the device list.
+static int launch_chunk(f12int_ctx *ctx, const f12int_ctx::BasisData &B, int cls, const int32_t *d_quartets,
+                        const int64_t *d_pqoff, int64_t n, int64_t qa, int64_t qb, int64_t pqa, int64_t pqb,
+                        size_t smem, double *out_dev, const int64_t *offsets_dev, cudaStream_t st) {
   PairView PV{B.d_pair_start, B.d_pp_p, B.d_pp_P, B.d_pp_ab, B.d_pp_eoff, B.d_epool, B.d_shell_l, B.nshell};
   QuartetView QV{d_quartets, d_pqoff, n};
-  if (npq > 0) {
-    int64_t nb = (npq + BLOCK_AUX - 1) / BLOCK_AUX;
-    k_aux_quartets<<<(unsigned)nb, BLOCK_AUX, 0, st>>>(ctx->tables, PV, QV, cls, npq, ctx->d_scratch,
-                                                       ctx->d_status);
-    ctx->launches++;
+  const int kcls = cls == 5 ? 3 : cls;
+  const int nf = ctx->tables.nfam[kcls];
+  const int64_t nitems = (pqb - pqa) * nf;
+  if (nitems > 0) {
+    int rc = ensure_buf(ctx, (void **)&ctx->d_keys, &ctx->keys_cap, sizeof(int) * nitems);
+    if (rc == F12INT_OK) rc = ensure_buf(ctx, (void **)&ctx->d_order, &ctx->order_cap, sizeof(unsigned) * nitems);
+    if (rc == F12INT_OK) rc = ensure_buf(ctx, (void **)&ctx->d_part, &ctx->part_cap, sizeof(double) * nitems * (LAUX + 1));
+    if (rc == F12INT_OK) rc = ensure_buf(ctx, (void **)&ctx->d_hist, &ctx->hist_cap, sizeof(unsigned) * kNKeys);
+    if (rc != F12INT_OK) return rc;
+    CK(cudaMemsetAsync(ctx->d_hist, 0, sizeof(unsigned) * kNKeys, st));
+    const unsigned nb = (unsigned)((nitems + BLOCK_AUX - 1) / BLOCK_AUX);
+    k_items_classify<<<nb, BLOCK_AUX, 0, st>>>(ctx->tables, PV, QV, cls, pqa, nitems, ctx->d_keys, ctx->d_hist);
+    k_items_scan<<<1, 1024, 0, st>>>(ctx->d_hist, kNKeys);
+    k_items_scatter<<<nb, BLOCK_AUX, 0, st>>>(ctx->d_keys, ctx->d_hist, nitems, ctx->d_order);
+    k_items_eval<<<nb, BLOCK_AUX, 0, st>>>(ctx->tables, PV, QV, cls, pqa, nitems, ctx->d_order, ctx->d_part,
+                                           ctx->d_status);
+    ctx->launches += 4;
     CK(cudaGetLastError());
   }
   if (smem > 48 * 1024) CK(cudaFuncSetAttribute(k_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_contract<<<(unsigned)n, BLOCK_CONTRACT, smem, st>>>(PV, QV, cls, ctx->d_scratch, out_dev, offsets_dev,
-                                                         ctx->d_status);
+  k_contract<<<(unsigned)(qb - qa), BLOCK_CONTRACT, smem, st>>>(PV, QV, cls, nf, pqa, qa, ctx->d_part, out_dev,
+                                                                offsets_dev, ctx->d_status);
   ctx->launches++;
   CK(cudaGetLastError());
   return F12INT_OK;
@@ -841,18 +950,20 @@ int f12int_compute_class(f12int_ctx *ctx, int basis_id, int cls, const int32_t *
   }
   pqoff[n] = npq;
   if (smem > 227 * 1024) return F12INT_EINVAL;
-  int rc = ensure_scratch(ctx, sizeof(double) * (size_t)npq * (LAUX + 1));
+  int rc = ensure_buf(ctx, (void **)&ctx->d_pqoff, &ctx->pqoff_cap, sizeof(int64_t) * ((size_t)n + 1));
   if (rc != F12INT_OK) return rc;
-  if (ctx->pqoff_cap < (size_t)n + 1) {
-    dfree(ctx, ctx->d_pqoff, ctx->pqoff_cap * sizeof(int64_t));
-    ctx->pqoff_cap = 0;
-    rc = dalloc(ctx, &ctx->d_pqoff, sizeof(int64_t) * ((size_t)n + 1));
-    if (rc != F12INT_OK) return rc;
-    ctx->pqoff_cap = (size_t)n + 1;
-  }
   CK(cudaMemcpyAsync(ctx->d_pqoff, pqoff.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, st));
-  rc = launch_batch(ctx, B, cls, quartets_dev, ctx->d_pqoff, n, npq, smem, out_dev, offsets_dev, st);
-  if (rc != F12INT_OK) return rc;
+  const int kcls = cls == 5 ? 3 : cls;
+  const int64_t nf = ctx->tables.nfam[kcls];
+  const int64_t pq_chunk = std::max<int64_t>(1, kItemChunk / std::max<int64_t>(nf, 1));
+  for (int64_t qa = 0; qa < n;) {
+    int64_t qb = qa + 1;
+    while (qb < n && pqoff[qb + 1] - pqoff[qa] <= pq_chunk) ++qb;
+    rc = launch_chunk(ctx, B, cls, quartets_dev, ctx->d_pqoff, n, qa, qb, pqoff[qa], pqoff[qb], smem, out_dev,
+                      offsets_dev, st);
+    if (rc != F12INT_OK) return rc;
+    qa = qb;
+  }
   // keep the host buffer alive until the copy has been consumed
   CK(cudaStreamSynchronize(st));
   return F12INT_OK;
