@@ -43,7 +43,8 @@ constexpr int LAUX = 14;     // highest radial order (f shells, I5: 3+3+3+3+2)
 constexpr int JMAX = 48;     // longest family polynomial
 constexpr int WIN = 64;      // circular window over the S sequence (> JMAX + 2)
 constexpr int KMAX = 1500;   // series length cap
-constexpr int NGH = 48;      // Gauss-Hermite nodes
+constexpr int NGH = 24;      // Gauss-Hermite nodes
+constexpr int KTAB = 320;    // tabulated series coefficient ratios
 constexpr int MAXFAM = 24;   // families per kernel
 constexpr int NCLASS = 7;    // index by class 1..6
 
@@ -68,6 +69,8 @@ struct Tables {
 
 __constant__ double c_gh_x[NGH];
 __constant__ double c_gh_w[NGH];
+// c_{l,k+1}/c_{l,k} = (k+l+1) / ((k+1)(2k+2l+2)(2k+2l+3)),  c_{l,k} = 2^l (k+l)!/(k!(2k+2l+1)!)
+__constant__ double c_cratio[LAUX + 1][KTAB];
 
 __device__ __forceinline__ double threshold_z(int l) { return 36.0 + 4.5 * l; }
 
@@ -76,7 +79,7 @@ __device__ __forceinline__ double threshold_z(int l) { return 36.0 + 4.5 * l; }
 // small z; closed forms of j_0, j_1 and the upward recurrence for large z.
 __device__ inline void jhat_all(double z, int N, double *jh) {
   if (z > 2.0 * N + 30.0) {
-    double e2 = exp(-2.0 * z), iz = 1.0 / z;
+    double e2 = z < 40.0 ? exp(-2.0 * z) : 0.0, iz = 1.0 / z;
     jh[0] = 0.5 * (1.0 - e2) * iz;
     if (N >= 1) jh[1] = 0.5 * ((1.0 - iz) + e2 * (1.0 + iz)) * iz * iz;
     for (int m = 1; m < N; ++m) jh[m + 1] = (jh[m - 1] - (2 * m + 1) * jh[m]) * iz * iz;
@@ -218,10 +221,9 @@ __device__ inline int family_eval(const Tables &T, const FamDev &F, double xi, d
       const double *P = T.coef + F.coff[l];
       const int sp = F.span[l];
       double q[JMAX];
-      double qabs = 0.0, gp = gpow0;
+      double gp = gpow0;
       for (int j = 0; j < sp; ++j) {
         q[j] = P[j] * gp;
-        qabs += fabs(q[j]);
         gp *= rgam;
       }
       // c_{l,0} = 1/(2l+1)!!
@@ -234,7 +236,10 @@ __device__ inline int family_eval(const Tables &T, const FamDev &F, double xi, d
       win[m0 & (WIN - 1)] = J0;
       win[(m0 + 1) & (WIN - 1)] = J1;
       int mfill = m0 + 2;
-      double abs_total = 0.0, prev_mag = 0.0;
+      double abs_total = 0.0;
+      int small = 0;
+      // past the largest term: the terms behave like z^k/k!
+      const int kmin = (int)(0.5 * v) + 2;
       int k;
       for (k = 0; k < KMAX; ++k) {
         const int need = sp - 1 + 2 * k;
@@ -252,15 +257,17 @@ __device__ inline int family_eval(const Tables &T, const FamDev &F, double xi, d
         const int jlo = (F.fp_minus1 && k == 0) ? 1 : 0;
         double part = 0.0;
         for (int j = jlo; j < sp; ++j) part = fma(q[j], win[(j + 2 * k) & (WIN - 1)], part);
-        sum = fma(common, part, sum);
-        const double mag = fabs(common) * qabs *
-                           fmax(fabs(win[max(2 * k, m0) & (WIN - 1)]), fabs(win[(2 * k + sp - 1) & (WIN - 1)]));
+        const double term = common * part;
+        sum += term;
+        const double mag = fabs(term);
         abs_total += mag;
-        if (k > 2 && mag <= 1e-17 * abs_total && mag <= prev_mag) break;
-        prev_mag = mag;
+        small = (mag <= 1e-17 * abs_total) ? small + 1 : 0;
+        if (small >= 2 && k >= kmin) break;
         // c_{l,k+1}/c_{l,k} v
-        common *= v * (double)(k + l + 1) / ((double)(k + 1) * (2.0 * k + 2.0 * l + 2.0) * (2.0 * k + 2.0 * l + 3.0));
-        if (common != 0.0 && fabs(common) < MTWO600 && mfill > 0) {
+        const double cr = k < KTAB ? c_cratio[l][k]
+                                   : (double)(k + l + 1) / ((double)(k + 1) * (2.0 * k + 2.0 * l + 2.0) * (2.0 * k + 2.0 * l + 3.0));
+        common *= v * cr;
+        if (common != 0.0 && fabs(common) < MTWO600) {
           // move scale from the coefficient back into the window when it underflows
           bool ok = true;
           for (int r = mfill - WIN; r < mfill; ++r)

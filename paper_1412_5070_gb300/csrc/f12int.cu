@@ -273,18 +273,26 @@ __global__ void k_aux_points(Tables T, int cls, int64_t npts, const double *xi, 
 }
 
 // -------------------------------------------------------------- contract --
-// One block per shell quartet.  Shared memory:
-//   R0, R1   two levels of the Hermite recursion        2 * nh(L)
-//   W        ket-contracted integrals, summed over the
-//            ket primitive pairs, bra order <= lab(+2)    nh(Lb) * ncd
-//   O        output accumulator                           nab * ncd
+// One block per shell quartet; its NW warps split the ket primitive pairs.
+// Shared memory (doubles):
+//   per warp: R0, R1  two levels of the Hermite recursion    2 * nh(L)
+//             W       ket-contracted integrals, bra order
+//                     <= lab (+2 for I5), summed over the
+//                     warp's ket primitive pairs              nh(Lb) * ncd
+//             g       the radial derivatives g_n              LAUX + 1
+//   block:    O       output accumulator                      nab * ncd
+// The per-warp W are summed in warp order, so results do not depend on
+// scheduling.
+__host__ __device__ __forceinline__ size_t contract_warp_doubles(int nhL, int nhB, int ncd) {
+  return (size_t)2 * nhL + (size_t)nhB * ncd + (LAUX + 1);
+}
+
 __global__ void __launch_bounds__(BLOCK_CONTRACT)
 k_contract(PairView PV, QuartetView QV, int cls, int nf, int64_t pq0, int64_t q0, const double *part,
            double *out, const int64_t *offsets, unsigned int *status) {
   extern __shared__ double smem[];
   const int64_t q = q0 + blockIdx.x;
   if (q >= QV.n) return;
-  __shared__ double gsh[LAUX + 1];
   const int32_t *s = QV.quartets + 4 * q;
   const int ns = PV.nshell;
   const int la = PV.shell_l[s[0]], lb = PV.shell_l[s[1]], lc = PV.shell_l[s[2]], ld = PV.shell_l[s[3]];
@@ -295,51 +303,53 @@ k_contract(PairView PV, QuartetView QV, int cls, int nf, int64_t pq0, int64_t q0
   const int na = ncart(la), nb = ncart(lb), nc = ncart(lc), nd = ncart(ld);
   const int ncd = nc * nd, nab = na * nb;
   const int nhL = nh_count(L), nhB = nh_count(Lb);
-  double *R0 = smem;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
+  const size_t wsz = contract_warp_doubles(nhL, nhB, ncd);
+  double *R0 = smem + warp * wsz;
   double *R1 = R0 + nhL;
   double *W = R1 + nhL;
-  double *Oacc = W + (size_t)nhB * ncd;
+  double *gw = W + (size_t)nhB * ncd;
+  double *Oacc = smem + nw * wsz;
   const int ab = s[0] * ns + s[1], cd = s[2] * ns + s[3];
   const int ab0 = PV.pair_start[ab], npab = PV.pair_start[ab + 1] - ab0;
   const int cd0 = PV.pair_start[cd], npcd = PV.pair_start[cd + 1] - cd0;
-  const int tid = threadIdx.x, nthr = blockDim.x;
   const int ntab = lab + 1, ntcd = lcd + 1;
-  const int n1ab = na > 0 ? (la + 1) * (lb + 1) * ntab : 0;
+  const int n1ab = (la + 1) * (lb + 1) * ntab;
   const int n1cd = (lc + 1) * (ld + 1) * ntcd;
+  const double pi52 = 17.493418327624862846;  // pi^{5/2}
 
   for (int i = tid; i < nab * ncd; i += nthr) Oacc[i] = 0.0;
 
   for (int iab = 0; iab < npab; ++iab) {
     const int pab = ab0 + iab;
-    for (int i = tid; i < nhB * ncd; i += nthr) W[i] = 0.0;
-    __syncthreads();
-    for (int icd = 0; icd < npcd; ++icd) {
+    for (int i = lane; i < nhB * ncd; i += 32) W[i] = 0.0;
+    __syncwarp();
+    for (int icd = warp; icd < npcd; icd += nw) {
       const int pcd = cd0 + icd;
       const int64_t pq = QV.pq_off[q] + (int64_t)iab * npcd + icd - pq0;
       const double X = PV.pp_P[3 * pcd] - PV.pp_P[3 * pab];
       const double Y = PV.pp_P[3 * pcd + 1] - PV.pp_P[3 * pab + 1];
       const double Z = PV.pp_P[3 * pcd + 2] - PV.pp_P[3 * pab + 2];
-      // g_n = sqrt(pi^5/(p+q))/(pq) * sum over families, summed in a fixed order
-      if (tid <= L) {
+      // g_n = sqrt(pi^5/(p+q))/(pq) * sum over families (fixed order)
+      if (lane <= L) {
         const double p = PV.pp_p[pab], qq = PV.pp_p[pcd];
-        const double pi52 = 17.493418327624862846;  // pi^{5/2}
         double acc = 0.0;
-        for (int fm = 0; fm < nf; ++fm) acc += part[(pq * nf + fm) * (LAUX + 1) + tid];
-        gsh[tid] = pi52 / (sqrt(p + qq) * p * qq) * acc;
+        for (int fm = 0; fm < nf; ++fm) acc += part[(pq * nf + fm) * (LAUX + 1) + lane];
+        gw[lane] = pi52 / (sqrt(p + qq) * p * qq) * acc;
       }
-      __syncthreads();
-      const double *g = gsh;
+      __syncwarp();
       // Hermite recursion from level n = L down to 0, ping-pong between R0/R1
       double *cur = R0, *nxt = R1;
-      if (tid == 0) cur[0] = g[L];
-      __syncthreads();
+      if (lane == 0) cur[0] = gw[L];
+      __syncwarp();
       for (int n = L - 1; n >= 0; --n) {
         const int cnt = nh_count(L - n);
-        for (int idx = tid; idx < cnt; idx += nthr) {
+        for (int idx = lane; idx < cnt; idx += 32) {
           const int t = c_tuv[idx][0], u = c_tuv[idx][1], v = c_tuv[idx][2];
           double val;
           if (idx == 0) {
-            val = g[n];
+            val = gw[n];
           } else if (t > 0) {
             val = X * cur[hidx(t - 1, u, v)];
             if (t > 1) val += (t - 1) * cur[hidx(t - 2, u, v)];
@@ -352,14 +362,14 @@ k_contract(PairView PV, QuartetView QV, int cls, int nf, int64_t pq0, int64_t q0
           }
           nxt[idx] = val;
         }
-        __syncthreads();
+        __syncwarp();
         double *tmp = cur;
         cur = nxt;
         nxt = tmp;
       }
       // inner (ket) sum of Eq. ii:  W[tuv][cd] += sum E^{cd}_{t'u'v'} R_{t+t',u+u',v+v'}
       const double *Ecd = PV.epool + PV.pp_eoff[pcd];
-      for (int i = tid; i < nhB * ncd; i += nthr) {
+      for (int i = lane; i < nhB * ncd; i += 32) {
         const int bi = i / ncd, j = i - bi * ncd;
         const int ic = j / nd, id = j - ic * nd;
         const int t = c_tuv[bi][0], u = c_tuv[bi][1], v = c_tuv[bi][2];
@@ -372,12 +382,21 @@ k_contract(PairView PV, QuartetView QV, int cls, int nf, int64_t pq0, int64_t q0
         for (int t2 = 0; t2 <= tx; ++t2)
           for (int u2 = 0; u2 <= ty; ++u2) {
             const double exy = ex[t2] * ey[u2];
-            for (int v2 = 0; v2 <= tz; ++v2) acc += exy * ez[v2] * cur[hidx(t + t2, u + u2, v + v2)];
+            for (int v2 = 0; v2 <= tz; ++v2) acc = fma(exy * ez[v2], cur[hidx(t + t2, u + u2, v + v2)], acc);
           }
         W[i] += acc;
       }
-      __syncthreads();
+      __syncwarp();
     }
+    __syncthreads();
+    // sum the warps' W into warp 0's buffer (fixed order)
+    double *W0 = smem + 2 * nhL;
+    for (int i = tid; i < nhB * ncd; i += nthr) {
+      double acc = W0[i];
+      for (int w = 1; w < nw; ++w) acc += smem[w * wsz + 2 * nhL + i];
+      W0[i] = acc;
+    }
+    __syncthreads();
     // outer (bra) sum
     const double *Eab = PV.epool + PV.pp_eoff[pab];
     const double *Fab = Eab + 3 * n1ab;
@@ -397,15 +416,15 @@ k_contract(PairView PV, QuartetView QV, int cls, int nf, int64_t pq0, int64_t q0
           for (int v = 0; v <= tz; ++v) {
             const double sgn = ((t + u + v) & 1) ? -1.0 : 1.0;
             if (cls != 5) {
-              acc += sgn * Eab[ox + t] * Eab[oy + u] * Eab[oz + v] * W[hidx(t, u, v) * ncd + j];
+              acc += sgn * Eab[ox + t] * Eab[oy + u] * Eab[oz + v] * W0[hidx(t, u, v) * ncd + j];
             } else {
               // Eq. I5byI3_ with the second coefficient -1 (see the derivation note below)
               const double e = Eab[ox + t] * Eab[oy + u] * Eab[oz + v];
-              const double lap = W[hidx(t + 2, u, v) * ncd + j] + W[hidx(t, u + 2, v) * ncd + j] +
-                                 W[hidx(t, u, v + 2) * ncd + j];
-              const double grad = Fab[ox + t] * Eab[oy + u] * Eab[oz + v] * W[hidx(t + 1, u, v) * ncd + j] +
-                                  Eab[ox + t] * Fab[oy + u] * Eab[oz + v] * W[hidx(t, u + 1, v) * ncd + j] +
-                                  Eab[ox + t] * Eab[oy + u] * Fab[oz + v] * W[hidx(t, u, v + 1) * ncd + j];
+              const double lap = W0[hidx(t + 2, u, v) * ncd + j] + W0[hidx(t, u + 2, v) * ncd + j] +
+                                 W0[hidx(t, u, v + 2) * ncd + j];
+              const double grad = Fab[ox + t] * Eab[oy + u] * Eab[oz + v] * W0[hidx(t + 1, u, v) * ncd + j] +
+                                  Eab[ox + t] * Fab[oy + u] * Eab[oz + v] * W0[hidx(t, u + 1, v) * ncd + j] +
+                                  Eab[ox + t] * Eab[oy + u] * Fab[oz + v] * W0[hidx(t, u, v + 1) * ncd + j];
               acc += sgn * (c5 * e * lap - grad);
             }
           }
@@ -457,7 +476,11 @@ struct f12int_ctx {
   int *d_keys = nullptr;
   unsigned *d_order = nullptr, *d_hist = nullptr;
   double *d_part = nullptr;
-  size_t pqoff_cap = 0, keys_cap = 0, order_cap = 0, hist_cap = 0, part_cap = 0;
+  int32_t *d_qperm = nullptr;
+  int64_t *d_operm = nullptr;
+  size_t pqoff_cap = 0, keys_cap = 0, order_cap = 0, hist_cap = 0, part_cap = 0, qperm_cap = 0, operm_cap = 0;
+  std::vector<int> h_nw;       // warps per contraction block, per quartet in the working order
+  std::vector<size_t> h_smem;  // contraction shared memory, per quartet in the working order
   std::mutex mu;
 };
 
@@ -567,6 +590,11 @@ int upload_constants() {
   }
   double gx[NGH], gw[NGH];
   gauss_hermite(NGH, gx, gw);
+  static double cr[LAUX + 1][KTAB];
+  for (int l = 0; l <= LAUX; ++l)
+    for (int k = 0; k < KTAB; ++k)
+      cr[l][k] = (double)(k + l + 1) / ((double)(k + 1) * (2.0 * k + 2.0 * l + 2.0) * (2.0 * k + 2.0 * l + 3.0));
+  CK(cudaMemcpyToSymbol(c_cratio, cr, sizeof(cr)));
   CK(cudaMemcpyToSymbol(c_tuv, tuv, sizeof(tuv)));
   CK(cudaMemcpyToSymbol(c_cart, cart, sizeof(cart)));
   CK(cudaMemcpyToSymbol(c_gh_x, gx, sizeof(gx)));
@@ -648,6 +676,8 @@ int f12int_destroy(f12int_ctx *ctx) {
   cudaFree(ctx->d_order);
   cudaFree(ctx->d_hist);
   cudaFree(ctx->d_part);
+  cudaFree(ctx->d_qperm);
+  cudaFree(ctx->d_operm);
   cudaFree(ctx->d_status);
   delete ctx;
   return F12INT_OK;
@@ -874,12 +904,19 @@ static int ensure_buf(f12int_ctx *ctx, void **p, size_t *cap, size_t bytes) {
   return rc;
 }
 
-static size_t contract_smem(int la, int lb, int lc, int ld, int cls) {
+static size_t contract_smem(int la, int lb, int lc, int ld, int cls, int nw) {
   int ext = cls == 5 ? 2 : 0;
   int L = la + lb + lc + ld + ext;
   int nhL = nh_count(L), nhB = nh_count(la + lb + ext);
   int ncd = ncart(lc) * ncart(ld), nab = ncart(la) * ncart(lb);
-  return sizeof(double) * ((size_t)2 * nhL + (size_t)nhB * ncd + (size_t)nab * ncd);
+  return sizeof(double) * ((size_t)nw * contract_warp_doubles(nhL, nhB, ncd) + (size_t)nab * ncd);
+}
+
+// warps per contraction block: 4 unless the shared memory does not fit
+static int contract_warps(int la, int lb, int lc, int ld, int cls) {
+  for (int nw = BLOCK_CONTRACT / 32; nw > 1; nw /= 2)
+    if (contract_smem(la, lb, lc, ld, cls, nw) <= 200 * 1024) return nw;
+  return 1;
 }
 
 // items of the auxiliary stage per chunk (bounds the scratch memory)
@@ -912,11 +949,20 @@ static int launch_chunk(f12int_ctx *ctx, const f12int_ctx::BasisData &B, int cls
     ctx->launches += 4;
     CK(cudaGetLastError());
   }
-  if (smem > 48 * 1024) CK(cudaFuncSetAttribute(k_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_contract<<<(unsigned)(qb - qa), BLOCK_CONTRACT, smem, st>>>(PV, QV, cls, nf, pqa, qa, ctx->d_part, out_dev,
-                                                                offsets_dev, ctx->d_status);
-  ctx->launches++;
-  CK(cudaGetLastError());
+  // contraction: quartets are ordered by decreasing shared-memory need; one
+  // launch per tier of warps and shared memory (powers of two)
+  for (int64_t ra = qa; ra < qb;) {
+    const int nw = ctx->h_nw[ra];
+    const size_t sm0 = ctx->h_smem[ra];
+    int64_t rb = ra + 1;
+    while (rb < qb && ctx->h_nw[rb] == nw && 2 * ctx->h_smem[rb] > sm0) ++rb;
+    if (sm0 > 48 * 1024) CK(cudaFuncSetAttribute(k_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm0));
+    k_contract<<<(unsigned)(rb - ra), 32 * nw, sm0, st>>>(PV, QV, cls, nf, pqa, ra, ctx->d_part, out_dev, offsets_dev,
+                                                         ctx->d_status);
+    ctx->launches++;
+    CK(cudaGetLastError());
+    ra = rb;
+  }
   return F12INT_OK;
 }
 
@@ -932,35 +978,70 @@ int f12int_compute_class(f12int_ctx *ctx, int basis_id, int cls, const int32_t *
   CK(cudaSetDevice(ctx->device));
   const f12int_ctx::BasisData &B = ctx->bases[basis_id];
   cudaStream_t st = pick_stream(ctx, cuda_stream);
-  // quartet metadata: primitive-quartet offsets and shared-memory need
-  std::vector<int32_t> hq((size_t)4 * n);
-  CK(cudaMemcpyAsync(hq.data(), quartets_dev, sizeof(int32_t) * 4 * n, cudaMemcpyDeviceToHost, st));
+  // quartet metadata: order by (la, lb, lc, ld), primitive-quartet offsets
+  std::vector<int32_t> hq0((size_t)4 * n);
+  std::vector<int64_t> ho0((size_t)n);
+  CK(cudaMemcpyAsync(hq0.data(), quartets_dev, sizeof(int32_t) * 4 * n, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(ho0.data(), offsets_dev, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  const int ns = B.nshell;
+  std::vector<int> key0((size_t)n);
+  for (int64_t i = 0; i < n; ++i) {
+    const int32_t *s = &hq0[4 * i];
+    for (int k = 0; k < 4; ++k)
+      if (s[k] < 0 || s[k] >= ns) return F12INT_EINVAL;
+    key0[i] = (B.l[s[0]] << 6) | (B.l[s[1]] << 4) | (B.l[s[2]] << 2) | B.l[s[3]];
+  }
+  std::vector<int64_t> perm((size_t)n);
+  for (int64_t i = 0; i < n; ++i) perm[i] = i;
+  // decreasing shared-memory need (long blocks first), then by class key
+  std::vector<size_t> sm0((size_t)n);
+  std::vector<int> nw0((size_t)n);
+  for (int64_t i = 0; i < n; ++i) {
+    const int k = key0[i];
+    nw0[i] = contract_warps((k >> 6) & 3, (k >> 4) & 3, (k >> 2) & 3, k & 3, cls);
+    sm0[i] = contract_smem((k >> 6) & 3, (k >> 4) & 3, (k >> 2) & 3, k & 3, cls, nw0[i]);
+  }
+  std::stable_sort(perm.begin(), perm.end(), [&](int64_t x, int64_t y) {
+    if (sm0[x] != sm0[y]) return sm0[x] > sm0[y];
+    return key0[x] < key0[y];
+  });
+  std::vector<int32_t> hq((size_t)4 * n);
+  std::vector<int64_t> ho((size_t)n);
+  ctx->h_nw.resize((size_t)n);
+  ctx->h_smem.resize((size_t)n);
+  for (int64_t i = 0; i < n; ++i) {
+    for (int k = 0; k < 4; ++k) hq[4 * i + k] = hq0[4 * perm[i] + k];
+    ho[i] = ho0[perm[i]];
+    ctx->h_nw[i] = nw0[perm[i]];
+    ctx->h_smem[i] = sm0[perm[i]];
+  }
   std::vector<int64_t> pqoff((size_t)n + 1);
   int64_t npq = 0;
   size_t smem = 0;
-  const int ns = B.nshell;
   for (int64_t i = 0; i < n; ++i) {
     const int32_t *s = &hq[4 * i];
-    for (int k = 0; k < 4; ++k)
-      if (s[k] < 0 || s[k] >= ns) return F12INT_EINVAL;
     pqoff[i] = npq;
     npq += (int64_t)B.nprim[s[0]] * B.nprim[s[1]] * B.nprim[s[2]] * B.nprim[s[3]];
-    smem = std::max(smem, contract_smem(B.l[s[0]], B.l[s[1]], B.l[s[2]], B.l[s[3]], cls));
+    smem = std::max(smem, ctx->h_smem[i]);
   }
   pqoff[n] = npq;
   if (smem > 227 * 1024) return F12INT_EINVAL;
   int rc = ensure_buf(ctx, (void **)&ctx->d_pqoff, &ctx->pqoff_cap, sizeof(int64_t) * ((size_t)n + 1));
+  if (rc == F12INT_OK) rc = ensure_buf(ctx, (void **)&ctx->d_qperm, &ctx->qperm_cap, sizeof(int32_t) * 4 * n);
+  if (rc == F12INT_OK) rc = ensure_buf(ctx, (void **)&ctx->d_operm, &ctx->operm_cap, sizeof(int64_t) * n);
   if (rc != F12INT_OK) return rc;
   CK(cudaMemcpyAsync(ctx->d_pqoff, pqoff.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->d_qperm, hq.data(), sizeof(int32_t) * 4 * n, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->d_operm, ho.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, st));
   const int kcls = cls == 5 ? 3 : cls;
   const int64_t nf = ctx->tables.nfam[kcls];
   const int64_t pq_chunk = std::max<int64_t>(1, kItemChunk / std::max<int64_t>(nf, 1));
   for (int64_t qa = 0; qa < n;) {
     int64_t qb = qa + 1;
     while (qb < n && pqoff[qb + 1] - pqoff[qa] <= pq_chunk) ++qb;
-    rc = launch_chunk(ctx, B, cls, quartets_dev, ctx->d_pqoff, n, qa, qb, pqoff[qa], pqoff[qb], smem, out_dev,
-                      offsets_dev, st);
+    rc = launch_chunk(ctx, B, cls, ctx->d_qperm, ctx->d_pqoff, n, qa, qb, pqoff[qa], pqoff[qb], smem, out_dev,
+                      ctx->d_operm, st);
     if (rc != F12INT_OK) return rc;
     qa = qb;
   }
