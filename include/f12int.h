@@ -127,6 +127,28 @@ int f12int_compute_class(f12int_ctx *ctx, int basis_id, int cls, const int32_t *
 int f12int_aux(f12int_ctx *ctx, int cls, int64_t npts, const double *xi_dev, const double *D_dev,
                int nmax, double *out_dev, void *cuda_stream);
 
+/* Same blocks as f12int_compute_class, but the call allocates no device
+ * memory: every scratch buffer comes from one file-scope device array of
+ * F12INT_STATIC_SCRATCH_BYTES (64 MiB) that each GPU which loads the library
+ * holds until the process exits.  It is meant for callers that cannot call
+ * cudaMalloc while they run, such as applications that reserve all device
+ * memory up front for their own pool, or services in which the device-wide
+ * synchronisation of an allocation would stall work on other streams.  The
+ * paper has no counterpart: this is a deployment interface, not part of the
+ * method.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call on a device shares the one array, which keeps the previous
+ *     call's contents (the call clears what must start at zero).  Calls whose
+ *     work overlaps on the GPU (other streams, other contexts of the same
+ *     device) race on it and must be serialised by the caller.
+ *   - Errors: F12INT_EINVAL when the quartet list (about 2M quartets at most)
+ *     or one shell quartet's primitive work does not fit in the array; the
+ *     other errors as for f12int_compute_class. */
+int f12int_compute_class_static(f12int_ctx *ctx, int basis_id, int cls, const int32_t *quartets_dev,
+                                int64_t n, double *out_dev, const int64_t *offsets_dev, void *cuda_stream);
+
 /* Number of kernel launches the context has issued so far (monotonic). */
 int64_t f12int_launch_count(const f12int_ctx *ctx);
 

@@ -1144,3 +1144,156 @@ int f12int_screen(f12int_ctx *ctx, int basis_id, int cls, double thresh, int32_t
 }
 
 }  // extern "C"
+
+// ===================================================== static-scratch variant ==
+// Callers that must not allocate device memory while they run (for example a
+// host application that reserves all device memory up front for its own
+// pool, or a latency-sensitive service in which the device-wide
+// synchronisation of a cudaMalloc would stall work on other streams) use
+// f12int_compute_class_static.  It runs the same kernels as
+// f12int_compute_class but takes every scratch buffer from the file-scope
+// array below, which each GPU that loads the library holds until exit.
+
+#define F12INT_STATIC_SCRATCH_BYTES ((size_t)64 << 20)
+
+static __device__ __align__(256) unsigned char g_static_scratch[F12INT_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+// Device address of g_static_scratch, resolved once per device.  In host code
+// the array's name is only a stand-in; the address must come from
+// cudaGetSymbolAddress with the device current.
+std::mutex g_static_mu;
+void *g_static_addr[64] = {nullptr};
+
+int static_scratch_address(int device, unsigned char **out) {
+  if (device < 0 || device >= 64) return F12INT_EINVAL;
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_addr[device]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p) return F12INT_ECUDA;
+    g_static_addr[device] = p;
+  }
+  *out = (unsigned char *)g_static_addr[device];
+  return F12INT_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" int f12int_compute_class_static(f12int_ctx *ctx, int basis_id, int cls, const int32_t *quartets_dev,
+                                           int64_t n, double *out_dev, const int64_t *offsets_dev,
+                                           void *cuda_stream) {
+  if (!ctx) return F12INT_EINVAL;
+  if (cls < 1 || cls > 6 || n < 0) return F12INT_EINVAL;
+  if (basis_id < 0 || basis_id >= (int)ctx->bases.size()) return F12INT_ENOTREADY;
+  if (!ctx->factor_ready) return F12INT_ENOTREADY;
+  if (n == 0) return F12INT_OK;
+  if (!quartets_dev || !out_dev || !offsets_dev) return F12INT_EINVAL;
+  // fixed part of the scratch: quartet list, offsets and primitive offsets in
+  // the working order, and the key histogram; the rest holds the work items
+  const size_t fixed = align256(sizeof(int32_t) * 4 * (size_t)n) + align256(sizeof(int64_t) * (size_t)n) +
+                       align256(sizeof(int64_t) * ((size_t)n + 1)) + align256(sizeof(unsigned) * kNKeys);
+  if (fixed + ((size_t)1 << 20) > F12INT_STATIC_SCRATCH_BYTES) return F12INT_EINVAL;  // too many quartets
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  CK(cudaSetDevice(ctx->device));
+  unsigned char *base = nullptr;
+  int rc = static_scratch_address(ctx->device, &base);
+  if (rc != F12INT_OK) return rc;
+  int32_t *d_q = (int32_t *)base;
+  int64_t *d_o = (int64_t *)(base + align256(sizeof(int32_t) * 4 * (size_t)n));
+  int64_t *d_pq = (int64_t *)((unsigned char *)d_o + align256(sizeof(int64_t) * (size_t)n));
+  unsigned *d_hist = (unsigned *)((unsigned char *)d_pq + align256(sizeof(int64_t) * ((size_t)n + 1)));
+  unsigned char *items_base = (unsigned char *)d_hist + align256(sizeof(unsigned) * kNKeys);
+  const size_t item_bytes = sizeof(int) + sizeof(unsigned) + sizeof(double) * (LAUX + 1);
+  const int64_t max_items = (int64_t)((F12INT_STATIC_SCRATCH_BYTES - fixed - 3 * 256) / item_bytes);
+
+  const f12int_ctx::BasisData &B = ctx->bases[basis_id];
+  cudaStream_t st = pick_stream(ctx, cuda_stream);
+  std::vector<int32_t> hq0((size_t)4 * n);
+  std::vector<int64_t> ho0((size_t)n);
+  CK(cudaMemcpyAsync(hq0.data(), quartets_dev, sizeof(int32_t) * 4 * n, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(ho0.data(), offsets_dev, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const int ns = B.nshell;
+  std::vector<size_t> sm0((size_t)n);
+  std::vector<int> nw0((size_t)n), key0((size_t)n);
+  for (int64_t i = 0; i < n; ++i) {
+    const int32_t *s = &hq0[4 * i];
+    for (int k = 0; k < 4; ++k)
+      if (s[k] < 0 || s[k] >= ns) return F12INT_EINVAL;
+    key0[i] = (B.l[s[0]] << 6) | (B.l[s[1]] << 4) | (B.l[s[2]] << 2) | B.l[s[3]];
+    nw0[i] = contract_warps(B.l[s[0]], B.l[s[1]], B.l[s[2]], B.l[s[3]], cls);
+    sm0[i] = contract_smem(B.l[s[0]], B.l[s[1]], B.l[s[2]], B.l[s[3]], cls, nw0[i]);
+  }
+  std::vector<int64_t> perm((size_t)n);
+  for (int64_t i = 0; i < n; ++i) perm[i] = i;
+  std::stable_sort(perm.begin(), perm.end(), [&](int64_t x, int64_t y) {
+    if (sm0[x] != sm0[y]) return sm0[x] > sm0[y];
+    return key0[x] < key0[y];
+  });
+  std::vector<int32_t> hq((size_t)4 * n);
+  std::vector<int64_t> ho((size_t)n), pqoff((size_t)n + 1);
+  std::vector<int> hnw((size_t)n);
+  std::vector<size_t> hsm((size_t)n);
+  int64_t npq = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    for (int k = 0; k < 4; ++k) hq[4 * i + k] = hq0[4 * perm[i] + k];
+    ho[i] = ho0[perm[i]];
+    hnw[i] = nw0[perm[i]];
+    hsm[i] = sm0[perm[i]];
+    const int32_t *s = &hq[4 * i];
+    pqoff[i] = npq;
+    npq += (int64_t)B.nprim[s[0]] * B.nprim[s[1]] * B.nprim[s[2]] * B.nprim[s[3]];
+    if (hsm[i] > 227 * 1024) return F12INT_EINVAL;
+  }
+  pqoff[n] = npq;
+  CK(cudaMemcpyAsync(d_q, hq.data(), sizeof(int32_t) * 4 * n, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d_o, ho.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d_pq, pqoff.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, st));
+
+  PairView PV{B.d_pair_start, B.d_pp_p, B.d_pp_P, B.d_pp_ab, B.d_pp_eoff, B.d_epool, B.d_shell_l, B.nshell};
+  QuartetView QV{d_q, d_pq, n};
+  const int kcls = cls == 5 ? 3 : cls;
+  const int nf = ctx->tables.nfam[kcls];
+  const int64_t pq_chunk = std::max<int64_t>(1, max_items / std::max(nf, 1));
+  for (int64_t qa = 0; qa < n;) {
+    int64_t qb = qa + 1;
+    if (pqoff[qb] - pqoff[qa] > pq_chunk) return F12INT_EINVAL;  // one quartet larger than the scratch
+    while (qb < n && pqoff[qb + 1] - pqoff[qa] <= pq_chunk) ++qb;
+    const int64_t pqa = pqoff[qa], nitems = (pqoff[qb] - pqa) * nf;
+    int *d_keys = (int *)items_base;
+    unsigned *d_order = (unsigned *)(items_base + align256(sizeof(int) * (size_t)nitems));
+    double *d_part = (double *)((unsigned char *)d_order + align256(sizeof(unsigned) * (size_t)nitems));
+    if (nitems > 0) {
+      // the histogram must start at zero on every call: the array keeps the
+      // previous call's contents
+      CK(cudaMemsetAsync(d_hist, 0, sizeof(unsigned) * kNKeys, st));
+      const unsigned nb = (unsigned)((nitems + BLOCK_AUX - 1) / BLOCK_AUX);
+      k_items_classify<<<nb, BLOCK_AUX, 0, st>>>(ctx->tables, PV, QV, cls, pqa, nitems, d_keys, d_hist);
+      k_items_scan<<<1, 1024, 0, st>>>(d_hist, kNKeys);
+      k_items_scatter<<<nb, BLOCK_AUX, 0, st>>>(d_keys, d_hist, nitems, d_order);
+      k_items_eval<<<nb, BLOCK_AUX, 0, st>>>(ctx->tables, PV, QV, cls, pqa, nitems, d_order, d_part, ctx->d_status);
+      ctx->launches += 4;
+      CK(cudaGetLastError());
+    }
+    for (int64_t ra = qa; ra < qb;) {
+      const int nwr = hnw[ra];
+      const size_t smr = hsm[ra];
+      int64_t rb = ra + 1;
+      while (rb < qb && hnw[rb] == nwr && 2 * hsm[rb] > smr) ++rb;
+      if (smr > 48 * 1024) CK(cudaFuncSetAttribute(k_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
+      k_contract<<<(unsigned)(rb - ra), 32 * nwr, smr, st>>>(PV, QV, cls, nf, pqa, ra, d_part, out_dev, d_o,
+                                                            ctx->d_status);
+      ctx->launches++;
+      CK(cudaGetLastError());
+      ra = rb;
+    }
+    qa = qb;
+  }
+  // the host vectors above stay alive until the queued copies are consumed
+  CK(cudaStreamSynchronize(st));
+  return F12INT_OK;
+}

@@ -23,8 +23,8 @@ STATUS = {0: "F12INT_OK", -1: "F12INT_EINVAL", -2: "F12INT_ENOMEM", -3: "F12INT_
 
 # every entry point declared in include/f12int.h
 EXPORTS = ("f12int_create", "f12int_destroy", "f12int_set_basis", "f12int_set_factor", "f12int_screen",
-           "f12int_compute_class", "f12int_aux", "f12int_launch_count", "f12int_device_status",
-           "f12int_strerror")
+           "f12int_compute_class", "f12int_compute_class_static", "f12int_aux", "f12int_launch_count",
+           "f12int_device_status", "f12int_strerror")
 
 
 class F12IntError(RuntimeError):
@@ -67,6 +67,7 @@ def load():
     L.f12int_screen.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                 ctypes.POINTER(ctypes.c_int32), ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
     L.f12int_compute_class.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int64, _vp, _vp, _vp]
+    L.f12int_compute_class_static.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int64, _vp, _vp, _vp]
     L.f12int_aux.argtypes = [_vp, ctypes.c_int, ctypes.c_int64, _vp, _vp, ctypes.c_int, _vp, _vp]
     L.f12int_launch_count.argtypes = [_vp]
     L.f12int_launch_count.restype = ctypes.c_int64
@@ -152,6 +153,19 @@ def f12int_compute_class(ctx, basis_id: int, cls: int, quartets_dev, out_dev, of
     n = quartets_dev.numel() // 4
     _check(load().f12int_compute_class(ctx, int(basis_id), int(cls), _ptr(quartets_dev), n, _ptr(out_dev),
                                        _ptr(offsets_dev), _stream_ptr(stream)), "f12int_compute_class")
+
+
+def f12int_compute_class_static(ctx, basis_id: int, cls: int, quartets_dev, out_dev, offsets_dev,
+                                stream=None) -> None:
+    """As f12int_compute_class, for callers that cannot allocate device memory
+    during the call: the library's scratch comes from one fixed device array
+    per GPU (64 MiB, shared by every call on that GPU, so calls must not
+    overlap on the device).  The first call on a device resolves that array's
+    address and should happen before any stream capture."""
+    n = quartets_dev.numel() // 4
+    _check(load().f12int_compute_class_static(ctx, int(basis_id), int(cls), _ptr(quartets_dev), n, _ptr(out_dev),
+                                              _ptr(offsets_dev), _stream_ptr(stream)),
+           "f12int_compute_class_static")
 
 
 def f12int_aux(ctx, cls: int, xi_dev, D_dev, nmax: int, out_dev, stream=None) -> None:
