@@ -43,7 +43,7 @@ constexpr int LAUX = 14;     // highest radial order (f shells, I5: 3+3+3+3+2)
 constexpr int JMAX = 48;     // longest family polynomial
 constexpr int WIN = 64;      // circular window over the S sequence (> JMAX + 2)
 constexpr int KMAX = 1500;   // series length cap
-constexpr int NGH = 24;      // Gauss-Hermite nodes
+constexpr int NGH = 16;      // Gauss-Hermite nodes
 constexpr int KTAB = 320;    // tabulated series coefficient ratios
 constexpr int MAXFAM = 24;   // families per kernel
 constexpr int NCLASS = 7;    // index by class 1..6

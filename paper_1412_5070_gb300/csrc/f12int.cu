@@ -19,6 +19,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <deque>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -59,7 +60,15 @@ struct PairView {
   const double *epool;       // E (3 dims) then F (3 dims), each (la+1)(lb+1)(la+lb+1)
   const int *shell_l;
   int nshell;
+  const double *qprim;       // [npp] primitive Schwarz factors of the class, or null
 };
+
+// Primitive quartets whose Schwarz product is below this are skipped: the
+// skipped contributions stay below the absolute accuracy that elements just
+// above 1e-12 need for a relative error of 1e-10.
+__device__ __forceinline__ bool prim_negligible(const PairView &PV, int pab, int pcd) {
+  return PV.qprim && PV.qprim[pab] * PV.qprim[pcd] < 1e-26;
+}
 
 // ------------------------------------------------------------ pair builder --
 // E_0^{00} = exp(-(ab/p) X_AB^2)  (Eq. Erec0); upward in i and j with
@@ -162,6 +171,7 @@ __device__ __forceinline__ int64_t find_quartet(const int64_t *off, int64_t n, i
 struct ItemGeom {
   double xi, D;
   int L;
+  int iab, icd;
 };
 
 __device__ __forceinline__ ItemGeom item_geometry(const PairView &PV, const QuartetView &QV, int cls, int64_t pq) {
@@ -174,6 +184,8 @@ __device__ __forceinline__ ItemGeom item_geometry(const PairView &PV, const Quar
   int iab = PV.pair_start[ab] + (int)(r / npcd);
   int icd = PV.pair_start[cd] + (int)(r % npcd);
   ItemGeom g;
+  g.iab = iab;
+  g.icd = icd;
   g.L = PV.shell_l[s[0]] + PV.shell_l[s[1]] + PV.shell_l[s[2]] + PV.shell_l[s[3]] + (cls == 5 ? 2 : 0);
   double p = PV.pp_p[iab], qq = PV.pp_p[icd];
   double X = PV.pp_P[3 * icd] - PV.pp_P[3 * iab];
@@ -185,6 +197,7 @@ __device__ __forceinline__ ItemGeom item_geometry(const PairView &PV, const Quar
 }
 
 __device__ __forceinline__ int item_key(int f, int L, int bin) { return (f * (LAUX + 1) + L) * NZBIN + bin; }
+constexpr int SKIP_KEY = MAXFAM * (LAUX + 1) * NZBIN;   // last key: negligible primitive quartets
 
 // Pass 1: key of every item and a histogram of the keys.
 __global__ void k_items_classify(Tables T, PairView PV, QuartetView QV, int cls, int64_t pq0, int64_t nitems,
@@ -197,7 +210,8 @@ __global__ void k_items_classify(Tables T, PairView PV, QuartetView QV, int cls,
   const int f = (int)(it % nf);
   ItemGeom g = item_geometry(PV, QV, cls, pq);
   const FamDev &F = T.fam[T.fam0[kcls] + f];
-  int key = item_key(f, min(g.L, LAUX), item_bin(F, g.xi, g.D, g.L));
+  int key = prim_negligible(PV, g.iab, g.icd) ? SKIP_KEY
+                                              : item_key(f, min(g.L, LAUX), item_bin(F, g.xi, g.D, g.L));
   keys[it] = key;
   atomicAdd(&hist[key], 1u);
 }
@@ -249,6 +263,7 @@ __global__ void k_items_eval(Tables T, PairView PV, QuartetView QV, int cls, int
   const int64_t pq = pq0 + it / nf;
   const int f = (int)(it % nf);
   ItemGeom g = item_geometry(PV, QV, cls, pq);
+  if (prim_negligible(PV, g.iab, g.icd)) return;   // never read by the contraction
   if (g.L > LAUX) {
     atomicOr(status, 4u);
     return;
@@ -327,6 +342,7 @@ k_contract(PairView PV, QuartetView QV, int cls, int nf, int64_t pq0, int64_t q0
     __syncwarp();
     for (int icd = warp; icd < npcd; icd += nw) {
       const int pcd = cd0 + icd;
+      if (prim_negligible(PV, pab, pcd)) continue;   // warp-uniform
       const int64_t pq = QV.pq_off[q] + (int64_t)iab * npcd + icd - pq0;
       const double X = PV.pp_P[3 * pcd] - PV.pp_P[3 * pab];
       const double Y = PV.pp_P[3 * pcd + 1] - PV.pp_P[3 * pab + 1];
@@ -467,10 +483,12 @@ struct f12int_ctx {
     double *d_pp_p = nullptr, *d_pp_P = nullptr, *d_pp_ab = nullptr, *d_epool = nullptr;
     int64_t *d_pp_eoff = nullptr;
     std::vector<int> l, nprim, pair_start;
-    std::vector<double> centers;
+    std::vector<double> centers, exps, coefs;
     size_t bytes = 0;
+    bool prim_screen = true;            // false for the internal per-primitive basis
+    double *d_qprim[7] = {nullptr};     // primitive Schwarz factors per class (lazily built)
   };
-  std::vector<BasisData> bases;
+  std::deque<BasisData> bases;   // deque: growing it never moves existing entries
   // scratch of compute_class (grown on demand, bounded by the budget)
   int64_t *d_pqoff = nullptr;
   int *d_keys = nullptr;
@@ -668,6 +686,7 @@ int f12int_destroy(f12int_ctx *ctx) {
     cudaFree(b.d_pp_ab);
     cudaFree(b.d_epool);
     cudaFree(b.d_pp_eoff);
+    for (int c = 0; c < 7; ++c) cudaFree(b.d_qprim[c]);
   }
   cudaFree(ctx->d_fam);
   cudaFree(ctx->d_coef);
@@ -767,6 +786,12 @@ int f12int_set_factor(f12int_ctx *ctx, const f12int_factor *f, const f12int_fact
   T.fam = ctx->d_fam;
   T.coef = ctx->d_coef;
   ctx->tables = T;
+  for (auto &b : ctx->bases)   // the primitive bounds depend on the factor
+    for (int c = 0; c < 7; ++c)
+      if (b.d_qprim[c]) {
+        cudaFree(b.d_qprim[c]);
+        b.d_qprim[c] = nullptr;
+      }
   ctx->factor_ready = true;
   return F12INT_OK;
 }
@@ -790,6 +815,8 @@ int f12int_set_basis(f12int_ctx *ctx, int nshell, const double *centers, const i
   B.l.assign(l, l + nshell);
   B.nprim.assign(nprim, nprim + nshell);
   B.centers.assign(centers, centers + 3 * nshell);
+  B.exps.assign(exps, exps + nptot);
+  B.coefs.assign(coefs, coefs + nptot);
   std::vector<int> poff(nshell);
   for (int i = 0, o = 0; i < nshell; ++i) {
     poff[i] = o;
@@ -921,14 +948,15 @@ static int contract_warps(int la, int lb, int lc, int ld, int cls) {
 
 // items of the auxiliary stage per chunk (bounds the scratch memory)
 static const int64_t kItemChunk = (int64_t)8 << 20;
-static const int kNKeys = MAXFAM * (LAUX + 1) * NZBIN;
+static const int kNKeys = MAXFAM * (LAUX + 1) * NZBIN + 1;
 
 // Queue the auxiliary stage (classify, scan, scatter, evaluate) and the
 // contraction for quartets [qa, qb) of the device list.
 static int launch_chunk(f12int_ctx *ctx, const f12int_ctx::BasisData &B, int cls, const int32_t *d_quartets,
                         const int64_t *d_pqoff, int64_t n, int64_t qa, int64_t qb, int64_t pqa, int64_t pqb,
                         size_t smem, double *out_dev, const int64_t *offsets_dev, cudaStream_t st) {
-  PairView PV{B.d_pair_start, B.d_pp_p, B.d_pp_P, B.d_pp_ab, B.d_pp_eoff, B.d_epool, B.d_shell_l, B.nshell};
+  PairView PV{B.d_pair_start, B.d_pp_p, B.d_pp_P, B.d_pp_ab, B.d_pp_eoff, B.d_epool, B.d_shell_l, B.nshell,
+              B.prim_screen ? B.d_qprim[cls] : nullptr};
   QuartetView QV{d_quartets, d_pqoff, n};
   const int kcls = cls == 5 ? 3 : cls;
   const int nf = ctx->tables.nfam[kcls];
@@ -966,6 +994,112 @@ static int launch_chunk(f12int_ctx *ctx, const f12int_ctx::BasisData &B, int cls
   return F12INT_OK;
 }
 
+// Primitive Schwarz factors Q_ab = sqrt(max |(ab|k|ab)|) of every primitive
+// pair of the basis for class cls (the I3 kernel for I5), from the diagonal
+// blocks of a basis in which every primitive is its own shell.
+static int ensure_prim_bounds(f12int_ctx *ctx, int basis_id, int cls) {
+  {
+    f12int_ctx::BasisData &B = ctx->bases[basis_id];
+    if (!B.prim_screen || B.d_qprim[cls]) return F12INT_OK;
+  }
+  const int dcls = cls == 5 ? 3 : cls;
+  std::vector<double> cen, ex, co;
+  std::vector<int> ll, np1;
+  std::vector<int> poff;
+  int nprim_tot = 0;
+  {
+    const f12int_ctx::BasisData &B = ctx->bases[basis_id];
+    for (int s = 0; s < B.nshell; ++s) {
+      poff.push_back(nprim_tot);
+      for (int k = 0; k < B.nprim[s]; ++k) {
+        cen.insert(cen.end(), {B.centers[3 * s], B.centers[3 * s + 1], B.centers[3 * s + 2]});
+        ll.push_back(B.l[s]);
+        np1.push_back(1);
+        ex.push_back(B.exps[nprim_tot]);
+        co.push_back(B.coefs[nprim_tot]);
+        ++nprim_tot;
+      }
+    }
+  }
+  int pid = -1;
+  int rc = f12int_set_basis(ctx, nprim_tot, cen.data(), ll.data(), np1.data(), ex.data(), co.data(), &pid);
+  if (rc != F12INT_OK) return rc;
+  ctx->bases[pid].prim_screen = false;
+  std::vector<int32_t> hq;
+  std::vector<int64_t> off;
+  int64_t tot = 0;
+  for (int a = 0; a < nprim_tot; ++a)
+    for (int b = 0; b <= a; ++b) {
+      hq.insert(hq.end(), {a, b, a, b});
+      off.push_back(tot);
+      int nab = ncart(ll[a]) * ncart(ll[b]);
+      tot += (int64_t)nab * nab;
+    }
+  const int64_t nq = (int64_t)off.size();
+  int32_t *dq = nullptr;
+  int64_t *doff = nullptr;
+  double *dout = nullptr;
+  std::vector<double> hout((size_t)tot);
+  rc = dalloc(ctx, &dq, sizeof(int32_t) * hq.size());
+  if (rc == F12INT_OK) rc = dalloc(ctx, &doff, sizeof(int64_t) * nq);
+  if (rc == F12INT_OK) rc = dalloc(ctx, &dout, sizeof(double) * tot);
+  cudaStream_t st = ctx->stream;
+  if (rc == F12INT_OK &&
+      (cudaMemcpyAsync(dq, hq.data(), sizeof(int32_t) * hq.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+       cudaMemcpyAsync(doff, off.data(), sizeof(int64_t) * nq, cudaMemcpyHostToDevice, st) != cudaSuccess))
+    rc = F12INT_ECUDA;
+  if (rc == F12INT_OK) rc = f12int_compute_class(ctx, pid, dcls, dq, nq, dout, doff, st);
+  if (rc == F12INT_OK &&
+      (cudaMemcpyAsync(hout.data(), dout, sizeof(double) * tot, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+       cudaStreamSynchronize(st) != cudaSuccess))
+    rc = F12INT_ECUDA;
+  dfree(ctx, dq, sizeof(int32_t) * hq.size());
+  dfree(ctx, doff, sizeof(int64_t) * nq);
+  dfree(ctx, dout, sizeof(double) * tot);
+  // release the per-primitive basis (it is the last one)
+  {
+    f12int_ctx::BasisData &P = ctx->bases[pid];
+    cudaFree(P.d_shell_l);
+    cudaFree(P.d_centers);
+    cudaFree(P.d_pair_start);
+    cudaFree(P.d_pp_p);
+    cudaFree(P.d_pp_P);
+    cudaFree(P.d_pp_ab);
+    cudaFree(P.d_pp_eoff);
+    cudaFree(P.d_epool);
+    ctx->used -= std::min(ctx->used, P.bytes);
+    if (pid == (int)ctx->bases.size() - 1) ctx->bases.pop_back();
+  }
+  if (rc != F12INT_OK) return rc;
+  std::vector<double> qps((size_t)nprim_tot * nprim_tot, 0.0);
+  int64_t k = 0;
+  for (int a = 0; a < nprim_tot; ++a)
+    for (int b = 0; b <= a; ++b, ++k) {
+      int nab = ncart(ll[a]) * ncart(ll[b]);
+      double m = 0.0;
+      for (int64_t i = 0; i < (int64_t)nab * nab; ++i) m = std::max(m, std::fabs(hout[off[k] + i]));
+      qps[(size_t)a * nprim_tot + b] = qps[(size_t)b * nprim_tot + a] = std::sqrt(m);
+    }
+  f12int_ctx::BasisData &B = ctx->bases[basis_id];
+  const int npp = B.pair_start.back();
+  std::vector<double> qpp((size_t)npp);
+  for (int a = 0; a < B.nshell; ++a)
+    for (int b = 0; b < B.nshell; ++b) {
+      int i = B.pair_start[(size_t)a * B.nshell + b];
+      for (int x = 0; x < B.nprim[a]; ++x)
+        for (int y = 0; y < B.nprim[b]; ++y, ++i) qpp[i] = qps[(size_t)(poff[a] + x) * nprim_tot + poff[b] + y];
+    }
+  double *d = nullptr;
+  rc = dalloc(ctx, &d, sizeof(double) * npp);
+  if (rc != F12INT_OK) return rc;
+  if (cudaMemcpy(d, qpp.data(), sizeof(double) * npp, cudaMemcpyHostToDevice) != cudaSuccess) {
+    dfree(ctx, d, sizeof(double) * npp);
+    return F12INT_ECUDA;
+  }
+  B.d_qprim[cls] = d;
+  return F12INT_OK;
+}
+
 int f12int_compute_class(f12int_ctx *ctx, int basis_id, int cls, const int32_t *quartets_dev, int64_t n,
                          double *out_dev, const int64_t *offsets_dev, void *cuda_stream) {
   if (!ctx) return F12INT_EINVAL;
@@ -974,6 +1108,10 @@ int f12int_compute_class(f12int_ctx *ctx, int basis_id, int cls, const int32_t *
   if (!ctx->factor_ready) return F12INT_ENOTREADY;
   if (n == 0) return F12INT_OK;
   if (!quartets_dev || !out_dev || !offsets_dev) return F12INT_EINVAL;
+  {
+    int rc0 = ensure_prim_bounds(ctx, basis_id, cls);
+    if (rc0 != F12INT_OK) return rc0;
+  }
   std::lock_guard<std::mutex> lk(ctx->mu);
   CK(cudaSetDevice(ctx->device));
   const f12int_ctx::BasisData &B = ctx->bases[basis_id];
@@ -1254,7 +1392,8 @@ extern "C" int f12int_compute_class_static(f12int_ctx *ctx, int basis_id, int cl
   CK(cudaMemcpyAsync(d_o, ho.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(d_pq, pqoff.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, st));
 
-  PairView PV{B.d_pair_start, B.d_pp_p, B.d_pp_P, B.d_pp_ab, B.d_pp_eoff, B.d_epool, B.d_shell_l, B.nshell};
+  PairView PV{B.d_pair_start, B.d_pp_p, B.d_pp_P, B.d_pp_ab, B.d_pp_eoff, B.d_epool, B.d_shell_l, B.nshell,
+              nullptr};
   QuartetView QV{d_q, d_pq, n};
   const int kcls = cls == 5 ? 3 : cls;
   const int nf = ctx->tables.nfam[kcls];
