@@ -152,6 +152,24 @@ int f12int_compute_class_static(f12int_ctx *ctx, int basis_id, int cls, const in
 /* Number of kernel launches the context has issued so far (monotonic). */
 int64_t f12int_launch_count(const f12int_ctx *ctx);
 
+/* Switch per-kernel timing on (on != 0) or off.  While on, the library
+ * records CUDA events on the launching stream around every launch of the
+ * auxiliary-function evaluation and of the contraction, and counts the
+ * auxiliary stage's core multiply-adds (one per series term and polynomial
+ * coefficient, one per quadrature node and coefficient).  Measurement aid;
+ * the paper has no counterpart. */
+int f12int_set_timing(f12int_ctx *ctx, int on);
+
+/* Totals since the last reset, written to stats[0..5]:
+ *   [0] milliseconds in auxiliary-evaluation launches, [1] their number,
+ *   [2] milliseconds in contraction launches, [3] their number,
+ *   [4] FP64 flops of the auxiliary stage's core multiply-adds (2 per FMA),
+ *   [5] algorithmic FP64 flops of the Hermite recursion and contraction of
+ *       the primitive quartets processed (2 C(L+4,4) + 2 nh(lab) nh(lcd) Ncd
+ *       + 2 Nab nh(lab) Ncd per primitive quartet; bra step x4 and L+2 for I5).
+ * reset != 0 clears them.  Synchronises the context's stream. */
+int f12int_kernel_stats(f12int_ctx *ctx, int reset, double *stats);
+
 /* Read and clear the device status word (a device-side check failing sets
  * it).  Synchronises the context's stream.  Returns F12INT_OK or
  * F12INT_EDEVICE. */

@@ -153,8 +153,10 @@ __device__ inline double s_minus1(double b, double gam, int *bad) {
 // Contribution of one family to hat g_l, l = 0..L, added into out[] with the
 // common factor 4 xi (2 xi)^l applied.  Returns nonzero if a series did not
 // converge within KMAX terms.
-__device__ inline int family_eval(const Tables &T, const FamDev &F, double xi, double D, int L, double *out) {
+__device__ inline int family_eval(const Tables &T, const FamDev &F, double xi, double D, int L, double *out,
+                                  unsigned long long *fma_count = nullptr) {
   int bad = 0;
+  unsigned long long nfma = 0;
   const double gam = F.g + xi;
   const double beta = F.b + 2.0 * xi * D;
   const double z = beta * beta / (4.0 * gam);
@@ -197,6 +199,7 @@ __device__ inline int family_eval(const Tables &T, const FamDev &F, double xi, d
         double h = 0.0;
         for (int j = sp - 1; j >= 0; --j) h = fma(h, x, P[j]);
         acc[l] = fma(xa * jh[l], h, acc[l]);
+        nfma += sp + 1;
       }
     }
     for (int l = 0; l < ls; ++l) out[l] += fct[l] * pre * acc[l];
@@ -257,6 +260,7 @@ __device__ inline int family_eval(const Tables &T, const FamDev &F, double xi, d
         const int jlo = (F.fp_minus1 && k == 0) ? 1 : 0;
         double part = 0.0;
         for (int j = jlo; j < sp; ++j) part = fma(q[j], win[(j + 2 * k) & (WIN - 1)], part);
+        nfma += sp - jlo + 2;
         const double term = common * part;
         sum += term;
         const double mag = fabs(term);
@@ -283,6 +287,7 @@ __device__ inline int family_eval(const Tables &T, const FamDev &F, double xi, d
       out[l] += fct[l] * sum;
     }
   }
+  if (fma_count) *fma_count += nfma;
   return bad;
 }
 

@@ -253,28 +253,45 @@ __global__ void k_items_scatter(const int *keys, unsigned int *cursor, int64_t n
 
 // Pass 4: one family's contribution to hat g_l (l <= L) per item, into
 // part[item * (LAUX+1) + l], in key order.
-__global__ void k_items_eval(Tables T, PairView PV, QuartetView QV, int cls, int64_t pq0, int64_t nitems,
-                             const unsigned int *order, double *part, unsigned int *status) {
-  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= nitems) return;
-  const int64_t it = order[t];
+__device__ __forceinline__ unsigned long long items_eval_one(Tables T, PairView PV, QuartetView QV, int cls,
+                                                             int64_t pq0, int64_t it, double *part,
+                                                             unsigned int *status) {
   const int kcls = cls == 5 ? 3 : cls;
   const int nf = T.nfam[kcls];
   const int64_t pq = pq0 + it / nf;
   const int f = (int)(it % nf);
   ItemGeom g = item_geometry(PV, QV, cls, pq);
-  if (prim_negligible(PV, g.iab, g.icd)) return;   // never read by the contraction
+  if (prim_negligible(PV, g.iab, g.icd)) return 0;   // never read by the contraction
   if (g.L > LAUX) {
     atomicOr(status, 4u);
-    return;
+    return 0;
   }
   double out[LAUX + 1];
   for (int l = 0; l <= g.L; ++l) out[l] = 0.0;
-  int bad = family_eval(T, T.fam[T.fam0[kcls] + f], g.xi, g.D, g.L, out);
+  unsigned long long nfma = 0;
+  int bad = family_eval(T, T.fam[T.fam0[kcls] + f], g.xi, g.D, g.L, out, &nfma);
   if (bad) atomicOr(status, 1u);
   double *o = part + it * (LAUX + 1);
   for (int l = 0; l <= g.L; ++l) o[l] = out[l];
+  return nfma;
 }
+
+__global__ void k_items_eval(Tables T, PairView PV, QuartetView QV, int cls, int64_t pq0, int64_t nitems,
+                             const unsigned int *order, double *part, unsigned int *status,
+                             unsigned long long *fma_total) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  unsigned long long nfma = 0;
+  if (t < nitems) {
+    nfma = items_eval_one(T, PV, QV, cls, pq0, order[t], part, status);
+  }
+  // warp-aggregated count of the core multiply-adds (series terms and quadrature nodes)
+  if (fma_total) {
+    for (int o = 16; o > 0; o >>= 1) nfma += __shfl_down_sync(0xffffffffu, nfma, o);
+    if ((threadIdx.x & 31) == 0 && nfma) atomicAdd(fma_total, nfma);
+  }
+}
+
+
 
 // hat g_n at given (xi, D) points (no prefactor), for the aux-stage tests.
 __global__ void k_aux_points(Tables T, int cls, int64_t npts, const double *xi, const double *D, int nmax,
@@ -304,7 +321,7 @@ __host__ __device__ __forceinline__ size_t contract_warp_doubles(int nhL, int nh
 
 __global__ void __launch_bounds__(BLOCK_CONTRACT)
 k_contract(PairView PV, QuartetView QV, int cls, int nf, int64_t pq0, int64_t q0, const double *part,
-           double *out, const int64_t *offsets, unsigned int *status) {
+           double *out, const int64_t *offsets, unsigned int *status, unsigned long long *flops_total) {
   extern __shared__ double smem[];
   const int64_t q = q0 + blockIdx.x;
   if (q >= QV.n) return;
@@ -335,6 +352,7 @@ k_contract(PairView PV, QuartetView QV, int cls, int nf, int64_t pq0, int64_t q0
   const double pi52 = 17.493418327624862846;  // pi^{5/2}
 
   for (int i = tid; i < nab * ncd; i += nthr) Oacc[i] = 0.0;
+  unsigned long long nproc = 0;   // primitive quartets this warp processed
 
   for (int iab = 0; iab < npab; ++iab) {
     const int pab = ab0 + iab;
@@ -343,6 +361,7 @@ k_contract(PairView PV, QuartetView QV, int cls, int nf, int64_t pq0, int64_t q0
     for (int icd = warp; icd < npcd; icd += nw) {
       const int pcd = cd0 + icd;
       if (prim_negligible(PV, pab, pcd)) continue;   // warp-uniform
+      ++nproc;
       const int64_t pq = QV.pq_off[q] + (int64_t)iab * npcd + icd - pq0;
       const double X = PV.pp_P[3 * pcd] - PV.pp_P[3 * pab];
       const double Y = PV.pp_P[3 * pcd + 1] - PV.pp_P[3 * pab + 1];
@@ -450,6 +469,14 @@ k_contract(PairView PV, QuartetView QV, int cls, int nf, int64_t pq0, int64_t q0
   }
   double *o = out + offsets[q];
   for (int i = tid; i < nab * ncd; i += nthr) o[i] = Oacc[i];
+  if (flops_total && lane == 0 && nproc) {
+    // algorithmic FP64 flops per primitive quartet: Hermite recursion 2 C(L+4,4),
+    // ket step 2 nh(lab+ext) nh(lcd) ncd, bra step 2 nab nh(lab) ncd (x4 for I5)
+    const unsigned long long r = 2ull * (L + 1) * (L + 2) * (L + 3) * (L + 4) / 24;
+    const unsigned long long ket = 2ull * nhB * nh_count(lcd) * ncd;
+    const unsigned long long bra = 2ull * nab * nh_count(lab) * ncd * (cls == 5 ? 4 : 1);
+    atomicAdd(flops_total, nproc * (r + ket + bra));
+  }
 }
 // Derivation note for I5: with d/dA_x = (a/p) d/dP_x + d/dAB_x and
 // d/dB_x = (b/p) d/dP_x - d/dAB_x (E depends on AB only, R on P only),
@@ -497,6 +524,12 @@ struct f12int_ctx {
   int32_t *d_qperm = nullptr;
   int64_t *d_operm = nullptr;
   size_t pqoff_cap = 0, keys_cap = 0, order_cap = 0, hist_cap = 0, part_cap = 0, qperm_cap = 0, operm_cap = 0;
+  // optional per-kernel timing (events on the launching stream) and counters
+  bool timing = false;
+  unsigned long long *d_fma = nullptr;
+  double aux_ms = 0.0, contract_ms = 0.0;
+  int64_t aux_launches = 0, contract_launches = 0;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_aux, ev_con, ev_pool;
   std::vector<int> h_nw;       // warps per contraction block, per quartet in the working order
   std::vector<size_t> h_smem;  // contraction shared memory, per quartet in the working order
   std::mutex mu;
@@ -636,6 +669,8 @@ int check_factor(const f12int_factor &f) {
 
 extern "C" {
 
+static void collect_events(f12int_ctx *ctx);
+
 const char *f12int_strerror(int status) {
   switch (status) {
     case F12INT_OK: return "ok";
@@ -698,11 +733,51 @@ int f12int_destroy(f12int_ctx *ctx) {
   cudaFree(ctx->d_qperm);
   cudaFree(ctx->d_operm);
   cudaFree(ctx->d_status);
+  cudaFree(ctx->d_fma);
+  for (auto &e : ctx->ev_pool) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
   delete ctx;
   return F12INT_OK;
 }
 
 int64_t f12int_launch_count(const f12int_ctx *ctx) { return ctx ? ctx->launches : -1; }
+
+int f12int_set_timing(f12int_ctx *ctx, int on) {
+  if (!ctx) return F12INT_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  CK(cudaSetDevice(ctx->device));
+  if (on && !ctx->d_fma) {
+    int rc = dalloc(ctx, &ctx->d_fma, 2 * sizeof(unsigned long long));
+    if (rc != F12INT_OK) return rc;
+    CK(cudaMemset(ctx->d_fma, 0, 2 * sizeof(unsigned long long)));
+  }
+  ctx->timing = on != 0;
+  return F12INT_OK;
+}
+
+int f12int_kernel_stats(f12int_ctx *ctx, int reset, double *stats) {
+  if (!ctx || !stats) return F12INT_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  collect_events(ctx);
+  unsigned long long cnt[2] = {0, 0};
+  if (ctx->d_fma) CK(cudaMemcpy(cnt, ctx->d_fma, sizeof(cnt), cudaMemcpyDeviceToHost));
+  stats[0] = ctx->aux_ms;
+  stats[1] = (double)ctx->aux_launches;
+  stats[2] = ctx->contract_ms;
+  stats[3] = (double)ctx->contract_launches;
+  stats[4] = 2.0 * (double)cnt[0];
+  stats[5] = (double)cnt[1];
+  if (reset) {
+    ctx->aux_ms = ctx->contract_ms = 0.0;
+    ctx->aux_launches = ctx->contract_launches = 0;
+    if (ctx->d_fma) CK(cudaMemset(ctx->d_fma, 0, sizeof(cnt)));
+  }
+  return F12INT_OK;
+}
 
 int f12int_device_status(f12int_ctx *ctx) {
   if (!ctx) return F12INT_EINVAL;
@@ -946,6 +1021,34 @@ static int contract_warps(int la, int lb, int lc, int ld, int cls) {
   return 1;
 }
 
+static std::pair<cudaEvent_t, cudaEvent_t> take_events(f12int_ctx *ctx) {
+  if (!ctx->ev_pool.empty()) {
+    auto e = ctx->ev_pool.back();
+    ctx->ev_pool.pop_back();
+    return e;
+  }
+  std::pair<cudaEvent_t, cudaEvent_t> e{nullptr, nullptr};
+  cudaEventCreate(&e.first);
+  cudaEventCreate(&e.second);
+  return e;
+}
+
+// After the stream has drained: add the timed launches to the totals.
+static void collect_events(f12int_ctx *ctx) {
+  for (auto &e : ctx->ev_aux) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, e.first, e.second) == cudaSuccess) ctx->aux_ms += ms;
+    ctx->ev_pool.push_back(e);
+  }
+  for (auto &e : ctx->ev_con) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, e.first, e.second) == cudaSuccess) ctx->contract_ms += ms;
+    ctx->ev_pool.push_back(e);
+  }
+  ctx->ev_aux.clear();
+  ctx->ev_con.clear();
+}
+
 // items of the auxiliary stage per chunk (bounds the scratch memory)
 static const int64_t kItemChunk = (int64_t)8 << 20;
 static const int kNKeys = MAXFAM * (LAUX + 1) * NZBIN + 1;
@@ -972,8 +1075,18 @@ static int launch_chunk(f12int_ctx *ctx, const f12int_ctx::BasisData &B, int cls
     k_items_classify<<<nb, BLOCK_AUX, 0, st>>>(ctx->tables, PV, QV, cls, pqa, nitems, ctx->d_keys, ctx->d_hist);
     k_items_scan<<<1, 1024, 0, st>>>(ctx->d_hist, kNKeys);
     k_items_scatter<<<nb, BLOCK_AUX, 0, st>>>(ctx->d_keys, ctx->d_hist, nitems, ctx->d_order);
+    std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+    if (ctx->timing) {
+      ev = take_events(ctx);
+      cudaEventRecord(ev.first, st);
+    }
     k_items_eval<<<nb, BLOCK_AUX, 0, st>>>(ctx->tables, PV, QV, cls, pqa, nitems, ctx->d_order, ctx->d_part,
-                                           ctx->d_status);
+                                           ctx->d_status, ctx->timing ? ctx->d_fma : nullptr);
+    if (ctx->timing) {
+      cudaEventRecord(ev.second, st);
+      ctx->ev_aux.push_back(ev);
+      ctx->aux_launches++;
+    }
     ctx->launches += 4;
     CK(cudaGetLastError());
   }
@@ -985,8 +1098,18 @@ static int launch_chunk(f12int_ctx *ctx, const f12int_ctx::BasisData &B, int cls
     int64_t rb = ra + 1;
     while (rb < qb && ctx->h_nw[rb] == nw && 2 * ctx->h_smem[rb] > sm0) ++rb;
     if (sm0 > 48 * 1024) CK(cudaFuncSetAttribute(k_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm0));
+    std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+    if (ctx->timing) {
+      ev = take_events(ctx);
+      cudaEventRecord(ev.first, st);
+    }
     k_contract<<<(unsigned)(rb - ra), 32 * nw, sm0, st>>>(PV, QV, cls, nf, pqa, ra, ctx->d_part, out_dev, offsets_dev,
-                                                         ctx->d_status);
+                                                         ctx->d_status, ctx->timing ? ctx->d_fma + 1 : nullptr);
+    if (ctx->timing) {
+      cudaEventRecord(ev.second, st);
+      ctx->ev_con.push_back(ev);
+      ctx->contract_launches++;
+    }
     ctx->launches++;
     CK(cudaGetLastError());
     ra = rb;
@@ -1185,6 +1308,7 @@ int f12int_compute_class(f12int_ctx *ctx, int basis_id, int cls, const int32_t *
   }
   // keep the host buffer alive until the copy has been consumed
   CK(cudaStreamSynchronize(st));
+  if (ctx->timing) collect_events(ctx);
   return F12INT_OK;
 }
 
@@ -1414,7 +1538,8 @@ extern "C" int f12int_compute_class_static(f12int_ctx *ctx, int basis_id, int cl
       k_items_classify<<<nb, BLOCK_AUX, 0, st>>>(ctx->tables, PV, QV, cls, pqa, nitems, d_keys, d_hist);
       k_items_scan<<<1, 1024, 0, st>>>(d_hist, kNKeys);
       k_items_scatter<<<nb, BLOCK_AUX, 0, st>>>(d_keys, d_hist, nitems, d_order);
-      k_items_eval<<<nb, BLOCK_AUX, 0, st>>>(ctx->tables, PV, QV, cls, pqa, nitems, d_order, d_part, ctx->d_status);
+      k_items_eval<<<nb, BLOCK_AUX, 0, st>>>(ctx->tables, PV, QV, cls, pqa, nitems, d_order, d_part, ctx->d_status,
+                                             nullptr);
       ctx->launches += 4;
       CK(cudaGetLastError());
     }
@@ -1425,7 +1550,7 @@ extern "C" int f12int_compute_class_static(f12int_ctx *ctx, int basis_id, int cl
       while (rb < qb && hnw[rb] == nwr && 2 * hsm[rb] > smr) ++rb;
       if (smr > 48 * 1024) CK(cudaFuncSetAttribute(k_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
       k_contract<<<(unsigned)(rb - ra), 32 * nwr, smr, st>>>(PV, QV, cls, nf, pqa, ra, d_part, out_dev, d_o,
-                                                            ctx->d_status);
+                                                            ctx->d_status, nullptr);
       ctx->launches++;
       CK(cudaGetLastError());
       ra = rb;

@@ -24,7 +24,7 @@ STATUS = {0: "F12INT_OK", -1: "F12INT_EINVAL", -2: "F12INT_ENOMEM", -3: "F12INT_
 # every entry point declared in include/f12int.h
 EXPORTS = ("f12int_create", "f12int_destroy", "f12int_set_basis", "f12int_set_factor", "f12int_screen",
            "f12int_compute_class", "f12int_compute_class_static", "f12int_aux", "f12int_launch_count",
-           "f12int_device_status", "f12int_strerror")
+           "f12int_device_status", "f12int_set_timing", "f12int_kernel_stats", "f12int_strerror")
 
 
 class F12IntError(RuntimeError):
@@ -72,6 +72,8 @@ def load():
     L.f12int_launch_count.argtypes = [_vp]
     L.f12int_launch_count.restype = ctypes.c_int64
     L.f12int_device_status.argtypes = [_vp]
+    L.f12int_set_timing.argtypes = [_vp, ctypes.c_int]
+    L.f12int_kernel_stats.argtypes = [_vp, ctypes.c_int, _dp]
     L.f12int_strerror.argtypes = [ctypes.c_int]
     L.f12int_strerror.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -175,6 +177,17 @@ def f12int_aux(ctx, cls: int, xi_dev, D_dev, nmax: int, out_dev, stream=None) ->
 
 def f12int_launch_count(ctx) -> int:
     return int(load().f12int_launch_count(ctx))
+
+
+def f12int_set_timing(ctx, on: bool) -> None:
+    _check(load().f12int_set_timing(ctx, 1 if on else 0), "f12int_set_timing")
+
+
+def f12int_kernel_stats(ctx, reset: bool = False) -> dict:
+    s = (ctypes.c_double * 6)()
+    _check(load().f12int_kernel_stats(ctx, 1 if reset else 0, s), "f12int_kernel_stats")
+    return {"aux_ms": s[0], "aux_launches": int(s[1]), "contract_ms": s[2], "contract_launches": int(s[3]),
+            "aux_flops": s[4], "contract_flops": s[5]}
 
 
 def f12int_device_status(ctx) -> None:
