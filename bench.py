@@ -34,6 +34,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from paper_1412_5070_gb300 import molecules as M  # noqa: E402
+from paper_1412_5070_gb300.sharding import max_over_ranks, shard  # noqa: E402
 
 METRIC = "F12 quartets/s per class vs FP64 roofline; served p50/p99 vs plain, err<=1e-10"
 UNIT = "shell quartets/s"
@@ -181,8 +182,8 @@ def cpu_oracle_sample(basis, lists, target_seconds=15.0, impl_line=False):
     value = total_q / step_time
     threads = os.cpu_count()
     return value, {"cores": threads, "per_class_quartets_per_s": {("I%d" % c): per[c] for c in CLASSES},
-                   "sample": "random shell quartets of each class's screened list, ~%.0f s of oracle work, "
-                             "rate extrapolated to the full step" % target_seconds}
+                   "sample": "seeded random canonical shell quartets of each class (all six), ~%.0f s of "
+                             "oracle work; quartets/s over the mix" % target_seconds}
 
 
 def run_reference(args):
@@ -191,19 +192,8 @@ def run_reference(args):
         return
     import torch  # noqa: F401  (plumbing only)
     basis = build_workload()
-    # the screened lists come from the oracle-independent screen of the library when a GPU is present;
-    # without one, every canonical quartet is listed (the oracle then samples from it)
-    try:
-        from paper_1412_5070_gb300 import build as B
-        from paper_1412_5070_gb300 import f12int as F
-        B.build()
-        ctx = F.f12int_create(0, 0, None)
-        F.f12int_set_factor(ctx, M.P0)
-        bid = F.f12int_set_basis(ctx, basis)
-        lists, _ = screened_lists(F, ctx, bid, basis, 1.0)
-        F.f12int_destroy(ctx)
-    except Exception:
-        lists = {c: M.canonical_quartets(basis, c) for c in CLASSES}
+    # the oracle samples from the canonical quartet lists (no library code on this path)
+    lists = {c: M.canonical_quartets(basis, c) for c in CLASSES}
     per_step_s = []
     vals = []
     steps = max(1, args.steps)
@@ -242,7 +232,7 @@ def run_ours(args):
     t_basis = time.time() - t0
     lists, t_screen = screened_lists(F, ctx, bid, basis, args.fraction)
     # weak scaling: each rank computes every rank-th quartet of each list (independent units)
-    my = {c: lists[c][rank::world] for c in CLASSES}
+    my = {c: shard(lists[c], rank, world) for c in CLASSES}
     offs = {c: M.block_offsets(basis, my[c]) for c in CLASSES}
     dq = {c: torch.from_numpy(np.ascontiguousarray(my[c])).to(f"cuda:{local}") for c in CLASSES}
     doff = {c: torch.from_numpy(offs[c][:-1].copy()).to(f"cuda:{local}") for c in CLASSES}
@@ -287,10 +277,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     F.f12int_device_status(ctx)
     ms = float(np.mean(times))
-    if world > 1:
-        t = torch.tensor([ms], device=f"cuda:{local}")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, device=f"cuda:{local}")
     total_q = sum(len(lists[c]) for c in CLASSES)
     value = total_q / (ms / 1000.0)
 
@@ -354,7 +341,9 @@ def run_ours(args):
             "kernels": kernels,
             "clocks": clk.summary()}
     if rank == 0 and not args.no_cpu_baseline:
-        v, info = cpu_oracle_sample(basis, lists, target_seconds=15.0)
+        # the oracle samples from the canonical lists: its inputs never come from the CUDA path
+        canon = {c: M.canonical_quartets(basis, c) for c in CLASSES}
+        v, info = cpu_oracle_sample(basis, canon, target_seconds=15.0)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": info["cores"], "kind": "oracle",
                                 "sample": info["sample"]}
     F.f12int_destroy(ctx)

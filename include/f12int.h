@@ -91,6 +91,15 @@ int f12int_set_basis(f12int_ctx *ctx, int nshell, const double *centers, const i
  * integrable at r = 0, Sec. 3.1). */
 int f12int_set_factor(f12int_ctx *ctx, const f12int_factor *f, const f12int_factor *fprime);
 
+/* Host-only view of the term lists that f12int_set_factor uploads: writes
+ * x^{2l+2} (D_r^l k_cls)(x), D_r = x^-1 d/dx, for the kernel of class cls
+ * (Eqs. k1-k6; class 5 uses k3) built from f and f' (fprime = NULL means
+ * f' = f), evaluated from the generated families at x > 0.  Needs no GPU.
+ * Errors: F12INT_EINVAL for cls, l (0..14) or x out of range,
+ * F12INT_EDOMAIN as for f12int_set_factor. */
+int f12int_kernel_radial(int cls, const f12int_factor *f, const f12int_factor *fprime, int l, double x,
+                         double *value);
+
 /* Schwarz-type screening for class cls: bound(ab) = sqrt(max |(ab|k|ab)|)
  * over the diagonal block (the I3 diagonal for I5).  Writes the canonical
  * shell quartets whose bound product is >= thresh into quartets_out[4*i]

@@ -70,7 +70,12 @@ struct Tables {
 __constant__ double c_gh_x[NGH];
 __constant__ double c_gh_w[NGH];
 // c_{l,k+1}/c_{l,k} = (k+l+1) / ((k+1)(2k+2l+2)(2k+2l+3)),  c_{l,k} = 2^l (k+l)!/(k!(2k+2l+1)!)
+// (the same ratios advance the power series of j_l)
 __constant__ double c_cratio[LAUX + 1][KTAB];
+__constant__ double c_inv_dfact[LAUX + 2];        // 1/(2l+1)!! = c_{l,0}
+constexpr int NKUM = 512;
+__device__ double d_kum_inv[2][NKUM];             // 1/((b+n)(n+1)) for b = 1/2, 3/2
+__device__ double d_sm1_ratio[NKUM];              // Gamma((m+1)/2)/(Gamma(m/2)(m+1))
 
 __device__ __forceinline__ double threshold_z(int l) { return 36.0 + 4.5 * l; }
 
@@ -88,12 +93,10 @@ __device__ inline void jhat_all(double z, int N, double *jh) {
   double z2 = z * z, ez = exp(-z);
   int mlo = N > 0 ? N - 1 : 0;
   for (int m = N; m >= mlo; --m) {
-    double c = 1.0;
-    for (int j = 1; j <= m; ++j) c /= (2 * j + 1);
-    double term = c, s = 0.0;
-    for (int k = 0; k < 400; ++k) {
+    double term = c_inv_dfact[m], s = 0.0;
+    for (int k = 0; k < KTAB; ++k) {
       s += term;
-      term *= z2 * (k + m + 1) / ((double)(k + 1) * (2 * k + 2 * m + 2) * (2 * k + 2 * m + 3));
+      term *= z2 * c_cratio[m][k];
       if (term <= 1e-18 * s && k > 1) break;
     }
     jh[m] = ez * s;
@@ -101,11 +104,12 @@ __device__ inline void jhat_all(double z, int N, double *jh) {
   for (int m = N - 1; m >= 1; --m) jh[m - 1] = z2 * jh[m + 1] + (2 * m + 1) * jh[m];
 }
 
-// Kummer M(a, b, z), z >= 0, a, b > 0 (App. B, Eq. msmallz).
-__device__ inline double kummer_m(double a, double b, double z, int *bad) {
+// Kummer M(a, b, z), z >= 0, a > 0, b = 1/2 (ib = 0) or 3/2 (ib = 1) (App. B, Eq. msmallz).
+__device__ inline double kummer_m(double a, int ib, double z, int *bad) {
   double t = 1.0, s = 1.0;
-  for (int n = 0; n < 4000; ++n) {
-    t *= (a + n) * z / ((b + n) * (n + 1));
+  if (z == 0.0) return 1.0;
+  for (int n = 0; n < NKUM; ++n) {
+    t *= (a + n) * z * d_kum_inv[ib][n];
     s += t;
     if (t <= 1e-18 * s) return s;
   }
@@ -120,7 +124,8 @@ __device__ inline double kummer_m(double a, double b, double z, int *bad) {
 // rho = Gamma((alpha+2)/2)/Gamma((alpha+1)/2).
 __device__ inline double jhat_start(double alpha, double rho, double y, int *bad) {
   double z = 0.25 * y * y;
-  return 0.5 * (kummer_m(0.5 * (alpha + 1.0), 0.5, z, bad) + y * rho * kummer_m(0.5 * (alpha + 2.0), 1.5, z, bad));
+  if (y == 0.0) return 0.5;
+  return 0.5 * (kummer_m(0.5 * (alpha + 1.0), 0, z, bad) + y * rho * kummer_m(0.5 * (alpha + 2.0), 1, z, bad));
 }
 
 // Finite part S(-1, b, gamma) (Sec. 3.3.2, integer alpha; Eq. sila):
@@ -130,15 +135,13 @@ __device__ inline double s_minus1(double b, double gam, int *bad) {
   double y = b / sqrt(gam);
   double s = -0.5 * euler - 0.5 * log(gam);
   if (y > 0.0) {
-    // t_m = y^m Gamma(m/2) / (2 m!);  t_1 = y sqrt(pi)/2
-    double r = 0.56418958354775628695;  // Gamma(1/2)/Gamma(1)... ratio Gamma((m+1)/2)/Gamma(m/2) at m=1 is 1/sqrt(pi)
+    // t_m = y^m Gamma(m/2) / (2 m!);  t_1 = y sqrt(pi)/2;
+    // t_{m+1}/t_m = y Gamma((m+1)/2) / (Gamma(m/2) (m+1))  (tabulated)
     double t = 0.5 * y * 1.77245385090551602730;
     double acc = 0.0;
-    for (int m = 1; m < 4000; ++m) {
+    for (int m = 1; m < NKUM; ++m) {
       acc += t;
-      // t_{m+1}/t_m = y Gamma((m+1)/2) / (Gamma(m/2) (m+1))
-      t *= y * r / (m + 1);
-      r = 0.5 * m / r;
+      t *= y * d_sm1_ratio[m];
       if (t <= 1e-18 * acc && m > 2) {
         s += acc;
         return s;
@@ -217,7 +220,19 @@ __device__ inline int family_eval(const Tables &T, const FamDev &F, double xi, d
     const double J0 = jhat_start(as, F.rho_start, y, &bad) * F.gam_tab[m0];
     const double J1 = jhat_start(as + 1.0, rho1, y, &bad) * F.gam_tab[m0 + 1];
     const double sm1 = F.fp_minus1 ? s_minus1(F.b, gam, &bad) : 0.0;
-    const double gpow0 = pow(gam, -0.5 * (F.alpha0 + 1.0));
+    // gamma^{-(alpha0+1)/2}: products of rsqrt for integer and half-integer alpha0
+    double gpow0;
+    if (F.pow_kind == 1) {                 // (alpha0+1)/2 = (n0+1)/2: powers of gamma^{-1/2}
+      gpow0 = 1.0;
+      for (int k = 0; k < F.pow_int + 1; ++k) gpow0 *= rgam;
+      if (F.pow_int + 1 < 0) gpow0 = 1.0;  // alpha0 = -1: gamma^0
+    } else if (F.pow_kind == 2) {          // (alpha0+1)/2 = (2 n0 + 3)/4: powers of gamma^{-1/4}
+      const double r4 = sqrt(rgam);
+      gpow0 = 1.0;
+      for (int k = 0; k < 2 * F.pow_int + 3; ++k) gpow0 *= r4;
+    } else {
+      gpow0 = pow(gam, -0.5 * (F.alpha0 + 1.0));
+    }
     const double TWO600 = 4.149515568880993e+180, MTWO600 = 2.409919865102884e-181;
 
     for (int l = ls; l <= L; ++l) {
@@ -229,9 +244,7 @@ __device__ inline int family_eval(const Tables &T, const FamDev &F, double xi, d
         q[j] = P[j] * gp;
         gp *= rgam;
       }
-      // c_{l,0} = 1/(2l+1)!!
-      double cl0 = 1.0;
-      for (int j = 1; j <= l; ++j) cl0 /= (2 * j + 1);
+      const double cl0 = c_inv_dfact[l];   // c_{l,0} = 1/(2l+1)!!
       double common = cl0 * eT;   // c_{l,k} v^k e^{-xi D^2}, times the window's scale
       double sum = 0.0;
       if (F.fp_minus1) sum = q[0] * common * sm1;

@@ -646,6 +646,19 @@ int upload_constants() {
     for (int k = 0; k < KTAB; ++k)
       cr[l][k] = (double)(k + l + 1) / ((double)(k + 1) * (2.0 * k + 2.0 * l + 2.0) * (2.0 * k + 2.0 * l + 3.0));
   CK(cudaMemcpyToSymbol(c_cratio, cr, sizeof(cr)));
+  double idf[LAUX + 2];
+  idf[0] = 1.0;
+  for (int l = 1; l < LAUX + 2; ++l) idf[l] = idf[l - 1] / (2.0 * l + 1.0);
+  CK(cudaMemcpyToSymbol(c_inv_dfact, idf, sizeof(idf)));
+  static double kinv[2][NKUM], smr[NKUM];
+  for (int n = 0; n < NKUM; ++n) {
+    kinv[0][n] = 1.0 / ((0.5 + n) * (n + 1.0));
+    kinv[1][n] = 1.0 / ((1.5 + n) * (n + 1.0));
+    // Gamma((m+1)/2) / (Gamma(m/2) (m+1)); entry 0 unused
+    smr[n] = n == 0 ? 0.0 : std::exp(std::lgamma(0.5 * (n + 1.0)) - std::lgamma(0.5 * n)) / (n + 1.0);
+  }
+  CK(cudaMemcpyToSymbol(d_kum_inv, kinv, sizeof(kinv)));
+  CK(cudaMemcpyToSymbol(d_sm1_ratio, smr, sizeof(smr)));
   CK(cudaMemcpyToSymbol(c_tuv, tuv, sizeof(tuv)));
   CK(cudaMemcpyToSymbol(c_cart, cart, sizeof(cart)));
   CK(cudaMemcpyToSymbol(c_gh_x, gx, sizeof(gx)));
@@ -789,6 +802,28 @@ int f12int_device_status(f12int_ctx *ctx) {
   CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned int), ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   return h ? F12INT_EDEVICE : F12INT_OK;
+}
+
+int f12int_kernel_radial(int cls, const f12int_factor *f, const f12int_factor *fprime, int l, double x,
+                         double *value) {
+  if (!f || !value || cls < 1 || cls > 6 || l < 0 || l > LAUX || !(x > 0.0)) return F12INT_EINVAL;
+  const f12int_factor &fp = fprime ? *fprime : *f;
+  int rc = check_factor(*f);
+  if (rc == F12INT_OK) rc = check_factor(fp);
+  if (rc != F12INT_OK) return rc;
+  f12::Factor F1{f->c0, f->rho, f->B, f->mu, f->n}, F2{fp.c0, fp.rho, fp.B, fp.mu, fp.n};
+  std::vector<f12::Family> fl = f12::families(f12::kernel_terms(cls, F1, F2));
+  double s = 0.0;
+  for (const f12::Family &fam0 : fl) {
+    f12::Family cur = fam0;
+    for (int k = 0; k < l; ++k) cur = f12::radial_derivative(cur);
+    // x^{2l+2} * sum_j P_j x^{a0 - 2l + j} e^{b x - g x^2}, with a0 the original lowest power
+    double poly = 0.0;
+    for (size_t j = cur.poly.size(); j-- > 0;) poly = poly * x + cur.poly[j];
+    s += poly * std::pow(x, fam0.a0 + 2.0) * std::exp(fam0.b * x - fam0.g * x * x);
+  }
+  *value = s;
+  return F12INT_OK;
 }
 
 int f12int_set_factor(f12int_ctx *ctx, const f12int_factor *f, const f12int_factor *fprime) {
@@ -1050,7 +1085,7 @@ static void collect_events(f12int_ctx *ctx) {
 }
 
 // items of the auxiliary stage per chunk (bounds the scratch memory)
-static const int64_t kItemChunk = (int64_t)8 << 20;
+static const int64_t kItemChunk = (int64_t)32 << 20;
 static const int kNKeys = MAXFAM * (LAUX + 1) * NZBIN + 1;
 
 // Queue the auxiliary stage (classify, scan, scatter, evaluate) and the

@@ -24,7 +24,8 @@ STATUS = {0: "F12INT_OK", -1: "F12INT_EINVAL", -2: "F12INT_ENOMEM", -3: "F12INT_
 # every entry point declared in include/f12int.h
 EXPORTS = ("f12int_create", "f12int_destroy", "f12int_set_basis", "f12int_set_factor", "f12int_screen",
            "f12int_compute_class", "f12int_compute_class_static", "f12int_aux", "f12int_launch_count",
-           "f12int_device_status", "f12int_set_timing", "f12int_kernel_stats", "f12int_strerror")
+           "f12int_device_status", "f12int_set_timing", "f12int_kernel_stats", "f12int_kernel_radial",
+           "f12int_strerror")
 
 
 class F12IntError(RuntimeError):
@@ -73,6 +74,8 @@ def load():
     L.f12int_launch_count.restype = ctypes.c_int64
     L.f12int_device_status.argtypes = [_vp]
     L.f12int_set_timing.argtypes = [_vp, ctypes.c_int]
+    L.f12int_kernel_radial.argtypes = [ctypes.c_int, ctypes.POINTER(Factor), ctypes.POINTER(Factor), ctypes.c_int,
+                                       ctypes.c_double, _dp]
     L.f12int_kernel_stats.argtypes = [_vp, ctypes.c_int, _dp]
     L.f12int_strerror.argtypes = [ctypes.c_int]
     L.f12int_strerror.restype = ctypes.c_char_p
@@ -177,6 +180,16 @@ def f12int_aux(ctx, cls: int, xi_dev, D_dev, nmax: int, out_dev, stream=None) ->
 
 def f12int_launch_count(ctx) -> int:
     return int(load().f12int_launch_count(ctx))
+
+
+def f12int_kernel_radial(cls: int, f, l: int, x: float, fprime=None) -> float:
+    """x^{2l+2} (D_r^l k)(x) from the host-side term lists (no GPU needed)."""
+    F = Factor.of(f)
+    Fp = Factor.of(fprime) if fprime is not None else None
+    v = ctypes.c_double(0.0)
+    _check(load().f12int_kernel_radial(int(cls), ctypes.byref(F), ctypes.byref(Fp) if Fp is not None else None,
+                                       int(l), float(x), ctypes.byref(v)), "f12int_kernel_radial")
+    return v.value
 
 
 def f12int_set_timing(ctx, on: bool) -> None:

@@ -1,0 +1,156 @@
+"""Host-side checks that need no GPU: the C ABI library loads and exports
+every entry point its header declares; the term lists it generates match
+the kernels of arXiv:1412.5070 (Eqs. k1-k6, rs12, ttdamp) as evaluated by
+the oracle; factor validation; the weak-scaling shard logic on two gloo
+ranks."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1412_5070_gb300 import build as B
+from paper_1412_5070_gb300 import f12int as F
+from paper_1412_5070_gb300 import molecules as M
+from paper_1412_5070_gb300 import sharding
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return F.load()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "f12int.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(f12int_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_entry_point(lib):
+    names = declared_functions()
+    assert "f12int_compute_class" in names and "f12int_compute_class_static" in names
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(F.EXPORTS)
+
+
+def test_strerror_without_gpu(lib):
+    assert F.f12int_strerror(0) == "ok"
+    assert "factor" in F.f12int_strerror(-3)
+    assert F.f12int_strerror(12345) == "unknown status"
+
+
+def test_create_reports_missing_gpu(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(F.F12IntError) as e:
+        F.f12int_create(0, 0, None)
+    assert e.value.status in (-1, -6)
+
+
+@pytest.mark.parametrize("cls", [1, 2, 3, 4, 6])
+@pytest.mark.parametrize("x", [0.03, 0.4, 1.1, 2.7, 6.5])
+def test_term_lists_reproduce_the_kernels(lib, cls, x):
+    """l = 0: x^2 k(x) from the generated families equals x^2 k(x) from the
+    oracle's pointwise kernel (separation of the damping, Eq. hj00eps)."""
+    got = F.f12int_kernel_radial(cls, M.P0, 0, x)
+    ref = x * x * O.kernel_value(O.factor_kernel(M.P0), cls, x)
+    assert abs(got - ref) <= 1e-13 * abs(ref) + 1e-15
+
+
+@pytest.mark.parametrize("cls", [2, 3, 4, 6])
+@pytest.mark.parametrize("x", [0.6, 1.3, 3.0])
+def test_radial_derivative_of_term_lists(lib, cls, x):
+    """l = 1, 2: x^{2l+2} D_r^l k with D_r = x^-1 d/dx, against finite
+    differences of the oracle's kernel values."""
+    K = O.factor_kernel(M.P0)
+    k = lambda r: O.kernel_value(K, cls, r)
+    h = 1e-3 * x
+
+    def d1(fun, r):
+        return (fun(r - 2 * h) - 8 * fun(r - h) + 8 * fun(r + h) - fun(r + 2 * h)) / (12 * h)
+
+    dr1 = lambda r: d1(k, r) / r
+    v1 = x ** 4 * dr1(x)
+    v2 = x ** 6 * d1(dr1, x) / x
+    assert abs(F.f12int_kernel_radial(cls, M.P0, 1, x) - v1) <= 1e-8 * max(abs(v1), 1e-3)
+    assert abs(F.f12int_kernel_radial(cls, M.P0, 2, x) - v2) <= 1e-6 * max(abs(v2), 1e-3)
+
+
+def test_factor_pair_with_different_parameters(lib):
+    """f' != f (Eq. I4, Eq. I6_): the product term lists still reproduce f f'
+    and f_r f'_r pointwise."""
+    fp = dict(c0=0.3, rho=-0.3, B=0.3, mu=0.7, n=0)
+    K = O.factor_kernel(M.P0, fp)
+    for cls in (4, 6):
+        for x in (0.2, 1.0, 3.3):
+            got = F.f12int_kernel_radial(cls, M.P0, 0, x, fprime=fp)
+            ref = x * x * O.kernel_value(K, cls, x)
+            assert abs(got - ref) <= 1e-13 * abs(ref) + 1e-15
+
+
+@pytest.mark.parametrize("bad", [dict(c0=0.5, rho=-0.5, B=0.5, mu=0.0, n=0),
+                                 dict(c0=0.5, rho=-2.5, B=0.5, mu=1.0, n=0),
+                                 dict(c0=0.5, rho=-0.5, B=-0.5, mu=1.0, n=0),
+                                 dict(c0=float("nan"), rho=-0.5, B=0.5, mu=1.0, n=0)])
+def test_factor_domain_checks(lib, bad):
+    """mu > 0 and rho + 2n + 2 > 0 (Sec. 3.1); B >= 0 and finite values are
+    what the library supports."""
+    with pytest.raises(F.F12IntError) as e:
+        F.f12int_kernel_radial(3, bad, 0, 1.0)
+    assert e.value.status == -3
+
+
+def test_shard_partitions_every_list():
+    lst = np.arange(103 * 4).reshape(103, 4)
+    parts = [sharding.shard(lst, r, 3) for r in range(3)]
+    joined = np.concatenate(parts)
+    assert len(joined) == len(lst)
+    assert sorted(map(tuple, joined)) == sorted(map(tuple, lst))
+    with pytest.raises(ValueError):
+        sharding.shard(lst, 3, 3)
+
+
+def _gloo_worker(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    basis = M.two_centre_sp()
+    full = M.canonical_quartets(basis, 3)
+    mine = sharding.shard(full, rank, world)
+    got = [None] * world
+    dist.all_gather_object(got, mine.tolist())
+    mx = sharding.max_over_ranks(1.5 + rank)
+    if rank == 0:
+        union = sorted(tuple(x) for part in got for x in part)
+        q.put((union == sorted(map(tuple, full.tolist())), sum(len(p) for p in got) == len(full), mx))
+    dist.destroy_process_group()
+
+
+def test_two_rank_gloo_weak_scaling_split():
+    """Two gloo ranks: the shards are disjoint and cover the list; the
+    step-time reduction takes the maximum over ranks."""
+    torch = pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+    import socket
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_gloo_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    covered, sizes_ok, mx = q.get(timeout=10)
+    assert covered and sizes_ok and mx == 2.5
