@@ -235,30 +235,42 @@ __device__ inline int family_eval(const Tables &T, const FamDev &F, double xi, d
     }
     const double TWO600 = 4.149515568880993e+180, MTWO600 = 2.409919865102884e-181;
 
+    // all orders l = ls..L advance together over the series index k: the S
+    // window is extended once per k, each order adds one FMA per coefficient
+    constexpr int QMAX = 512;
+    double qv[QMAX];
+    int qoff[LAUX + 2];
+    double common[LAUX + 1], sum[LAUX + 1];
+    int tot = 0;
     for (int l = ls; l <= L; ++l) {
-      const double *P = T.coef + F.coff[l];
-      const int sp = F.span[l];
-      double q[JMAX];
-      double gp = gpow0;
-      for (int j = 0; j < sp; ++j) {
-        q[j] = P[j] * gp;
-        gp *= rgam;
+      qoff[l] = tot;
+      tot += F.span[l];
+    }
+    qoff[L + 1] = tot;
+    if (tot > QMAX) {
+      bad = 1;
+    } else {
+      for (int l = ls; l <= L; ++l) {
+        const double *P = T.coef + F.coff[l];
+        double gp = gpow0;
+        for (int j = 0; j < F.span[l]; ++j) {
+          qv[qoff[l] + j] = P[j] * gp;
+          gp *= rgam;
+        }
+        common[l] = c_inv_dfact[l] * eT;   // c_{l,0} e^{-xi D^2}
+        sum[l] = F.fp_minus1 ? qv[qoff[l]] * common[l] * sm1 : 0.0;
       }
-      const double cl0 = c_inv_dfact[l];   // c_{l,0} = 1/(2l+1)!!
-      double common = cl0 * eT;   // c_{l,k} v^k e^{-xi D^2}, times the window's scale
-      double sum = 0.0;
-      if (F.fp_minus1) sum = q[0] * common * sm1;
+      const int spmax = F.span[L];
       double win[WIN];
       win[m0 & (WIN - 1)] = J0;
       win[(m0 + 1) & (WIN - 1)] = J1;
       int mfill = m0 + 2;
-      double abs_total = 0.0;
+      double abs_lo = 0.0, abs_hi = 0.0;
       int small = 0;
-      // past the largest term: the terms behave like z^k/k!
-      const int kmin = (int)(0.5 * v) + 2;
+      const int kmin = (int)(0.5 * v) + 2;   // past the largest term (terms ~ z^k/k!)
       int k;
       for (k = 0; k < KMAX; ++k) {
-        const int need = sp - 1 + 2 * k;
+        const int need = spmax - 1 + 2 * k;
         while (mfill <= need) {
           const double a = F.alpha0 + (mfill - 1);
           double jn = 0.5 * fma(y, win[(mfill - 1) & (WIN - 1)], a * win[(mfill - 2) & (WIN - 1)]);
@@ -267,37 +279,32 @@ __device__ inline int family_eval(const Tables &T, const FamDev &F, double xi, d
           if (fabs(jn) > TWO600) {   // keep the window in range; exact power-of-two rescale
             for (int r = mfill - WIN; r < mfill; ++r)
               if (r >= 0) win[r & (WIN - 1)] *= MTWO600;
-            common *= TWO600;
+            for (int l = ls; l <= L; ++l) common[l] *= TWO600;
           }
         }
         const int jlo = (F.fp_minus1 && k == 0) ? 1 : 0;
-        double part = 0.0;
-        for (int j = jlo; j < sp; ++j) part = fma(q[j], win[(j + 2 * k) & (WIN - 1)], part);
-        nfma += sp - jlo + 2;
-        const double term = common * part;
-        sum += term;
-        const double mag = fabs(term);
-        abs_total += mag;
-        small = (mag <= 1e-17 * abs_total) ? small + 1 : 0;
-        if (small >= 2 && k >= kmin) break;
-        // c_{l,k+1}/c_{l,k} v
-        const double cr = k < KTAB ? c_cratio[l][k]
-                                   : (double)(k + l + 1) / ((double)(k + 1) * (2.0 * k + 2.0 * l + 2.0) * (2.0 * k + 2.0 * l + 3.0));
-        common *= v * cr;
-        if (common != 0.0 && fabs(common) < MTWO600) {
-          // move scale from the coefficient back into the window when it underflows
-          bool ok = true;
-          for (int r = mfill - WIN; r < mfill; ++r)
-            if (r >= 0 && fabs(win[r & (WIN - 1)]) > MTWO600 * 1e100) ok = false;
-          if (ok) {
-            for (int r = mfill - WIN; r < mfill; ++r)
-              if (r >= 0) win[r & (WIN - 1)] *= TWO600;
-            common *= MTWO600;
-          }
+        double mag_lo = 0.0, mag_hi = 0.0;
+        for (int l = ls; l <= L; ++l) {
+          const double *q = qv + qoff[l];
+          const int sp = F.span[l];
+          double part = 0.0;
+          for (int j = jlo; j < sp; ++j) part = fma(q[j], win[(j + 2 * k) & (WIN - 1)], part);
+          const double term = common[l] * part;
+          sum[l] += term;
+          if (l == ls) mag_lo = fabs(term);
+          if (l == L) mag_hi = fabs(term);
+          nfma += sp - jlo + 2;
+          const double cr = k < KTAB ? c_cratio[l][k]
+                                     : (double)(k + l + 1) / ((double)(k + 1) * (2.0 * k + 2.0 * l + 2.0) * (2.0 * k + 2.0 * l + 3.0));
+          common[l] *= v * cr;
         }
+        abs_lo += mag_lo;
+        abs_hi += mag_hi;
+        small = (mag_lo <= 1e-17 * abs_lo && mag_hi <= 1e-17 * abs_hi) ? small + 1 : 0;
+        if (small >= 2 && k >= kmin) break;
       }
       if (k == KMAX) bad = 1;
-      out[l] += fct[l] * sum;
+      for (int l = ls; l <= L; ++l) out[l] += fct[l] * sum[l];
     }
   }
   if (fma_count) *fma_count += nfma;
