@@ -307,22 +307,38 @@ __global__ void k_aux_points(Tables T, int cls, int64_t npts, const double *xi, 
 // -------------------------------------------------------------- contract --
 // One block per shell quartet; its NW warps split the ket primitive pairs.
 // Shared memory (doubles):
-//   per warp: R0, R1  two levels of the Hermite recursion    2 * nh(L)
-//             W       ket-contracted integrals, bra order
-//                     <= lab (+2 for I5), summed over the
-//                     warp's ket primitive pairs              nh(Lb) * ncd
-//             g       the radial derivatives g_n              LAUX + 1
-//   block:    O       output accumulator                      nab * ncd
+//   per warp: R0, R1  two levels of the Hermite recursion        2 * nh(L)
+//             W       ket-contracted integrals, bra order <= lab
+//                     (+2 for I5), summed over the warp's ket
+//                     primitive pairs                             nh(Lb) * ncd
+//             g       the radial derivatives g_n                  LAUX + 1
+//             E3cd    E^{cd}_{t'u'v'} = E_t' E_u' E_v' of the
+//                     current ket primitive pair, per component   ne3(lc, ld)
+//   block:    O       output accumulator                          nab * ncd
+//             E3ab    E^{ab}_{tuv} of the current bra primitive
+//                     pair (times (a-b)/2p for I5), and for I5 the
+//                     three dE/dAB-weighted products              ne3(la, lb) (x4 for I5)
 // The per-warp W are summed in warp order, so results do not depend on
-// scheduling.
-__host__ __device__ __forceinline__ size_t contract_warp_doubles(int nhL, int nhB, int ncd) {
-  return (size_t)2 * nhL + (size_t)nhB * ncd + (LAUX + 1);
+// scheduling; the sum also applies the bra sign (-1)^{t+u+v} of Eq. ii.
+__host__ __device__ __forceinline__ size_t contract_warp_doubles(int nhL, int nhB, int ncd, int ne3cd) {
+  return (size_t)2 * nhL + (size_t)nhB * ncd + (LAUX + 1) + (size_t)ne3cd;
+}
+
+// number of Hermite products over all component pairs of shells (l1, l2)
+__host__ __device__ inline int ne3_count(int l1, int l2) {
+  int n = 0;
+  for (int i = l1; i >= 0; --i)
+    for (int j = l1 - i; j >= 0; --j)
+      for (int i2 = l2; i2 >= 0; --i2)
+        for (int j2 = l2 - i2; j2 >= 0; --j2) n += (i + i2 + 1) * (j + j2 + 1) * (l1 - i - j + l2 - i2 - j2 + 1);
+  return n;
 }
 
 __global__ void __launch_bounds__(BLOCK_CONTRACT)
 k_contract(PairView PV, QuartetView QV, int cls, int nf, int64_t pq0, int64_t q0, const double *part,
            double *out, const int64_t *offsets, unsigned int *status, unsigned long long *flops_total) {
   extern __shared__ double smem[];
+  __shared__ int off_ab[101], off_cd[101];
   const int64_t q = q0 + blockIdx.x;
   if (q >= QV.n) return;
   const int32_t *s = QV.quartets + 4 * q;
@@ -337,12 +353,33 @@ k_contract(PairView PV, QuartetView QV, int cls, int nf, int64_t pq0, int64_t q0
   const int nhL = nh_count(L), nhB = nh_count(Lb);
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
-  const size_t wsz = contract_warp_doubles(nhL, nhB, ncd);
+  if (tid == 0) {
+    int o = 0;
+    for (int j = 0; j < ncd; ++j) {
+      off_cd[j] = o;
+      const unsigned char *ec = c_cart[lc][j / nd], *ed = c_cart[ld][j % nd];
+      o += (ec[0] + ed[0] + 1) * (ec[1] + ed[1] + 1) * (ec[2] + ed[2] + 1);
+    }
+    off_cd[ncd] = o;
+    o = 0;
+    for (int j = 0; j < nab; ++j) {
+      off_ab[j] = o;
+      const unsigned char *ea = c_cart[la][j / nb], *eb = c_cart[lb][j % nb];
+      o += (ea[0] + eb[0] + 1) * (ea[1] + eb[1] + 1) * (ea[2] + eb[2] + 1);
+    }
+    off_ab[nab] = o;
+  }
+  __syncthreads();
+  const int ne3cd = off_cd[ncd], ne3ab = off_ab[nab];
+  const size_t wsz = contract_warp_doubles(nhL, nhB, ncd, ne3cd);
   double *R0 = smem + warp * wsz;
   double *R1 = R0 + nhL;
   double *W = R1 + nhL;
   double *gw = W + (size_t)nhB * ncd;
+  double *E3cd = gw + (LAUX + 1);
   double *Oacc = smem + nw * wsz;
+  double *E3ab = Oacc + (size_t)nab * ncd;
+  double *E3fx = E3ab + ne3ab, *E3fy = E3fx + ne3ab, *E3fz = E3fy + ne3ab;
   const int ab = s[0] * ns + s[1], cd = s[2] * ns + s[3];
   const int ab0 = PV.pair_start[ab], npab = PV.pair_start[ab + 1] - ab0;
   const int cd0 = PV.pair_start[cd], npcd = PV.pair_start[cd + 1] - cd0;
@@ -372,6 +409,22 @@ k_contract(PairView PV, QuartetView QV, int cls, int nf, int64_t pq0, int64_t q0
         double acc = 0.0;
         for (int fm = 0; fm < nf; ++fm) acc += part[(pq * nf + fm) * (LAUX + 1) + lane];
         gw[lane] = pi52 / (sqrt(p + qq) * p * qq) * acc;
+      }
+      // E^{cd}_{t'u'v'} products of this ket primitive pair
+      const double *Ecd = PV.epool + PV.pp_eoff[pcd];
+      for (int j = lane; j < ncd; j += 32) {
+        const unsigned char *ec = c_cart[lc][j / nd], *ed = c_cart[ld][j % nd];
+        const double *ex = Ecd + (ec[0] * (ld + 1) + ed[0]) * ntcd;
+        const double *ey = Ecd + n1cd + (ec[1] * (ld + 1) + ed[1]) * ntcd;
+        const double *ez = Ecd + 2 * n1cd + (ec[2] * (ld + 1) + ed[2]) * ntcd;
+        const int tx = ec[0] + ed[0], ty = ec[1] + ed[1], tz = ec[2] + ed[2];
+        double *e = E3cd + off_cd[j];
+        int m = 0;
+        for (int t2 = 0; t2 <= tx; ++t2)
+          for (int u2 = 0; u2 <= ty; ++u2) {
+            const double exy = ex[t2] * ey[u2];
+            for (int v2 = 0; v2 <= tz; ++v2) e[m++] = exy * ez[v2];
+          }
       }
       __syncwarp();
       // Hermite recursion from level n = L down to 0, ping-pong between R0/R1
@@ -403,64 +456,82 @@ k_contract(PairView PV, QuartetView QV, int cls, int nf, int64_t pq0, int64_t q0
         nxt = tmp;
       }
       // inner (ket) sum of Eq. ii:  W[tuv][cd] += sum E^{cd}_{t'u'v'} R_{t+t',u+u',v+v'}
-      const double *Ecd = PV.epool + PV.pp_eoff[pcd];
       for (int i = lane; i < nhB * ncd; i += 32) {
         const int bi = i / ncd, j = i - bi * ncd;
         const int ic = j / nd, id = j - ic * nd;
         const int t = c_tuv[bi][0], u = c_tuv[bi][1], v = c_tuv[bi][2];
         const unsigned char *ec = c_cart[lc][ic], *ed = c_cart[ld][id];
-        const double *ex = Ecd + (ec[0] * (ld + 1) + ed[0]) * ntcd;
-        const double *ey = Ecd + n1cd + (ec[1] * (ld + 1) + ed[1]) * ntcd;
-        const double *ez = Ecd + 2 * n1cd + (ec[2] * (ld + 1) + ed[2]) * ntcd;
         const int tx = ec[0] + ed[0], ty = ec[1] + ed[1], tz = ec[2] + ed[2];
+        const double *e = E3cd + off_cd[j];
         double acc = 0.0;
+        int m = 0;
         for (int t2 = 0; t2 <= tx; ++t2)
-          for (int u2 = 0; u2 <= ty; ++u2) {
-            const double exy = ex[t2] * ey[u2];
-            for (int v2 = 0; v2 <= tz; ++v2) acc = fma(exy * ez[v2], cur[hidx(t + t2, u + u2, v + v2)], acc);
-          }
+          for (int u2 = 0; u2 <= ty; ++u2)
+            for (int v2 = 0; v2 <= tz; ++v2) acc = fma(e[m++], cur[hidx(t + t2, u + u2, v + v2)], acc);
         W[i] += acc;
       }
       __syncwarp();
     }
     __syncthreads();
-    // sum the warps' W into warp 0's buffer (fixed order)
+    // sum the warps' W into warp 0's buffer (fixed order), with the bra sign
     double *W0 = smem + 2 * nhL;
     for (int i = tid; i < nhB * ncd; i += nthr) {
       double acc = W0[i];
       for (int w = 1; w < nw; ++w) acc += smem[w * wsz + 2 * nhL + i];
-      W0[i] = acc;
+      const int bi = i / ncd;
+      W0[i] = ((c_tuv[bi][0] + c_tuv[bi][1] + c_tuv[bi][2]) & 1) ? -acc : acc;
     }
-    __syncthreads();
-    // outer (bra) sum
+    // E^{ab}_{tuv} products of this bra primitive pair
     const double *Eab = PV.epool + PV.pp_eoff[pab];
     const double *Fab = Eab + 3 * n1ab;
     const double a = PV.pp_ab[2 * pab], b = PV.pp_ab[2 * pab + 1];
     const double c5 = (a - b) / (2.0 * (a + b));
-    for (int i = tid; i < nab * ncd; i += nthr) {
-      const int iabc = i / ncd, j = i - iabc * ncd;
-      const int ia = iabc / nb, ib = iabc - ia * nb;
-      const unsigned char *ea = c_cart[la][ia], *eb = c_cart[lb][ib];
+    for (int c = tid; c < nab; c += nthr) {
+      const unsigned char *ea = c_cart[la][c / nb], *eb = c_cart[lb][c % nb];
       const int ox = (ea[0] * (lb + 1) + eb[0]) * ntab;
       const int oy = n1ab + (ea[1] * (lb + 1) + eb[1]) * ntab;
       const int oz = 2 * n1ab + (ea[2] * (lb + 1) + eb[2]) * ntab;
       const int tx = ea[0] + eb[0], ty = ea[1] + eb[1], tz = ea[2] + eb[2];
-      double acc = 0.0;
+      const int o = off_ab[c];
+      int m = 0;
       for (int t = 0; t <= tx; ++t)
         for (int u = 0; u <= ty; ++u)
-          for (int v = 0; v <= tz; ++v) {
-            const double sgn = ((t + u + v) & 1) ? -1.0 : 1.0;
+          for (int v = 0; v <= tz; ++v, ++m) {
+            const double exy = Eab[ox + t] * Eab[oy + u];
             if (cls != 5) {
-              acc += sgn * Eab[ox + t] * Eab[oy + u] * Eab[oz + v] * W0[hidx(t, u, v) * ncd + j];
+              E3ab[o + m] = exy * Eab[oz + v];
             } else {
-              // Eq. I5byI3_ with the second coefficient -1 (see the derivation note below)
-              const double e = Eab[ox + t] * Eab[oy + u] * Eab[oz + v];
+              E3ab[o + m] = c5 * exy * Eab[oz + v];
+              E3fx[o + m] = Fab[ox + t] * Eab[oy + u] * Eab[oz + v];
+              E3fy[o + m] = Eab[ox + t] * Fab[oy + u] * Eab[oz + v];
+              E3fz[o + m] = exy * Fab[oz + v];
+            }
+          }
+    }
+    __syncthreads();
+    // outer (bra) sum
+    for (int i = tid; i < nab * ncd; i += nthr) {
+      const int iabc = i / ncd, j = i - iabc * ncd;
+      const int ia = iabc / nb, ib = iabc - ia * nb;
+      const unsigned char *ea = c_cart[la][ia], *eb = c_cart[lb][ib];
+      const int tx = ea[0] + eb[0], ty = ea[1] + eb[1], tz = ea[2] + eb[2];
+      const int o = off_ab[iabc];
+      double acc = 0.0;
+      int m = 0;
+      for (int t = 0; t <= tx; ++t)
+        for (int u = 0; u <= ty; ++u)
+          for (int v = 0; v <= tz; ++v, ++m) {
+            if (cls != 5) {
+              acc = fma(E3ab[o + m], W0[hidx(t, u, v) * ncd + j], acc);
+            } else {
+              // Eq. I5byI3_ with the second coefficient -1 (see the derivation note
+              // below); W0 carries the bra sign, so the gradient term changes sign
               const double lap = W0[hidx(t + 2, u, v) * ncd + j] + W0[hidx(t, u + 2, v) * ncd + j] +
                                  W0[hidx(t, u, v + 2) * ncd + j];
-              const double grad = Fab[ox + t] * Eab[oy + u] * Eab[oz + v] * W0[hidx(t + 1, u, v) * ncd + j] +
-                                  Eab[ox + t] * Fab[oy + u] * Eab[oz + v] * W0[hidx(t, u + 1, v) * ncd + j] +
-                                  Eab[ox + t] * Eab[oy + u] * Fab[oz + v] * W0[hidx(t, u, v + 1) * ncd + j];
-              acc += sgn * (c5 * e * lap - grad);
+              acc = fma(E3ab[o + m], lap, acc);
+              acc = fma(E3fx[o + m], W0[hidx(t + 1, u, v) * ncd + j], acc);
+              acc = fma(E3fy[o + m], W0[hidx(t, u + 1, v) * ncd + j], acc);
+              acc = fma(E3fz[o + m], W0[hidx(t, u, v + 1) * ncd + j], acc);
             }
           }
       Oacc[i] += acc;
@@ -1046,7 +1117,9 @@ static size_t contract_smem(int la, int lb, int lc, int ld, int cls, int nw) {
   int L = la + lb + lc + ld + ext;
   int nhL = nh_count(L), nhB = nh_count(la + lb + ext);
   int ncd = ncart(lc) * ncart(ld), nab = ncart(la) * ncart(lb);
-  return sizeof(double) * ((size_t)nw * contract_warp_doubles(nhL, nhB, ncd) + (size_t)nab * ncd);
+  size_t e3ab = (size_t)ne3_count(la, lb) * (cls == 5 ? 4 : 1);
+  return sizeof(double) * ((size_t)nw * contract_warp_doubles(nhL, nhB, ncd, ne3_count(lc, ld)) +
+                           (size_t)nab * ncd + e3ab);
 }
 
 // warps per contraction block: 4 unless the shared memory does not fit
