@@ -171,6 +171,143 @@ static real kernel_value(const ork_kernel *K, int cls, real r) {
   }
 }
 
+/* ------------------------------------------------------- Taylor jets -- */
+
+/* Truncated Taylor series c[k] = f^(k)(x0) / k!, k < ORK_JET, about a point
+ * x0, carried through the kernel's formula by the standard recurrences of
+ * automatic differentiation (products by the Cauchy rule; b = e^a from
+ * b' = a' b; b = a^e from a b' = e a' b).  Used by the large-T form of the
+ * radial integral, which needs d^m/dx^m [x k(x)] up to m = ORK_MAXN. */
+#define ORK_JET (ORK_MAXN + 2)
+typedef struct {
+  int n;              /* coefficients kept: c[0..n-1] */
+  real c[ORK_JET];
+} jet;
+
+static jet jet_cst(real v, int n) {
+  jet r;
+  memset(&r, 0, sizeof r);
+  r.n = n;
+  r.c[0] = v;
+  return r;
+}
+
+static jet jet_var(real x0, int n) {
+  jet r = jet_cst(x0, n);
+  if (n > 1) r.c[1] = 1;
+  return r;
+}
+
+static jet jet_add(jet a, jet b) {
+  for (int k = 0; k < a.n; ++k) a.c[k] += b.c[k];
+  return a;
+}
+
+static jet jet_scale(jet a, real s) {
+  for (int k = 0; k < a.n; ++k) a.c[k] *= s;
+  return a;
+}
+
+static jet jet_mul(jet a, jet b) {
+  jet r = jet_cst(0, a.n);
+  for (int k = 0; k < a.n; ++k) {
+    real s = 0;
+    for (int j = 0; j <= k; ++j) s += a.c[j] * b.c[k - j];
+    r.c[k] = s;
+  }
+  return r;
+}
+
+static jet jet_exp(jet a) {
+  jet r = jet_cst(R_EXP(a.c[0]), a.n);
+  for (int k = 1; k < a.n; ++k) {
+    real s = 0;
+    for (int j = 1; j <= k; ++j) s += (real)j * a.c[j] * r.c[k - j];
+    r.c[k] = s / k;
+  }
+  return r;
+}
+
+/* a^e for a.c[0] > 0 */
+static jet jet_pow(jet a, real e) {
+  jet r = jet_cst(R_POW(a.c[0], e), a.n);
+  for (int k = 1; k < a.n; ++k) {
+    real s = 0;
+    for (int j = 1; j <= k; ++j) s += (e * j - (k - j)) * a.c[j] * r.c[k - j];
+    r.c[k] = s / (k * a.c[0]);
+  }
+  return r;
+}
+
+/* d/dx (the top coefficient becomes unknown and is set to zero) */
+static jet jet_der(jet a) {
+  jet r = jet_cst(0, a.n);
+  for (int k = 0; k + 1 < a.n; ++k) r.c[k] = (real)(k + 1) * a.c[k + 1];
+  return r;
+}
+
+/* antiderivative with value v at x0 */
+static jet jet_int(jet a, real v) {
+  jet r = jet_cst(v, a.n);
+  for (int k = 1; k < a.n; ++k) r.c[k] = a.c[k - 1] / k;
+  return r;
+}
+
+/* f(r) of Eq. rs12 as a jet in r; the Tang-Toennies factor S_n(mu r^2) is
+ * carried through S_n' = e^{-x} x^n / n! (Eq. ttdamp), so that its small-x
+ * cancellation never enters the higher coefficients. */
+static jet factor_jet(jet r, double c0, double rho, double B, double mu, int n) {
+  jet x = jet_scale(jet_mul(r, r), (real)mu);
+  jet g = jet_exp(jet_scale(x, -1));
+  jet f = jet_mul(jet_add(jet_cst(1, r.n), jet_scale(r, (real)0.5)), g);
+  if (c0 != 0.0) {
+    jet xn = jet_cst(1, r.n);
+    real nf = 1;
+    for (int k = 1; k <= n; ++k) {
+      xn = jet_mul(xn, x);
+      nf *= k;
+    }
+    jet dS = jet_mul(jet_scale(jet_mul(g, xn), 1 / nf), jet_der(x)); /* dS/dr */
+    jet S = jet_int(dS, tt_damp(x.c[0], n));
+    jet pw = jet_mul(jet_pow(r, (real)rho), jet_exp(jet_scale(r, (real)B)));
+    f = jet_add(f, jet_scale(jet_mul(S, pw), (real)c0));
+  }
+  return f;
+}
+
+/* x k_i(x) of Eqs. k1-k6 as a jet about x0 > 0 with coefficients up to order
+ * nord (test kernels as in kernel_value); f_r takes one order more. */
+static jet phi_jet(const ork_kernel *K, int cls, real x0, int nord) {
+  jet r = jet_var(x0, nord + 2), k;
+  if (K->id) {
+    switch (K->id) {
+      case 10: k = jet_cst(1, r.n); break;
+      case 11: k = jet_exp(jet_scale(jet_mul(r, r), -(real)K->gam)); break;
+      case 12: k = r; break;
+      case 13: k = jet_pow(r, -1); break;
+      case 14: k = jet_exp(jet_scale(r, -(real)K->gam)); break;
+      default: k = jet_cst(0, r.n);
+    }
+    return jet_mul(r, k);
+  }
+  switch (cls) {
+    case 1: return jet_cst(1, r.n);
+    case 2: return factor_jet(r, K->c0, K->rho, K->B, K->mu, K->n);
+    case 3:
+    case 5: k = factor_jet(r, K->c0, K->rho, K->B, K->mu, K->n); break;
+    case 4:
+      k = jet_mul(factor_jet(r, K->c0, K->rho, K->B, K->mu, K->n),
+                  factor_jet(r, K->c0p, K->rhop, K->Bp, K->mup, K->np));
+      break;
+    case 6:
+      k = jet_mul(jet_der(factor_jet(r, K->c0, K->rho, K->B, K->mu, K->n)),
+                  jet_der(factor_jet(r, K->c0p, K->rhop, K->Bp, K->mup, K->np)));
+      break;
+    default: k = jet_cst(0, r.n);
+  }
+  return jet_mul(r, k);
+}
+
 /* Largest exponential growth rate of the kernel (the e^{B r} factors). */
 static double kernel_growth(const ork_kernel *K, int cls) {
   if (K->id) return 0.0;
@@ -218,7 +355,8 @@ static void jhat(real z, int N, real *jh) {
 typedef struct {
   const ork_kernel *K;
   int cls, N;
-  int mode;   /* 0: Bessel form (small T), 1: separated exponentials (large T) */
+  int mode;   /* 0: Bessel form (small T), 1: separated exponentials,
+                 2: derivatives moved onto x k(x) (very large T) */
   real xi, D;
   real binom[ORK_MAXN + 1][ORK_MAXN + 1];
   real anm[ORK_MAXN + 1][ORK_MAXN + 1];   /* D_Q^n (h/D) = sum_m a_nm h^(m) / D^(2n+1-m) */
@@ -270,6 +408,39 @@ static void radial_integrand_sep(const radial_ctx *c, real x, real *out, real *m
   }
 }
 
+/* Very-large-T form.  With h(D) as above, drop the image term
+ * e^{-xi (x+D)^2} (below e^{-T}) and the range x < x_c = D - 16/sqrt(xi)
+ * (Gaussian weight below e^{-256}); on the rest, d/dD e^{-xi(x-D)^2} =
+ * -d/dx e^{-xi(x-D)^2} and m integrations by parts (boundary terms of the
+ * same e^{-256} size) give
+ *   h^(m)(D) = int_{x_c}^inf [x k(x)]^(m) e^{-xi (x-D)^2} dx,
+ * whose integrand has no cancellation: the Hermite-polynomial form loses
+ * about T^{m/2} to it, which exceeds binary128 for T near 1e4 and m = 14. */
+static void radial_integrand_ibp(const radial_ctx *c, real x, real *out, real *mag) {
+  const int N = c->N;
+  real D = c->D, dx = x - D;
+  real G = R_EXP(-c->xi * dx * dx);
+  jet ph = phi_jet(c->K, c->cls, x, N);
+  real hm[ORK_MAXN + 1], fact = 1;
+  for (int m = 0; m <= N; ++m) {
+    if (m > 0) fact *= m;
+    hm[m] = fact * ph.c[m] * G;
+  }
+  real iD = 1 / D, pw[2 * ORK_MAXN + 2];
+  pw[0] = 1;
+  for (int k = 1; k <= 2 * N + 1; ++k) pw[k] = pw[k - 1] * iD;
+  for (int n = 0; n <= N; ++n) {
+    real s = 0, sa = 0;
+    for (int m = 0; m <= n; ++m) {
+      real term = c->anm[n][m] * hm[m] * pw[2 * n + 1 - m];
+      s += term;
+      sa += R_FABS(term);
+    }
+    out[n] = s;
+    mag[n] = sa;
+  }
+}
+
 /* The integrand of hat g_n for n = 0..N at r12 = x:
  *   k(x) x D_Q^n [ (e^{-xi (x-D)^2} - e^{-xi (x+D)^2}) / D ]
  * with D_Q = D^-1 d/dD applied analytically.  Writing the bracket as
@@ -281,6 +452,10 @@ static void radial_integrand(const radial_ctx *c, real x, real *out, real *mag) 
   real xi = c->xi, D = c->D;
   if (x <= 0) {
     for (int n = 0; n <= N; ++n) out[n] = mag[n] = 0;
+    return;
+  }
+  if (c->mode == 2) {
+    radial_integrand_ibp(c, x, out, mag);
     return;
   }
   if (c->mode) {
@@ -441,6 +616,8 @@ static int tanh_sinh0(const radial_ctx *c, real b, real tol, real *I, real *A) {
  *   g_n = sqrt(pi^5/(p+q)) / (p q) * hat g_n.
  * Returns 0 on success, nonzero when a quadrature piece did not converge. */
 #define ORK_T_SWITCH 16
+#define ORK_T_SWITCH2 1000
+#define ORK_IBP_CUT 16
 static int radial_hat(const ork_kernel *K, int cls, real xi, real D, int N, real *out,
                       int mode_override) {
   radial_ctx c;
@@ -459,7 +636,8 @@ static int radial_hat(const ork_kernel *K, int cls, real xi, real D, int N, real
   for (int n = 0; n < N; ++n)
     for (int m = 0; m <= n + 1; ++m)
       c.anm[n + 1][m] = (m > 0 ? c.anm[n][m - 1] : 0) - (real)(2 * n + 1 - m) * (m <= n ? c.anm[n][m] : 0);
-  c.mode = (mode_override >= 0) ? mode_override : (xi * D * D >= (real)ORK_T_SWITCH);
+  real T = xi * D * D;
+  c.mode = (mode_override >= 0) ? mode_override : (T >= (real)ORK_T_SWITCH2 ? 2 : T >= (real)ORK_T_SWITCH);
   real I[ORK_MAXN + 1], A[ORK_MAXN + 1];
   for (int n = 0; n <= N; ++n) I[n] = A[n] = 0;
   real w = 1 / R_SQRT(xi);
@@ -467,6 +645,17 @@ static int radial_hat(const ork_kernel *K, int cls, real xi, real D, int N, real
   real xend = cen + 18 * w;
   real tol = (real)1e-28;
   int err = 0;
+  if (c.mode == 2) {
+    real xc = D - ORK_IBP_CUT * w;
+    if (!(xc > 0)) return 2;
+    for (real a = xc; a < xend; a += w) {
+      real b = a + w;
+      if (b > xend) b = xend;
+      err |= gl_adapt(&c, a, b, tol, 0, I, A);
+    }
+    for (int n = 0; n <= N; ++n) out[n] = I[n];
+    return err;
+  }
   /* piece 1: [0, x_ts] by tanh-sinh (end-point behaviour of k(x) x at 0) */
   real x_ts = w / 2;
   if (x_ts > (real)0.5) x_ts = (real)0.5;
@@ -720,11 +909,12 @@ int ork_radial(const ork_kernel *K, int cls, double xi, double D, int nmax, doub
 }
 
 /* As ork_radial with the integrand form forced (0: Bessel form, 1: separated
- * exponentials, -1: by T); lets the tests check that both forms agree. */
+ * exponentials, 2: derivatives moved onto x k(x), needs sqrt(xi) D > 16;
+ * -1: by T); lets the tests check that the forms agree. */
 int ork_radial_mode(const ork_kernel *K, int cls, double xi, double D, int nmax, int mode,
                     double *out) {
   if (nmax < 0 || nmax > ORK_MAXN || !(xi > 0) || !(D >= 0)) return 2;
-  if (mode == 1 && !(D > 0)) return 2;
+  if (mode >= 1 && !(D > 0)) return 2;
   if (!gl_ready) gl_build();
   real g[ORK_MAXN + 1];
   int e = radial_hat(K, cls, (real)xi, (real)D, nmax, g, mode);

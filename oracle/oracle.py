@@ -119,7 +119,8 @@ def radial(kern: OrkKernel, cls: int, xi: float, D: float, nmax: int) -> np.ndar
 
 
 def radial_mode(kern: OrkKernel, cls: int, xi: float, D: float, nmax: int, mode: int) -> np.ndarray:
-    """As :func:`radial` with the integrand form forced (0 Bessel, 1 separated)."""
+    """As :func:`radial` with the integrand form forced (0 Bessel, 1 separated
+    exponentials, 2 derivatives on x k(x) for very large T)."""
     out = np.zeros(nmax + 1)
     rc = lib().ork_radial_mode(ctypes.byref(kern), cls, float(xi), float(D), nmax, int(mode), _dp(out))
     if rc:

@@ -55,6 +55,59 @@ def test_radial_gaussian_closed_form(gam, xi, D):
     np.testing.assert_allclose(g, ref, rtol=2e-13, atol=0)
 
 
+@pytest.mark.parametrize("xi,D", [(200.0, 7.0), (20.0, 30.0), (200.0, 15.0), (3.0, 60.0)])
+def test_radial_coulomb_is_boys_large_T(xi, D):
+    """k = 1/r at T = xi D^2 from 9800 to 45000 and orders up to 14: the
+    integration-by-parts form of the oracle against the Boys function."""
+    g = O.radial(O.test_kernel(O.K_COULOMB), 3, xi, D, 14)
+    T = xi * D * D
+    ref = np.array([2 * (-2 * xi) ** n * boys(n, T) for n in range(15)])
+    np.testing.assert_allclose(g, ref, rtol=2e-13, atol=0)
+
+
+@pytest.mark.parametrize("gam", [0.3, 4.0])
+@pytest.mark.parametrize("xi,D", [(200.0, 5.0), (80.0, 9.0), (3000.0, 1.5)])
+def test_radial_gaussian_closed_form_large_T(gam, xi, D):
+    """k = exp(-gam r^2) at T from 2000 to 6750, orders up to 14:
+    hat g_n = (-2w)^n sqrt(pi) xi (xi+gam)^{-3/2} e^{-w D^2}, w = xi gam/(xi+gam)."""
+    w = xi * gam / (xi + gam)
+    g = O.radial(O.test_kernel(O.K_GAUSS, gam), 3, xi, D, 14)
+    g0 = math.sqrt(math.pi) * xi * (xi + gam) ** -1.5 * math.exp(-w * D * D)
+    ref = np.array([(-2 * w) ** n * g0 for n in range(15)])
+    np.testing.assert_allclose(g, ref, rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("xi,D", [(50.0, 6.0), (400.0, 4.0), (2.0, 40.0)])
+def test_radial_linear_kernel_large_T(xi, D):
+    """k = r: up to terms of order e^{-T}, hat g_0 = sqrt(pi/xi) (D + 1/(2 xi D)),
+    so hat g_n = sqrt(pi/xi) [(-1)^{n-1} (2n-3)!! D^{1-2n} + (-1)^n (2n-1)!! D^{-1-2n}/(2 xi)]
+    for n >= 1 (D_Q D = 1/D, D_Q^n (1/D) = (-1)^n (2n-1)!! / D^{2n+1})."""
+    g = O.radial(O.test_kernel(O.K_R), 3, xi, D, 14)
+
+    def dfact(k):
+        return 1.0 if k <= 0 else float(np.prod(np.arange(k, 0, -2)))
+
+    s = math.sqrt(math.pi / xi)
+    ref = [s * (D + 1 / (2 * xi * D))]
+    for n in range(1, 15):
+        ref.append(s * ((-1) ** (n - 1) * dfact(2 * n - 3) * D ** (1 - 2 * n)
+                        + (-1) ** n * dfact(2 * n - 1) * D ** (-1 - 2 * n) / (2 * xi)))
+    np.testing.assert_allclose(g, np.array(ref), rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("cls", [1, 2, 3, 4, 6])
+@pytest.mark.parametrize("xi,D", [(100.0, 3.2), (10.0, 11.0), (400.0, 1.8)])
+def test_radial_ibp_form_agrees_with_hermite_form(cls, xi, D):
+    """Near T = 1000, where the separated-exponential form is still accurate,
+    the integration-by-parts form (derivatives of x k(x) by Taylor jets) must
+    agree with it for every order up to 14."""
+    K = O.factor_kernel(P0)
+    a = O.radial_mode(K, cls, xi, D, 14, 1)
+    b = O.radial_mode(K, cls, xi, D, 14, 2)
+    scale = np.maximum(np.abs(a), np.abs(b))
+    assert np.all(np.abs(a - b) <= 1e-13 * scale + 1e-300), (a, b)
+
+
 @pytest.mark.parametrize("cls", [2, 3, 4, 6])
 @pytest.mark.parametrize("xi,D", [(0.3, 13.0), (2.0, 2.9), (8.0, 1.5), (0.9, 5.0)])
 def test_radial_two_forms_agree(cls, xi, D):
