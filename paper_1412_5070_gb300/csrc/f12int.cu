@@ -54,7 +54,7 @@ __host__ __device__ __forceinline__ int hidx(int t, int u, int v) {
 struct PairView {
   const int *pair_start;     // [nshell*nshell + 1] first primitive pair of shell pair (i,j)
   const double *pp_p;        // exponent sum p
-  const double *pp_P;        // [3*npp] centre P
+  const double *pp_P;        // [6*npp] centre P as heavy centre H (3) + offset P - H (3)
   const double *pp_ab;       // [2*npp] exponents a, b
   const int64_t *pp_eoff;    // offset into epool of this primitive pair's tables
   const double *epool;       // E (3 dims) then F (3 dims), each (la+1)(lb+1)(la+lb+1)
@@ -68,6 +68,11 @@ struct PairView {
 // above 1e-12 need for a relative error of 1e-10.
 __device__ __forceinline__ bool prim_negligible(const PairView &PV, int pab, int pcd) {
   return PV.qprim && PV.qprim[pab] * PV.qprim[pcd] < 1e-26;
+}
+
+// X_PQ component k = Q - P = (H_cd - H_ab) + (offset_cd - offset_ab).
+__device__ __forceinline__ double pair_sep(const double *ppP, int pab, int pcd, int k) {
+  return (ppP[6 * pcd + k] - ppP[6 * pab + k]) + (ppP[6 * pcd + 3 + k] - ppP[6 * pab + 3 + k]);
 }
 
 // ------------------------------------------------------------ pair builder --
@@ -96,11 +101,17 @@ __global__ void k_build_pairs(int npp, const int *pp_shell_a, const int *pp_shel
   const int n1 = (la + 1) * (lb + 1) * nt;
   double *E = epool + pp_eoff[i];
   double *F = E + 3 * n1;
+  // P is kept as the centre of the larger exponent H plus the offset P - H,
+  // and X_PA, X_PB come from X_AB: both stay exact (zero) for one-centre
+  // pairs, and X_PQ formed from them keeps its relative accuracy when P and
+  // Q nearly coincide; the parity cancellations of one-centre blocks rely on
+  // that.
+  const bool heavy_a = a >= b;
   for (int k = 0; k < 3; ++k) {
     double A = centers[3 * sa + k], B = centers[3 * sb + k];
-    double P = (a * A + b * B) / p;
-    pp_P[3 * i + k] = P;
-    double XAB = A - B, XPA = P - A, XPB = P - B;
+    double XAB = A - B, XPA = -(b / p) * XAB, XPB = (a / p) * XAB;
+    pp_P[6 * i + k] = heavy_a ? A : B;
+    pp_P[6 * i + 3 + k] = heavy_a ? XPA : XPB;
     double K = exp(-a * b / p * XAB * XAB);
     double scale = (k == 0) ? da * db : 1.0;
     double *Ek = E + k * n1, *Fk = F + k * n1;
@@ -188,9 +199,7 @@ __device__ __forceinline__ ItemGeom item_geometry(const PairView &PV, const Quar
   g.icd = icd;
   g.L = PV.shell_l[s[0]] + PV.shell_l[s[1]] + PV.shell_l[s[2]] + PV.shell_l[s[3]] + (cls == 5 ? 2 : 0);
   double p = PV.pp_p[iab], qq = PV.pp_p[icd];
-  double X = PV.pp_P[3 * icd] - PV.pp_P[3 * iab];
-  double Y = PV.pp_P[3 * icd + 1] - PV.pp_P[3 * iab + 1];
-  double Z = PV.pp_P[3 * icd + 2] - PV.pp_P[3 * iab + 2];
+  double X = pair_sep(PV.pp_P, iab, icd, 0), Y = pair_sep(PV.pp_P, iab, icd, 1), Z = pair_sep(PV.pp_P, iab, icd, 2);
   g.D = sqrt(X * X + Y * Y + Z * Z);
   g.xi = p * qq / (p + qq);
   return g;
@@ -305,7 +314,12 @@ __global__ void k_aux_points(Tables T, int cls, int64_t npts, const double *xi, 
 }
 
 // -------------------------------------------------------------- contract --
-// One block per shell quartet; its NW warps split the ket primitive pairs.
+// One block per shell quartet and range of ket components: a quartet whose
+// buffers would not fit in shared memory is split into NSPLIT blocks, each
+// owning a contiguous range of the c*d Cartesian components (every block
+// repeats the Hermite recursion, which is a small part of the work at the
+// angular momenta that need a split).  The NW warps of a block split the ket
+// primitive pairs.  Below, ncd is the number of ket components of the block.
 // Shared memory (doubles):
 //   per warp: R0, R1  two levels of the Hermite recursion        2 * nh(L)
 //             W       ket-contracted integrals, bra order <= lab
@@ -334,12 +348,30 @@ __host__ __device__ inline int ne3_count(int l1, int l2) {
   return n;
 }
 
+// largest number of Hermite products over the ranges of jc consecutive
+// component pairs (same lexicographic order as the kernel's)
+static inline int ne3_chunk_max(int l1, int l2, int jc) {
+  int best = 0, cur = 0, k = 0;
+  for (int i = l1; i >= 0; --i)
+    for (int j = l1 - i; j >= 0; --j)
+      for (int i2 = l2; i2 >= 0; --i2)
+        for (int j2 = l2 - i2; j2 >= 0; --j2) {
+          cur += (i + i2 + 1) * (j + j2 + 1) * (l1 - i - j + l2 - i2 - j2 + 1);
+          if (++k == jc) {
+            best = cur > best ? cur : best;
+            cur = k = 0;
+          }
+        }
+  return cur > best ? cur : best;
+}
+
 __global__ void __launch_bounds__(BLOCK_CONTRACT)
-k_contract(PairView PV, QuartetView QV, int cls, int nf, int64_t pq0, int64_t q0, const double *part,
+k_contract(PairView PV, QuartetView QV, int cls, int nf, int64_t pq0, int64_t q0, int nsplit, const double *part,
            double *out, const int64_t *offsets, unsigned int *status, unsigned long long *flops_total) {
   extern __shared__ double smem[];
   __shared__ int off_ab[101], off_cd[101];
-  const int64_t q = q0 + blockIdx.x;
+  const int64_t q = q0 + blockIdx.x / nsplit;
+  const int split = blockIdx.x % nsplit;
   if (q >= QV.n) return;
   const int32_t *s = QV.quartets + 4 * q;
   const int ns = PV.nshell;
@@ -349,7 +381,10 @@ k_contract(PairView PV, QuartetView QV, int cls, int nf, int64_t pq0, int64_t q0
   const int L = lab + lcd + ext;
   const int Lb = lab + ext;
   const int na = ncart(la), nb = ncart(lb), nc = ncart(lc), nd = ncart(ld);
-  const int ncd = nc * nd, nab = na * nb;
+  const int ncd_all = nc * nd, nab = na * nb;
+  const int jc = (ncd_all + nsplit - 1) / nsplit, j0 = split * jc;
+  const int ncd = min(jc, ncd_all - j0);   // ket components of this block: j0 .. j0+ncd-1
+  if (ncd <= 0) return;                     // block-uniform
   const int nhL = nh_count(L), nhB = nh_count(Lb);
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
@@ -357,7 +392,7 @@ k_contract(PairView PV, QuartetView QV, int cls, int nf, int64_t pq0, int64_t q0
     int o = 0;
     for (int j = 0; j < ncd; ++j) {
       off_cd[j] = o;
-      const unsigned char *ec = c_cart[lc][j / nd], *ed = c_cart[ld][j % nd];
+      const unsigned char *ec = c_cart[lc][(j0 + j) / nd], *ed = c_cart[ld][(j0 + j) % nd];
       o += (ec[0] + ed[0] + 1) * (ec[1] + ed[1] + 1) * (ec[2] + ed[2] + 1);
     }
     off_cd[ncd] = o;
@@ -400,9 +435,8 @@ k_contract(PairView PV, QuartetView QV, int cls, int nf, int64_t pq0, int64_t q0
       if (prim_negligible(PV, pab, pcd)) continue;   // warp-uniform
       ++nproc;
       const int64_t pq = QV.pq_off[q] + (int64_t)iab * npcd + icd - pq0;
-      const double X = PV.pp_P[3 * pcd] - PV.pp_P[3 * pab];
-      const double Y = PV.pp_P[3 * pcd + 1] - PV.pp_P[3 * pab + 1];
-      const double Z = PV.pp_P[3 * pcd + 2] - PV.pp_P[3 * pab + 2];
+      const double X = pair_sep(PV.pp_P, pab, pcd, 0), Y = pair_sep(PV.pp_P, pab, pcd, 1),
+                   Z = pair_sep(PV.pp_P, pab, pcd, 2);
       // g_n = sqrt(pi^5/(p+q))/(pq) * sum over families (fixed order)
       if (lane <= L) {
         const double p = PV.pp_p[pab], qq = PV.pp_p[pcd];
@@ -413,7 +447,7 @@ k_contract(PairView PV, QuartetView QV, int cls, int nf, int64_t pq0, int64_t q0
       // E^{cd}_{t'u'v'} products of this ket primitive pair
       const double *Ecd = PV.epool + PV.pp_eoff[pcd];
       for (int j = lane; j < ncd; j += 32) {
-        const unsigned char *ec = c_cart[lc][j / nd], *ed = c_cart[ld][j % nd];
+        const unsigned char *ec = c_cart[lc][(j0 + j) / nd], *ed = c_cart[ld][(j0 + j) % nd];
         const double *ex = Ecd + (ec[0] * (ld + 1) + ed[0]) * ntcd;
         const double *ey = Ecd + n1cd + (ec[1] * (ld + 1) + ed[1]) * ntcd;
         const double *ez = Ecd + 2 * n1cd + (ec[2] * (ld + 1) + ed[2]) * ntcd;
@@ -458,7 +492,7 @@ k_contract(PairView PV, QuartetView QV, int cls, int nf, int64_t pq0, int64_t q0
       // inner (ket) sum of Eq. ii:  W[tuv][cd] += sum E^{cd}_{t'u'v'} R_{t+t',u+u',v+v'}
       for (int i = lane; i < nhB * ncd; i += 32) {
         const int bi = i / ncd, j = i - bi * ncd;
-        const int ic = j / nd, id = j - ic * nd;
+        const int ic = (j0 + j) / nd, id = (j0 + j) - ic * nd;
         const int t = c_tuv[bi][0], u = c_tuv[bi][1], v = c_tuv[bi][2];
         const unsigned char *ec = c_cart[lc][ic], *ed = c_cart[ld][id];
         const int tx = ec[0] + ed[0], ty = ec[1] + ed[1], tz = ec[2] + ed[2];
@@ -539,11 +573,15 @@ k_contract(PairView PV, QuartetView QV, int cls, int nf, int64_t pq0, int64_t q0
     __syncthreads();
   }
   double *o = out + offsets[q];
-  for (int i = tid; i < nab * ncd; i += nthr) o[i] = Oacc[i];
+  for (int i = tid; i < nab * ncd; i += nthr) {
+    const int iabc = i / ncd;
+    o[(size_t)iabc * ncd_all + j0 + (i - iabc * ncd)] = Oacc[i];
+  }
   if (flops_total && lane == 0 && nproc) {
-    // algorithmic FP64 flops per primitive quartet: Hermite recursion 2 C(L+4,4),
-    // ket step 2 nh(lab+ext) nh(lcd) ncd, bra step 2 nab nh(lab) ncd (x4 for I5)
-    const unsigned long long r = 2ull * (L + 1) * (L + 2) * (L + 3) * (L + 4) / 24;
+    // algorithmic FP64 flops per primitive quartet: Hermite recursion 2 C(L+4,4)
+    // (counted once per quartet, not per split), ket step 2 nh(lab+ext) nh(lcd)
+    // ncd, bra step 2 nab nh(lab) ncd (x4 for I5)
+    const unsigned long long r = split == 0 ? 2ull * (L + 1) * (L + 2) * (L + 3) * (L + 4) / 24 : 0ull;
     const unsigned long long ket = 2ull * nhB * nh_count(lcd) * ncd;
     const unsigned long long bra = 2ull * nab * nh_count(lab) * ncd * (cls == 5 ? 4 : 1);
     atomicAdd(flops_total, nproc * (r + ket + bra));
@@ -602,6 +640,7 @@ struct f12int_ctx {
   int64_t aux_launches = 0, contract_launches = 0;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_aux, ev_con, ev_pool;
   std::vector<int> h_nw;       // warps per contraction block, per quartet in the working order
+  std::vector<int> h_split;    // ket-component ranges (blocks) per quartet, same order
   std::vector<size_t> h_smem;  // contraction shared memory, per quartet in the working order
   std::mutex mu;
 };
@@ -1038,7 +1077,7 @@ int f12int_set_basis(f12int_ctx *ctx, int nshell, const double *centers, const i
   A(&B.d_centers, sizeof(double) * 3 * nshell);
   A(&B.d_pair_start, sizeof(int) * B.pair_start.size());
   A(&B.d_pp_p, sizeof(double) * npp);
-  A(&B.d_pp_P, sizeof(double) * 3 * npp);
+  A(&B.d_pp_P, sizeof(double) * 6 * npp);
   A(&B.d_pp_ab, sizeof(double) * 2 * npp);
   A(&B.d_pp_eoff, sizeof(int64_t) * npp);
   A(&B.d_epool, sizeof(double) * std::max<int64_t>(epos, 1));
@@ -1112,21 +1151,42 @@ static int ensure_buf(f12int_ctx *ctx, void **p, size_t *cap, size_t bytes) {
   return rc;
 }
 
-static size_t contract_smem(int la, int lb, int lc, int ld, int cls, int nw) {
+// shared memory of a contraction block with nw warps and nsplit ket ranges
+static size_t contract_smem(int la, int lb, int lc, int ld, int cls, int nw, int nsplit) {
   int ext = cls == 5 ? 2 : 0;
   int L = la + lb + lc + ld + ext;
   int nhL = nh_count(L), nhB = nh_count(la + lb + ext);
   int ncd = ncart(lc) * ncart(ld), nab = ncart(la) * ncart(lb);
+  int jc = (ncd + nsplit - 1) / nsplit;
   size_t e3ab = (size_t)ne3_count(la, lb) * (cls == 5 ? 4 : 1);
-  return sizeof(double) * ((size_t)nw * contract_warp_doubles(nhL, nhB, ncd, ne3_count(lc, ld)) +
-                           (size_t)nab * ncd + e3ab);
+  return sizeof(double) * ((size_t)nw * contract_warp_doubles(nhL, nhB, jc, ne3_chunk_max(lc, ld, jc)) +
+                           (size_t)nab * jc + e3ab);
 }
 
-// warps per contraction block: 4 unless the shared memory does not fit
-static int contract_warps(int la, int lb, int lc, int ld, int cls) {
-  for (int nw = BLOCK_CONTRACT / 32; nw > 1; nw /= 2)
-    if (contract_smem(la, lb, lc, ld, cls, nw) <= 200 * 1024) return nw;
-  return 1;
+struct ContractPlan {
+  int nw, nsplit;
+  size_t smem;
+};
+
+// Warps and ket ranges per contraction block: 4 warps, else 2, on the whole
+// ket; where neither fits in 200 KB of shared memory, the fewest ket ranges
+// that fit with 4 warps, else 2, else 1.  smem = 0 when nothing fits.
+static ContractPlan contract_plan(int la, int lb, int lc, int ld, int cls) {
+  const size_t cap = 200 * 1024;
+  for (int nw = BLOCK_CONTRACT / 32; nw > 1; nw /= 2) {
+    size_t sm = contract_smem(la, lb, lc, ld, cls, nw, 1);
+    if (sm <= cap) return ContractPlan{nw, 1, sm};
+  }
+  const int ncd = ncart(lc) * ncart(ld);
+  for (int nw = BLOCK_CONTRACT / 32; nw >= 1; nw /= 2)
+    for (int ns = 2; ns <= ncd; ++ns) {
+      const int jc = (ncd + ns - 1) / ns;
+      const int nsn = (ncd + jc - 1) / jc;   // no empty ranges
+      if (nsn != ns) continue;
+      size_t sm = contract_smem(la, lb, lc, ld, cls, nw, ns);
+      if (sm <= cap) return ContractPlan{nw, ns, sm};
+    }
+  return ContractPlan{1, 1, 0};
 }
 
 static std::pair<cudaEvent_t, cudaEvent_t> take_events(f12int_ctx *ctx) {
@@ -1201,18 +1261,19 @@ static int launch_chunk(f12int_ctx *ctx, const f12int_ctx::BasisData &B, int cls
   // contraction: quartets are ordered by decreasing shared-memory need; one
   // launch per tier of warps and shared memory (powers of two)
   for (int64_t ra = qa; ra < qb;) {
-    const int nw = ctx->h_nw[ra];
+    const int nw = ctx->h_nw[ra], nsp = ctx->h_split[ra];
     const size_t sm0 = ctx->h_smem[ra];
     int64_t rb = ra + 1;
-    while (rb < qb && ctx->h_nw[rb] == nw && 2 * ctx->h_smem[rb] > sm0) ++rb;
+    while (rb < qb && ctx->h_nw[rb] == nw && ctx->h_split[rb] == nsp && 2 * ctx->h_smem[rb] > sm0) ++rb;
     if (sm0 > 48 * 1024) CK(cudaFuncSetAttribute(k_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm0));
     std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
     if (ctx->timing) {
       ev = take_events(ctx);
       cudaEventRecord(ev.first, st);
     }
-    k_contract<<<(unsigned)(rb - ra), 32 * nw, sm0, st>>>(PV, QV, cls, nf, pqa, ra, ctx->d_part, out_dev, offsets_dev,
-                                                         ctx->d_status, ctx->timing ? ctx->d_fma + 1 : nullptr);
+    k_contract<<<(unsigned)((rb - ra) * nsp), 32 * nw, sm0, st>>>(PV, QV, cls, nf, pqa, ra, nsp, ctx->d_part, out_dev,
+                                                                 offsets_dev, ctx->d_status,
+                                                                 ctx->timing ? ctx->d_fma + 1 : nullptr);
     if (ctx->timing) {
       cudaEventRecord(ev.second, st);
       ctx->ev_con.push_back(ev);
@@ -1365,11 +1426,14 @@ int f12int_compute_class(f12int_ctx *ctx, int basis_id, int cls, const int32_t *
   for (int64_t i = 0; i < n; ++i) perm[i] = i;
   // decreasing shared-memory need (long blocks first), then by class key
   std::vector<size_t> sm0((size_t)n);
-  std::vector<int> nw0((size_t)n);
+  std::vector<int> nw0((size_t)n), sp0((size_t)n);
   for (int64_t i = 0; i < n; ++i) {
     const int k = key0[i];
-    nw0[i] = contract_warps((k >> 6) & 3, (k >> 4) & 3, (k >> 2) & 3, k & 3, cls);
-    sm0[i] = contract_smem((k >> 6) & 3, (k >> 4) & 3, (k >> 2) & 3, k & 3, cls, nw0[i]);
+    const ContractPlan pl = contract_plan((k >> 6) & 3, (k >> 4) & 3, (k >> 2) & 3, k & 3, cls);
+    if (pl.smem == 0) return F12INT_EINVAL;
+    nw0[i] = pl.nw;
+    sp0[i] = pl.nsplit;
+    sm0[i] = pl.smem;
   }
   std::stable_sort(perm.begin(), perm.end(), [&](int64_t x, int64_t y) {
     if (sm0[x] != sm0[y]) return sm0[x] > sm0[y];
@@ -1378,11 +1442,13 @@ int f12int_compute_class(f12int_ctx *ctx, int basis_id, int cls, const int32_t *
   std::vector<int32_t> hq((size_t)4 * n);
   std::vector<int64_t> ho((size_t)n);
   ctx->h_nw.resize((size_t)n);
+  ctx->h_split.resize((size_t)n);
   ctx->h_smem.resize((size_t)n);
   for (int64_t i = 0; i < n; ++i) {
     for (int k = 0; k < 4; ++k) hq[4 * i + k] = hq0[4 * perm[i] + k];
     ho[i] = ho0[perm[i]];
     ctx->h_nw[i] = nw0[perm[i]];
+    ctx->h_split[i] = sp0[perm[i]];
     ctx->h_smem[i] = sm0[perm[i]];
   }
   std::vector<int64_t> pqoff((size_t)n + 1);
@@ -1589,14 +1655,17 @@ extern "C" int f12int_compute_class_static(f12int_ctx *ctx, int basis_id, int cl
   CK(cudaStreamSynchronize(st));
   const int ns = B.nshell;
   std::vector<size_t> sm0((size_t)n);
-  std::vector<int> nw0((size_t)n), key0((size_t)n);
+  std::vector<int> nw0((size_t)n), sp0((size_t)n), key0((size_t)n);
   for (int64_t i = 0; i < n; ++i) {
     const int32_t *s = &hq0[4 * i];
     for (int k = 0; k < 4; ++k)
       if (s[k] < 0 || s[k] >= ns) return F12INT_EINVAL;
     key0[i] = (B.l[s[0]] << 6) | (B.l[s[1]] << 4) | (B.l[s[2]] << 2) | B.l[s[3]];
-    nw0[i] = contract_warps(B.l[s[0]], B.l[s[1]], B.l[s[2]], B.l[s[3]], cls);
-    sm0[i] = contract_smem(B.l[s[0]], B.l[s[1]], B.l[s[2]], B.l[s[3]], cls, nw0[i]);
+    const ContractPlan pl = contract_plan(B.l[s[0]], B.l[s[1]], B.l[s[2]], B.l[s[3]], cls);
+    if (pl.smem == 0) return F12INT_EINVAL;
+    nw0[i] = pl.nw;
+    sp0[i] = pl.nsplit;
+    sm0[i] = pl.smem;
   }
   std::vector<int64_t> perm((size_t)n);
   for (int64_t i = 0; i < n; ++i) perm[i] = i;
@@ -1606,13 +1675,14 @@ extern "C" int f12int_compute_class_static(f12int_ctx *ctx, int basis_id, int cl
   });
   std::vector<int32_t> hq((size_t)4 * n);
   std::vector<int64_t> ho((size_t)n), pqoff((size_t)n + 1);
-  std::vector<int> hnw((size_t)n);
+  std::vector<int> hnw((size_t)n), hsp((size_t)n);
   std::vector<size_t> hsm((size_t)n);
   int64_t npq = 0;
   for (int64_t i = 0; i < n; ++i) {
     for (int k = 0; k < 4; ++k) hq[4 * i + k] = hq0[4 * perm[i] + k];
     ho[i] = ho0[perm[i]];
     hnw[i] = nw0[perm[i]];
+    hsp[i] = sp0[perm[i]];
     hsm[i] = sm0[perm[i]];
     const int32_t *s = &hq[4 * i];
     pqoff[i] = npq;
@@ -1652,13 +1722,13 @@ extern "C" int f12int_compute_class_static(f12int_ctx *ctx, int basis_id, int cl
       CK(cudaGetLastError());
     }
     for (int64_t ra = qa; ra < qb;) {
-      const int nwr = hnw[ra];
+      const int nwr = hnw[ra], nspr = hsp[ra];
       const size_t smr = hsm[ra];
       int64_t rb = ra + 1;
-      while (rb < qb && hnw[rb] == nwr && 2 * hsm[rb] > smr) ++rb;
+      while (rb < qb && hnw[rb] == nwr && hsp[rb] == nspr && 2 * hsm[rb] > smr) ++rb;
       if (smr > 48 * 1024) CK(cudaFuncSetAttribute(k_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
-      k_contract<<<(unsigned)(rb - ra), 32 * nwr, smr, st>>>(PV, QV, cls, nf, pqa, ra, d_part, out_dev, d_o,
-                                                            ctx->d_status, nullptr);
+      k_contract<<<(unsigned)((rb - ra) * nspr), 32 * nwr, smr, st>>>(PV, QV, cls, nf, pqa, ra, nspr, d_part,
+                                                                     out_dev, d_o, ctx->d_status, nullptr);
       ctx->launches++;
       CK(cudaGetLastError());
       ra = rb;
