@@ -744,28 +744,22 @@ static void cart_list(int l, int (*e)[3]) {
 /* One primitive quartet.  Computes, for the given class, the block
  * out[a][b][c][d] over Cartesian components.  Returns nonzero on a
  * quadrature failure. */
-static int prim_block(const ork_kernel *K, int cls, const int l[4], const real ex[4],
-                      const real cen[4][3], real *out) {
+/* Hermite recursion and contraction of Eq. ii for one primitive quartet from
+ * its radial derivatives g_n (prefactor included).  absval != 0 evaluates the
+ * same expression with every factor replaced by its absolute value (|g_n|,
+ * |X_PQ|, |E|, no bra sign, Laplacian coefficients taken positive): the
+ * magnitude M of the terms that Eq. ii sums, which bounds to first order how
+ * far relative errors in the g_n (and rounding in the recursion and sums)
+ * can move each element. */
+static int md_contract(int cls, const int l[4], const real ex[4], const real cen[4][3], const real *g,
+                       const real Xin[3], int absval, real *out) {
   int la = l[0], lb = l[1], lc = l[2], ld = l[3];
-  int ext = cls == 5 ? 2 : 0;             /* kinetic transform raises la or lb by 2 */
+  int ext = cls == 5 ? 2 : 0;
   int lab = la + lb + ext, lcd = lc + ld;
   int L = lab + lcd;
-  if (L > ORK_MAXN || la + ext > ORK_MAXL || lb + ext > ORK_MAXL) return 2;
   real a = ex[0], b = ex[1], cc = ex[2], d = ex[3];
-  real p = a + b, q = cc + d;
-  real P[3], Q[3], X[3];
-  for (int k = 0; k < 3; ++k) {
-    P[k] = (a * cen[0][k] + b * cen[1][k]) / p;
-    Q[k] = (cc * cen[2][k] + d * cen[3][k]) / q;
-    X[k] = Q[k] - P[k];
-  }
-  real xi = p * q / (p + q);
-  real D = R_SQRT(X[0] * X[0] + X[1] * X[1] + X[2] * X[2]);
-  real gh[ORK_MAXN + 1];
-  int kcls = cls == 5 ? 3 : cls;
-  int err = radial_hat(K, kcls, xi, D, L, gh, -1);
-  const real pi = R_ACOS((real)-1);
-  real pref = R_SQRT(pi * pi * pi * pi * pi / (p + q)) / (p * q);
+  real X[3];
+  for (int k = 0; k < 3; ++k) X[k] = absval ? R_FABS(Xin[k]) : Xin[k];
 
   /* R^{(n)}_{tuv}: R^{(n)}_{000} = g_n; raising t uses
    *   R^{(n)}_{t+1,u,v} = t R^{(n+1)}_{t-1,u,v} + X R^{(n+1)}_{t,u,v},
@@ -774,7 +768,7 @@ static int prim_block(const ork_kernel *K, int cls, const int l[4], const real e
   real *R = (real *)calloc((size_t)S * S * S * S, sizeof(real));
   if (!R) return 3;
 #define RIX(n, t, u, v) R[(((size_t)(n) * S + (t)) * S + (u)) * S + (v)]
-  for (int n = 0; n <= L; ++n) RIX(n, 0, 0, 0) = pref * gh[n];
+  for (int n = 0; n <= L; ++n) RIX(n, 0, 0, 0) = absval ? R_FABS(g[n]) : g[n];
   for (int n = L - 1; n >= 0; --n)
     for (int tot = 1; tot <= L - n; ++tot)
       for (int t = tot; t >= 0; --t)
@@ -800,6 +794,14 @@ static int prim_block(const ork_kernel *K, int cls, const int l[4], const real e
   for (int k = 0; k < 3; ++k) {
     hermite_E(a, b, cen[0][k], cen[1][k], la + ext, lb + ext, Eab[k]);
     hermite_E(cc, d, cen[2][k], cen[3][k], lc, ld, Ecd[k]);
+    if (absval) {
+      for (int i = 0; i <= ORK_MAXL; ++i)
+        for (int j = 0; j <= ORK_MAXL; ++j)
+          for (int t = 0; t < EDIM; ++t) {
+            Eab[k][i][j][t] = R_FABS(Eab[k][i][j][t]);
+            Ecd[k][i][j][t] = R_FABS(Ecd[k][i][j][t]);
+          }
+    }
   }
   int ea[64][3], eb[64][3], ec[64][3], ed[64][3];
   cart_list(la, ea);
@@ -841,7 +843,7 @@ static int prim_block(const ork_kernel *K, int cls, const int l[4], const real e
         for (int v_ = 0; v_ <= (A3)[2] + (B3)[2]; ++v_) {                                      \
           real e_ = Eab[0][(A3)[0]][(B3)[0]][t_] * Eab[1][(A3)[1]][(B3)[1]][u_] *              \
                     Eab[2][(A3)[2]][(B3)[2]][v_];                                              \
-          if ((t_ + u_ + v_) & 1) e_ = -e_;                                                    \
+          if (((t_ + u_ + v_) & 1) && !absval) e_ = -e_;                                       \
           s_ += e_ * WIX(t_, u_, v_, j);                                                       \
         }                                                                                      \
     (res) = s_;                                                                                \
@@ -868,7 +870,7 @@ static int prim_block(const ork_kernel *K, int cls, const int l[4], const real e
             }
             A3[k] = i0;
             BRA(A3, eb[ib], j, tmp);
-            lapa -= 2 * a * (2 * i0 + 1) * tmp;
+            lapa += (absval ? 1 : -1) * 2 * a * (2 * i0 + 1) * tmp;
             A3[k] = i0 + 2;
             BRA(A3, eb[ib], j, tmp);
             lapa += 4 * a * a * tmp;
@@ -881,12 +883,12 @@ static int prim_block(const ork_kernel *K, int cls, const int l[4], const real e
             }
             B3[k] = j0;
             BRA(ea[ia], B3, j, tmp);
-            lapb -= 2 * b * (2 * j0 + 1) * tmp;
+            lapb += (absval ? 1 : -1) * 2 * b * (2 * j0 + 1) * tmp;
             B3[k] = j0 + 2;
             BRA(ea[ia], B3, j, tmp);
             lapb += 4 * b * b * tmp;
           }
-          val = (lapa - lapb) / 2;
+          val = absval ? (lapa + lapb) / 2 : (lapa - lapb) / 2;
         }
         out[((size_t)ia * nb + ib) * ncd + j] = val;
       }
@@ -895,8 +897,37 @@ static int prim_block(const ork_kernel *K, int cls, const int l[4], const real e
 #undef RIX
   free(W);
   free(R);
-  return err;
+  return 0;
 }
+
+static int prim_block(const ork_kernel *K, int cls, const int l[4], const real ex[4],
+                      const real cen[4][3], real *out, real *mag) {
+  int la = l[0], lb = l[1], lc = l[2], ld = l[3];
+  int ext = cls == 5 ? 2 : 0;             /* kinetic transform raises la or lb by 2 */
+  int lab = la + lb + ext, lcd = lc + ld;
+  int L = lab + lcd;
+  if (L > ORK_MAXN || la + ext > ORK_MAXL || lb + ext > ORK_MAXL) return 2;
+  real a = ex[0], b = ex[1], cc = ex[2], d = ex[3];
+  real p = a + b, q = cc + d;
+  real P[3], Q[3], X[3];
+  for (int k = 0; k < 3; ++k) {
+    P[k] = (a * cen[0][k] + b * cen[1][k]) / p;
+    Q[k] = (cc * cen[2][k] + d * cen[3][k]) / q;
+    X[k] = Q[k] - P[k];
+  }
+  real xi = p * q / (p + q);
+  real D = R_SQRT(X[0] * X[0] + X[1] * X[1] + X[2] * X[2]);
+  real gh[ORK_MAXN + 1];
+  int kcls = cls == 5 ? 3 : cls;
+  int err = radial_hat(K, kcls, xi, D, L, gh, -1);
+  const real pi = R_ACOS((real)-1);
+  real pref = R_SQRT(pi * pi * pi * pi * pi / (p + q)) / (p * q);
+  for (int n = 0; n <= L; ++n) gh[n] *= pref;
+  int e = md_contract(cls, l, ex, cen, gh, X, 0, out);
+  if (!e && mag) e = md_contract(cls, l, ex, cen, gh, X, 1, mag);
+  return e ? e : err;
+}
+
 
 /* ------------------------------------------------------------ public API -- */
 
@@ -937,7 +968,7 @@ int ork_prim_block(const ork_kernel *K, int cls, const int *l, const double *exp
   size_t nblk = (size_t)ncart(l[0]) * ncart(l[1]) * ncart(l[2]) * ncart(l[3]);
   real *blk = (real *)malloc(nblk * sizeof(real));
   if (!blk) return 3;
-  int e = prim_block(K, cls, l, ex, cen, blk);
+  int e = prim_block(K, cls, l, ex, cen, blk, NULL);
   for (size_t i = 0; i < nblk; ++i) out[i] = (double)blk[i];
   free(blk);
   return e;
@@ -951,11 +982,14 @@ int ork_prim_block(const ork_kernel *K, int cls, const int *l, const double *exp
  *   [a][b][c][d] in lexicographic Cartesian order.
  * Work is spread over primitive quartets with OpenMP; every shell quartet is
  * summed over its primitive quartets in a fixed order.  Returns the number
- * of primitive quartets whose quadrature reported non-convergence. */
+ * of primitive quartets whose quadrature reported non-convergence.
+ * mag (may be NULL) receives, in the same layout, the magnitude of the terms
+ * summed for each element: sum over primitive quartets of |coefficient
+ * product| times the absolute-value evaluation of Eq. ii (see md_contract). */
 int64_t ork_shell_blocks(const ork_kernel *K, int cls, const double *centers, const int *l,
                          const int *nprim, const int *prim_off, const double *exps,
                          const double *coefs, int64_t nq, const int32_t *quartets,
-                         const int64_t *offsets, double *out, int nthreads) {
+                         const int64_t *offsets, double *out, double *mag, int nthreads) {
   if (!gl_ready) gl_build();
   int64_t nbad = 0;
   for (int64_t q0 = 0; q0 < nq;) {
@@ -984,6 +1018,7 @@ int64_t ork_shell_blocks(const ork_kernel *K, int cls, const double *centers, co
       }
     }
     real *buf = (real *)malloc(sizeof(real) * (tot ? tot : 1));
+    real *mbuf = mag ? (real *)malloc(sizeof(real) * (tot ? tot : 1)) : NULL;
     int64_t bad = 0;
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 1) reduction(+ : bad) num_threads(nthreads > 0 ? nthreads : omp_get_max_threads())
@@ -1005,10 +1040,13 @@ int64_t ork_shell_blocks(const ork_kernel *K, int cls, const double *centers, co
         for (int m = 0; m < 3; ++m) cen[k][m] = centers[3 * s[k] + m];
       }
       real *blk = buf + task_off[i];
-      int e = prim_block(K, cls, ll, ex, cen, blk);
+      real *mblk = mbuf ? mbuf + task_off[i] : NULL;
+      int e = prim_block(K, cls, ll, ex, cen, blk, mblk);
       if (e) ++bad;
       size_t nb = (size_t)ncart(ll[0]) * ncart(ll[1]) * ncart(ll[2]) * ncart(ll[3]);
       for (size_t j = 0; j < nb; ++j) blk[j] *= coef;
+      if (mblk)
+        for (size_t j = 0; j < nb; ++j) mblk[j] *= R_FABS(coef);
     }
     nbad += bad;
     for (int64_t i = 0; i < ntask;) {
@@ -1019,10 +1057,16 @@ int64_t ork_shell_blocks(const ork_kernel *K, int cls, const double *centers, co
         real acc = 0;
         for (int64_t k = i; k < ntask && task_q[k] == q; ++k) acc += buf[task_off[k] + j];
         out[offsets[q] + j] = (double)acc;
+        if (mbuf) {
+          real macc = 0;
+          for (int64_t k = i; k < ntask && task_q[k] == q; ++k) macc += mbuf[task_off[k] + j];
+          mag[offsets[q] + j] = (double)macc;
+        }
       }
       while (i < ntask && task_q[i] == q) ++i;
     }
     free(buf);
+    free(mbuf);
     free(task_q);
     free(task_p);
     free(task_off);

@@ -74,7 +74,7 @@ def lib():
             L.ork_prim_block.restype = ctypes.c_int
             L.ork_shell_blocks.argtypes = [ctypes.POINTER(OrkKernel), ctypes.c_int, dp, ip, ip, ip, dp, dp,
                                            ctypes.c_int64, ctypes.POINTER(ctypes.c_int32),
-                                           ctypes.POINTER(ctypes.c_int64), dp, ctypes.c_int]
+                                           ctypes.POINTER(ctypes.c_int64), dp, dp, ctypes.c_int]
             L.ork_shell_blocks.restype = ctypes.c_int64
             L.ork_jhat.argtypes = [ctypes.c_double, ctypes.c_int, dp]
             L.ork_jhat.restype = ctypes.c_int
@@ -155,12 +155,15 @@ def prim_block(kern: OrkKernel, cls: int, ls, exps, centers) -> np.ndarray:
     return out.reshape(shape)
 
 
-def shell_blocks(kern: OrkKernel, cls: int, basis, quartets, offsets=None, nthreads: int = 0):
+def shell_blocks(kern: OrkKernel, cls: int, basis, quartets, offsets=None, nthreads: int = 0,
+                 with_mag: bool = False):
     """Contracted blocks for a list of shell quartets.
 
     ``basis`` has arrays centers[nshell,3], l[nshell], nprim[nshell],
     exps[total], coefs[total] (attribute or key access).  Returns
-    (out, offsets) with each block stored row-major [a][b][c][d].
+    (out, offsets) with each block stored row-major [a][b][c][d]; with
+    ``with_mag`` also the magnitude of the terms each element sums,
+    (out, offsets, mag).
     """
     get = (lambda k: basis[k]) if isinstance(basis, dict) else (lambda k: getattr(basis, k))
     centers = np.ascontiguousarray(get("centers"), dtype=np.float64)
@@ -176,10 +179,14 @@ def shell_blocks(kern: OrkKernel, cls: int, basis, quartets, offsets=None, nthre
     offsets = np.ascontiguousarray(offsets, dtype=np.int64)
     total = int(offsets[-1] + sizes[-1]) if len(q) else 0
     out = np.zeros(max(total, 1))
+    mag = np.zeros(max(total, 1)) if with_mag else None
     nbad = lib().ork_shell_blocks(ctypes.byref(kern), cls, _dp(centers), _ip(l), _ip(nprim), _ip(prim_off),
                                   _dp(exps), _dp(coefs), len(q),
                                   q.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
-                                  offsets.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _dp(out), nthreads)
+                                  offsets.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _dp(out),
+                                  _dp(mag) if with_mag else None, nthreads)
     if nbad:
         raise RuntimeError("oracle quadrature did not converge for %d primitive quartets" % nbad)
+    if with_mag:
+        return out[:total], offsets, mag[:total]
     return out[:total], offsets

@@ -443,3 +443,35 @@ def test_contracted_blocks_sum_primitives():
                     acc = acc + co * O.prim_block(K, 3, ls, [basis.exps[i] for i in idx],
                                                   [basis.centers[s] for s in q[0]])
     np.testing.assert_allclose(out.reshape(acc.shape), acc, rtol=1e-13, atol=0)
+
+
+# --------------------------------------------------- term magnitude block --
+
+@pytest.mark.parametrize("cls", [1, 3, 5, 6])
+def test_term_magnitude_bounds_block(cls):
+    """The magnitude block (absolute-value evaluation of the sum of Eq. ii)
+    bounds every element: |I| <= M (triangle inequality), and M is unchanged
+    when the sign of a contraction coefficient flips."""
+    basis = M.twelve_atom_spd(2)
+    q = np.array([[5, 3, 1, 0], [7, 7, 2, 1], [11, 4, 9, 6]], dtype=np.int32)
+    K = O.factor_kernel(P0)
+    out, off, mag = O.shell_blocks(K, cls, basis, q, with_mag=True)
+    assert np.all(mag >= np.abs(out) * (1 - 1e-14))
+    assert np.all(mag[out != 0] > 0)
+    flipped = M.Basis(**{**basis.__dict__, "coefs": -basis.coefs})
+    out2, _, mag2 = O.shell_blocks(K, cls, flipped, q, with_mag=True)
+    np.testing.assert_allclose(mag2, mag, rtol=1e-14)
+    np.testing.assert_allclose(out2, out, rtol=1e-14)   # four coefficients: sign cancels
+
+
+def test_term_magnitude_single_term():
+    """An (ss|ss) primitive block has one term, so M = |I|; with cancelling
+    contraction coefficients M is the sum of the primitive magnitudes while I
+    shrinks."""
+    K = O.factor_kernel(P0)
+    basis = M.Basis(name="ss", centers=np.array([[0.0, 0.0, 0.0], [0.0, 0.0, 1.4]]), l=np.array([0, 0]),
+                    nprim=np.array([2, 1]), exps=np.array([1.2, 1.19, 0.8]), coefs=np.array([1.0, -1.0, 1.0]))
+    q = np.array([[0, 0, 1, 1], [1, 1, 1, 1]], dtype=np.int32)
+    out, off, mag = O.shell_blocks(K, 3, basis, q, with_mag=True)
+    assert mag[1] == pytest.approx(abs(out[1]), rel=1e-15)
+    assert abs(out[0]) < 0.05 * mag[0]
