@@ -152,11 +152,60 @@ int f12int_aux(f12int_ctx *ctx, int cls, int64_t npts, const double *xi_dev, con
  *     call's contents (the call clears what must start at zero).  Calls whose
  *     work overlaps on the GPU (other streams, other contexts of the same
  *     device) race on it and must be serialised by the caller.
- *   - Errors: F12INT_EINVAL when the quartet list (about 2M quartets at most)
+ *   - Errors: F12INT_EINVAL when the quartet list (about 1.6M quartets at most)
  *     or one shell quartet's primitive work does not fit in the array; the
  *     other errors as for f12int_compute_class. */
 int f12int_compute_class_static(f12int_ctx *ctx, int basis_id, int cls, const int32_t *quartets_dev,
                                 int64_t n, double *out_dev, const int64_t *offsets_dev, void *cuda_stream);
+
+/* ---------------------------------------------------------------------------
+ * Batched requests.  A request asks for the blocks of one or more classes over
+ * one list of shell quartets of a basis (the integrals of
+ * f12int_compute_class).  f12int_submit copies the request and queues it; a
+ * worker thread of the context merges the pending requests of any bases into
+ * batches and runs each batch as one replay of a captured CUDA graph on the
+ * context's own batch stream.  The paper has no counterpart: this is the
+ * scheduling layer for many small requests.
+ */
+typedef struct {
+  int64_t n_quartets;          /* number of shell quartets (>= 0)                        */
+  const int32_t *quartets;     /* host [n_quartets][4] shell indices; copied by submit   */
+  uint32_t class_mask;         /* bit c-1 set: compute class c (1..6); at least one bit  */
+  int precision;               /* 0: FP64 (the only value accepted)                      */
+  double schwarz_thresh;       /* > 0: quartets whose shell-pair bound product (as in
+                                  f12int_screen) is below it get zero blocks; 0: none     */
+  double *out_dev;             /* device output, FP64, caller-owned; must stay valid and
+                                  untouched until the request is done                    */
+  const int64_t *offsets;      /* host [nclass][n_quartets] element offsets into out_dev,
+                                  one row per requested class in increasing class order;
+                                  copied by submit                                       */
+} f12int_request;
+
+/* Queue a request; *ticket identifies it in f12int_poll.  The first request
+ * of a (basis, class) computes that class's primitive and shell-pair bounds
+ * synchronously; the first request of the context allocates the batch
+ * buffers (see f12int_batch_limits) and starts the worker.
+ * Errors: F12INT_EINVAL for bad arguments (shell index out of range, empty or
+ * unknown class mask, precision != 0), F12INT_ENOTREADY without basis or
+ * factor, F12INT_ENOMEM when the request alone exceeds one batch (split it). */
+int f12int_submit(f12int_ctx *ctx, int basis_id, const f12int_request *req, uint64_t *ticket);
+
+/* Wait at most timeout_us microseconds (0: do not wait) for a request.
+ * *done = 1 once it has finished; the call then returns the request's status
+ * (F12INT_OK, or F12INT_EDEVICE if a device-side check of its batch failed)
+ * and forgets the ticket.  *done = 0 and F12INT_OK while it is queued or
+ * running.  F12INT_EINVAL for an unknown or already reported ticket. */
+int f12int_poll(f12int_ctx *ctx, uint64_t ticket, int64_t timeout_us, int *done);
+
+/* Capacity of one batch, per class: max_quartets shell quartets and
+ * max_items auxiliary work items (primitive quartets times the kernel's term
+ * families).  Defaults 2^19 and 2^24 (about 2.2 GB of device buffers and
+ * 0.4 GB of pinned staging).  Only before the first f12int_submit. */
+int f12int_batch_limits(f12int_ctx *ctx, int64_t max_quartets, int64_t max_items);
+
+/* stats[0] batches launched, stats[1] requests finished, stats[2] requests
+ * waiting for a batch. */
+int f12int_batch_stats(f12int_ctx *ctx, int64_t *stats);
 
 /* Number of kernel launches the context has issued so far (monotonic). */
 int64_t f12int_launch_count(const f12int_ctx *ctx);

@@ -1,0 +1,624 @@
+// engine.cuh -- batched execution of requests (f12int_submit / f12int_poll).
+//
+// Included by f12int.cu after the kernels and the context definition.
+//
+// A request asks for the blocks of some classes over one quartet list of one
+// basis.  A worker thread merges the pending requests -- of any bases and any
+// mix of (la, lb, lc, ld) -- into a batch, writes the batch's lists to pinned
+// staging memory, copies them to fixed device buffers and replays one
+// captured CUDA graph.  The graph holds, for every class, the four passes of
+// the auxiliary stage and one contraction launch per shared-memory tier, all
+// persistent (grid-stride over counts read from device memory), so the same
+// graph serves every batch.  Two staging buffers let the host build batch
+// k+1 while batch k runs.  The method is that of f12int_compute_class; only
+// the scheduling differs.
+
+namespace {
+
+constexpr int kTiers = 4;
+constexpr size_t kTierCap[kTiers] = {32 * 1024, 64 * 1024, 112 * 1024, 200 * 1024};
+constexpr int kTierWarps = 4;
+
+struct EngineReq {
+  uint64_t ticket = 0;
+  int basis = 0;
+  const f12int_ctx::BasisData *B = nullptr;   // stable: the deque never moves its elements
+  uint32_t mask = 0;
+  double thresh = 0.0;
+  double *out = nullptr;
+  std::vector<int32_t> q;
+  std::vector<int64_t> off;       // [nclass][n]
+  int64_t quartets[7] = {0};      // quartets per class (before screening)
+  int64_t items[7] = {0};         // work items per class (before screening)
+};
+
+struct TicketState {
+  bool done = false;
+  int rc = F12INT_OK;
+  int batch = -1;                 // staging buffer of the batch that runs it
+};
+
+// Contraction plan of a quartet in a batch: tier and ket ranges at 4 warps.
+struct BatchPlan {
+  int tier, nsplit;
+};
+
+static bool batch_plan(int la, int lb, int lc, int ld, int cls, BatchPlan *bp) {
+  const int ncd = ncart(lc) * ncart(ld);
+  for (int ns = 1; ns <= ncd; ++ns) {
+    const int jc = (ncd + ns - 1) / ns;
+    if ((ncd + jc - 1) / jc != ns) continue;   // no empty ranges
+    const size_t sm = contract_smem(la, lb, lc, ld, cls, kTierWarps, ns);
+    for (int t = 0; t < kTiers; ++t)
+      if (sm <= kTierCap[t]) {
+        bp->tier = t;
+        bp->nsplit = ns;
+        return true;
+      }
+  }
+  return false;
+}
+
+// Per-class lists of a batch; the same layout on the device and in each
+// pinned staging buffer.
+struct ClassLists {
+  int32_t *quartets = nullptr;    // [qcap][4]
+  int64_t *pq_off = nullptr;      // [qcap + 1]
+  int64_t *offsets = nullptr;     // [qcap]
+  int32_t *qslot = nullptr;       // [qcap]
+  CTask *tasks = nullptr;         // [tcap], tier after tier
+  int64_t *counts = nullptr;      // n, npq, then (begin, end) of the tasks of each tier
+  PairView *views = nullptr;      // [scap]
+  double **outs = nullptr;        // [scap]
+};
+constexpr int kCounts = 2 + 2 * kTiers;
+
+struct Engine {
+  // limits
+  int64_t qcap = (int64_t)1 << 19;   // quartets per class per batch
+  int64_t icap = (int64_t)1 << 24;   // work items per class per batch
+  int64_t tcap = 0;                   // contraction tasks per class per batch
+  int64_t scap = 4096;                // requests per batch
+  int64_t zcap = 0;                   // zero-filled blocks per batch
+  bool ready = false;
+  // device buffers
+  ClassLists dev[7];
+  double **zero_dst = nullptr;
+  int64_t *zero_len = nullptr, *zero_count = nullptr;
+  int *keys = nullptr;
+  unsigned *order = nullptr, *hist = nullptr, *status = nullptr;
+  double *part = nullptr;
+  size_t bytes = 0;
+  // staging (pinned), two buffers
+  ClassLists stage[2][7];
+  double **zstage_dst[2] = {nullptr, nullptr};
+  int64_t *zstage_len[2] = {nullptr, nullptr}, *zstage_count[2] = {nullptr, nullptr};
+  unsigned *stage_status[2] = {nullptr, nullptr};
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  std::vector<uint64_t> inflight[2];
+  // graph
+  cudaStream_t stream = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool graph_dirty = true;
+  int items_blocks = 0, classify_blocks = 0, tier_blocks[kTiers] = {0};
+  // queue
+  std::thread worker;
+  std::mutex mu;
+  std::condition_variable cv;
+  bool stop = false;
+  std::deque<EngineReq *> pending;
+  std::unordered_map<uint64_t, TicketState> tickets;
+  uint64_t next_ticket = 1;
+  int cur = 0;
+  int64_t batches = 0, requests_done = 0;
+};
+
+template <class T>
+static int engine_alloc(f12int_ctx *ctx, Engine &E, T **p, size_t n) {
+  int rc = dalloc(ctx, p, sizeof(T) * std::max<size_t>(n, 1));
+  if (rc == F12INT_OK) E.bytes += sizeof(T) * std::max<size_t>(n, 1);
+  return rc;
+}
+
+template <class T>
+static int stage_alloc(T **p, size_t n) {
+  return cudaHostAlloc((void **)p, sizeof(T) * std::max<size_t>(n, 1), cudaHostAllocDefault) == cudaSuccess
+             ? F12INT_OK
+             : F12INT_ENOMEM;
+}
+
+static int lists_alloc_dev(f12int_ctx *ctx, Engine &E, ClassLists &L) {
+  int rc = engine_alloc(ctx, E, &L.quartets, 4 * (size_t)E.qcap);
+  if (rc == F12INT_OK) rc = engine_alloc(ctx, E, &L.pq_off, (size_t)E.qcap + 1);
+  if (rc == F12INT_OK) rc = engine_alloc(ctx, E, &L.offsets, (size_t)E.qcap);
+  if (rc == F12INT_OK) rc = engine_alloc(ctx, E, &L.qslot, (size_t)E.qcap);
+  if (rc == F12INT_OK) rc = engine_alloc(ctx, E, &L.tasks, (size_t)E.tcap);
+  if (rc == F12INT_OK) rc = engine_alloc(ctx, E, &L.counts, (size_t)kCounts);
+  if (rc == F12INT_OK) rc = engine_alloc(ctx, E, &L.views, (size_t)E.scap);
+  if (rc == F12INT_OK) rc = engine_alloc(ctx, E, &L.outs, (size_t)E.scap);
+  return rc;
+}
+
+static int lists_alloc_host(Engine &E, ClassLists &L) {
+  int rc = stage_alloc(&L.quartets, 4 * (size_t)E.qcap);
+  if (rc == F12INT_OK) rc = stage_alloc(&L.pq_off, (size_t)E.qcap + 1);
+  if (rc == F12INT_OK) rc = stage_alloc(&L.offsets, (size_t)E.qcap);
+  if (rc == F12INT_OK) rc = stage_alloc(&L.qslot, (size_t)E.qcap);
+  if (rc == F12INT_OK) rc = stage_alloc(&L.tasks, (size_t)E.tcap);
+  if (rc == F12INT_OK) rc = stage_alloc(&L.counts, (size_t)kCounts);
+  if (rc == F12INT_OK) rc = stage_alloc(&L.views, (size_t)E.scap);
+  if (rc == F12INT_OK) rc = stage_alloc(&L.outs, (size_t)E.scap);
+  return rc;
+}
+
+static void lists_free(ClassLists &L, bool host) {
+  void *ps[] = {L.quartets, L.pq_off, L.offsets, L.qslot, L.tasks, L.counts, L.views, L.outs};
+  for (void *p : ps)
+    if (p) host ? cudaFreeHost(p) : cudaFree(p);
+  L = ClassLists{};
+}
+
+// Zero-fill the blocks of screened-out quartets.
+__global__ void k_zero_blocks(double *const *dst, const int64_t *len, const int64_t *count) {
+  const int64_t n = *count;
+  for (int64_t b = blockIdx.x; b < n; b += gridDim.x) {
+    double *d = dst[b];
+    for (int64_t i = threadIdx.x; i < len[b]; i += blockDim.x) d[i] = 0.0;
+  }
+}
+
+// Capture the launch sequence of one batch (every class, every tier).
+static int engine_capture(f12int_ctx *ctx, Engine &E) {
+  if (E.exec) {
+    cudaGraphExecDestroy(E.exec);
+    E.exec = nullptr;
+  }
+  for (int t = 0; t < kTiers; ++t)
+    if (kTierCap[t] > 48 * 1024)
+      CK(cudaFuncSetAttribute(k_contract<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTierCap[t]));
+  cudaStream_t cs = nullptr;
+  CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  const PairView none{};
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    k_zero_blocks<<<4 * 152, 128, 0, cs>>>(E.zero_dst, E.zero_len, E.zero_count);
+    for (int cls = 1; cls <= 6; ++cls) {
+      const int kcls = cls == 5 ? 3 : cls;
+      const int nf = ctx->tables.nfam[kcls];
+      const ClassLists &L = E.dev[cls];
+      QuartetView QV{L.quartets, L.pq_off, 0, L.counts, L.qslot, L.views, L.outs};
+      cudaMemsetAsync(E.hist, 0, sizeof(unsigned) * kNKeys, cs);
+      k_items_classify<true><<<E.classify_blocks, BLOCK_AUX, 0, cs>>>(ctx->tables, none, QV, cls, 0, 0, E.keys,
+                                                                      E.hist);
+      k_items_scan<<<1, 1024, 0, cs>>>(E.hist, kNKeys);
+      k_items_scatter<<<E.classify_blocks, BLOCK_AUX, 0, cs>>>(QV, nf, 0, E.keys, E.hist, 0, E.order);
+      k_items_eval<true><<<E.items_blocks, BLOCK_AUX, 0, cs>>>(ctx->tables, none, QV, cls, 0, 0, E.order, E.part,
+                                                               E.status, nullptr);
+      for (int t = 0; t < kTiers; ++t)
+        k_contract<true><<<E.tier_blocks[t], 32 * kTierWarps, kTierCap[t], cs>>>(
+            none, QV, cls, nf, 0, L.tasks, 0, L.counts + 2 + 2 * t, E.part, nullptr, L.offsets, E.status, nullptr);
+    }
+    e = cudaStreamEndCapture(cs, &g);
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&E.exec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess) return cuda_fail(e);
+  E.graph_dirty = false;
+  return F12INT_OK;
+}
+
+// Buffers, streams and launch shapes; called once, at the first submit.
+static int engine_init(f12int_ctx *ctx, Engine &E) {
+  E.tcap = 2 * E.qcap;
+  E.zcap = 6 * E.qcap;
+  int rc = F12INT_OK;
+  for (int c = 1; c <= 6 && rc == F12INT_OK; ++c) rc = lists_alloc_dev(ctx, E, E.dev[c]);
+  if (rc == F12INT_OK) rc = engine_alloc(ctx, E, &E.zero_dst, (size_t)E.zcap);
+  if (rc == F12INT_OK) rc = engine_alloc(ctx, E, &E.zero_len, (size_t)E.zcap);
+  if (rc == F12INT_OK) rc = engine_alloc(ctx, E, &E.zero_count, 1);
+  if (rc == F12INT_OK) rc = engine_alloc(ctx, E, &E.keys, (size_t)E.icap);
+  if (rc == F12INT_OK) rc = engine_alloc(ctx, E, &E.order, (size_t)E.icap);
+  if (rc == F12INT_OK) rc = engine_alloc(ctx, E, &E.part, (size_t)E.icap * (LAUX + 1));
+  if (rc == F12INT_OK) rc = engine_alloc(ctx, E, &E.hist, (size_t)kNKeys);
+  if (rc == F12INT_OK) rc = engine_alloc(ctx, E, &E.status, 1);
+  for (int b = 0; b < 2 && rc == F12INT_OK; ++b) {
+    for (int c = 1; c <= 6 && rc == F12INT_OK; ++c) rc = lists_alloc_host(E, E.stage[b][c]);
+    if (rc == F12INT_OK) rc = stage_alloc(&E.zstage_dst[b], (size_t)E.zcap);
+    if (rc == F12INT_OK) rc = stage_alloc(&E.zstage_len[b], (size_t)E.zcap);
+    if (rc == F12INT_OK) rc = stage_alloc(&E.zstage_count[b], 1);
+    if (rc == F12INT_OK) rc = stage_alloc(&E.stage_status[b], 1);
+    if (rc == F12INT_OK && cudaEventCreateWithFlags(&E.ev[b], cudaEventDisableTiming) != cudaSuccess)
+      rc = F12INT_ECUDA;
+  }
+  if (rc == F12INT_OK && cudaStreamCreateWithFlags(&E.stream, cudaStreamNonBlocking) != cudaSuccess)
+    rc = F12INT_ECUDA;
+  if (rc == F12INT_OK && cudaMemset(E.status, 0, sizeof(unsigned)) != cudaSuccess) rc = F12INT_ECUDA;
+  if (rc != F12INT_OK) return rc;
+  // persistent launch shapes: resident blocks per SM from registers and shared memory
+  int nsm = 0;
+  CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
+  int per = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_items_eval<true>, BLOCK_AUX, 0));
+  E.items_blocks = nsm * std::max(per, 1);
+  E.classify_blocks = nsm * 8;
+  for (int t = 0; t < kTiers; ++t) {
+    if (kTierCap[t] > 48 * 1024)
+      CK(cudaFuncSetAttribute(k_contract<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTierCap[t]));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_contract<true>, 32 * kTierWarps, kTierCap[t]));
+    E.tier_blocks[t] = nsm * std::max(per, 1);
+  }
+  E.ready = true;
+  return F12INT_OK;
+}
+
+// Mark the requests of the batch in staging buffer b done (the batch's event
+// has completed).  Caller holds E.mu.
+static void engine_finish_batch(Engine &E, int b) {
+  const int rc = *E.stage_status[b] ? F12INT_EDEVICE : F12INT_OK;
+  for (uint64_t t : E.inflight[b]) {
+    auto it = E.tickets.find(t);
+    if (it != E.tickets.end()) {
+      it->second.done = true;
+      it->second.rc = rc;
+      it->second.batch = -1;
+    }
+    ++E.requests_done;
+  }
+  E.inflight[b].clear();
+}
+
+// Build the lists of one batch in staging buffer b and launch it.
+static int engine_launch(f12int_ctx *ctx, Engine &E, const std::vector<EngineReq *> &batch, int b) {
+  struct Item {
+    int64_t src;      // index into the flat per-class arrays below
+    int tier, nsplit, key;
+  };
+  int64_t nzero = 0;
+  for (int cls = 1; cls <= 6; ++cls) {
+    ClassLists &S = E.stage[b][cls];
+    int64_t n = 0;
+    std::vector<Item> items;
+    // gather the class's quartets of every request
+    for (size_t r = 0; r < batch.size(); ++r) {
+      const EngineReq &R = *batch[r];
+      if (!(R.mask & (1u << (cls - 1)))) continue;
+      int row = 0;
+      for (int c = 1; c < cls; ++c) row += (R.mask >> (c - 1)) & 1;
+      const f12int_ctx::BasisData &B = *R.B;
+      const int nq = (int)(R.q.size() / 4);
+      const std::vector<double> &bound = B.pair_bound[cls == 5 ? 3 : cls];
+      for (int i = 0; i < nq; ++i) {
+        const int32_t *s = &R.q[4 * (size_t)i];
+        const int64_t off = R.off[(size_t)row * nq + i];
+        const int la = B.l[s[0]], lb = B.l[s[1]], lc = B.l[s[2]], ld = B.l[s[3]];
+        if (R.thresh > 0.0 &&
+            bound[(size_t)s[0] * B.nshell + s[1]] * bound[(size_t)s[2] * B.nshell + s[3]] < R.thresh) {
+          E.zstage_dst[b][nzero] = R.out + off;
+          E.zstage_len[b][nzero] = (int64_t)ncart(la) * ncart(lb) * ncart(lc) * ncart(ld);
+          ++nzero;
+          continue;
+        }
+        BatchPlan bp{};
+        batch_plan(la, lb, lc, ld, cls, &bp);   // checked at submit
+        for (int k = 0; k < 4; ++k) S.quartets[4 * n + k] = s[k];
+        S.offsets[n] = off;
+        S.qslot[n] = (int32_t)r;
+        items.push_back(Item{n, bp.tier, bp.nsplit, (la << 6) | (lb << 4) | (lc << 2) | ld});
+        ++n;
+      }
+      S.views[r] = PairView{B.d_pair_start, B.d_pp_p, B.d_pp_P, B.d_pp_ab, B.d_pp_eoff, B.d_epool, B.d_shell_l,
+                            B.nshell, B.prim_screen ? B.d_qprim[cls] : nullptr};
+      S.outs[r] = R.out;
+    }
+    // working order: by tier, then angular-momentum key; permute the lists
+    std::stable_sort(items.begin(), items.end(), [](const Item &x, const Item &y) {
+      if (x.tier != y.tier) return x.tier < y.tier;
+      return x.key < y.key;
+    });
+    std::vector<int32_t> q2((size_t)4 * n), sl2((size_t)n);
+    std::vector<int64_t> of2((size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+      const int64_t j = items[i].src;
+      for (int k = 0; k < 4; ++k) q2[4 * i + k] = S.quartets[4 * j + k];
+      of2[i] = S.offsets[j];
+      sl2[i] = S.qslot[j];
+    }
+    int64_t npq = 0, nt = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      for (int k = 0; k < 4; ++k) S.quartets[4 * i + k] = q2[4 * i + k];
+      S.offsets[i] = of2[i];
+      S.qslot[i] = sl2[i];
+      const f12int_ctx::BasisData &B = *batch[sl2[i]]->B;
+      S.pq_off[i] = npq;
+      npq += (int64_t)B.nprim[q2[4 * i]] * B.nprim[q2[4 * i + 1]] * B.nprim[q2[4 * i + 2]] * B.nprim[q2[4 * i + 3]];
+    }
+    S.pq_off[n] = npq;
+    S.counts[0] = n;
+    S.counts[1] = npq;
+    int64_t i = 0;
+    for (int t = 0; t < kTiers; ++t) {
+      S.counts[2 + 2 * t] = nt;
+      for (; i < n && items[i].tier == t; ++i)
+        for (int sp = 0; sp < items[i].nsplit; ++sp) S.tasks[nt++] = CTask{(int32_t)i, (int16_t)sp, (int16_t)items[i].nsplit};
+      S.counts[3 + 2 * t] = nt;
+    }
+    // copy what this batch uses
+    const ClassLists &D = E.dev[cls];
+    cudaStream_t st = E.stream;
+    const size_t ns = batch.size();
+    CK(cudaMemcpyAsync(D.counts, S.counts, sizeof(int64_t) * kCounts, cudaMemcpyHostToDevice, st));
+    if (n > 0) {
+      CK(cudaMemcpyAsync(D.quartets, S.quartets, sizeof(int32_t) * 4 * n, cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(D.pq_off, S.pq_off, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(D.offsets, S.offsets, sizeof(int64_t) * n, cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(D.qslot, S.qslot, sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(D.tasks, S.tasks, sizeof(CTask) * nt, cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(D.views, S.views, sizeof(PairView) * ns, cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(D.outs, S.outs, sizeof(double *) * ns, cudaMemcpyHostToDevice, st));
+    }
+  }
+  *E.zstage_count[b] = nzero;
+  cudaStream_t st = E.stream;
+  CK(cudaMemcpyAsync(E.zero_count, E.zstage_count[b], sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  if (nzero > 0) {
+    CK(cudaMemcpyAsync(E.zero_dst, E.zstage_dst[b], sizeof(double *) * nzero, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(E.zero_len, E.zstage_len[b], sizeof(int64_t) * nzero, cudaMemcpyHostToDevice, st));
+  }
+  CK(cudaGraphLaunch(E.exec, st));
+  CK(cudaMemcpyAsync(E.stage_status[b], E.status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemsetAsync(E.status, 0, sizeof(unsigned), st));
+  CK(cudaEventRecord(E.ev[b], st));
+  return F12INT_OK;
+}
+
+static void engine_worker(f12int_ctx *ctx, Engine *Ep) {
+  Engine &E = *Ep;
+  cudaSetDevice(ctx->device);
+  std::unique_lock<std::mutex> lk(E.mu);
+  for (;;) {
+    E.cv.wait(lk, [&] { return E.stop || !E.pending.empty(); });
+    if (E.pending.empty()) break;   // stop requested and nothing left
+    const int b = E.cur;
+    E.cur ^= 1;
+    // staging buffer b is free once the batch that used it has finished
+    if (!E.inflight[b].empty()) {
+      lk.unlock();
+      cudaEventSynchronize(E.ev[b]);
+      lk.lock();
+      engine_finish_batch(E, b);
+    }
+    // admission: take requests while every class fits the batch limits
+    std::vector<EngineReq *> batch;
+    int64_t nq[7] = {0}, ni[7] = {0};
+    while (!E.pending.empty() && (int64_t)batch.size() < E.scap) {
+      EngineReq *R = E.pending.front();
+      bool fits = true;
+      for (int c = 1; c <= 6; ++c)
+        if (nq[c] + R->quartets[c] > E.qcap || ni[c] + R->items[c] > E.icap) fits = false;
+      if (!fits && !batch.empty()) break;
+      for (int c = 1; c <= 6; ++c) {
+        nq[c] += R->quartets[c];
+        ni[c] += R->items[c];
+      }
+      batch.push_back(R);
+      E.pending.pop_front();
+    }
+    int rc = F12INT_OK;
+    if (E.graph_dirty) rc = engine_capture(ctx, E);
+    for (EngineReq *R : batch) E.tickets[R->ticket].batch = b;
+    lk.unlock();
+    if (rc == F12INT_OK) rc = engine_launch(ctx, E, batch, b);
+    lk.lock();
+    for (EngineReq *R : batch) {
+      if (rc == F12INT_OK) {
+        E.inflight[b].push_back(R->ticket);
+      } else {
+        TicketState &T = E.tickets[R->ticket];
+        T.done = true;
+        T.rc = rc;
+        T.batch = -1;
+      }
+      delete R;
+    }
+    ++E.batches;
+  }
+}
+
+}  // namespace
+
+static void engine_shutdown(f12int_ctx *ctx) {
+  Engine *E = ctx->engine;
+  if (!E) return;
+  {
+    std::lock_guard<std::mutex> lk(E->mu);
+    E->stop = true;
+  }
+  E->cv.notify_all();
+  if (E->worker.joinable()) E->worker.join();
+  if (E->stream) cudaStreamSynchronize(E->stream);
+  for (int c = 1; c <= 6; ++c) lists_free(E->dev[c], false);
+  for (int b = 0; b < 2; ++b) {
+    for (int c = 1; c <= 6; ++c) lists_free(E->stage[b][c], true);
+    cudaFreeHost(E->zstage_dst[b]);
+    cudaFreeHost(E->zstage_len[b]);
+    cudaFreeHost(E->zstage_count[b]);
+    cudaFreeHost(E->stage_status[b]);
+    if (E->ev[b]) cudaEventDestroy(E->ev[b]);
+  }
+  void *ds[] = {E->zero_dst, E->zero_len, E->zero_count, E->keys, E->order, E->part, E->hist, E->status};
+  for (void *p : ds)
+    if (p) cudaFree(p);
+  ctx->used -= std::min(ctx->used, E->bytes);
+  if (E->exec) cudaGraphExecDestroy(E->exec);
+  if (E->stream) cudaStreamDestroy(E->stream);
+  for (EngineReq *R : E->pending) delete R;
+  delete E;
+  ctx->engine = nullptr;
+}
+
+// No request queued or running.
+static bool engine_idle(f12int_ctx *ctx) {
+  Engine *E = ctx->engine;
+  if (!E) return true;
+  std::lock_guard<std::mutex> lk(E->mu);
+  for (const auto &kv : E->tickets)
+    if (!kv.second.done) {
+      const int b = kv.second.batch;
+      if (b < 0 || cudaEventQuery(E->ev[b]) != cudaSuccess) return false;
+    }
+  return E->pending.empty();
+}
+
+// The captured graph holds the factor's tables by value.
+static void engine_factor_changed(f12int_ctx *ctx) {
+  if (ctx->engine) {
+    std::lock_guard<std::mutex> lk(ctx->engine->mu);
+    ctx->engine->graph_dirty = true;
+  }
+}
+
+extern "C" {
+
+int f12int_batch_limits(f12int_ctx *ctx, int64_t max_quartets, int64_t max_items) {
+  if (!ctx || max_quartets < 1 || max_items < 1 || max_quartets > ((int64_t)1 << 30)) return F12INT_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (ctx->engine && ctx->engine->ready) return F12INT_EINVAL;   // fixed once the engine runs
+  if (!ctx->engine) ctx->engine = new (std::nothrow) Engine();
+  if (!ctx->engine) return F12INT_ENOMEM;
+  ctx->engine->qcap = max_quartets;
+  ctx->engine->icap = max_items;
+  return F12INT_OK;
+}
+
+int f12int_submit(f12int_ctx *ctx, int basis_id, const f12int_request *req, uint64_t *ticket) {
+  if (!ctx || !req || !ticket) return F12INT_EINVAL;
+  if (basis_id < 0 || basis_id >= (int)ctx->bases.size() || !ctx->factor_ready) return F12INT_ENOTREADY;
+  if (req->n_quartets < 0 || (req->n_quartets > 0 && (!req->quartets || !req->offsets || !req->out_dev)))
+    return F12INT_EINVAL;
+  if (req->class_mask == 0 || (req->class_mask >> 6) != 0) return F12INT_EINVAL;
+  if (req->precision != 0) return F12INT_EINVAL;
+  if (!(req->schwarz_thresh >= 0.0)) return F12INT_EINVAL;
+  const f12int_ctx::BasisData &B = ctx->bases[basis_id];
+  const int64_t n = req->n_quartets;
+  int nclass = 0;
+  for (int c = 1; c <= 6; ++c) nclass += (req->class_mask >> (c - 1)) & 1;
+  EngineReq *R = new (std::nothrow) EngineReq();
+  if (!R) return F12INT_ENOMEM;
+  R->basis = basis_id;
+  R->B = &B;
+  R->mask = req->class_mask;
+  R->thresh = req->schwarz_thresh;
+  R->out = req->out_dev;
+  R->q.assign(req->quartets, req->quartets + 4 * n);
+  R->off.assign(req->offsets, req->offsets + (size_t)nclass * n);
+  int64_t npq = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    const int32_t *s = &R->q[4 * (size_t)i];
+    for (int k = 0; k < 4; ++k)
+      if (s[k] < 0 || s[k] >= B.nshell) {
+        delete R;
+        return F12INT_EINVAL;
+      }
+    npq += (int64_t)B.nprim[s[0]] * B.nprim[s[1]] * B.nprim[s[2]] * B.nprim[s[3]];
+  }
+  // one-time per (basis, class) work: primitive and shell-pair bounds
+  for (int c = 1; c <= 6; ++c) {
+    if (!((R->mask >> (c - 1)) & 1)) continue;
+    for (int64_t i = 0; i < n; ++i) {
+      const int32_t *s = &R->q[4 * (size_t)i];
+      BatchPlan bp{};
+      if (!batch_plan(B.l[s[0]], B.l[s[1]], B.l[s[2]], B.l[s[3]], c, &bp)) {
+        delete R;
+        return F12INT_EINVAL;
+      }
+    }
+    int rc = ensure_prim_bounds(ctx, basis_id, c);
+    if (rc == F12INT_OK && R->thresh > 0.0) rc = ensure_pair_bounds(ctx, basis_id, c);
+    if (rc != F12INT_OK) {
+      delete R;
+      return rc;
+    }
+    R->quartets[c] = n;
+    R->items[c] = npq * ctx->tables.nfam[c == 5 ? 3 : c];
+  }
+  Engine *E = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (!ctx->engine) ctx->engine = new (std::nothrow) Engine();
+    E = ctx->engine;
+    if (!E) {
+      delete R;
+      return F12INT_ENOMEM;
+    }
+    if (!E->ready) {
+      CK(cudaSetDevice(ctx->device));
+      int rc = engine_init(ctx, *E);
+      if (rc != F12INT_OK) {
+        delete R;
+        return rc;
+      }
+      E->worker = std::thread(engine_worker, ctx, E);
+    }
+  }
+  for (int c = 1; c <= 6; ++c)
+    if (R->quartets[c] > E->qcap || R->items[c] > E->icap) {
+      delete R;
+      return F12INT_ENOMEM;   // larger than one batch: not admitted
+    }
+  {
+    std::lock_guard<std::mutex> lk(E->mu);
+    R->ticket = E->next_ticket++;
+    *ticket = R->ticket;
+    E->tickets[R->ticket] = TicketState{};
+    E->pending.push_back(R);
+  }
+  E->cv.notify_one();
+  return F12INT_OK;
+}
+
+int f12int_poll(f12int_ctx *ctx, uint64_t ticket, int64_t timeout_us, int *done) {
+  if (!ctx || !done || timeout_us < 0) return F12INT_EINVAL;
+  Engine *E = ctx->engine;
+  if (!E) return F12INT_EINVAL;
+  *done = 0;
+  const auto deadline = std::chrono::steady_clock::now() + std::chrono::microseconds(timeout_us);
+  for (;;) {
+    {
+      std::lock_guard<std::mutex> lk(E->mu);
+      auto it = E->tickets.find(ticket);
+      if (it == E->tickets.end()) return F12INT_EINVAL;
+      if (!it->second.done && it->second.batch >= 0) {
+        const int b = it->second.batch;
+        bool mine = false;
+        for (uint64_t t : E->inflight[b]) mine |= (t == ticket);
+        if (mine && cudaEventQuery(E->ev[b]) == cudaSuccess) engine_finish_batch(*E, b);
+      }
+      if (it->second.done) {
+        const int rc = it->second.rc;
+        E->tickets.erase(it);
+        *done = 1;
+        return rc;
+      }
+    }
+    if (std::chrono::steady_clock::now() >= deadline) return F12INT_OK;
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+}
+
+int f12int_batch_stats(f12int_ctx *ctx, int64_t *stats) {
+  if (!ctx || !stats) return F12INT_EINVAL;
+  Engine *E = ctx->engine;
+  if (!E) {
+    stats[0] = stats[1] = stats[2] = 0;
+    return F12INT_OK;
+  }
+  std::lock_guard<std::mutex> lk(E->mu);
+  stats[0] = E->batches;
+  stats[1] = E->requests_done;
+  stats[2] = (int64_t)E->pending.size();
+  return F12INT_OK;
+}
+
+}  // extern "C"

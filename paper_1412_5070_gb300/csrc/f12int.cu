@@ -15,13 +15,17 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <condition_variable>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <deque>
 #include <mutex>
 #include <new>
+#include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/f12int.h"
@@ -163,10 +167,37 @@ __global__ void k_build_pairs(int npp, const int *pp_shell_a, const int *pp_shel
 }
 
 // ------------------------------------------------------------------- aux --
+// A list of shell quartets.  In a batch (qslot != null) every quartet names a
+// slot, which gives the pair data of its basis and the output array of its
+// request; counts then live in device memory (count_dev[0] quartets,
+// count_dev[1] primitive quartets), so one captured launch sequence serves
+// every batch.
 struct QuartetView {
-  const int32_t *quartets;   // [n][4]
-  const int64_t *pq_off;     // [n+1] first primitive quartet of each shell quartet
+  const int32_t *quartets;     // [n][4]
+  const int64_t *pq_off;       // [n+1] first primitive quartet of each shell quartet
   int64_t n;
+  const int64_t *count_dev;    // batch: {n, pq_off[n]} on the device, else null
+  const int32_t *qslot;        // batch: slot of each quartet, else null
+  const PairView *slot_view;   // batch: pair data per slot
+  double *const *slot_out;     // batch: output array per slot
+};
+
+__device__ __forceinline__ int64_t qv_count(const QuartetView &QV) { return QV.count_dev ? QV.count_dev[0] : QV.n; }
+
+// Pair data of quartet q: the kernel's own view, or the slot's in a batch
+// (a compile-time choice, so that the single-basis kernels keep their view in
+// the parameter space).
+template <bool BATCH>
+__device__ __forceinline__ const PairView &qv_view(const PairView &PV, const QuartetView &QV, int64_t q) {
+  if constexpr (BATCH) return QV.slot_view[QV.qslot[q]];
+  else return PV;
+}
+
+// One block of contraction work: quartet q (index into the list), ket range
+// split of nsplit.
+struct CTask {
+  int32_t q;
+  int16_t split, nsplit;
 };
 
 __device__ __forceinline__ int64_t find_quartet(const int64_t *off, int64_t n, int64_t pq) {
@@ -183,10 +214,13 @@ struct ItemGeom {
   double xi, D;
   int L;
   int iab, icd;
+  const PairView *pv;
 };
 
-__device__ __forceinline__ ItemGeom item_geometry(const PairView &PV, const QuartetView &QV, int cls, int64_t pq) {
-  int64_t q = find_quartet(QV.pq_off, QV.n, pq);
+template <bool BATCH>
+__device__ __forceinline__ ItemGeom item_geometry(const PairView &PV0, const QuartetView &QV, int cls, int64_t pq) {
+  int64_t q = find_quartet(QV.pq_off, qv_count(QV), pq);
+  const PairView &PV = qv_view<BATCH>(PV0, QV, q);
   const int32_t *s = QV.quartets + 4 * q;
   const int ns = PV.nshell;
   int ab = s[0] * ns + s[1], cd = s[2] * ns + s[3];
@@ -197,6 +231,7 @@ __device__ __forceinline__ ItemGeom item_geometry(const PairView &PV, const Quar
   ItemGeom g;
   g.iab = iab;
   g.icd = icd;
+  g.pv = &PV;
   g.L = PV.shell_l[s[0]] + PV.shell_l[s[1]] + PV.shell_l[s[2]] + PV.shell_l[s[3]] + (cls == 5 ? 2 : 0);
   double p = PV.pp_p[iab], qq = PV.pp_p[icd];
   double X = pair_sep(PV.pp_P, iab, icd, 0), Y = pair_sep(PV.pp_P, iab, icd, 1), Z = pair_sep(PV.pp_P, iab, icd, 2);
@@ -209,20 +244,29 @@ __device__ __forceinline__ int item_key(int f, int L, int bin) { return (f * (LA
 constexpr int SKIP_KEY = MAXFAM * (LAUX + 1) * NZBIN;   // last key: negligible primitive quartets
 
 // Pass 1: key of every item and a histogram of the keys.
+// Items of a list: (pq_off[n] - pq0) * nf, from the device counts in a batch.
+__device__ __forceinline__ int64_t item_count(const QuartetView &QV, int nf, int64_t pq0, int64_t nitems) {
+  return QV.count_dev ? (QV.count_dev[1] - pq0) * nf : nitems;
+}
+
+// Pass 1: key of every item and a histogram of the keys.
+template <bool BATCH>
 __global__ void k_items_classify(Tables T, PairView PV, QuartetView QV, int cls, int64_t pq0, int64_t nitems,
                                  int *keys, unsigned int *hist) {
-  int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (it >= nitems) return;
   const int kcls = cls == 5 ? 3 : cls;
   const int nf = T.nfam[kcls];
-  const int64_t pq = pq0 + it / nf;
-  const int f = (int)(it % nf);
-  ItemGeom g = item_geometry(PV, QV, cls, pq);
-  const FamDev &F = T.fam[T.fam0[kcls] + f];
-  int key = prim_negligible(PV, g.iab, g.icd) ? SKIP_KEY
-                                              : item_key(f, min(g.L, LAUX), item_bin(F, g.xi, g.D, g.L));
-  keys[it] = key;
-  atomicAdd(&hist[key], 1u);
+  const int64_t nit = item_count(QV, nf, pq0, nitems);
+  for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < nit;
+       it += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t pq = pq0 + it / nf;
+    const int f = (int)(it % nf);
+    ItemGeom g = item_geometry<BATCH>(PV, QV, cls, pq);
+    const FamDev &F = T.fam[T.fam0[kcls] + f];
+    int key = prim_negligible(*g.pv, g.iab, g.icd) ? SKIP_KEY
+                                                   : item_key(f, min(g.L, LAUX), item_bin(F, g.xi, g.D, g.L));
+    keys[it] = key;
+    atomicAdd(&hist[key], 1u);
+  }
 }
 
 // Pass 2: exclusive scan of the histogram (one block).
@@ -253,15 +297,19 @@ __global__ void k_items_scan(unsigned int *hist, int nkeys) {
 
 // Pass 3: scatter item indices into key order (order inside a key is free:
 // every item is evaluated independently, so results do not depend on it).
-__global__ void k_items_scatter(const int *keys, unsigned int *cursor, int64_t nitems, unsigned int *order) {
-  int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (it >= nitems) return;
-  unsigned int pos = atomicAdd(&cursor[keys[it]], 1u);
-  order[pos] = (unsigned int)it;
+__global__ void k_items_scatter(QuartetView QV, int nf, int64_t pq0, const int *keys, unsigned int *cursor,
+                                int64_t nitems, unsigned int *order) {
+  const int64_t nit = item_count(QV, nf, pq0, nitems);
+  for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < nit;
+       it += (int64_t)gridDim.x * blockDim.x) {
+    unsigned int pos = atomicAdd(&cursor[keys[it]], 1u);
+    order[pos] = (unsigned int)it;
+  }
 }
 
 // Pass 4: one family's contribution to hat g_l (l <= L) per item, into
 // part[item * (LAUX+1) + l], in key order.
+template <bool BATCH>
 __device__ __forceinline__ unsigned long long items_eval_one(Tables T, PairView PV, QuartetView QV, int cls,
                                                              int64_t pq0, int64_t it, double *part,
                                                              unsigned int *status) {
@@ -269,8 +317,8 @@ __device__ __forceinline__ unsigned long long items_eval_one(Tables T, PairView 
   const int nf = T.nfam[kcls];
   const int64_t pq = pq0 + it / nf;
   const int f = (int)(it % nf);
-  ItemGeom g = item_geometry(PV, QV, cls, pq);
-  if (prim_negligible(PV, g.iab, g.icd)) return 0;   // never read by the contraction
+  ItemGeom g = item_geometry<BATCH>(PV, QV, cls, pq);
+  if (prim_negligible(*g.pv, g.iab, g.icd)) return 0;   // never read by the contraction
   if (g.L > LAUX) {
     atomicOr(status, 4u);
     return 0;
@@ -285,13 +333,18 @@ __device__ __forceinline__ unsigned long long items_eval_one(Tables T, PairView 
   return nfma;
 }
 
+template <bool BATCH>
 __global__ void k_items_eval(Tables T, PairView PV, QuartetView QV, int cls, int64_t pq0, int64_t nitems,
                              const unsigned int *order, double *part, unsigned int *status,
                              unsigned long long *fma_total) {
-  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   unsigned long long nfma = 0;
-  if (t < nitems) {
-    nfma = items_eval_one(T, PV, QV, cls, pq0, order[t], part, status);
+  if constexpr (BATCH) {
+    const int64_t nit = item_count(QV, T.nfam[cls == 5 ? 3 : cls], pq0, nitems);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nit; t += (int64_t)gridDim.x * blockDim.x)
+      nfma += items_eval_one<BATCH>(T, PV, QV, cls, pq0, order[t], part, status);
+  } else {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < nitems) nfma = items_eval_one<BATCH>(T, PV, QV, cls, pq0, order[t], part, status);
   }
   // warp-aggregated count of the core multiply-adds (series terms and quadrature nodes)
   if (fma_total) {
@@ -365,14 +418,15 @@ static inline int ne3_chunk_max(int l1, int l2, int jc) {
   return cur > best ? cur : best;
 }
 
-__global__ void __launch_bounds__(BLOCK_CONTRACT)
-k_contract(PairView PV, QuartetView QV, int cls, int nf, int64_t pq0, int64_t q0, int nsplit, const double *part,
-           double *out, const int64_t *offsets, unsigned int *status, unsigned long long *flops_total) {
-  extern __shared__ double smem[];
-  __shared__ int off_ab[101], off_cd[101];
-  const int64_t q = q0 + blockIdx.x / nsplit;
-  const int split = blockIdx.x % nsplit;
-  if (q >= QV.n) return;
+// One contraction task (quartet and ket range) by the whole block.
+template <bool BATCH>
+__device__ __forceinline__ void contract_task(const PairView &PV0, const QuartetView &QV, int cls, int nf,
+                                              int64_t pq0, const CTask task, const double *part, double *out,
+                                              const int64_t *offsets, unsigned long long *flops_total,
+                                              double *smem, int *off_ab, int *off_cd) {
+  const int64_t q = task.q;
+  const int split = task.split, nsplit = task.nsplit;
+  const PairView &PV = qv_view<BATCH>(PV0, QV, q);
   const int32_t *s = QV.quartets + 4 * q;
   const int ns = PV.nshell;
   const int la = PV.shell_l[s[0]], lb = PV.shell_l[s[1]], lc = PV.shell_l[s[2]], ld = PV.shell_l[s[3]];
@@ -572,7 +626,9 @@ k_contract(PairView PV, QuartetView QV, int cls, int nf, int64_t pq0, int64_t q0
     }
     __syncthreads();
   }
-  double *o = out + offsets[q];
+  double *o;
+  if constexpr (BATCH) o = QV.slot_out[QV.qslot[q]] + offsets[q];
+  else o = out + offsets[q];
   for (int i = tid; i < nab * ncd; i += nthr) {
     const int iabc = i / ncd;
     o[(size_t)iabc * ncd_all + j0 + (i - iabc * ncd)] = Oacc[i];
@@ -587,6 +643,27 @@ k_contract(PairView PV, QuartetView QV, int cls, int nf, int64_t pq0, int64_t q0
     atomicAdd(flops_total, nproc * (r + ket + bra));
   }
 }
+
+template <bool BATCH>
+__global__ void __launch_bounds__(BLOCK_CONTRACT)
+k_contract(PairView PV0, QuartetView QV, int cls, int nf, int64_t pq0, const CTask *tasks, int64_t ntask,
+           const int64_t *ntask_dev, const double *part, double *out, const int64_t *offsets,
+           unsigned int *status, unsigned long long *flops_total) {
+  extern __shared__ double smem[];
+  __shared__ int off_ab[101], off_cd[101];
+  if constexpr (BATCH) {
+    // ntask_dev = {first, end} of this launch's tasks
+    const int64_t te = ntask_dev[1];
+    for (int64_t tk = ntask_dev[0] + blockIdx.x; tk < te; tk += gridDim.x) {
+      __syncthreads();   // the previous task's shared-memory reads are done
+      contract_task<BATCH>(PV0, QV, cls, nf, pq0, tasks[tk], part, out, offsets, flops_total, smem, off_ab, off_cd);
+    }
+  } else {
+    if (blockIdx.x < ntask)
+      contract_task<BATCH>(PV0, QV, cls, nf, pq0, tasks[blockIdx.x], part, out, offsets, flops_total, smem, off_ab,
+                           off_cd);
+  }
+}
 // Derivation note for I5: with d/dA_x = (a/p) d/dP_x + d/dAB_x and
 // d/dB_x = (b/p) d/dP_x - d/dAB_x (E depends on AB only, R on P only),
 //   1/2 (lap_A - lap_B) = sum_x [ (a-b)/(2p) d^2/dP_x^2 + d/dP_x d/dAB_x ],
@@ -596,6 +673,10 @@ k_contract(PairView PV, QuartetView QV, int cls, int nf, int64_t pq0, int64_t q0
 }  // namespace
 
 // ================================================================ host API ==
+
+namespace {
+struct Engine;   // batched requests (engine.cuh)
+}
 
 struct f12int_ctx {
   int device = 0;
@@ -623,6 +704,7 @@ struct f12int_ctx {
     size_t bytes = 0;
     bool prim_screen = true;            // false for the internal per-primitive basis
     double *d_qprim[7] = {nullptr};     // primitive Schwarz factors per class (lazily built)
+    std::vector<double> pair_bound[7];  // shell-pair bounds sqrt(max |(ab|k|ab)|) per class (lazily built)
   };
   std::deque<BasisData> bases;   // deque: growing it never moves existing entries
   // scratch of compute_class (grown on demand, bounded by the budget)
@@ -632,7 +714,9 @@ struct f12int_ctx {
   double *d_part = nullptr;
   int32_t *d_qperm = nullptr;
   int64_t *d_operm = nullptr;
+  CTask *d_tasks = nullptr;
   size_t pqoff_cap = 0, keys_cap = 0, order_cap = 0, hist_cap = 0, part_cap = 0, qperm_cap = 0, operm_cap = 0;
+  size_t tasks_cap = 0;
   // optional per-kernel timing (events on the launching stream) and counters
   bool timing = false;
   unsigned long long *d_fma = nullptr;
@@ -643,6 +727,8 @@ struct f12int_ctx {
   std::vector<int> h_split;    // ket-component ranges (blocks) per quartet, same order
   std::vector<size_t> h_smem;  // contraction shared memory, per quartet in the working order
   std::mutex mu;
+  std::recursive_mutex bounds_mu;   // first-time primitive and shell-pair bounds
+  Engine *engine = nullptr;
 };
 
 namespace {
@@ -831,9 +917,14 @@ int f12int_create(f12int_ctx **out, int device, size_t hbm_budget_bytes, void *c
   return F12INT_OK;
 }
 
+static void engine_shutdown(f12int_ctx *ctx);
+static bool engine_idle(f12int_ctx *ctx);
+static void engine_factor_changed(f12int_ctx *ctx);
+
 int f12int_destroy(f12int_ctx *ctx) {
   if (!ctx) return F12INT_EINVAL;
   cudaSetDevice(ctx->device);
+  engine_shutdown(ctx);
   cudaDeviceSynchronize();
   for (auto &b : ctx->bases) {
     cudaFree(b.d_shell_l);
@@ -855,6 +946,7 @@ int f12int_destroy(f12int_ctx *ctx) {
   cudaFree(ctx->d_part);
   cudaFree(ctx->d_qperm);
   cudaFree(ctx->d_operm);
+  cudaFree(ctx->d_tasks);
   cudaFree(ctx->d_status);
   cudaFree(ctx->d_fma);
   for (auto &e : ctx->ev_pool) {
@@ -942,6 +1034,7 @@ int f12int_set_factor(f12int_ctx *ctx, const f12int_factor *f, const f12int_fact
   int rc = check_factor(*f);
   if (rc == F12INT_OK) rc = check_factor(fp);
   if (rc != F12INT_OK) return rc;
+  if (!engine_idle(ctx)) return F12INT_EINVAL;   // submitted requests still use the current factor
   std::lock_guard<std::mutex> lk(ctx->mu);
   CK(cudaSetDevice(ctx->device));
   f12::Factor F1{f->c0, f->rho, f->B, f->mu, f->n}, F2{fp.c0, fp.rho, fp.B, fp.mu, fp.n};
@@ -1012,6 +1105,9 @@ int f12int_set_factor(f12int_ctx *ctx, const f12int_factor *f, const f12int_fact
         cudaFree(b.d_qprim[c]);
         b.d_qprim[c] = nullptr;
       }
+  for (auto &b : ctx->bases)   // and so do the shell-pair bounds
+    for (int c = 0; c < 7; ++c) b.pair_bound[c].clear();
+  engine_factor_changed(ctx);
   ctx->factor_ready = true;
   return F12INT_OK;
 }
@@ -1228,7 +1324,7 @@ static int launch_chunk(f12int_ctx *ctx, const f12int_ctx::BasisData &B, int cls
                         size_t smem, double *out_dev, const int64_t *offsets_dev, cudaStream_t st) {
   PairView PV{B.d_pair_start, B.d_pp_p, B.d_pp_P, B.d_pp_ab, B.d_pp_eoff, B.d_epool, B.d_shell_l, B.nshell,
               B.prim_screen ? B.d_qprim[cls] : nullptr};
-  QuartetView QV{d_quartets, d_pqoff, n};
+  QuartetView QV{d_quartets, d_pqoff, n, nullptr, nullptr, nullptr, nullptr};
   const int kcls = cls == 5 ? 3 : cls;
   const int nf = ctx->tables.nfam[kcls];
   const int64_t nitems = (pqb - pqa) * nf;
@@ -1240,15 +1336,15 @@ static int launch_chunk(f12int_ctx *ctx, const f12int_ctx::BasisData &B, int cls
     if (rc != F12INT_OK) return rc;
     CK(cudaMemsetAsync(ctx->d_hist, 0, sizeof(unsigned) * kNKeys, st));
     const unsigned nb = (unsigned)((nitems + BLOCK_AUX - 1) / BLOCK_AUX);
-    k_items_classify<<<nb, BLOCK_AUX, 0, st>>>(ctx->tables, PV, QV, cls, pqa, nitems, ctx->d_keys, ctx->d_hist);
+    k_items_classify<false><<<nb, BLOCK_AUX, 0, st>>>(ctx->tables, PV, QV, cls, pqa, nitems, ctx->d_keys, ctx->d_hist);
     k_items_scan<<<1, 1024, 0, st>>>(ctx->d_hist, kNKeys);
-    k_items_scatter<<<nb, BLOCK_AUX, 0, st>>>(ctx->d_keys, ctx->d_hist, nitems, ctx->d_order);
+    k_items_scatter<<<nb, BLOCK_AUX, 0, st>>>(QV, nf, pqa, ctx->d_keys, ctx->d_hist, nitems, ctx->d_order);
     std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
     if (ctx->timing) {
       ev = take_events(ctx);
       cudaEventRecord(ev.first, st);
     }
-    k_items_eval<<<nb, BLOCK_AUX, 0, st>>>(ctx->tables, PV, QV, cls, pqa, nitems, ctx->d_order, ctx->d_part,
+    k_items_eval<false><<<nb, BLOCK_AUX, 0, st>>>(ctx->tables, PV, QV, cls, pqa, nitems, ctx->d_order, ctx->d_part,
                                            ctx->d_status, ctx->timing ? ctx->d_fma : nullptr);
     if (ctx->timing) {
       cudaEventRecord(ev.second, st);
@@ -1259,21 +1355,33 @@ static int launch_chunk(f12int_ctx *ctx, const f12int_ctx::BasisData &B, int cls
     CK(cudaGetLastError());
   }
   // contraction: quartets are ordered by decreasing shared-memory need; one
-  // launch per tier of warps and shared memory (powers of two)
+  // launch per tier of warps and shared memory (powers of two), one block per
+  // (quartet, ket range) task
+  std::vector<CTask> tasks;
+  for (int64_t i = qa; i < qb; ++i)
+    for (int sp = 0; sp < ctx->h_split[i]; ++sp) tasks.push_back(CTask{(int32_t)i, (int16_t)sp, (int16_t)ctx->h_split[i]});
+  {
+    int rc = ensure_buf(ctx, (void **)&ctx->d_tasks, &ctx->tasks_cap, sizeof(CTask) * tasks.size());
+    if (rc != F12INT_OK) return rc;
+    CK(cudaMemcpyAsync(ctx->d_tasks, tasks.data(), sizeof(CTask) * tasks.size(), cudaMemcpyHostToDevice, st));
+  }
+  int64_t t0 = 0;
   for (int64_t ra = qa; ra < qb;) {
     const int nw = ctx->h_nw[ra], nsp = ctx->h_split[ra];
     const size_t sm0 = ctx->h_smem[ra];
     int64_t rb = ra + 1;
     while (rb < qb && ctx->h_nw[rb] == nw && ctx->h_split[rb] == nsp && 2 * ctx->h_smem[rb] > sm0) ++rb;
-    if (sm0 > 48 * 1024) CK(cudaFuncSetAttribute(k_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm0));
+    const int64_t nt = (rb - ra) * nsp;
+    if (sm0 > 48 * 1024) CK(cudaFuncSetAttribute(k_contract<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm0));
     std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
     if (ctx->timing) {
       ev = take_events(ctx);
       cudaEventRecord(ev.first, st);
     }
-    k_contract<<<(unsigned)((rb - ra) * nsp), 32 * nw, sm0, st>>>(PV, QV, cls, nf, pqa, ra, nsp, ctx->d_part, out_dev,
-                                                                 offsets_dev, ctx->d_status,
-                                                                 ctx->timing ? ctx->d_fma + 1 : nullptr);
+    k_contract<false><<<(unsigned)nt, 32 * nw, sm0, st>>>(PV, QV, cls, nf, pqa, ctx->d_tasks + t0, nt, nullptr, ctx->d_part,
+                                                  out_dev, offsets_dev, ctx->d_status,
+                                                  ctx->timing ? ctx->d_fma + 1 : nullptr);
+    t0 += nt;
     if (ctx->timing) {
       cudaEventRecord(ev.second, st);
       ctx->ev_con.push_back(ev);
@@ -1290,6 +1398,7 @@ static int launch_chunk(f12int_ctx *ctx, const f12int_ctx::BasisData &B, int cls
 // pair of the basis for class cls (the I3 kernel for I5), from the diagonal
 // blocks of a basis in which every primitive is its own shell.
 static int ensure_prim_bounds(f12int_ctx *ctx, int basis_id, int cls) {
+  std::lock_guard<std::recursive_mutex> blk(ctx->bounds_mu);
   {
     f12int_ctx::BasisData &B = ctx->bases[basis_id];
     if (!B.prim_screen || B.d_qprim[cls]) return F12INT_OK;
@@ -1503,14 +1612,14 @@ int f12int_aux(f12int_ctx *ctx, int cls, int64_t npts, const double *xi_dev, con
   return F12INT_OK;
 }
 
-int f12int_screen(f12int_ctx *ctx, int basis_id, int cls, double thresh, int32_t *quartets_out, int64_t cap,
-                  int64_t *n_out) {
-  if (!ctx || cls < 1 || cls > 6 || !n_out || cap < 0 || (cap > 0 && !quartets_out)) return F12INT_EINVAL;
-  if (basis_id < 0 || basis_id >= (int)ctx->bases.size() || !ctx->factor_ready) return F12INT_ENOTREADY;
-  if (!(thresh >= 0.0)) return F12INT_EINVAL;
+// Shell-pair bounds bound(ab) = sqrt(max |(ab|k|ab)|) over the diagonal block
+// (the I3 kernel for I5), cached per basis and class.
+static int ensure_pair_bounds(f12int_ctx *ctx, int basis_id, int cls) {
+  const int dcls = cls == 5 ? 3 : cls;
+  std::lock_guard<std::recursive_mutex> blk(ctx->bounds_mu);
+  if (!ctx->bases[basis_id].pair_bound[dcls].empty()) return F12INT_OK;
   const f12int_ctx::BasisData &B = ctx->bases[basis_id];
   const int ns = B.nshell;
-  const int dcls = cls == 5 ? 3 : cls;
   // diagonal blocks (ab|ab) for a >= b
   std::vector<int32_t> hq;
   std::vector<int64_t> off;
@@ -1545,7 +1654,6 @@ int f12int_screen(f12int_ctx *ctx, int basis_id, int cls, double thresh, int32_t
   dfree(ctx, doff, sizeof(int64_t) * nq);
   dfree(ctx, dout, sizeof(double) * tot);
   if (rc != F12INT_OK) return rc;
-  // bound(ab) = sqrt(max |(ab|k|ab)|)
   std::vector<double> bound((size_t)ns * ns, 0.0);
   int64_t k = 0;
   for (int a = 0; a < ns; ++a)
@@ -1555,6 +1663,20 @@ int f12int_screen(f12int_ctx *ctx, int basis_id, int cls, double thresh, int32_t
       for (int64_t i = 0; i < (int64_t)nab * nab; ++i) m = std::max(m, std::fabs(hout[off[k] + i]));
       bound[(size_t)a * ns + b] = bound[(size_t)b * ns + a] = std::sqrt(m);
     }
+  ctx->bases[basis_id].pair_bound[dcls] = std::move(bound);
+  return F12INT_OK;
+}
+
+int f12int_screen(f12int_ctx *ctx, int basis_id, int cls, double thresh, int32_t *quartets_out, int64_t cap,
+                  int64_t *n_out) {
+  if (!ctx || cls < 1 || cls > 6 || !n_out || cap < 0 || (cap > 0 && !quartets_out)) return F12INT_EINVAL;
+  if (basis_id < 0 || basis_id >= (int)ctx->bases.size() || !ctx->factor_ready) return F12INT_ENOTREADY;
+  if (!(thresh >= 0.0)) return F12INT_EINVAL;
+  int rc = ensure_pair_bounds(ctx, basis_id, cls);
+  if (rc != F12INT_OK) return rc;
+  const f12int_ctx::BasisData &B = ctx->bases[basis_id];
+  const int ns = B.nshell;
+  const std::vector<double> &bound = B.pair_bound[cls == 5 ? 3 : cls];
   std::vector<std::pair<int, int>> pairs;
   for (int a = 0; a < ns; ++a)
     for (int b = 0; b <= a; ++b) pairs.emplace_back(a, b);
@@ -1631,7 +1753,8 @@ extern "C" int f12int_compute_class_static(f12int_ctx *ctx, int basis_id, int cl
   // fixed part of the scratch: quartet list, offsets and primitive offsets in
   // the working order, and the key histogram; the rest holds the work items
   const size_t fixed = align256(sizeof(int32_t) * 4 * (size_t)n) + align256(sizeof(int64_t) * (size_t)n) +
-                       align256(sizeof(int64_t) * ((size_t)n + 1)) + align256(sizeof(unsigned) * kNKeys);
+                       align256(sizeof(int64_t) * ((size_t)n + 1)) + align256(sizeof(unsigned) * kNKeys) +
+                       align256(sizeof(CTask) * (size_t)n);
   if (fixed + ((size_t)1 << 20) > F12INT_STATIC_SCRATCH_BYTES) return F12INT_EINVAL;  // too many quartets
   std::lock_guard<std::mutex> lk(ctx->mu);
   CK(cudaSetDevice(ctx->device));
@@ -1642,9 +1765,8 @@ extern "C" int f12int_compute_class_static(f12int_ctx *ctx, int basis_id, int cl
   int64_t *d_o = (int64_t *)(base + align256(sizeof(int32_t) * 4 * (size_t)n));
   int64_t *d_pq = (int64_t *)((unsigned char *)d_o + align256(sizeof(int64_t) * (size_t)n));
   unsigned *d_hist = (unsigned *)((unsigned char *)d_pq + align256(sizeof(int64_t) * ((size_t)n + 1)));
-  unsigned char *items_base = (unsigned char *)d_hist + align256(sizeof(unsigned) * kNKeys);
+  unsigned char *after_hist = (unsigned char *)d_hist + align256(sizeof(unsigned) * kNKeys);
   const size_t item_bytes = sizeof(int) + sizeof(unsigned) + sizeof(double) * (LAUX + 1);
-  const int64_t max_items = (int64_t)((F12INT_STATIC_SCRATCH_BYTES - fixed - 3 * 256) / item_bytes);
 
   const f12int_ctx::BasisData &B = ctx->bases[basis_id];
   cudaStream_t st = pick_stream(ctx, cuda_stream);
@@ -1690,13 +1812,25 @@ extern "C" int f12int_compute_class_static(f12int_ctx *ctx, int basis_id, int cl
     if (hsm[i] > 227 * 1024) return F12INT_EINVAL;
   }
   pqoff[n] = npq;
+  // contraction tasks (one per quartet and ket range), then the work items
+  std::vector<CTask> tasks;
+  for (int64_t i = 0; i < n; ++i)
+    for (int sp = 0; sp < hsp[i]; ++sp) tasks.push_back(CTask{(int32_t)i, (int16_t)sp, (int16_t)hsp[i]});
+  std::vector<int64_t> tfirst((size_t)n + 1, 0);
+  for (int64_t i = 0; i < n; ++i) tfirst[i + 1] = tfirst[i] + hsp[i];
+  CTask *d_tk = (CTask *)after_hist;
+  unsigned char *items_base = after_hist + align256(sizeof(CTask) * tasks.size());
+  const size_t used_fixed = (size_t)(items_base - base);
+  if (used_fixed + 3 * 256 + item_bytes > F12INT_STATIC_SCRATCH_BYTES) return F12INT_EINVAL;
+  const int64_t max_items = (int64_t)((F12INT_STATIC_SCRATCH_BYTES - used_fixed - 3 * 256) / item_bytes);
+  CK(cudaMemcpyAsync(d_tk, tasks.data(), sizeof(CTask) * tasks.size(), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(d_q, hq.data(), sizeof(int32_t) * 4 * n, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(d_o, ho.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(d_pq, pqoff.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, st));
 
   PairView PV{B.d_pair_start, B.d_pp_p, B.d_pp_P, B.d_pp_ab, B.d_pp_eoff, B.d_epool, B.d_shell_l, B.nshell,
               nullptr};
-  QuartetView QV{d_q, d_pq, n};
+  QuartetView QV{d_q, d_pq, n, nullptr, nullptr, nullptr, nullptr};
   const int kcls = cls == 5 ? 3 : cls;
   const int nf = ctx->tables.nfam[kcls];
   const int64_t pq_chunk = std::max<int64_t>(1, max_items / std::max(nf, 1));
@@ -1713,10 +1847,10 @@ extern "C" int f12int_compute_class_static(f12int_ctx *ctx, int basis_id, int cl
       // previous call's contents
       CK(cudaMemsetAsync(d_hist, 0, sizeof(unsigned) * kNKeys, st));
       const unsigned nb = (unsigned)((nitems + BLOCK_AUX - 1) / BLOCK_AUX);
-      k_items_classify<<<nb, BLOCK_AUX, 0, st>>>(ctx->tables, PV, QV, cls, pqa, nitems, d_keys, d_hist);
+      k_items_classify<false><<<nb, BLOCK_AUX, 0, st>>>(ctx->tables, PV, QV, cls, pqa, nitems, d_keys, d_hist);
       k_items_scan<<<1, 1024, 0, st>>>(d_hist, kNKeys);
-      k_items_scatter<<<nb, BLOCK_AUX, 0, st>>>(d_keys, d_hist, nitems, d_order);
-      k_items_eval<<<nb, BLOCK_AUX, 0, st>>>(ctx->tables, PV, QV, cls, pqa, nitems, d_order, d_part, ctx->d_status,
+      k_items_scatter<<<nb, BLOCK_AUX, 0, st>>>(QV, nf, pqa, d_keys, d_hist, nitems, d_order);
+      k_items_eval<false><<<nb, BLOCK_AUX, 0, st>>>(ctx->tables, PV, QV, cls, pqa, nitems, d_order, d_part, ctx->d_status,
                                              nullptr);
       ctx->launches += 4;
       CK(cudaGetLastError());
@@ -1726,9 +1860,10 @@ extern "C" int f12int_compute_class_static(f12int_ctx *ctx, int basis_id, int cl
       const size_t smr = hsm[ra];
       int64_t rb = ra + 1;
       while (rb < qb && hnw[rb] == nwr && hsp[rb] == nspr && 2 * hsm[rb] > smr) ++rb;
-      if (smr > 48 * 1024) CK(cudaFuncSetAttribute(k_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
-      k_contract<<<(unsigned)((rb - ra) * nspr), 32 * nwr, smr, st>>>(PV, QV, cls, nf, pqa, ra, nspr, d_part,
-                                                                     out_dev, d_o, ctx->d_status, nullptr);
+      const int64_t nt = (rb - ra) * nspr;
+      if (smr > 48 * 1024) CK(cudaFuncSetAttribute(k_contract<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
+      k_contract<false><<<(unsigned)nt, 32 * nwr, smr, st>>>(PV, QV, cls, nf, pqa, d_tk + tfirst[ra], nt, nullptr, d_part,
+                                                     out_dev, d_o, ctx->d_status, nullptr);
       ctx->launches++;
       CK(cudaGetLastError());
       ra = rb;
@@ -1739,3 +1874,5 @@ extern "C" int f12int_compute_class_static(f12int_ctx *ctx, int basis_id, int cl
   CK(cudaStreamSynchronize(st));
   return F12INT_OK;
 }
+
+#include "engine.cuh"

@@ -25,7 +25,7 @@ STATUS = {0: "F12INT_OK", -1: "F12INT_EINVAL", -2: "F12INT_ENOMEM", -3: "F12INT_
 EXPORTS = ("f12int_create", "f12int_destroy", "f12int_set_basis", "f12int_set_factor", "f12int_screen",
            "f12int_compute_class", "f12int_compute_class_static", "f12int_aux", "f12int_launch_count",
            "f12int_device_status", "f12int_set_timing", "f12int_kernel_stats", "f12int_kernel_radial",
-           "f12int_strerror")
+           "f12int_submit", "f12int_poll", "f12int_batch_limits", "f12int_batch_stats", "f12int_strerror")
 
 
 class F12IntError(RuntimeError):
@@ -42,6 +42,12 @@ class Factor(ctypes.Structure):
     @classmethod
     def of(cls, d):
         return cls(float(d["c0"]), float(d["rho"]), float(d["B"]), float(d["mu"]), int(d["n"]))
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("n_quartets", ctypes.c_int64), ("quartets", ctypes.POINTER(ctypes.c_int32)),
+                ("class_mask", ctypes.c_uint32), ("precision", ctypes.c_int), ("schwarz_thresh", ctypes.c_double),
+                ("out_dev", ctypes.c_void_p), ("offsets", ctypes.POINTER(ctypes.c_int64))]
 
 
 _lib = None
@@ -77,6 +83,10 @@ def load():
     L.f12int_kernel_radial.argtypes = [ctypes.c_int, ctypes.POINTER(Factor), ctypes.POINTER(Factor), ctypes.c_int,
                                        ctypes.c_double, _dp]
     L.f12int_kernel_stats.argtypes = [_vp, ctypes.c_int, _dp]
+    L.f12int_submit.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
+    L.f12int_poll.argtypes = [_vp, ctypes.c_uint64, ctypes.c_int64, _ip]
+    L.f12int_batch_limits.argtypes = [_vp, ctypes.c_int64, ctypes.c_int64]
+    L.f12int_batch_stats.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
     L.f12int_strerror.argtypes = [ctypes.c_int]
     L.f12int_strerror.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -205,3 +215,39 @@ def f12int_kernel_stats(ctx, reset: bool = False) -> dict:
 
 def f12int_device_status(ctx) -> None:
     _check(load().f12int_device_status(ctx), "f12int_device_status")
+
+
+def f12int_submit(ctx, basis_id: int, quartets, classes, out_dev, offsets, schwarz_thresh: float = 0.0,
+                  precision: int = 0) -> int:
+    """Queue the blocks of ``classes`` (iterable of 1..6) over the host quartet
+    list ``quartets`` [n, 4] into the CUDA tensor ``out_dev``; ``offsets`` is a
+    host int64 array [len(classes), n] (rows in increasing class order).
+    Returns the ticket."""
+    q = np.ascontiguousarray(quartets, dtype=np.int32).reshape(-1, 4)
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    mask = 0
+    for c in classes:
+        mask |= 1 << (int(c) - 1)
+    req = Request(len(q), q.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), mask, int(precision),
+                  float(schwarz_thresh), _ptr(out_dev), off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+    t = ctypes.c_uint64(0)
+    _check(load().f12int_submit(ctx, int(basis_id), ctypes.byref(req), ctypes.byref(t)), "f12int_submit")
+    return t.value
+
+
+def f12int_poll(ctx, ticket: int, timeout_us: int = 0) -> bool:
+    """True once the request has finished (its status is checked: a failed
+    request raises F12IntError); False while it is queued or running."""
+    done = ctypes.c_int(0)
+    _check(load().f12int_poll(ctx, ctypes.c_uint64(ticket), int(timeout_us), ctypes.byref(done)), "f12int_poll")
+    return bool(done.value)
+
+
+def f12int_batch_limits(ctx, max_quartets: int, max_items: int) -> None:
+    _check(load().f12int_batch_limits(ctx, int(max_quartets), int(max_items)), "f12int_batch_limits")
+
+
+def f12int_batch_stats(ctx) -> dict:
+    s = (ctypes.c_int64 * 3)()
+    _check(load().f12int_batch_stats(ctx, s), "f12int_batch_stats")
+    return {"batches": int(s[0]), "requests_done": int(s[1]), "pending": int(s[2])}
