@@ -16,6 +16,19 @@ the timed region (they are reported separately).
 
 Prints one JSON line.  --impl reference times the CPU oracle on a bounded
 sample of the same workload on the host cores.
+
+Two further workloads, each printing its own JSON line:
+  --workload batch64  64 molecules (2-30 atoms, 4s3p2d1f, 1-6 primitives,
+                      exponents in [0.03, 200]); per molecule a block of 64 x 64
+                      significant shell pairs, all six classes: the batched
+                      request path (f12int_submit) against one plain
+                      f12int_compute_class launch per class and molecule.
+  --workload serve    Poisson request streams at 10..2000 requests/s over 12
+                      molecules of 2-60 atoms; half the requests ask for one
+                      class, half for I2..I6, each over U{8..64} x U{8..64}
+                      significant shell pairs: p50/p99 latency (submit to done)
+                      and throughput of the request path against serial plain
+                      launches in arrival order.
 """
 from __future__ import annotations
 
@@ -50,6 +63,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--workload", default="spd12", choices=("spd12", "batch64", "serve"))
     ap.add_argument("--fraction", type=float, default=1.0, help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu-baseline", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -353,10 +367,217 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def _sizes(basis, quartets):
+    nc = (basis.l + 1) * (basis.l + 2) // 2
+    q = np.asarray(quartets)
+    return nc[q[:, 0]] * nc[q[:, 1]] * nc[q[:, 2]] * nc[q[:, 3]]
+
+
+def _request_layout(basis, quartets, classes):
+    sz = _sizes(basis, quartets).astype(np.int64)
+    per = int(sz.sum())
+    first = np.concatenate([[0], np.cumsum(sz)[:-1]]).astype(np.int64)
+    return np.stack([first + k * per for k in range(len(classes))]), per * len(classes)
+
+
+def run_batching(args):
+    """64 uneven molecules, all six classes: batched requests vs plain launches."""
+    import torch
+    from paper_1412_5070_gb300 import build as B
+    from paper_1412_5070_gb300 import f12int as F
+    B.build()
+    work = M.batching_workload(64)
+    stream = torch.cuda.Stream()
+    ctx = F.f12int_create(0, 0, stream)
+    F.f12int_set_factor(ctx, M.P0)
+    F.f12int_batch_limits(ctx, 1 << 19, 1 << 27)
+    t0 = time.time()
+    bids = [F.f12int_set_basis(ctx, b) for b, _ in work]
+    t_basis = time.time() - t0
+    lay = [_request_layout(b, q, CLASSES) for b, q in work]
+    outs = [torch.empty(tot, dtype=torch.float64, device="cuda") for _, tot in lay]
+    nq = sum(len(q) * len(CLASSES) for _, q in work)
+    npq = sum(int(np.sum(np.prod(b.nprim[q], axis=1))) * len(CLASSES) for b, q in work)
+
+    def batched():
+        ts = [F.f12int_submit(ctx, bids[i], work[i][1], CLASSES, outs[i], lay[i][0]) for i in range(len(work))]
+        left = ts
+        while left:
+            left = [t for t in left if not F.f12int_poll(ctx, t, 200)]
+
+    dq = [torch.from_numpy(np.ascontiguousarray(q)).cuda() for _, q in work]
+    doff = [[torch.from_numpy(lay[i][0][k].copy()).cuda() for k in range(len(CLASSES))] for i in range(len(work))]
+
+    def plain():
+        for i in range(len(work)):
+            for k, c in enumerate(CLASSES):
+                F.f12int_compute_class(ctx, bids[i], c, dq[i], outs[i], doff[i][k], stream)
+        stream.synchronize()
+
+    t0 = time.time()
+    batched()   # first pass: primitive bounds of every (molecule, class), buffers, graph capture
+    t_first = time.time() - t0
+    for _ in range(max(0, args.warmup - 1)):
+        batched()
+        plain()
+    res = {}
+    for name, fn in (("batched", batched), ("plain", plain)):
+        ts = []
+        for _ in range(max(1, args.steps)):
+            torch.cuda.synchronize()
+            l0 = F.f12int_launch_count(ctx)
+            b0 = F.f12int_batch_stats(ctx)["batches"]
+            t = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t)
+            launches = F.f12int_launch_count(ctx) - l0
+            batches = F.f12int_batch_stats(ctx)["batches"] - b0
+        sec = float(np.median(ts))
+        res[name] = {"s_per_pass": sec, "shell_quartets_per_s": nq / sec, "prim_quartets_per_s": npq / sec,
+                     "graph_replays": batches if name == "batched" else 0,
+                     "plain_launches": launches if name == "plain" else 0}
+    F.f12int_device_status(ctx)
+    line = {"metric": "F12 quartets/s over an uneven 64-molecule batch, graph-replayed requests vs plain launches",
+            "value": res["batched"]["shell_quartets_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "64 molecules (seeds 1000-1063, 2-30 atoms, 4s3p2d1f, 1-6 primitives, "
+                                   "exponents [0.03, 200]); 64 x 64 significant shell pairs each; I1..I6",
+                       "shell_quartets_per_pass": nq, "prim_quartets_per_pass": npq,
+                       "batch_limits": {"quartets_per_class": 1 << 19, "items_per_class": 1 << 27}},
+            "batched": res["batched"], "plain": res["plain"],
+            "speedup": res["plain"]["s_per_pass"] / res["batched"]["s_per_pass"],
+            "setup_s": {"set_basis_64": t_basis, "first_pass_with_bounds": t_first},
+            "timing": "wall clock from first submit to last completion (host list building included)"}
+    F.f12int_destroy(ctx)
+    print(json.dumps(line), flush=True)
+
+
+def run_serving(args):
+    """Poisson request streams: latency and throughput, requests vs serial plain launches."""
+    import torch
+    from paper_1412_5070_gb300 import build as B
+    from paper_1412_5070_gb300 import f12int as F
+    B.build()
+    pool = M.serving_pool(12)
+    stream = torch.cuda.Stream()
+    ctx = F.f12int_create(0, 0, stream)
+    F.f12int_set_factor(ctx, M.P0)
+    F.f12int_batch_limits(ctx, 1 << 18, 1 << 25)
+    bids = [F.f12int_set_basis(ctx, b) for b in pool]
+    # one-time bounds of every (molecule, class) before any timing
+    t0 = time.time()
+    warm = []
+    for i, b in enumerate(pool):
+        q = M.pair_block(b, 2, 2, 7)
+        off, tot = _request_layout(b, q, (2, 3, 4, 5, 6))
+        o = torch.empty(tot, dtype=torch.float64, device="cuda")
+        warm.append((o, F.f12int_submit(ctx, bids[i], q, (2, 3, 4, 5, 6), o, off)))
+    for _, t in warm:
+        while not F.f12int_poll(ctx, t, 1000):
+            pass
+    t_setup = time.time() - t0
+    print("serving: setup %.1f s" % t_setup, file=sys.stderr, flush=True)
+    rates = (10, 20, 50, 100, 200, 500, 1000, 2000)
+    rows = []
+    for lam in rates:
+        n = int(min(200, max(40, lam * 8)))
+        reqs = M.serving_requests(n, float(lam), pool, seed=5 + lam)
+        prep = []
+        for (ta, m, classes, q) in reqs:
+            off, tot = _request_layout(pool[m], q, classes)
+            o = torch.empty(tot, dtype=torch.float64, device="cuda")
+            dq = torch.from_numpy(np.ascontiguousarray(q)).cuda()
+            doff = [torch.from_numpy(off[k].copy()).cuda() for k in range(len(classes))]
+            prep.append((ta, m, classes, q, off, o, dq, doff))
+        nq = sum(len(r[3]) * len(r[2]) for r in prep)
+        torch.cuda.synchronize()
+        # request path: submit at the arrival times, a poller records completions
+        done = {}
+        tickets = {}
+        lock = threading.Lock()
+        stop = [False]
+
+        def poller():
+            while True:
+                with lock:
+                    items = list(tickets.items())
+                for k, t in items:
+                    if F.f12int_poll(ctx, t, 0):
+                        done[k] = time.perf_counter()
+                        with lock:
+                            del tickets[k]
+                if stop[0] and not tickets:
+                    return
+                time.sleep(50e-6)
+
+        th = threading.Thread(target=poller)
+        start = time.perf_counter()
+        th.start()
+        sub = {}
+        for k, (ta, m, classes, q, off, o, dq, doff) in enumerate(prep):
+            wait_s = start + ta - time.perf_counter()
+            if wait_s > 0:
+                time.sleep(wait_s)
+            sub[k] = start + ta
+            t = F.f12int_submit(ctx, bids[m], q, classes, o, off)
+            with lock:
+                tickets[k] = t
+        stop[0] = True
+        th.join()
+        lat = np.array([done[k] - sub[k] for k in range(len(prep))]) * 1e3
+        span = max(done.values()) - start
+        eng = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+               "shell_quartets_per_s": nq / span}
+        print("serving: rate %d/s, %d requests: requests path p50 %.1f ms p99 %.1f ms" % (
+            lam, len(prep), eng["p50_ms"], eng["p99_ms"]), file=sys.stderr, flush=True)
+        # serial plain launches in arrival order (capped at 90 s per rate)
+        lat2 = []
+        nq2 = 0
+        start = time.perf_counter()
+        for (ta, m, classes, q, off, o, dq, doff) in prep:
+            if time.perf_counter() - start > 90.0:
+                break
+            wait_s = start + ta - time.perf_counter()
+            if wait_s > 0:
+                time.sleep(wait_s)
+            for k, c in enumerate(classes):
+                F.f12int_compute_class(ctx, bids[m], c, dq, o, doff[k], stream)
+            stream.synchronize()
+            lat2.append(time.perf_counter() - (start + ta))
+            nq2 += len(q) * len(classes)
+        span2 = time.perf_counter() - start
+        lat2 = np.array(lat2) * 1e3
+        plain = {"p50_ms": float(np.percentile(lat2, 50)), "p99_ms": float(np.percentile(lat2, 99)),
+                 "shell_quartets_per_s": nq2 / span2, "requests_completed": len(lat2),
+                 "truncated": len(lat2) < len(prep)}
+        print("serving: rate %d/s: plain p50 %.1f ms p99 %.1f ms (%d of %d)" % (
+            lam, plain["p50_ms"], plain["p99_ms"], len(lat2), len(prep)), file=sys.stderr, flush=True)
+        rows.append({"rate_per_s": lam, "requests": len(prep), "shell_quartets": nq, "requests_path": eng,
+                     "plain_serial": plain})
+        del prep
+    F.f12int_device_status(ctx)
+    best = max(r["requests_path"]["shell_quartets_per_s"] for r in rows)
+    line = {"metric": "served p50/p99 latency (submit to done) and quartets/s, requests vs serial plain launches",
+            "value": best, "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "12 molecules (seeds 500-511, 2-60 atoms, 4s3p2d1f, 1-6 primitives); Poisson "
+                                   "arrivals; half one class of I2..I6, half all five; U{8..64} x U{8..64} "
+                                   "significant shell pairs per request",
+                       "batch_limits": {"quartets_per_class": 1 << 18, "items_per_class": 1 << 25}},
+            "rates": rows, "setup_s": t_setup}
+    F.f12int_destroy(ctx)
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch64":
+        run_batching(args)
+    elif args.workload == "serve":
+        run_serving(args)
     else:
         run_ours(args)
 

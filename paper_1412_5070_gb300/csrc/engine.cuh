@@ -30,6 +30,7 @@ struct EngineReq {
   std::vector<int64_t> off;       // [nclass][n]
   int64_t quartets[7] = {0};      // quartets per class (before screening)
   int64_t items[7] = {0};         // work items per class (before screening)
+  int64_t tasks[7] = {0};         // contraction tasks per class (before screening)
 };
 
 struct TicketState {
@@ -38,21 +39,27 @@ struct TicketState {
   int batch = -1;                 // staging buffer of the batch that runs it
 };
 
-// Contraction plan of a quartet in a batch: tier and ket ranges at 4 warps.
+// Contraction plan of a quartet of nprimq primitive quartets in a batch:
+// ket ranges at 4 warps (the fewest that fit the largest tier, more while a
+// task would exceed kTaskFlops), the tier that holds them, and the work of
+// one task.
 struct BatchPlan {
   int tier, nsplit;
+  double work;
 };
 
-static bool batch_plan(int la, int lb, int lc, int ld, int cls, BatchPlan *bp) {
+static bool batch_plan(int la, int lb, int lc, int ld, int cls, int64_t nprimq, BatchPlan *bp) {
   const int ncd = ncart(lc) * ncart(ld);
   for (int ns = 1; ns <= ncd; ++ns) {
-    const int jc = (ncd + ns - 1) / ns;
-    if ((ncd + jc - 1) / jc != ns) continue;   // no empty ranges
-    const size_t sm = contract_smem(la, lb, lc, ld, cls, kTierWarps, ns);
+    if (!valid_split(ncd, ns)) continue;
+    if (contract_smem(la, lb, lc, ld, cls, kTierWarps, ns) > kTierCap[kTiers - 1]) continue;
+    const int nsw = work_split(la, lb, lc, ld, cls, nprimq, ns);
+    const size_t sm = contract_smem(la, lb, lc, ld, cls, kTierWarps, nsw);
     for (int t = 0; t < kTiers; ++t)
       if (sm <= kTierCap[t]) {
         bp->tier = t;
-        bp->nsplit = ns;
+        bp->nsplit = nsw;
+        bp->work = (double)nprimq * task_flops(la, lb, lc, ld, cls, (ncd + nsw - 1) / nsw);
         return true;
       }
   }
@@ -211,7 +218,7 @@ static int engine_capture(f12int_ctx *ctx, Engine &E) {
 
 // Buffers, streams and launch shapes; called once, at the first submit.
 static int engine_init(f12int_ctx *ctx, Engine &E) {
-  E.tcap = 2 * E.qcap;
+  E.tcap = 4 * E.qcap;
   E.zcap = 6 * E.qcap;
   int rc = F12INT_OK;
   for (int c = 1; c <= 6 && rc == F12INT_OK; ++c) rc = lists_alloc_dev(ctx, E, E.dev[c]);
@@ -273,7 +280,8 @@ static void engine_finish_batch(Engine &E, int b) {
 static int engine_launch(f12int_ctx *ctx, Engine &E, const std::vector<EngineReq *> &batch, int b) {
   struct Item {
     int64_t src;      // index into the flat per-class arrays below
-    int tier, nsplit, key;
+    int tier, nsplit;
+    double work;      // per task
   };
   int64_t nzero = 0;
   for (int cls = 1; cls <= 6; ++cls) {
@@ -301,21 +309,23 @@ static int engine_launch(f12int_ctx *ctx, Engine &E, const std::vector<EngineReq
           continue;
         }
         BatchPlan bp{};
-        batch_plan(la, lb, lc, ld, cls, &bp);   // checked at submit
+        const int64_t np = (int64_t)B.nprim[s[0]] * B.nprim[s[1]] * B.nprim[s[2]] * B.nprim[s[3]];
+        batch_plan(la, lb, lc, ld, cls, np, &bp);   // checked at submit
         for (int k = 0; k < 4; ++k) S.quartets[4 * n + k] = s[k];
         S.offsets[n] = off;
         S.qslot[n] = (int32_t)r;
-        items.push_back(Item{n, bp.tier, bp.nsplit, (la << 6) | (lb << 4) | (lc << 2) | ld});
+        items.push_back(Item{n, bp.tier, bp.nsplit, bp.work});
         ++n;
       }
       S.views[r] = PairView{B.d_pair_start, B.d_pp_p, B.d_pp_P, B.d_pp_ab, B.d_pp_eoff, B.d_epool, B.d_shell_l,
                             B.nshell, B.prim_screen ? B.d_qprim[cls] : nullptr};
       S.outs[r] = R.out;
     }
-    // working order: by tier, then angular-momentum key; permute the lists
+    // working order: by tier, then decreasing work per task (the longest
+    // tasks start first); permute the lists
     std::stable_sort(items.begin(), items.end(), [](const Item &x, const Item &y) {
       if (x.tier != y.tier) return x.tier < y.tier;
-      return x.key < y.key;
+      return x.work > y.work;
     });
     std::vector<int32_t> q2((size_t)4 * n), sl2((size_t)n);
     std::vector<int64_t> of2((size_t)n);
@@ -391,16 +401,18 @@ static void engine_worker(f12int_ctx *ctx, Engine *Ep) {
     }
     // admission: take requests while every class fits the batch limits
     std::vector<EngineReq *> batch;
-    int64_t nq[7] = {0}, ni[7] = {0};
+    int64_t nq[7] = {0}, ni[7] = {0}, nt[7] = {0};
     while (!E.pending.empty() && (int64_t)batch.size() < E.scap) {
       EngineReq *R = E.pending.front();
       bool fits = true;
       for (int c = 1; c <= 6; ++c)
-        if (nq[c] + R->quartets[c] > E.qcap || ni[c] + R->items[c] > E.icap) fits = false;
+        if (nq[c] + R->quartets[c] > E.qcap || ni[c] + R->items[c] > E.icap || nt[c] + R->tasks[c] > E.tcap)
+          fits = false;
       if (!fits && !batch.empty()) break;
       for (int c = 1; c <= 6; ++c) {
         nq[c] += R->quartets[c];
         ni[c] += R->items[c];
+        nt[c] += R->tasks[c];
       }
       batch.push_back(R);
       E.pending.pop_front();
@@ -529,10 +541,12 @@ int f12int_submit(f12int_ctx *ctx, int basis_id, const f12int_request *req, uint
     for (int64_t i = 0; i < n; ++i) {
       const int32_t *s = &R->q[4 * (size_t)i];
       BatchPlan bp{};
-      if (!batch_plan(B.l[s[0]], B.l[s[1]], B.l[s[2]], B.l[s[3]], c, &bp)) {
+      const int64_t np = (int64_t)B.nprim[s[0]] * B.nprim[s[1]] * B.nprim[s[2]] * B.nprim[s[3]];
+      if (!batch_plan(B.l[s[0]], B.l[s[1]], B.l[s[2]], B.l[s[3]], c, np, &bp)) {
         delete R;
         return F12INT_EINVAL;
       }
+      R->tasks[c] += bp.nsplit;
     }
     int rc = ensure_prim_bounds(ctx, basis_id, c);
     if (rc == F12INT_OK && R->thresh > 0.0) rc = ensure_pair_bounds(ctx, basis_id, c);
@@ -563,7 +577,7 @@ int f12int_submit(f12int_ctx *ctx, int basis_id, const f12int_request *req, uint
     }
   }
   for (int c = 1; c <= 6; ++c)
-    if (R->quartets[c] > E->qcap || R->items[c] > E->icap) {
+    if (R->quartets[c] > E->qcap || R->items[c] > E->icap || R->tasks[c] > 4 * E->qcap) {
       delete R;
       return F12INT_ENOMEM;   // larger than one batch: not admitted
     }

@@ -1264,25 +1264,57 @@ struct ContractPlan {
   size_t smem;
 };
 
-// Warps and ket ranges per contraction block: 4 warps, else 2, on the whole
-// ket; where neither fits in 200 KB of shared memory, the fewest ket ranges
-// that fit with 4 warps, else 2, else 1.  smem = 0 when nothing fits.
-static ContractPlan contract_plan(int la, int lb, int lc, int ld, int cls) {
-  const size_t cap = 200 * 1024;
-  for (int nw = BLOCK_CONTRACT / 32; nw > 1; nw /= 2) {
-    size_t sm = contract_smem(la, lb, lc, ld, cls, nw, 1);
-    if (sm <= cap) return ContractPlan{nw, 1, sm};
-  }
+// Algorithmic FP64 flops per primitive quartet of a task that owns jc ket
+// components: Hermite recursion (repeated by every task of a quartet), ket
+// and bra steps (x4 for I5).
+static double task_flops(int la, int lb, int lc, int ld, int cls, int jc) {
+  const int ext = cls == 5 ? 2 : 0;
+  const int L = la + lb + lc + ld + ext;
+  const double r = 2.0 * (L + 1) * (L + 2) * (L + 3) * (L + 4) / 24.0;
+  const double ket = 2.0 * nh_count(la + lb + ext) * nh_count(lc + ld) * jc;
+  const double bra = 2.0 * ncart(la) * ncart(lb) * nh_count(la + lb) * jc * (cls == 5 ? 4 : 1);
+  return r + ket + bra;
+}
+
+// Work one contraction block should carry at most: a quartet with more is
+// split into more ket ranges than its shared memory needs, so that its
+// primitive quartets do not keep one SM busy while the others idle.
+constexpr double kTaskFlops = 5e7;
+
+static bool valid_split(int ncd, int ns) {
+  const int jc = (ncd + ns - 1) / ns;
+  return (ncd + jc - 1) / jc == ns;   // no empty ranges
+}
+
+static int work_split(int la, int lb, int lc, int ld, int cls, int64_t nprimq, int ns_min) {
   const int ncd = ncart(lc) * ncart(ld);
-  for (int nw = BLOCK_CONTRACT / 32; nw >= 1; nw /= 2)
-    for (int ns = 2; ns <= ncd; ++ns) {
-      const int jc = (ncd + ns - 1) / ns;
-      const int nsn = (ncd + jc - 1) / jc;   // no empty ranges
-      if (nsn != ns) continue;
-      size_t sm = contract_smem(la, lb, lc, ld, cls, nw, ns);
-      if (sm <= cap) return ContractPlan{nw, ns, sm};
-    }
-  return ContractPlan{1, 1, 0};
+  for (int ns = ns_min; ns <= ncd; ++ns) {
+    if (!valid_split(ncd, ns)) continue;
+    if ((double)nprimq * task_flops(la, lb, lc, ld, cls, (ncd + ns - 1) / ns) <= kTaskFlops) return ns;
+  }
+  return ncd;
+}
+
+// Warps and ket ranges per contraction block for a quartet of nprimq
+// primitive quartets: 4 warps, else 2, on the whole ket; where neither fits
+// in 200 KB of shared memory, the fewest ket ranges that fit with 4 warps,
+// else 2, else 1; then more ranges while a block would exceed kTaskFlops.
+// smem = 0 when nothing fits.
+static ContractPlan contract_plan(int la, int lb, int lc, int ld, int cls, int64_t nprimq) {
+  const size_t cap = 200 * 1024;
+  const int ncd = ncart(lc) * ncart(ld);
+  int nw = 0, ns = 1;
+  for (int w = BLOCK_CONTRACT / 32; w > 1 && !nw; w /= 2)
+    if (contract_smem(la, lb, lc, ld, cls, w, 1) <= cap) nw = w;
+  for (int w = BLOCK_CONTRACT / 32; w >= 1 && !nw; w /= 2)
+    for (int k = 2; k <= ncd && !nw; ++k)
+      if (valid_split(ncd, k) && contract_smem(la, lb, lc, ld, cls, w, k) <= cap) {
+        nw = w;
+        ns = k;
+      }
+  if (!nw) return ContractPlan{1, 1, 0};
+  ns = work_split(la, lb, lc, ld, cls, nprimq, ns);
+  return ContractPlan{nw, ns, contract_smem(la, lb, lc, ld, cls, nw, ns)};
 }
 
 static std::pair<cudaEvent_t, cudaEvent_t> take_events(f12int_ctx *ctx) {
@@ -1367,11 +1399,10 @@ static int launch_chunk(f12int_ctx *ctx, const f12int_ctx::BasisData &B, int cls
   }
   int64_t t0 = 0;
   for (int64_t ra = qa; ra < qb;) {
-    const int nw = ctx->h_nw[ra], nsp = ctx->h_split[ra];
+    const int nw = ctx->h_nw[ra];
     const size_t sm0 = ctx->h_smem[ra];
-    int64_t rb = ra + 1;
-    while (rb < qb && ctx->h_nw[rb] == nw && ctx->h_split[rb] == nsp && 2 * ctx->h_smem[rb] > sm0) ++rb;
-    const int64_t nt = (rb - ra) * nsp;
+    int64_t rb = ra + 1, nt = ctx->h_split[ra];
+    while (rb < qb && ctx->h_nw[rb] == nw && 2 * ctx->h_smem[rb] > sm0) nt += ctx->h_split[rb++];
     if (sm0 > 48 * 1024) CK(cudaFuncSetAttribute(k_contract<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm0));
     std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
     if (ctx->timing) {
@@ -1533,21 +1564,55 @@ int f12int_compute_class(f12int_ctx *ctx, int basis_id, int cls, const int32_t *
   }
   std::vector<int64_t> perm((size_t)n);
   for (int64_t i = 0; i < n; ++i) perm[i] = i;
-  // decreasing shared-memory need (long blocks first), then by class key
+  // decreasing shared-memory need, then decreasing work per task (long
+  // blocks first), then by class key; plans are memoised per (key, number of
+  // primitive quartets)
   std::vector<size_t> sm0((size_t)n);
   std::vector<int> nw0((size_t)n), sp0((size_t)n);
+  std::vector<double> wk0((size_t)n);
+  struct PlanMemo {
+    ContractPlan pl;
+    double work;
+    bool set;
+  };
+  std::unordered_map<int64_t, PlanMemo> memo;
   for (int64_t i = 0; i < n; ++i) {
     const int k = key0[i];
-    const ContractPlan pl = contract_plan((k >> 6) & 3, (k >> 4) & 3, (k >> 2) & 3, k & 3, cls);
-    if (pl.smem == 0) return F12INT_EINVAL;
-    nw0[i] = pl.nw;
-    sp0[i] = pl.nsplit;
-    sm0[i] = pl.smem;
+    const int32_t *s = &hq0[4 * i];
+    const int64_t np = (int64_t)B.nprim[s[0]] * B.nprim[s[1]] * B.nprim[s[2]] * B.nprim[s[3]];
+    PlanMemo &m = memo[(np << 8) | k];
+    if (!m.set) {
+      const int la = (k >> 6) & 3, lb = (k >> 4) & 3, lc = (k >> 2) & 3, ld = k & 3;
+      m.pl = contract_plan(la, lb, lc, ld, cls, np);
+      const int ncd = ncart(lc) * ncart(ld);
+      m.work = (double)np * task_flops(la, lb, lc, ld, cls, (ncd + m.pl.nsplit - 1) / m.pl.nsplit);
+      m.set = true;
+    }
+    if (m.pl.smem == 0) return F12INT_EINVAL;
+    nw0[i] = m.pl.nw;
+    sp0[i] = m.pl.nsplit;
+    sm0[i] = m.pl.smem;
+    wk0[i] = m.work;
   }
-  std::stable_sort(perm.begin(), perm.end(), [&](int64_t x, int64_t y) {
-    if (sm0[x] != sm0[y]) return sm0[x] > sm0[y];
-    return key0[x] < key0[y];
-  });
+  {
+    // one 64-bit key per quartet: shared memory (desc), work (desc, as the
+    // order-preserving bits of a positive double), then the class key
+    std::vector<std::pair<uint64_t, uint64_t>> sk((size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+      uint64_t wb;
+      float wf = (float)wk0[i];
+      uint32_t fb;
+      std::memcpy(&fb, &wf, sizeof fb);
+      wb = fb;
+      // exact shared memory (8-byte units, < 2^24): a tier launches with the
+      // need of its first quartet, so no later one may need more
+      const uint64_t hi = ((uint64_t)(0xFFFFFF - (sm0[i] >> 3)) << 40) |
+                          ((uint64_t)(0xFFFFFFFFu - (uint32_t)wb) << 8) | (uint64_t)key0[i];
+      sk[i] = {hi, (uint64_t)i};
+    }
+    std::sort(sk.begin(), sk.end());
+    for (int64_t i = 0; i < n; ++i) perm[i] = (int64_t)sk[i].second;
+  }
   std::vector<int32_t> hq((size_t)4 * n);
   std::vector<int64_t> ho((size_t)n);
   ctx->h_nw.resize((size_t)n);
@@ -1783,7 +1848,8 @@ extern "C" int f12int_compute_class_static(f12int_ctx *ctx, int basis_id, int cl
     for (int k = 0; k < 4; ++k)
       if (s[k] < 0 || s[k] >= ns) return F12INT_EINVAL;
     key0[i] = (B.l[s[0]] << 6) | (B.l[s[1]] << 4) | (B.l[s[2]] << 2) | B.l[s[3]];
-    const ContractPlan pl = contract_plan(B.l[s[0]], B.l[s[1]], B.l[s[2]], B.l[s[3]], cls);
+    const ContractPlan pl = contract_plan(B.l[s[0]], B.l[s[1]], B.l[s[2]], B.l[s[3]], cls,
+                                          (int64_t)B.nprim[s[0]] * B.nprim[s[1]] * B.nprim[s[2]] * B.nprim[s[3]]);
     if (pl.smem == 0) return F12INT_EINVAL;
     nw0[i] = pl.nw;
     sp0[i] = pl.nsplit;
@@ -1856,11 +1922,11 @@ extern "C" int f12int_compute_class_static(f12int_ctx *ctx, int basis_id, int cl
       CK(cudaGetLastError());
     }
     for (int64_t ra = qa; ra < qb;) {
-      const int nwr = hnw[ra], nspr = hsp[ra];
+      const int nwr = hnw[ra];
       const size_t smr = hsm[ra];
       int64_t rb = ra + 1;
-      while (rb < qb && hnw[rb] == nwr && hsp[rb] == nspr && 2 * hsm[rb] > smr) ++rb;
-      const int64_t nt = (rb - ra) * nspr;
+      while (rb < qb && hnw[rb] == nwr && 2 * hsm[rb] > smr) ++rb;
+      const int64_t nt = tfirst[rb] - tfirst[ra];
       if (smr > 48 * 1024) CK(cudaFuncSetAttribute(k_contract<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
       k_contract<false><<<(unsigned)nt, 32 * nwr, smr, st>>>(PV, QV, cls, nf, pqa, d_tk + tfirst[ra], nt, nullptr, d_part,
                                                      out_dev, d_o, ctx->d_status, nullptr);

@@ -124,3 +124,83 @@ def block_offsets(basis: Basis, quartets: np.ndarray) -> np.ndarray:
 
 # factor parameter set used throughout: f' = f
 P0 = dict(c0=0.5, rho=-0.5, B=0.5, mu=1.0, n=0)
+
+
+# ------------------------------------------------------- batching and serving --
+
+def significant_pairs(basis: Basis, cut: float = 1e-6) -> np.ndarray:
+    """Shell pairs (a >= b) whose largest primitive overlap factor
+    exp(-ab/(a+b) |AB|^2) is at least ``cut`` (a geometric estimate; it
+    needs no integrals)."""
+    shell = np.repeat(np.arange(basis.nshell), basis.nprim)
+    e = basis.exps
+    cen = basis.centers[shell]
+    r2 = np.sum((cen[:, None, :] - cen[None, :, :]) ** 2, axis=-1)
+    f = np.exp(-(e[:, None] * e[None, :] / (e[:, None] + e[None, :])) * r2)
+    po = basis.prim_off
+    g = np.maximum.reduceat(np.maximum.reduceat(f, po, axis=0), po, axis=1)
+    a, b = np.nonzero(np.tril(g >= cut))
+    return np.stack([a, b], axis=1).astype(np.int32).reshape(-1, 2)
+
+
+def c3_molecule(seed: int) -> Basis:
+    """Molecule of the batching workload: U{2..30} atoms (drawn first from
+    the seed's generator) in a 12 bohr cube with minimum separation 1.8 bohr,
+    4s3p2d1f shells per atom, U{1..6} primitives per shell, exponents
+    log-uniform in [0.03, 200], coefficients uniform in [0.1, 1]."""
+    natom = int(np.random.default_rng(seed).integers(2, 31))
+    return random_molecule(seed, natom, 12.0, 1.8, (4, 3, 2, 1), (1, 6), (0.03, 200.0),
+                           name="batch molecule %d" % seed)
+
+
+def pair_block(basis: Basis, nbra: int, nket: int, seed: int, pairs=None) -> np.ndarray:
+    """Shell quartets of a seeded block of nbra bra x nket ket significant
+    shell pairs (drawn with replacement); ``pairs`` may pass the molecule's
+    significant pairs when they are already known."""
+    if pairs is None:
+        pairs = significant_pairs(basis)
+    rng = np.random.default_rng(seed)
+    bra = pairs[rng.integers(0, len(pairs), size=nbra)]
+    ket = pairs[rng.integers(0, len(pairs), size=nket)]
+    return np.concatenate([np.repeat(bra, nket, axis=0), np.tile(ket, (nbra, 1))], axis=1).astype(np.int32)
+
+
+def batching_workload(nmol: int = 64, seed0: int = 1000, block: int = 64):
+    """(basis, quartets) of nmol molecules, seeds seed0.. : per molecule a
+    block x block significant-pair block (4096 shell quartets per class for
+    block = 64), the same list for every class."""
+    out = []
+    for i in range(nmol):
+        b = c3_molecule(seed0 + i)
+        out.append((b, pair_block(b, block, block, seed0 + i)))
+    return out
+
+
+def serving_requests(nreq: int, rate: float, pool, seed: int = 5):
+    """Poisson arrival stream: (arrival time s, molecule index, classes,
+    quartets) per request.  Half the requests ask for one class (uniform over
+    I2..I6), half for all five; each covers a seeded block of U{8..64} bra x
+    U{8..64} ket significant shell pairs of a molecule drawn uniformly from
+    ``pool``."""
+    rng = np.random.default_rng(seed)
+    sig = [significant_pairs(b) for b in pool]
+    t = 0.0
+    out = []
+    for k in range(nreq):
+        t += rng.exponential(1.0 / rate)
+        m = int(rng.integers(0, len(pool)))
+        classes = (int(rng.integers(2, 7)),) if rng.random() < 0.5 else (2, 3, 4, 5, 6)
+        nb, nk = int(rng.integers(8, 65)), int(rng.integers(8, 65))
+        out.append((t, m, classes, pair_block(pool[m], nb, nk, int(rng.integers(0, 2 ** 31)), sig[m])))
+    return out
+
+
+def serving_pool(npool: int = 12, seed0: int = 500):
+    """Molecules of the serving workload: U{2..60} atoms each (drawn first),
+    basis as the batching workload."""
+    out = []
+    for i in range(npool):
+        natom = int(np.random.default_rng(seed0 + i).integers(2, 61))
+        out.append(random_molecule(seed0 + i, natom, 12.0 + 4.0 * (natom > 30), 1.8, (4, 3, 2, 1), (1, 6),
+                                   (0.03, 200.0), name="serving molecule %d" % (seed0 + i)))
+    return out
