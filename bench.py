@@ -390,7 +390,7 @@ def run_batching(args):
     stream = torch.cuda.Stream()
     ctx = F.f12int_create(0, 0, stream)
     F.f12int_set_factor(ctx, M.P0)
-    F.f12int_batch_limits(ctx, 1 << 19, 1 << 27)
+    F.f12int_batch_limits(ctx, 1 << 19, 1 << 26)
     t0 = time.time()
     bids = [F.f12int_set_basis(ctx, b) for b, _ in work]
     t_basis = time.time() - t0
@@ -417,6 +417,10 @@ def run_batching(args):
     t0 = time.time()
     batched()   # first pass: primitive bounds of every (molecule, class), buffers, graph capture
     t_first = time.time() - t0
+    # per-class schedules measured on the first molecule's block
+    t0 = time.time()
+    tuned = F.f12int_batch_autotune(ctx, bids[0], work[0][1], CLASSES)
+    t_tune = time.time() - t0
     for _ in range(max(0, args.warmup - 1)):
         batched()
         plain()
@@ -444,10 +448,11 @@ def run_batching(args):
             "config": {"workload": "64 molecules (seeds 1000-1063, 2-30 atoms, 4s3p2d1f, 1-6 primitives, "
                                    "exponents [0.03, 200]); 64 x 64 significant shell pairs each; I1..I6",
                        "shell_quartets_per_pass": nq, "prim_quartets_per_pass": npq,
-                       "batch_limits": {"quartets_per_class": 1 << 19, "items_per_class": 1 << 27}},
+                       "batch_limits": {"quartets_per_class": 1 << 19, "items_per_class": 1 << 26}},
             "batched": res["batched"], "plain": res["plain"],
             "speedup": res["plain"]["s_per_pass"] / res["batched"]["s_per_pass"],
-            "setup_s": {"set_basis_64": t_basis, "first_pass_with_bounds": t_first},
+            "setup_s": {"set_basis_64": t_basis, "first_pass_with_bounds": t_first, "autotune": t_tune},
+            "schedule": {"I%d" % c: {"task_flops": v[0], "aux_grid_divisor": v[1]} for c, v in tuned.items()},
             "timing": "wall clock from first submit to last completion (host list building included)"}
     F.f12int_destroy(ctx)
     print(json.dumps(line), flush=True)
@@ -476,6 +481,10 @@ def run_serving(args):
     for _, t in warm:
         while not F.f12int_poll(ctx, t, 1000):
             pass
+    t_setup = time.time() - t0
+    # per-class schedules measured on one request-sized block (40 x 40 pairs of a mid-size molecule)
+    mid = int(np.argsort([b.nshell for b in pool])[len(pool) // 2])
+    tuned = F.f12int_batch_autotune(ctx, bids[mid], M.pair_block(pool[mid], 40, 40, 3), (2, 3, 4, 5, 6))
     t_setup = time.time() - t0
     print("serving: setup %.1f s" % t_setup, file=sys.stderr, flush=True)
     rates = (10, 20, 50, 100, 200, 500, 1000, 2000)
@@ -565,7 +574,8 @@ def run_serving(args):
                                    "arrivals; half one class of I2..I6, half all five; U{8..64} x U{8..64} "
                                    "significant shell pairs per request",
                        "batch_limits": {"quartets_per_class": 1 << 18, "items_per_class": 1 << 25}},
-            "rates": rows, "setup_s": t_setup}
+            "rates": rows, "setup_s": t_setup,
+            "schedule": {"I%d" % c: {"task_flops": v[0], "aux_grid_divisor": v[1]} for c, v in tuned.items()}}
     F.f12int_destroy(ctx)
     print(json.dumps(line), flush=True)
 

@@ -199,9 +199,24 @@ int f12int_poll(f12int_ctx *ctx, uint64_t ticket, int64_t timeout_us, int *done)
 
 /* Capacity of one batch, per class: max_quartets shell quartets and
  * max_items auxiliary work items (primitive quartets times the kernel's term
- * families).  Defaults 2^19 and 2^24 (about 2.2 GB of device buffers and
- * 0.4 GB of pinned staging).  Only before the first f12int_submit. */
+ * families); each class has its own item buffers (128 bytes per item).
+ * Default 2^19 quartets; the default item capacity is set from free device
+ * memory when the engine starts (the six classes' item buffers take at most
+ * a quarter of it, 2^26 items per class at most).  Only before the first
+ * f12int_submit. */
 int f12int_batch_limits(f12int_ctx *ctx, int64_t max_quartets, int64_t max_items);
+
+/* Pick each class's batch schedule by measurement: for every class in
+ * class_mask, run the n sample quartets (host [n][4] shell indices of the
+ * basis) alone through the batch path under each candidate -- the work
+ * target of one contraction task (6.25e6, 1.5e7, 5e7, 2e8 flops) times the
+ * grid of the persistent auxiliary-stage launch (full or half residency) --
+ * and keep the fastest.  report (may be NULL) receives, per class c,
+ * report[3(c-1)] the chosen target, [3(c-1)+1] the grid divisor and
+ * [3(c-1)+2] the best time in seconds.  Needs an idle engine (no request
+ * queued or running); allocates a temporary output. */
+int f12int_batch_autotune(f12int_ctx *ctx, int basis_id, const int32_t *quartets, int64_t n,
+                          uint32_t class_mask, double *report);
 
 /* stats[0] batches launched, stats[1] requests finished, stats[2] requests
  * waiting for a batch. */

@@ -9,7 +9,8 @@
 // captured CUDA graph.  The graph holds, for every class, the four passes of
 // the auxiliary stage and one contraction launch per shared-memory tier, all
 // persistent (grid-stride over counts read from device memory), so the same
-// graph serves every batch.  Two staging buffers let the host build batch
+// graph serves every batch.  The six class pipelines are parallel branches
+// of the graph, each with its own work-item buffers.  Two staging buffers let the host build batch
 // k+1 while batch k runs.  The method is that of f12int_compute_class; only
 // the scheduling differs.
 
@@ -48,12 +49,12 @@ struct BatchPlan {
   double work;
 };
 
-static bool batch_plan(int la, int lb, int lc, int ld, int cls, int64_t nprimq, BatchPlan *bp) {
+static bool batch_plan(int la, int lb, int lc, int ld, int cls, int64_t nprimq, double target, BatchPlan *bp) {
   const int ncd = ncart(lc) * ncart(ld);
   for (int ns = 1; ns <= ncd; ++ns) {
     if (!valid_split(ncd, ns)) continue;
     if (contract_smem(la, lb, lc, ld, cls, kTierWarps, ns) > kTierCap[kTiers - 1]) continue;
-    const int nsw = work_split(la, lb, lc, ld, cls, nprimq, ns);
+    const int nsw = work_split(la, lb, lc, ld, cls, nprimq, ns, target);
     const size_t sm = contract_smem(la, lb, lc, ld, cls, kTierWarps, nsw);
     for (int t = 0; t < kTiers; ++t)
       if (sm <= kTierCap[t]) {
@@ -83,7 +84,7 @@ constexpr int kCounts = 2 + 2 * kTiers;
 struct Engine {
   // limits
   int64_t qcap = (int64_t)1 << 19;   // quartets per class per batch
-  int64_t icap = (int64_t)1 << 24;   // work items per class per batch
+  int64_t icap = 0;                   // work items per class per batch (0: from free HBM)
   int64_t tcap = 0;                   // contraction tasks per class per batch
   int64_t scap = 4096;                // requests per batch
   int64_t zcap = 0;                   // zero-filled blocks per batch
@@ -92,9 +93,10 @@ struct Engine {
   ClassLists dev[7];
   double **zero_dst = nullptr;
   int64_t *zero_len = nullptr, *zero_count = nullptr;
-  int *keys = nullptr;
-  unsigned *order = nullptr, *hist = nullptr, *status = nullptr;
-  double *part = nullptr;
+  int *keys[7] = {nullptr};             // per class: item keys, key order, histogram, partials
+  unsigned *order[7] = {nullptr}, *hist[7] = {nullptr};
+  double *part[7] = {nullptr};
+  unsigned *status = nullptr;
   size_t bytes = 0;
   // staging (pinned), two buffers
   ClassLists stage[2][7];
@@ -105,9 +107,14 @@ struct Engine {
   std::vector<uint64_t> inflight[2];
   // graph
   cudaStream_t stream = nullptr;
+  cudaStream_t branch[7] = {nullptr};   // capture streams of the class branches
   cudaGraphExec_t exec = nullptr;
   bool graph_dirty = true;
   int items_blocks = 0, classify_blocks = 0, tier_blocks[kTiers] = {0};
+  // per-class schedule (f12int_batch_autotune): work target of a contraction
+  // task and the divisor of the auxiliary-stage grid
+  double task_target[7] = {kTaskFlops, kTaskFlops, kTaskFlops, kTaskFlops, kTaskFlops, kTaskFlops, kTaskFlops};
+  int items_div[7] = {1, 1, 1, 1, 1, 1, 1};
   // queue
   std::thread worker;
   std::mutex mu;
@@ -185,32 +192,45 @@ static int engine_capture(f12int_ctx *ctx, Engine &E) {
       CK(cudaFuncSetAttribute(k_contract<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTierCap[t]));
   cudaStream_t cs = nullptr;
   CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaEvent_t fork = nullptr, join[7] = {nullptr};
+  CK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+  for (int c = 1; c <= 6; ++c) CK(cudaEventCreateWithFlags(&join[c], cudaEventDisableTiming));
   const PairView none{};
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     k_zero_blocks<<<4 * 152, 128, 0, cs>>>(E.zero_dst, E.zero_len, E.zero_count);
+    cudaEventRecord(fork, cs);
     for (int cls = 1; cls <= 6; ++cls) {
+      cudaStream_t bs = E.branch[cls];
+      cudaStreamWaitEvent(bs, fork, 0);
       const int kcls = cls == 5 ? 3 : cls;
       const int nf = ctx->tables.nfam[kcls];
       const ClassLists &L = E.dev[cls];
       QuartetView QV{L.quartets, L.pq_off, 0, L.counts, L.qslot, L.views, L.outs};
-      cudaMemsetAsync(E.hist, 0, sizeof(unsigned) * kNKeys, cs);
-      k_items_classify<true><<<E.classify_blocks, BLOCK_AUX, 0, cs>>>(ctx->tables, none, QV, cls, 0, 0, E.keys,
-                                                                      E.hist);
-      k_items_scan<<<1, 1024, 0, cs>>>(E.hist, kNKeys);
-      k_items_scatter<<<E.classify_blocks, BLOCK_AUX, 0, cs>>>(QV, nf, 0, E.keys, E.hist, 0, E.order);
-      k_items_eval<true><<<E.items_blocks, BLOCK_AUX, 0, cs>>>(ctx->tables, none, QV, cls, 0, 0, E.order, E.part,
-                                                               E.status, nullptr);
+      cudaMemsetAsync(E.hist[cls], 0, sizeof(unsigned) * kNKeys, bs);
+      k_items_classify<true><<<E.classify_blocks, BLOCK_AUX, 0, bs>>>(ctx->tables, none, QV, cls, 0, 0,
+                                                                      E.keys[cls], E.hist[cls]);
+      k_items_scan<<<1, 1024, 0, bs>>>(E.hist[cls], kNKeys);
+      k_items_scatter<<<E.classify_blocks, BLOCK_AUX, 0, bs>>>(QV, nf, 0, E.keys[cls], E.hist[cls], 0,
+                                                               E.order[cls]);
+      k_items_eval<true><<<std::max(1, E.items_blocks / E.items_div[cls]), BLOCK_AUX, 0, bs>>>(
+          ctx->tables, none, QV, cls, 0, 0, E.order[cls],
+                                                               E.part[cls], E.status, nullptr);
       for (int t = 0; t < kTiers; ++t)
-        k_contract<true><<<E.tier_blocks[t], 32 * kTierWarps, kTierCap[t], cs>>>(
-            none, QV, cls, nf, 0, L.tasks, 0, L.counts + 2 + 2 * t, E.part, nullptr, L.offsets, E.status, nullptr);
+        k_contract<true><<<E.tier_blocks[t], 32 * kTierWarps, kTierCap[t], bs>>>(
+            none, QV, cls, nf, 0, L.tasks, 0, L.counts + 2 + 2 * t, E.part[cls], nullptr, L.offsets, E.status,
+            nullptr);
+      cudaEventRecord(join[cls], bs);
+      cudaStreamWaitEvent(cs, join[cls], 0);
     }
     e = cudaStreamEndCapture(cs, &g);
   }
   if (e == cudaSuccess) e = cudaGraphInstantiate(&E.exec, g, 0);
   if (g) cudaGraphDestroy(g);
   cudaStreamDestroy(cs);
+  cudaEventDestroy(fork);
+  for (int c = 1; c <= 6; ++c) cudaEventDestroy(join[c]);
   if (e != cudaSuccess) return cuda_fail(e);
   E.graph_dirty = false;
   return F12INT_OK;
@@ -218,6 +238,17 @@ static int engine_capture(f12int_ctx *ctx, Engine &E) {
 
 // Buffers, streams and launch shapes; called once, at the first submit.
 static int engine_init(f12int_ctx *ctx, Engine &E) {
+  if (E.icap == 0) {
+    // admission by free device memory: the six classes' item buffers take at
+    // most a quarter of what is free (and of what the budget leaves)
+    size_t free_b = 0, total_b = 0;
+    CK(cudaMemGetInfo(&free_b, &total_b));
+    if (ctx->budget) free_b = std::min(free_b, ctx->budget > ctx->used ? ctx->budget - ctx->used : (size_t)0);
+    const size_t per_item = sizeof(int) + sizeof(unsigned) + sizeof(double) * (LAUX + 1);
+    const int64_t fit = (int64_t)(free_b / 4 / (6 * per_item));
+    E.icap = std::min<int64_t>((int64_t)1 << 26, fit);
+    if (E.icap < ((int64_t)1 << 16)) return F12INT_ENOMEM;
+  }
   E.tcap = 4 * E.qcap;
   E.zcap = 6 * E.qcap;
   int rc = F12INT_OK;
@@ -225,10 +256,14 @@ static int engine_init(f12int_ctx *ctx, Engine &E) {
   if (rc == F12INT_OK) rc = engine_alloc(ctx, E, &E.zero_dst, (size_t)E.zcap);
   if (rc == F12INT_OK) rc = engine_alloc(ctx, E, &E.zero_len, (size_t)E.zcap);
   if (rc == F12INT_OK) rc = engine_alloc(ctx, E, &E.zero_count, 1);
-  if (rc == F12INT_OK) rc = engine_alloc(ctx, E, &E.keys, (size_t)E.icap);
-  if (rc == F12INT_OK) rc = engine_alloc(ctx, E, &E.order, (size_t)E.icap);
-  if (rc == F12INT_OK) rc = engine_alloc(ctx, E, &E.part, (size_t)E.icap * (LAUX + 1));
-  if (rc == F12INT_OK) rc = engine_alloc(ctx, E, &E.hist, (size_t)kNKeys);
+  for (int c = 1; c <= 6 && rc == F12INT_OK; ++c) {
+    rc = engine_alloc(ctx, E, &E.keys[c], (size_t)E.icap);
+    if (rc == F12INT_OK) rc = engine_alloc(ctx, E, &E.order[c], (size_t)E.icap);
+    if (rc == F12INT_OK) rc = engine_alloc(ctx, E, &E.part[c], (size_t)E.icap * (LAUX + 1));
+    if (rc == F12INT_OK) rc = engine_alloc(ctx, E, &E.hist[c], (size_t)kNKeys);
+    if (rc == F12INT_OK && cudaStreamCreateWithFlags(&E.branch[c], cudaStreamNonBlocking) != cudaSuccess)
+      rc = F12INT_ECUDA;
+  }
   if (rc == F12INT_OK) rc = engine_alloc(ctx, E, &E.status, 1);
   for (int b = 0; b < 2 && rc == F12INT_OK; ++b) {
     for (int c = 1; c <= 6 && rc == F12INT_OK; ++c) rc = lists_alloc_host(E, E.stage[b][c]);
@@ -310,7 +345,7 @@ static int engine_launch(f12int_ctx *ctx, Engine &E, const std::vector<EngineReq
         }
         BatchPlan bp{};
         const int64_t np = (int64_t)B.nprim[s[0]] * B.nprim[s[1]] * B.nprim[s[2]] * B.nprim[s[3]];
-        batch_plan(la, lb, lc, ld, cls, np, &bp);   // checked at submit
+        batch_plan(la, lb, lc, ld, cls, np, E.task_target[cls], &bp);   // checked at submit
         for (int k = 0; k < 4; ++k) S.quartets[4 * n + k] = s[k];
         S.offsets[n] = off;
         S.qslot[n] = (int32_t)r;
@@ -459,9 +494,15 @@ static void engine_shutdown(f12int_ctx *ctx) {
     cudaFreeHost(E->stage_status[b]);
     if (E->ev[b]) cudaEventDestroy(E->ev[b]);
   }
-  void *ds[] = {E->zero_dst, E->zero_len, E->zero_count, E->keys, E->order, E->part, E->hist, E->status};
+  void *ds[] = {E->zero_dst, E->zero_len, E->zero_count, E->status};
   for (void *p : ds)
     if (p) cudaFree(p);
+  for (int c = 1; c <= 6; ++c) {
+    void *cs[] = {E->keys[c], E->order[c], E->part[c], E->hist[c]};
+    for (void *p : cs)
+      if (p) cudaFree(p);
+    if (E->branch[c]) cudaStreamDestroy(E->branch[c]);
+  }
   ctx->used -= std::min(ctx->used, E->bytes);
   if (E->exec) cudaGraphExecDestroy(E->exec);
   if (E->stream) cudaStreamDestroy(E->stream);
@@ -542,7 +583,7 @@ int f12int_submit(f12int_ctx *ctx, int basis_id, const f12int_request *req, uint
       const int32_t *s = &R->q[4 * (size_t)i];
       BatchPlan bp{};
       const int64_t np = (int64_t)B.nprim[s[0]] * B.nprim[s[1]] * B.nprim[s[2]] * B.nprim[s[3]];
-      if (!batch_plan(B.l[s[0]], B.l[s[1]], B.l[s[2]], B.l[s[3]], c, np, &bp)) {
+      if (!batch_plan(B.l[s[0]], B.l[s[1]], B.l[s[2]], B.l[s[3]], c, np, kTaskFlops / 8, &bp)) {
         delete R;
         return F12INT_EINVAL;
       }
@@ -619,6 +660,81 @@ int f12int_poll(f12int_ctx *ctx, uint64_t ticket, int64_t timeout_us, int *done)
     if (std::chrono::steady_clock::now() >= deadline) return F12INT_OK;
     std::this_thread::sleep_for(std::chrono::microseconds(20));
   }
+}
+
+int f12int_batch_autotune(f12int_ctx *ctx, int basis_id, const int32_t *quartets, int64_t n, uint32_t class_mask,
+                          double *report) {
+  if (!ctx || !quartets || n <= 0 || class_mask == 0 || (class_mask >> 6) != 0) return F12INT_EINVAL;
+  if (basis_id < 0 || basis_id >= (int)ctx->bases.size() || !ctx->factor_ready) return F12INT_ENOTREADY;
+  if (!engine_idle(ctx)) return F12INT_EINVAL;
+  const f12int_ctx::BasisData &B = ctx->bases[basis_id];
+  std::vector<int64_t> off((size_t)n);
+  int64_t tot = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    const int32_t *s = quartets + 4 * i;
+    for (int k = 0; k < 4; ++k)
+      if (s[k] < 0 || s[k] >= B.nshell) return F12INT_EINVAL;
+    off[i] = tot;
+    tot += (int64_t)ncart(B.l[s[0]]) * ncart(B.l[s[1]]) * ncart(B.l[s[2]]) * ncart(B.l[s[3]]);
+  }
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (!ctx->engine) ctx->engine = new (std::nothrow) Engine();
+    if (!ctx->engine) return F12INT_ENOMEM;
+  }
+  double *out = nullptr;
+  int rc = dalloc(ctx, &out, sizeof(double) * (size_t)tot);
+  if (rc != F12INT_OK) return rc;
+  const double targets[4] = {kTaskFlops / 8, kTaskFlops * 0.3, kTaskFlops, kTaskFlops * 4};
+  const int divs[2] = {1, 2};
+  // one request of class c, alone in its batch; seconds from submit to done
+  auto run = [&](int c, double *sec) -> int {
+    f12int_request rq{n, quartets, 1u << (c - 1), 0, 0.0, out, off.data()};
+    uint64_t t = 0;
+    const auto t0 = std::chrono::steady_clock::now();
+    int r = f12int_submit(ctx, basis_id, &rq, &t);
+    int done = 0;
+    while (r == F12INT_OK && !done) r = f12int_poll(ctx, t, 100000, &done);
+    *sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return r;
+  };
+  for (int c = 1; c <= 6 && rc == F12INT_OK; ++c) {
+    if (!((class_mask >> (c - 1)) & 1)) continue;
+    double best = 1e300, bt = kTaskFlops;
+    int bd = 1;
+    for (double tg : targets)
+      for (int dv : divs) {
+        {
+          std::lock_guard<std::mutex> lk(ctx->engine->mu);
+          ctx->engine->task_target[c] = tg;
+          ctx->engine->items_div[c] = dv;
+          ctx->engine->graph_dirty = true;
+        }
+        double t1 = 0.0, t2 = 0.0;
+        rc = run(c, &t1);   // first run after a change includes the graph capture
+        if (rc == F12INT_OK) rc = run(c, &t2);
+        if (rc != F12INT_OK) break;
+        if (t2 < best) {
+          best = t2;
+          bt = tg;
+          bd = dv;
+        }
+      }
+    if (rc != F12INT_OK) break;
+    {
+      std::lock_guard<std::mutex> lk(ctx->engine->mu);
+      ctx->engine->task_target[c] = bt;
+      ctx->engine->items_div[c] = bd;
+      ctx->engine->graph_dirty = true;
+    }
+    if (report) {
+      report[3 * (c - 1)] = bt;
+      report[3 * (c - 1) + 1] = bd;
+      report[3 * (c - 1) + 2] = best;
+    }
+  }
+  dfree(ctx, out, sizeof(double) * (size_t)tot);
+  return rc;
 }
 
 int f12int_batch_stats(f12int_ctx *ctx, int64_t *stats) {

@@ -1286,11 +1286,12 @@ static bool valid_split(int ncd, int ns) {
   return (ncd + jc - 1) / jc == ns;   // no empty ranges
 }
 
-static int work_split(int la, int lb, int lc, int ld, int cls, int64_t nprimq, int ns_min) {
+static int work_split(int la, int lb, int lc, int ld, int cls, int64_t nprimq, int ns_min,
+                      double target = kTaskFlops) {
   const int ncd = ncart(lc) * ncart(ld);
   for (int ns = ns_min; ns <= ncd; ++ns) {
     if (!valid_split(ncd, ns)) continue;
-    if ((double)nprimq * task_flops(la, lb, lc, ld, cls, (ncd + ns - 1) / ns) <= kTaskFlops) return ns;
+    if ((double)nprimq * task_flops(la, lb, lc, ld, cls, (ncd + ns - 1) / ns) <= target) return ns;
   }
   return ncd;
 }

@@ -25,7 +25,8 @@ STATUS = {0: "F12INT_OK", -1: "F12INT_EINVAL", -2: "F12INT_ENOMEM", -3: "F12INT_
 EXPORTS = ("f12int_create", "f12int_destroy", "f12int_set_basis", "f12int_set_factor", "f12int_screen",
            "f12int_compute_class", "f12int_compute_class_static", "f12int_aux", "f12int_launch_count",
            "f12int_device_status", "f12int_set_timing", "f12int_kernel_stats", "f12int_kernel_radial",
-           "f12int_submit", "f12int_poll", "f12int_batch_limits", "f12int_batch_stats", "f12int_strerror")
+           "f12int_submit", "f12int_poll", "f12int_batch_limits", "f12int_batch_autotune", "f12int_batch_stats",
+           "f12int_strerror")
 
 
 class F12IntError(RuntimeError):
@@ -87,6 +88,8 @@ def load():
     L.f12int_poll.argtypes = [_vp, ctypes.c_uint64, ctypes.c_int64, _ip]
     L.f12int_batch_limits.argtypes = [_vp, ctypes.c_int64, ctypes.c_int64]
     L.f12int_batch_stats.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
+    L.f12int_batch_autotune.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int32), ctypes.c_int64,
+                                        ctypes.c_uint32, _dp]
     L.f12int_strerror.argtypes = [ctypes.c_int]
     L.f12int_strerror.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -251,3 +254,17 @@ def f12int_batch_stats(ctx) -> dict:
     s = (ctypes.c_int64 * 3)()
     _check(load().f12int_batch_stats(ctx, s), "f12int_batch_stats")
     return {"batches": int(s[0]), "requests_done": int(s[1]), "pending": int(s[2])}
+
+
+def f12int_batch_autotune(ctx, basis_id: int, quartets, classes) -> dict:
+    """Measure and keep the fastest batch schedule of each class on the host
+    sample ``quartets`` [n, 4]; returns {class: (task target, grid divisor,
+    seconds)}."""
+    q = np.ascontiguousarray(quartets, dtype=np.int32).reshape(-1, 4)
+    mask = 0
+    for c in classes:
+        mask |= 1 << (int(c) - 1)
+    rep = (ctypes.c_double * 18)()
+    _check(load().f12int_batch_autotune(ctx, int(basis_id), q.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                        len(q), mask, rep), "f12int_batch_autotune")
+    return {int(c): (rep[3 * (c - 1)], int(rep[3 * (c - 1) + 1]), rep[3 * (c - 1) + 2]) for c in classes}

@@ -190,3 +190,23 @@ def test_ticket_semantics(ctx):
         F.f12int_submit(ctx, bid, bad, (1,), out, off)
     stats = F.f12int_batch_stats(ctx)
     assert stats["batches"] >= 1 and stats["pending"] == 0
+
+
+def test_autotune_keeps_results(ctx):
+    """The autotuner picks one of its candidate schedules per class, and the
+    blocks computed under the chosen schedule still match the per-call path."""
+    basis = M.twelve_atom_spd(2)
+    bid = F.f12int_set_basis(ctx, basis)
+    q = sample(basis, 3, 500, 11)
+    rep = F.f12int_batch_autotune(ctx, bid, q, (3, 5))
+    for c in (3, 5):
+        target, div, sec = rep[c]
+        assert target in (5e7 / 8, 5e7 * 0.3, 5e7, 5e7 * 4) and div in (1, 2) and sec > 0
+    for c in (3, 5):
+        off, tot = layout(basis, q, (c,))
+        out = torch.full((tot,), float("nan"), dtype=torch.float64, device="cuda")
+        wait(ctx, [F.f12int_submit(ctx, bid, q, (c,), out, off)])
+        ref = per_call(ctx, bid, c, q, basis)
+        got = out.cpu().numpy()
+        tol = 1e-13 * np.abs(ref) + 1e-15 * np.max(np.abs(ref))
+        assert np.all(np.abs(got - ref) <= tol)
