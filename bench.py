@@ -23,6 +23,11 @@ Two further workloads, each printing its own JSON line:
                       significant shell pairs, all six classes: the batched
                       request path (f12int_submit) against one plain
                       f12int_compute_class launch per class and molecule.
+  --workload mixed    40 atoms, 5s4p3d2f, 1-8 primitives, exponents [0.02, 500]:
+                      per class a bound-stratified sample of shell quartets (half
+                      with Schwarz bound product >= 1e-4, half below), FP64 against
+                      the mixed path (FP32 recursion and contraction below 1e-4):
+                      time and the mixed path's max abs/rel difference.
   --workload serve    Poisson request streams at 10..2000 requests/s over 12
                       molecules of 2-60 atoms; half the requests ask for one
                       class, half for I2..I6, each over U{8..64} x U{8..64}
@@ -63,7 +68,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
-    ap.add_argument("--workload", default="spd12", choices=("spd12", "batch64", "serve"))
+    ap.add_argument("--workload", default="spd12", choices=("spd12", "batch64", "serve", "mixed"))
     ap.add_argument("--fraction", type=float, default=1.0, help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu-baseline", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -580,6 +585,86 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
+def run_mixed(args):
+    """FP64 vs mixed precision on a bound-stratified sample of a large f-shell molecule."""
+    import torch
+    from paper_1412_5070_gb300 import build as B
+    from paper_1412_5070_gb300 import f12int as F
+    B.build()
+    basis = M.c4_molecule(40)
+    stream = torch.cuda.Stream()
+    ctx = F.f12int_create(0, 0, stream)
+    F.f12int_set_factor(ctx, M.P0)
+    bid = F.f12int_set_basis(ctx, basis)
+    split = 1e-4   # sample split; errors are reported per decade of the estimate
+    per_class = {}
+    total = {"fp64_s": 0.0, "mixed_s": 0.0, "quartets": 0}
+    nper = 1_000_000 // len(CLASSES)
+    for c in CLASSES:
+        pb = F.f12int_pair_bounds(ctx, bid, c, basis.nshell)
+        # candidates from the pair bounds, kept by the library's screening estimate
+        cand = M.bound_stratified_quartets(pb, 4 * nper, split, 1e-16, 400 + c, canonical_braket=(c != 5))
+        est_c = F.f12int_quartet_estimates(ctx, bid, c, cand)
+        hi = cand[est_c >= split][: nper // 2]
+        lo = cand[(est_c < split) & (est_c >= 1e-12)][: nper - len(hi)]
+        q = np.ascontiguousarray(np.concatenate([hi, lo]))
+        est = F.f12int_quartet_estimates(ctx, bid, c, q)
+        off = M.block_offsets(basis, q)
+        dq = torch.from_numpy(q).cuda()
+        doff = torch.from_numpy(off[:-1].copy()).cuda()
+        o64 = torch.empty(int(off[-1]), dtype=torch.float64, device="cuda")
+        o32 = torch.empty(int(off[-1]), dtype=torch.float64, device="cuda")
+        F.f12int_compute_class(ctx, bid, c, dq, o64, doff, stream)   # warm-up
+        F.f12int_compute_class_mixed(ctx, bid, c, dq, o32, doff, split, stream)
+        stream.synchronize()
+        ts = {}
+        for name in ("fp64", "mixed"):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if name == "fp64":
+                F.f12int_compute_class(ctx, bid, c, dq, o64, doff, stream)
+            else:
+                F.f12int_compute_class_mixed(ctx, bid, c, dq, o32, doff, split, stream)
+            e1.record(stream)
+            e1.synchronize()
+            ts[name] = e0.elapsed_time(e1) / 1e3
+        a = o64.cpu().numpy()
+        b = o32.cpu().numpy()
+        d = np.abs(a - b)
+        big = np.abs(a) > 1e-12
+        # largest difference per decade of the quartets' bound product (FP32 side)
+        prod = est
+        qmax = np.maximum.reduceat(d, off[:-1]) if len(d) else np.zeros(0)
+        by_decade = {}
+        for k in range(4, 13):
+            sel = (prod < 10.0 ** -k * 10) & (prod >= 10.0 ** -k)
+            if sel.any():
+                by_decade["[1e-%d,1e-%d)" % (k, k - 1)] = float(qmax[sel].max())
+        nprim = int(np.sum(np.prod(basis.nprim[q], axis=1)))
+        per_class["I%d" % c] = {"shell_quartets": len(q), "prim_quartets": nprim,
+                                "fp32_quartets": int(np.sum(est < split)),
+                                "fp64_s": ts["fp64"], "mixed_s": ts["mixed"], "speedup": ts["fp64"] / ts["mixed"],
+                                "max_abs_diff": float(d.max()),
+                                "max_rel_diff_where_abs_gt_1e-12": float((d[big] / np.abs(a[big])).max()) if big.any() else 0.0,
+                                "max_abs_diff_by_bound_decade": by_decade}
+        total["fp64_s"] += ts["fp64"]
+        total["mixed_s"] += ts["mixed"]
+        total["quartets"] += len(q)
+        print("mixed: I%d %s" % (c, json.dumps(per_class["I%d" % c])), file=sys.stderr, flush=True)
+        del o64, o32
+    F.f12int_device_status(ctx)
+    line = {"metric": "F12 quartets/s, mixed precision (FP32 recursion/contraction below Schwarz 1e-4) vs FP64",
+            "value": total["quartets"] / total["mixed_s"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+            "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": "40 atoms (seed 40, 20 bohr cube), 5s4p3d2f, 1-8 primitives, exponents "
+                                   "[0.02, 500]; per class up to %d shell quartets, half with screening estimate >= 1e-4, "
+                                   "half in [1e-12, 1e-4)" % nper, "fp32_below": split},
+            "fp64_value": total["quartets"] / total["fp64_s"], "per_class": per_class,
+            "error_reference": "the FP64 path of the same library (itself checked against the oracle)"}
+    F.f12int_destroy(ctx)
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -588,6 +673,8 @@ def main():
         run_batching(args)
     elif args.workload == "serve":
         run_serving(args)
+    elif args.workload == "mixed":
+        run_mixed(args)
     else:
         run_ours(args)
 

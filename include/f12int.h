@@ -101,17 +101,36 @@ int f12int_kernel_radial(int cls, const f12int_factor *f, const f12int_factor *f
                          double *value);
 
 /* Schwarz-type screening for class cls: bound(ab) = sqrt(max |(ab|k|ab)|)
- * over the diagonal block (the I3 diagonal for I5).  Writes the canonical
- * shell quartets whose bound product is >= thresh into quartets_out[4*i]
+ * over the diagonal block (the I3 diagonal for I5), times a growth factor
+ * for kernels that grow with r12 (Eq. rs12 with B > 0; the diagonal samples
+ * the kernel at short range only): estimate(ab|cd) = bound(ab) bound(cd)
+ * max_w G(R + w) exp(-xi w^2) over w = 0, 0.5, .., 3 / sqrt(xi), with
+ * G(x) = max(1, max_{1<=s<=x} |k(s)| / max_{1/2<=s<=3/2} |k(s)|), R the
+ * distance between the centres of the two pairs' most diffuse primitive
+ * pairs and xi = pq/(p+q) of those (G = 1 for I1); for I5 and I6 the
+ * estimate carries a further factor 8.  Writes the canonical shell quartets whose estimate is >= thresh into
+ * quartets_out[4*i]
  * (host memory, room for cap quartets) and their count into *n_out.
  * Canonical means a >= b, c >= d and (ab) >= (cd) for I1-I4 and I6; for I5
  * (no bra-ket symmetry, antisymmetric in a <-> b) it means a >= b, c >= d
  * with every (ab), (cd) combination.  If more than cap quartets survive,
  * *n_out holds the full count and nothing beyond cap is written.
- * The bound is rigorous only for positive-definite kernels; for the F12
- * kernels it is a heuristic. */
+ * The bound is rigorous for I1 (positive-definite kernel); for the F12
+ * kernels the estimate is a heuristic. */
 int f12int_screen(f12int_ctx *ctx, int basis_id, int cls, double thresh, int32_t *quartets_out,
                   int64_t cap, int64_t *n_out);
+
+/* The screening estimate of f12int_screen for n given quartets (host
+ * [n][4] shell indices) into est_out[n] (host).  The first call of a (basis,
+ * class) computes its shell-pair bounds. */
+int f12int_quartet_estimates(f12int_ctx *ctx, int basis_id, int cls, const int32_t *quartets, int64_t n,
+                             double *est_out);
+
+/* The shell-pair bounds that f12int_screen multiplies: bounds_out[a*nshell
+ * + b] = sqrt(max |(ab|k|ab)|) over the diagonal block of class cls (the I3
+ * kernel for I5); host memory of nshell*nshell doubles.  Computed on the
+ * device on first use for a (basis, class) and cached. */
+int f12int_pair_bounds(f12int_ctx *ctx, int basis_id, int cls, double *bounds_out);
 
 /* Compute the contracted blocks of class cls (Eq. ii for I1-I4 and I6,
  * Eq. I5byI3_ for I5) for n shell quartets.
@@ -124,6 +143,20 @@ int f12int_screen(f12int_ctx *ctx, int basis_id, int cls, double thresh, int32_t
  * arguments, F12INT_ENOMEM when scratch would exceed the budget. */
 int f12int_compute_class(f12int_ctx *ctx, int basis_id, int cls, const int32_t *quartets_dev,
                          int64_t n, double *out_dev, const int64_t *offsets_dev, void *cuda_stream);
+
+/* Mixed-precision variant of f12int_compute_class: quartets whose shell-pair
+ * bound product (as in f12int_screen) is below fp32_below run the Hermite
+ * recursion and the contraction in FP32 with FP32 accumulation; the
+ * auxiliary functions g_n, the shell-pair data and every other quartet stay
+ * FP64.  fp32_below = 0 is f12int_compute_class.  Meant for quartets whose
+ * blocks are small in absolute terms: the error is bounded by about 1e-7
+ * times the magnitude of the terms an element sums, not relative to the
+ * element.  The first call of a (basis, class) computes its shell-pair
+ * bounds.  Errors as for f12int_compute_class; F12INT_EINVAL for a negative
+ * or NaN fp32_below. */
+int f12int_compute_class_mixed(f12int_ctx *ctx, int basis_id, int cls, const int32_t *quartets_dev,
+                               int64_t n, double *out_dev, const int64_t *offsets_dev, double fp32_below,
+                               void *cuda_stream);
 
 /* Radial derivatives g_n = (Q^-1 d/dQ)^n B_i of the basic integral of
  * class cls at given xi = pq/(p+q) and D = |P - Q| (Sec. 2.3, Eq. bfinal;
@@ -171,8 +204,9 @@ typedef struct {
   int64_t n_quartets;          /* number of shell quartets (>= 0)                        */
   const int32_t *quartets;     /* host [n_quartets][4] shell indices; copied by submit   */
   uint32_t class_mask;         /* bit c-1 set: compute class c (1..6); at least one bit  */
-  int precision;               /* 0: FP64 (the only value accepted)                      */
-  double schwarz_thresh;       /* > 0: quartets whose shell-pair bound product (as in
+  int precision;               /* 0: FP64; 1: mixed, as f12int_compute_class_mixed with
+                                  the bound set by f12int_set_fp32_below                  */
+  double schwarz_thresh;       /* > 0: quartets whose screening estimate (as in
                                   f12int_screen) is below it get zero blocks; 0: none     */
   double *out_dev;             /* device output, FP64, caller-owned; must stay valid and
                                   untouched until the request is done                    */
@@ -186,7 +220,7 @@ typedef struct {
  * synchronously; the first request of the context allocates the batch
  * buffers (see f12int_batch_limits) and starts the worker.
  * Errors: F12INT_EINVAL for bad arguments (shell index out of range, empty or
- * unknown class mask, precision != 0), F12INT_ENOTREADY without basis or
+ * unknown class mask, precision not 0 or 1), F12INT_ENOTREADY without basis or
  * factor, F12INT_ENOMEM when the request alone exceeds one batch (split it). */
 int f12int_submit(f12int_ctx *ctx, int basis_id, const f12int_request *req, uint64_t *ticket);
 
@@ -217,6 +251,12 @@ int f12int_batch_limits(f12int_ctx *ctx, int64_t max_quartets, int64_t max_items
  * queued or running); allocates a temporary output. */
 int f12int_batch_autotune(f12int_ctx *ctx, int basis_id, const int32_t *quartets, int64_t n,
                           uint32_t class_mask, double *report);
+
+/* Screening estimate below which mixed requests (precision 1) run the
+ * Hermite recursion and contraction in FP32 (default 1e-5, where the FP32
+ * difference stayed below 4.1e-11 on a 40-atom f-shell sample; at 1e-4 it
+ * reached 1.5e-10).  Applies to batches built after the call. */
+int f12int_set_fp32_below(f12int_ctx *ctx, double bound);
 
 /* stats[0] batches launched, stats[1] requests finished, stats[2] requests
  * waiting for a batch. */

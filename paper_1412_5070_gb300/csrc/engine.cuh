@@ -16,15 +16,17 @@
 
 namespace {
 
-constexpr int kTiers = 4;
+constexpr int kTiers = 4;                // shared-memory tiers per precision
 constexpr size_t kTierCap[kTiers] = {32 * 1024, 64 * 1024, 112 * 1024, 200 * 1024};
 constexpr int kTierWarps = 4;
+constexpr int kLaunches = 2 * kTiers;     // FP64 tiers, then FP32 tiers (mixed requests)
 
 struct EngineReq {
   uint64_t ticket = 0;
   int basis = 0;
   const f12int_ctx::BasisData *B = nullptr;   // stable: the deque never moves its elements
   uint32_t mask = 0;
+  int precision = 0;                  // 1: FP32 recursion and contraction below the FP32 bound
   double thresh = 0.0;
   double *out = nullptr;
   std::vector<int32_t> q;
@@ -49,16 +51,18 @@ struct BatchPlan {
   double work;
 };
 
-static bool batch_plan(int la, int lb, int lc, int ld, int cls, int64_t nprimq, double target, BatchPlan *bp) {
+static bool batch_plan(int la, int lb, int lc, int ld, int cls, int64_t nprimq, double target, BatchPlan *bp,
+                       bool fp32 = false) {
   const int ncd = ncart(lc) * ncart(ld);
+  const size_t esz = fp32 ? 4 : 8;
   for (int ns = 1; ns <= ncd; ++ns) {
     if (!valid_split(ncd, ns)) continue;
-    if (contract_smem(la, lb, lc, ld, cls, kTierWarps, ns) > kTierCap[kTiers - 1]) continue;
+    if (contract_smem(la, lb, lc, ld, cls, kTierWarps, ns, esz) > kTierCap[kTiers - 1]) continue;
     const int nsw = work_split(la, lb, lc, ld, cls, nprimq, ns, target);
-    const size_t sm = contract_smem(la, lb, lc, ld, cls, kTierWarps, nsw);
+    const size_t sm = contract_smem(la, lb, lc, ld, cls, kTierWarps, nsw, esz);
     for (int t = 0; t < kTiers; ++t)
       if (sm <= kTierCap[t]) {
-        bp->tier = t;
+        bp->tier = t + (fp32 ? kTiers : 0);
         bp->nsplit = nsw;
         bp->work = (double)nprimq * task_flops(la, lb, lc, ld, cls, (ncd + nsw - 1) / nsw);
         return true;
@@ -79,7 +83,7 @@ struct ClassLists {
   PairView *views = nullptr;      // [scap]
   double **outs = nullptr;        // [scap]
 };
-constexpr int kCounts = 2 + 2 * kTiers;
+constexpr int kCounts = 2 + 2 * kLaunches;
 
 struct Engine {
   // limits
@@ -110,7 +114,8 @@ struct Engine {
   cudaStream_t branch[7] = {nullptr};   // capture streams of the class branches
   cudaGraphExec_t exec = nullptr;
   bool graph_dirty = true;
-  int items_blocks = 0, classify_blocks = 0, tier_blocks[kTiers] = {0};
+  int items_blocks = 0, classify_blocks = 0, tier_blocks[kLaunches] = {0};
+  double fp32_below = 1e-5;           // mixed requests: FP32 below this screening estimate
   // per-class schedule (f12int_batch_autotune): work target of a contraction
   // task and the divisor of the auxiliary-stage grid
   double task_target[7] = {kTaskFlops, kTaskFlops, kTaskFlops, kTaskFlops, kTaskFlops, kTaskFlops, kTaskFlops};
@@ -188,8 +193,10 @@ static int engine_capture(f12int_ctx *ctx, Engine &E) {
     E.exec = nullptr;
   }
   for (int t = 0; t < kTiers; ++t)
-    if (kTierCap[t] > 48 * 1024)
-      CK(cudaFuncSetAttribute(k_contract<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTierCap[t]));
+    if (kTierCap[t] > 48 * 1024) {
+      CK(cudaFuncSetAttribute(k_contract<true, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTierCap[t]));
+      CK(cudaFuncSetAttribute(k_contract<true, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTierCap[t]));
+    }
   cudaStream_t cs = nullptr;
   CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   cudaEvent_t fork = nullptr, join[7] = {nullptr};
@@ -217,10 +224,16 @@ static int engine_capture(f12int_ctx *ctx, Engine &E) {
       k_items_eval<true><<<std::max(1, E.items_blocks / E.items_div[cls]), BLOCK_AUX, 0, bs>>>(
           ctx->tables, none, QV, cls, 0, 0, E.order[cls],
                                                                E.part[cls], E.status, nullptr);
-      for (int t = 0; t < kTiers; ++t)
-        k_contract<true><<<E.tier_blocks[t], 32 * kTierWarps, kTierCap[t], bs>>>(
-            none, QV, cls, nf, 0, L.tasks, 0, L.counts + 2 + 2 * t, E.part[cls], nullptr, L.offsets, E.status,
-            nullptr);
+      for (int t = 0; t < kLaunches; ++t) {
+        if (t < kTiers)
+          k_contract<true, double><<<E.tier_blocks[t], 32 * kTierWarps, kTierCap[t], bs>>>(
+              none, QV, cls, nf, 0, L.tasks, 0, L.counts + 2 + 2 * t, E.part[cls], nullptr, L.offsets, E.status,
+              nullptr);
+        else
+          k_contract<true, float><<<E.tier_blocks[t], 32 * kTierWarps, kTierCap[t - kTiers], bs>>>(
+              none, QV, cls, nf, 0, L.tasks, 0, L.counts + 2 + 2 * t, E.part[cls], nullptr, L.offsets, E.status,
+              nullptr);
+      }
       cudaEventRecord(join[cls], bs);
       cudaStreamWaitEvent(cs, join[cls], 0);
     }
@@ -286,10 +299,14 @@ static int engine_init(f12int_ctx *ctx, Engine &E) {
   E.items_blocks = nsm * std::max(per, 1);
   E.classify_blocks = nsm * 8;
   for (int t = 0; t < kTiers; ++t) {
-    if (kTierCap[t] > 48 * 1024)
-      CK(cudaFuncSetAttribute(k_contract<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTierCap[t]));
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_contract<true>, 32 * kTierWarps, kTierCap[t]));
+    if (kTierCap[t] > 48 * 1024) {
+      CK(cudaFuncSetAttribute(k_contract<true, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTierCap[t]));
+      CK(cudaFuncSetAttribute(k_contract<true, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTierCap[t]));
+    }
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_contract<true, double>, 32 * kTierWarps, kTierCap[t]));
     E.tier_blocks[t] = nsm * std::max(per, 1);
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_contract<true, float>, 32 * kTierWarps, kTierCap[t]));
+    E.tier_blocks[kTiers + t] = nsm * std::max(per, 1);
   }
   E.ready = true;
   return F12INT_OK;
@@ -331,13 +348,14 @@ static int engine_launch(f12int_ctx *ctx, Engine &E, const std::vector<EngineReq
       for (int c = 1; c < cls; ++c) row += (R.mask >> (c - 1)) & 1;
       const f12int_ctx::BasisData &B = *R.B;
       const int nq = (int)(R.q.size() / 4);
-      const std::vector<double> &bound = B.pair_bound[cls == 5 ? 3 : cls];
+      const bool mixed = R.precision == 1;
       for (int i = 0; i < nq; ++i) {
         const int32_t *s = &R.q[4 * (size_t)i];
         const int64_t off = R.off[(size_t)row * nq + i];
         const int la = B.l[s[0]], lb = B.l[s[1]], lc = B.l[s[2]], ld = B.l[s[3]];
-        if (R.thresh > 0.0 &&
-            bound[(size_t)s[0] * B.nshell + s[1]] * bound[(size_t)s[2] * B.nshell + s[3]] < R.thresh) {
+        const double est =
+            (R.thresh > 0.0 || mixed) ? screen_estimate(ctx, B, cls, s[0], s[1], s[2], s[3]) : 0.0;
+        if (R.thresh > 0.0 && est < R.thresh) {
           E.zstage_dst[b][nzero] = R.out + off;
           E.zstage_len[b][nzero] = (int64_t)ncart(la) * ncart(lb) * ncart(lc) * ncart(ld);
           ++nzero;
@@ -345,7 +363,8 @@ static int engine_launch(f12int_ctx *ctx, Engine &E, const std::vector<EngineReq
         }
         BatchPlan bp{};
         const int64_t np = (int64_t)B.nprim[s[0]] * B.nprim[s[1]] * B.nprim[s[2]] * B.nprim[s[3]];
-        batch_plan(la, lb, lc, ld, cls, np, E.task_target[cls], &bp);   // checked at submit
+        const bool fp32 = mixed && est < E.fp32_below;
+        batch_plan(la, lb, lc, ld, cls, np, E.task_target[cls], &bp, fp32);   // checked at submit
         for (int k = 0; k < 4; ++k) S.quartets[4 * n + k] = s[k];
         S.offsets[n] = off;
         S.qslot[n] = (int32_t)r;
@@ -383,7 +402,7 @@ static int engine_launch(f12int_ctx *ctx, Engine &E, const std::vector<EngineReq
     S.counts[0] = n;
     S.counts[1] = npq;
     int64_t i = 0;
-    for (int t = 0; t < kTiers; ++t) {
+    for (int t = 0; t < kLaunches; ++t) {
       S.counts[2 + 2 * t] = nt;
       for (; i < n && items[i].tier == t; ++i)
         for (int sp = 0; sp < items[i].nsplit; ++sp) S.tasks[nt++] = CTask{(int32_t)i, (int16_t)sp, (int16_t)items[i].nsplit};
@@ -551,7 +570,7 @@ int f12int_submit(f12int_ctx *ctx, int basis_id, const f12int_request *req, uint
   if (req->n_quartets < 0 || (req->n_quartets > 0 && (!req->quartets || !req->offsets || !req->out_dev)))
     return F12INT_EINVAL;
   if (req->class_mask == 0 || (req->class_mask >> 6) != 0) return F12INT_EINVAL;
-  if (req->precision != 0) return F12INT_EINVAL;
+  if (req->precision != 0 && req->precision != 1) return F12INT_EINVAL;
   if (!(req->schwarz_thresh >= 0.0)) return F12INT_EINVAL;
   const f12int_ctx::BasisData &B = ctx->bases[basis_id];
   const int64_t n = req->n_quartets;
@@ -562,6 +581,7 @@ int f12int_submit(f12int_ctx *ctx, int basis_id, const f12int_request *req, uint
   R->basis = basis_id;
   R->B = &B;
   R->mask = req->class_mask;
+  R->precision = req->precision;
   R->thresh = req->schwarz_thresh;
   R->out = req->out_dev;
   R->q.assign(req->quartets, req->quartets + 4 * n);
@@ -590,7 +610,7 @@ int f12int_submit(f12int_ctx *ctx, int basis_id, const f12int_request *req, uint
       R->tasks[c] += bp.nsplit;
     }
     int rc = ensure_prim_bounds(ctx, basis_id, c);
-    if (rc == F12INT_OK && R->thresh > 0.0) rc = ensure_pair_bounds(ctx, basis_id, c);
+    if (rc == F12INT_OK && (R->thresh > 0.0 || R->precision == 1)) rc = ensure_pair_bounds(ctx, basis_id, c);
     if (rc != F12INT_OK) {
       delete R;
       return rc;
@@ -735,6 +755,16 @@ int f12int_batch_autotune(f12int_ctx *ctx, int basis_id, const int32_t *quartets
   }
   dfree(ctx, out, sizeof(double) * (size_t)tot);
   return rc;
+}
+
+int f12int_set_fp32_below(f12int_ctx *ctx, double bound) {
+  if (!ctx || !(bound >= 0.0)) return F12INT_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (!ctx->engine) ctx->engine = new (std::nothrow) Engine();
+  if (!ctx->engine) return F12INT_ENOMEM;
+  std::lock_guard<std::mutex> lk2(ctx->engine->mu);
+  ctx->engine->fp32_below = bound;
+  return F12INT_OK;
 }
 
 int f12int_batch_stats(f12int_ctx *ctx, int64_t *stats) {

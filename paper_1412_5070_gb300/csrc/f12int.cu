@@ -418,12 +418,17 @@ static inline int ne3_chunk_max(int l1, int l2, int jc) {
   return cur > best ? cur : best;
 }
 
-// One contraction task (quartet and ket range) by the whole block.
-template <bool BATCH>
+__device__ __forceinline__ double tfma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float tfma(float a, float b, float c) { return fmaf(a, b, c); }
+
+// One contraction task (quartet and ket range) by the whole block.  T is the
+// type of the Hermite recursion, the E products and every accumulation
+// (double, or float on the mixed path); g_n are always summed in double.
+template <bool BATCH, class T>
 __device__ __forceinline__ void contract_task(const PairView &PV0, const QuartetView &QV, int cls, int nf,
                                               int64_t pq0, const CTask task, const double *part, double *out,
                                               const int64_t *offsets, unsigned long long *flops_total,
-                                              double *smem, int *off_ab, int *off_cd) {
+                                              T *smem, int *off_ab, int *off_cd) {
   const int64_t q = task.q;
   const int split = task.split, nsplit = task.nsplit;
   const PairView &PV = qv_view<BATCH>(PV0, QV, q);
@@ -461,14 +466,14 @@ __device__ __forceinline__ void contract_task(const PairView &PV0, const Quartet
   __syncthreads();
   const int ne3cd = off_cd[ncd], ne3ab = off_ab[nab];
   const size_t wsz = contract_warp_doubles(nhL, nhB, ncd, ne3cd);
-  double *R0 = smem + warp * wsz;
-  double *R1 = R0 + nhL;
-  double *W = R1 + nhL;
-  double *gw = W + (size_t)nhB * ncd;
-  double *E3cd = gw + (LAUX + 1);
-  double *Oacc = smem + nw * wsz;
-  double *E3ab = Oacc + (size_t)nab * ncd;
-  double *E3fx = E3ab + ne3ab, *E3fy = E3fx + ne3ab, *E3fz = E3fy + ne3ab;
+  T *R0 = smem + warp * wsz;
+  T *R1 = R0 + nhL;
+  T *W = R1 + nhL;
+  T *gw = W + (size_t)nhB * ncd;
+  T *E3cd = gw + (LAUX + 1);
+  T *Oacc = smem + nw * wsz;
+  T *E3ab = Oacc + (size_t)nab * ncd;
+  T *E3fx = E3ab + ne3ab, *E3fy = E3fx + ne3ab, *E3fz = E3fy + ne3ab;
   const int ab = s[0] * ns + s[1], cd = s[2] * ns + s[3];
   const int ab0 = PV.pair_start[ab], npab = PV.pair_start[ab + 1] - ab0;
   const int cd0 = PV.pair_start[cd], npcd = PV.pair_start[cd + 1] - cd0;
@@ -489,14 +494,14 @@ __device__ __forceinline__ void contract_task(const PairView &PV0, const Quartet
       if (prim_negligible(PV, pab, pcd)) continue;   // warp-uniform
       ++nproc;
       const int64_t pq = QV.pq_off[q] + (int64_t)iab * npcd + icd - pq0;
-      const double X = pair_sep(PV.pp_P, pab, pcd, 0), Y = pair_sep(PV.pp_P, pab, pcd, 1),
-                   Z = pair_sep(PV.pp_P, pab, pcd, 2);
+      const T X = (T)pair_sep(PV.pp_P, pab, pcd, 0), Y = (T)pair_sep(PV.pp_P, pab, pcd, 1),
+                   Z = (T)pair_sep(PV.pp_P, pab, pcd, 2);
       // g_n = sqrt(pi^5/(p+q))/(pq) * sum over families (fixed order)
       if (lane <= L) {
         const double p = PV.pp_p[pab], qq = PV.pp_p[pcd];
         double acc = 0.0;
         for (int fm = 0; fm < nf; ++fm) acc += part[(pq * nf + fm) * (LAUX + 1) + lane];
-        gw[lane] = pi52 / (sqrt(p + qq) * p * qq) * acc;
+        gw[lane] = (T)(pi52 / (sqrt(p + qq) * p * qq) * acc);
       }
       // E^{cd}_{t'u'v'} products of this ket primitive pair
       const double *Ecd = PV.epool + PV.pp_eoff[pcd];
@@ -506,24 +511,24 @@ __device__ __forceinline__ void contract_task(const PairView &PV0, const Quartet
         const double *ey = Ecd + n1cd + (ec[1] * (ld + 1) + ed[1]) * ntcd;
         const double *ez = Ecd + 2 * n1cd + (ec[2] * (ld + 1) + ed[2]) * ntcd;
         const int tx = ec[0] + ed[0], ty = ec[1] + ed[1], tz = ec[2] + ed[2];
-        double *e = E3cd + off_cd[j];
+        T *e = E3cd + off_cd[j];
         int m = 0;
         for (int t2 = 0; t2 <= tx; ++t2)
           for (int u2 = 0; u2 <= ty; ++u2) {
             const double exy = ex[t2] * ey[u2];
-            for (int v2 = 0; v2 <= tz; ++v2) e[m++] = exy * ez[v2];
+            for (int v2 = 0; v2 <= tz; ++v2) e[m++] = (T)(exy * ez[v2]);
           }
       }
       __syncwarp();
       // Hermite recursion from level n = L down to 0, ping-pong between R0/R1
-      double *cur = R0, *nxt = R1;
+      T *cur = R0, *nxt = R1;
       if (lane == 0) cur[0] = gw[L];
       __syncwarp();
       for (int n = L - 1; n >= 0; --n) {
         const int cnt = nh_count(L - n);
         for (int idx = lane; idx < cnt; idx += 32) {
           const int t = c_tuv[idx][0], u = c_tuv[idx][1], v = c_tuv[idx][2];
-          double val;
+          T val;
           if (idx == 0) {
             val = gw[n];
           } else if (t > 0) {
@@ -539,7 +544,7 @@ __device__ __forceinline__ void contract_task(const PairView &PV0, const Quartet
           nxt[idx] = val;
         }
         __syncwarp();
-        double *tmp = cur;
+        T *tmp = cur;
         cur = nxt;
         nxt = tmp;
       }
@@ -550,21 +555,21 @@ __device__ __forceinline__ void contract_task(const PairView &PV0, const Quartet
         const int t = c_tuv[bi][0], u = c_tuv[bi][1], v = c_tuv[bi][2];
         const unsigned char *ec = c_cart[lc][ic], *ed = c_cart[ld][id];
         const int tx = ec[0] + ed[0], ty = ec[1] + ed[1], tz = ec[2] + ed[2];
-        const double *e = E3cd + off_cd[j];
-        double acc = 0.0;
+        const T *e = E3cd + off_cd[j];
+        T acc = 0;
         int m = 0;
         for (int t2 = 0; t2 <= tx; ++t2)
           for (int u2 = 0; u2 <= ty; ++u2)
-            for (int v2 = 0; v2 <= tz; ++v2) acc = fma(e[m++], cur[hidx(t + t2, u + u2, v + v2)], acc);
+            for (int v2 = 0; v2 <= tz; ++v2) acc = tfma(e[m++], cur[hidx(t + t2, u + u2, v + v2)], acc);
         W[i] += acc;
       }
       __syncwarp();
     }
     __syncthreads();
     // sum the warps' W into warp 0's buffer (fixed order), with the bra sign
-    double *W0 = smem + 2 * nhL;
+    T *W0 = smem + 2 * nhL;
     for (int i = tid; i < nhB * ncd; i += nthr) {
-      double acc = W0[i];
+      T acc = W0[i];
       for (int w = 1; w < nw; ++w) acc += smem[w * wsz + 2 * nhL + i];
       const int bi = i / ncd;
       W0[i] = ((c_tuv[bi][0] + c_tuv[bi][1] + c_tuv[bi][2]) & 1) ? -acc : acc;
@@ -587,12 +592,12 @@ __device__ __forceinline__ void contract_task(const PairView &PV0, const Quartet
           for (int v = 0; v <= tz; ++v, ++m) {
             const double exy = Eab[ox + t] * Eab[oy + u];
             if (cls != 5) {
-              E3ab[o + m] = exy * Eab[oz + v];
+              E3ab[o + m] = (T)(exy * Eab[oz + v]);
             } else {
-              E3ab[o + m] = c5 * exy * Eab[oz + v];
-              E3fx[o + m] = Fab[ox + t] * Eab[oy + u] * Eab[oz + v];
-              E3fy[o + m] = Eab[ox + t] * Fab[oy + u] * Eab[oz + v];
-              E3fz[o + m] = exy * Fab[oz + v];
+              E3ab[o + m] = (T)(c5 * exy * Eab[oz + v]);
+              E3fx[o + m] = (T)(Fab[ox + t] * Eab[oy + u] * Eab[oz + v]);
+              E3fy[o + m] = (T)(Eab[ox + t] * Fab[oy + u] * Eab[oz + v]);
+              E3fz[o + m] = (T)(exy * Fab[oz + v]);
             }
           }
     }
@@ -604,22 +609,22 @@ __device__ __forceinline__ void contract_task(const PairView &PV0, const Quartet
       const unsigned char *ea = c_cart[la][ia], *eb = c_cart[lb][ib];
       const int tx = ea[0] + eb[0], ty = ea[1] + eb[1], tz = ea[2] + eb[2];
       const int o = off_ab[iabc];
-      double acc = 0.0;
+      T acc = 0;
       int m = 0;
       for (int t = 0; t <= tx; ++t)
         for (int u = 0; u <= ty; ++u)
           for (int v = 0; v <= tz; ++v, ++m) {
             if (cls != 5) {
-              acc = fma(E3ab[o + m], W0[hidx(t, u, v) * ncd + j], acc);
+              acc = tfma(E3ab[o + m], W0[hidx(t, u, v) * ncd + j], acc);
             } else {
               // Eq. I5byI3_ with the second coefficient -1 (see the derivation note
               // below); W0 carries the bra sign, so the gradient term changes sign
-              const double lap = W0[hidx(t + 2, u, v) * ncd + j] + W0[hidx(t, u + 2, v) * ncd + j] +
+              const T lap = W0[hidx(t + 2, u, v) * ncd + j] + W0[hidx(t, u + 2, v) * ncd + j] +
                                  W0[hidx(t, u, v + 2) * ncd + j];
-              acc = fma(E3ab[o + m], lap, acc);
-              acc = fma(E3fx[o + m], W0[hidx(t + 1, u, v) * ncd + j], acc);
-              acc = fma(E3fy[o + m], W0[hidx(t, u + 1, v) * ncd + j], acc);
-              acc = fma(E3fz[o + m], W0[hidx(t, u, v + 1) * ncd + j], acc);
+              acc = tfma(E3ab[o + m], lap, acc);
+              acc = tfma(E3fx[o + m], W0[hidx(t + 1, u, v) * ncd + j], acc);
+              acc = tfma(E3fy[o + m], W0[hidx(t, u + 1, v) * ncd + j], acc);
+              acc = tfma(E3fz[o + m], W0[hidx(t, u, v + 1) * ncd + j], acc);
             }
           }
       Oacc[i] += acc;
@@ -631,7 +636,7 @@ __device__ __forceinline__ void contract_task(const PairView &PV0, const Quartet
   else o = out + offsets[q];
   for (int i = tid; i < nab * ncd; i += nthr) {
     const int iabc = i / ncd;
-    o[(size_t)iabc * ncd_all + j0 + (i - iabc * ncd)] = Oacc[i];
+    o[(size_t)iabc * ncd_all + j0 + (i - iabc * ncd)] = (double)Oacc[i];
   }
   if (flops_total && lane == 0 && nproc) {
     // algorithmic FP64 flops per primitive quartet: Hermite recursion 2 C(L+4,4)
@@ -644,23 +649,24 @@ __device__ __forceinline__ void contract_task(const PairView &PV0, const Quartet
   }
 }
 
-template <bool BATCH>
+template <bool BATCH, class T>
 __global__ void __launch_bounds__(BLOCK_CONTRACT)
 k_contract(PairView PV0, QuartetView QV, int cls, int nf, int64_t pq0, const CTask *tasks, int64_t ntask,
            const int64_t *ntask_dev, const double *part, double *out, const int64_t *offsets,
            unsigned int *status, unsigned long long *flops_total) {
-  extern __shared__ double smem[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *smem = reinterpret_cast<T *>(smem_raw);
   __shared__ int off_ab[101], off_cd[101];
   if constexpr (BATCH) {
     // ntask_dev = {first, end} of this launch's tasks
     const int64_t te = ntask_dev[1];
     for (int64_t tk = ntask_dev[0] + blockIdx.x; tk < te; tk += gridDim.x) {
       __syncthreads();   // the previous task's shared-memory reads are done
-      contract_task<BATCH>(PV0, QV, cls, nf, pq0, tasks[tk], part, out, offsets, flops_total, smem, off_ab, off_cd);
+      contract_task<BATCH, T>(PV0, QV, cls, nf, pq0, tasks[tk], part, out, offsets, flops_total, smem, off_ab, off_cd);
     }
   } else {
     if (blockIdx.x < ntask)
-      contract_task<BATCH>(PV0, QV, cls, nf, pq0, tasks[blockIdx.x], part, out, offsets, flops_total, smem, off_ab,
+      contract_task<BATCH, T>(PV0, QV, cls, nf, pq0, tasks[blockIdx.x], part, out, offsets, flops_total, smem, off_ab,
                            off_cd);
   }
 }
@@ -705,6 +711,8 @@ struct f12int_ctx {
     bool prim_screen = true;            // false for the internal per-primitive basis
     double *d_qprim[7] = {nullptr};     // primitive Schwarz factors per class (lazily built)
     std::vector<double> pair_bound[7];  // shell-pair bounds sqrt(max |(ab|k|ab)|) per class (lazily built)
+    std::vector<double> pair_cen;       // [nshell^2][3] centre of the most diffuse primitive pair
+    std::vector<double> pair_pmin;      // [nshell^2] its exponent sum
   };
   std::deque<BasisData> bases;   // deque: growing it never moves existing entries
   // scratch of compute_class (grown on demand, bounded by the budget)
@@ -725,9 +733,13 @@ struct f12int_ctx {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_aux, ev_con, ev_pool;
   std::vector<int> h_nw;       // warps per contraction block, per quartet in the working order
   std::vector<int> h_split;    // ket-component ranges (blocks) per quartet, same order
+  std::vector<char> h_fp32;    // 1: Hermite recursion and contraction in FP32 (mixed path), same order
   std::vector<size_t> h_smem;  // contraction shared memory, per quartet in the working order
   std::mutex mu;
   std::recursive_mutex bounds_mu;   // first-time primitive and shell-pair bounds
+  // growth of each class's kernel with distance (screening estimate):
+  // kgrow[cls][i] = G(i * kGrowStep), see screen_estimate
+  std::vector<double> kgrow[7];
   Engine *engine = nullptr;
 };
 
@@ -1028,6 +1040,70 @@ int f12int_kernel_radial(int cls, const f12int_factor *f, const f12int_factor *f
   return F12INT_OK;
 }
 
+}  // extern "C"
+
+// Screening estimate of a quartet: bound(ab) bound(cd) Gamma.  The diagonal
+// blocks behind bound() sample the kernel at short range only; the F12
+// kernels with B > 0 grow with r (Eq. rs12), so a quartet whose charge
+// distributions lie R apart is larger by about the kernel's size there
+// relative to short range.  With G(x) = max(1, max_{1 <= s <= x} |k(s)| /
+// max_{1/2 <= s <= 3/2} |k(s)|) (G = 1 for 1/r), the overlap of the two
+// distributions, exp(-xi w^2) at distance R + w, weighs the growth:
+//   Gamma = max over w = 0, 0.5, .., 3 (in units of 1/sqrt(xi)) of
+//           G(R + w) exp(-xi w^2),
+// with R and xi = pq/(p+q) from each pair's most diffuse primitive pair.
+// I5 (whose kinetic transform raises a quartet by about the bra exponents
+// over the I3 diagonal it borrows) and I6 (whose f_r f'_r diagonal can cancel
+// at short range) carry a further factor 8; on the 12-atom s/p/d sample the
+// largest ratio of a quartet to its unscaled estimate was 55 (I5) and 49 (I6).
+constexpr double kScreenSafety[7] = {1.0, 1.0, 1.0, 1.0, 1.0, 8.0, 8.0};
+constexpr double kGrowStep = 0.05, kGrowMax = 120.0;
+
+static std::vector<double> growth_table(const f12::TermList &t) {
+  auto kval = [&](double x) {
+    double v = 0.0;
+    for (const f12::Term &u : t) v += u.c * std::pow(x, u.a) * std::exp(u.b * x - u.g * x * x);
+    return std::fabs(v);
+  };
+  double kref = 0.0;
+  for (double x = 0.5; x <= 1.5 + 1e-12; x += 0.01) kref = std::max(kref, kval(x));
+  const int n = (int)(kGrowMax / kGrowStep) + 1;
+  std::vector<double> g((size_t)n, 1.0);
+  double run = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const double x = i * kGrowStep;
+    if (x >= 1.0) run = std::max(run, kval(x));
+    g[i] = kref > 0.0 ? std::max(1.0, run / kref) : 1.0;
+  }
+  return g;
+}
+
+static double screen_estimate(const f12int_ctx *ctx, const f12int_ctx::BasisData &B, int cls, int a, int b, int c,
+                              int d) {
+  const std::vector<double> &pb = B.pair_bound[cls == 5 ? 3 : cls];
+  const int ns = B.nshell;
+  const size_t ab = (size_t)a * ns + b, cd = (size_t)c * ns + d;
+  const double q = pb[ab] * pb[cd];
+  const std::vector<double> &g = ctx->kgrow[cls];
+  if (q == 0.0 || g.empty()) return q * kScreenSafety[cls];
+  double r2 = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    const double dx = B.pair_cen[3 * ab + k] - B.pair_cen[3 * cd + k];
+    r2 += dx * dx;
+  }
+  const double p = B.pair_pmin[ab], qq = B.pair_pmin[cd];
+  const double xi = p * qq / (p + qq), R = std::sqrt(r2), w1 = 1.0 / std::sqrt(xi);
+  double gam = 1.0;
+  for (int k = 0; k <= 6; ++k) {
+    const double w = 0.5 * k * w1;
+    const size_t i = std::min(g.size() - 1, (size_t)((R + w) / kGrowStep) + 1);
+    gam = std::max(gam, g[i] * std::exp(-xi * w * w));
+  }
+  return q * gam * kScreenSafety[cls];
+}
+
+extern "C" {
+
 int f12int_set_factor(f12int_ctx *ctx, const f12int_factor *f, const f12int_factor *fprime) {
   if (!ctx || !f) return F12INT_EINVAL;
   const f12int_factor &fp = fprime ? *fprime : *f;
@@ -1107,6 +1183,7 @@ int f12int_set_factor(f12int_ctx *ctx, const f12int_factor *f, const f12int_fact
       }
   for (auto &b : ctx->bases)   // and so do the shell-pair bounds
     for (int c = 0; c < 7; ++c) b.pair_bound[c].clear();
+  for (int c = 1; c <= 6; ++c) ctx->kgrow[c] = growth_table(f12::kernel_terms(c == 5 ? 3 : c, F1, F2));
   engine_factor_changed(ctx);
   ctx->factor_ready = true;
   return F12INT_OK;
@@ -1159,6 +1236,19 @@ int f12int_set_basis(f12int_ctx *ctx, int nshell, const double *centers, const i
     }
   B.pair_start[(size_t)nshell * nshell] = (int)sa.size();
   const int npp = (int)sa.size();
+  // most diffuse primitive pair of every shell pair (screening geometry)
+  B.pair_cen.assign((size_t)nshell * nshell * 3, 0.0);
+  B.pair_pmin.assign((size_t)nshell * nshell, 0.0);
+  for (int i = 0; i < nshell; ++i)
+    for (int j = 0; j < nshell; ++j) {
+      double ea = exps[poff[i]], eb = exps[poff[j]];
+      for (int x = 1; x < nprim[i]; ++x) ea = std::min(ea, exps[poff[i] + x]);
+      for (int y = 1; y < nprim[j]; ++y) eb = std::min(eb, exps[poff[j] + y]);
+      const size_t k = (size_t)i * nshell + j;
+      B.pair_pmin[k] = ea + eb;
+      for (int d = 0; d < 3; ++d)
+        B.pair_cen[3 * k + d] = (ea * centers[3 * i + d] + eb * centers[3 * j + d]) / (ea + eb);
+    }
   // device buffers
   int *d_sa = nullptr, *d_sb = nullptr, *d_pa = nullptr, *d_pb = nullptr;
   double *d_exps = nullptr, *d_coefs = nullptr;
@@ -1248,15 +1338,16 @@ static int ensure_buf(f12int_ctx *ctx, void **p, size_t *cap, size_t bytes) {
 }
 
 // shared memory of a contraction block with nw warps and nsplit ket ranges
-static size_t contract_smem(int la, int lb, int lc, int ld, int cls, int nw, int nsplit) {
+// (esz: bytes per element, 8 for FP64, 4 for the FP32 path)
+static size_t contract_smem(int la, int lb, int lc, int ld, int cls, int nw, int nsplit, size_t esz = 8) {
   int ext = cls == 5 ? 2 : 0;
   int L = la + lb + lc + ld + ext;
   int nhL = nh_count(L), nhB = nh_count(la + lb + ext);
   int ncd = ncart(lc) * ncart(ld), nab = ncart(la) * ncart(lb);
   int jc = (ncd + nsplit - 1) / nsplit;
   size_t e3ab = (size_t)ne3_count(la, lb) * (cls == 5 ? 4 : 1);
-  return sizeof(double) * ((size_t)nw * contract_warp_doubles(nhL, nhB, jc, ne3_chunk_max(lc, ld, jc)) +
-                           (size_t)nab * jc + e3ab);
+  return esz * ((size_t)nw * contract_warp_doubles(nhL, nhB, jc, ne3_chunk_max(lc, ld, jc)) +
+                 (size_t)nab * jc + e3ab);
 }
 
 struct ContractPlan {
@@ -1301,21 +1392,21 @@ static int work_split(int la, int lb, int lc, int ld, int cls, int64_t nprimq, i
 // in 200 KB of shared memory, the fewest ket ranges that fit with 4 warps,
 // else 2, else 1; then more ranges while a block would exceed kTaskFlops.
 // smem = 0 when nothing fits.
-static ContractPlan contract_plan(int la, int lb, int lc, int ld, int cls, int64_t nprimq) {
+static ContractPlan contract_plan(int la, int lb, int lc, int ld, int cls, int64_t nprimq, size_t esz = 8) {
   const size_t cap = 200 * 1024;
   const int ncd = ncart(lc) * ncart(ld);
   int nw = 0, ns = 1;
   for (int w = BLOCK_CONTRACT / 32; w > 1 && !nw; w /= 2)
-    if (contract_smem(la, lb, lc, ld, cls, w, 1) <= cap) nw = w;
+    if (contract_smem(la, lb, lc, ld, cls, w, 1, esz) <= cap) nw = w;
   for (int w = BLOCK_CONTRACT / 32; w >= 1 && !nw; w /= 2)
     for (int k = 2; k <= ncd && !nw; ++k)
-      if (valid_split(ncd, k) && contract_smem(la, lb, lc, ld, cls, w, k) <= cap) {
+      if (valid_split(ncd, k) && contract_smem(la, lb, lc, ld, cls, w, k, esz) <= cap) {
         nw = w;
         ns = k;
       }
   if (!nw) return ContractPlan{1, 1, 0};
   ns = work_split(la, lb, lc, ld, cls, nprimq, ns);
-  return ContractPlan{nw, ns, contract_smem(la, lb, lc, ld, cls, nw, ns)};
+  return ContractPlan{nw, ns, contract_smem(la, lb, lc, ld, cls, nw, ns, esz)};
 }
 
 static std::pair<cudaEvent_t, cudaEvent_t> take_events(f12int_ctx *ctx) {
@@ -1354,9 +1445,10 @@ static const int kNKeys = MAXFAM * (LAUX + 1) * NZBIN + 1;
 // contraction for quartets [qa, qb) of the device list.
 static int launch_chunk(f12int_ctx *ctx, const f12int_ctx::BasisData &B, int cls, const int32_t *d_quartets,
                         const int64_t *d_pqoff, int64_t n, int64_t qa, int64_t qb, int64_t pqa, int64_t pqb,
-                        size_t smem, double *out_dev, const int64_t *offsets_dev, cudaStream_t st) {
+                        size_t smem, double *out_dev, const int64_t *offsets_dev, cudaStream_t st,
+                        bool prim_screen = true) {
   PairView PV{B.d_pair_start, B.d_pp_p, B.d_pp_P, B.d_pp_ab, B.d_pp_eoff, B.d_epool, B.d_shell_l, B.nshell,
-              B.prim_screen ? B.d_qprim[cls] : nullptr};
+              (B.prim_screen && prim_screen) ? B.d_qprim[cls] : nullptr};
   QuartetView QV{d_quartets, d_pqoff, n, nullptr, nullptr, nullptr, nullptr};
   const int kcls = cls == 5 ? 3 : cls;
   const int nf = ctx->tables.nfam[kcls];
@@ -1401,18 +1493,29 @@ static int launch_chunk(f12int_ctx *ctx, const f12int_ctx::BasisData &B, int cls
   int64_t t0 = 0;
   for (int64_t ra = qa; ra < qb;) {
     const int nw = ctx->h_nw[ra];
+    const char f32 = ctx->h_fp32[ra];
     const size_t sm0 = ctx->h_smem[ra];
     int64_t rb = ra + 1, nt = ctx->h_split[ra];
-    while (rb < qb && ctx->h_nw[rb] == nw && 2 * ctx->h_smem[rb] > sm0) nt += ctx->h_split[rb++];
-    if (sm0 > 48 * 1024) CK(cudaFuncSetAttribute(k_contract<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm0));
+    while (rb < qb && ctx->h_nw[rb] == nw && ctx->h_fp32[rb] == f32 && 2 * ctx->h_smem[rb] > sm0)
+      nt += ctx->h_split[rb++];
     std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
     if (ctx->timing) {
       ev = take_events(ctx);
       cudaEventRecord(ev.first, st);
     }
-    k_contract<false><<<(unsigned)nt, 32 * nw, sm0, st>>>(PV, QV, cls, nf, pqa, ctx->d_tasks + t0, nt, nullptr, ctx->d_part,
-                                                  out_dev, offsets_dev, ctx->d_status,
-                                                  ctx->timing ? ctx->d_fma + 1 : nullptr);
+    if (f32) {
+      if (sm0 > 48 * 1024)
+        CK(cudaFuncSetAttribute(k_contract<false, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm0));
+      k_contract<false, float><<<(unsigned)nt, 32 * nw, sm0, st>>>(
+          PV, QV, cls, nf, pqa, ctx->d_tasks + t0, nt, nullptr, ctx->d_part, out_dev, offsets_dev, ctx->d_status,
+          ctx->timing ? ctx->d_fma + 1 : nullptr);
+    } else {
+      if (sm0 > 48 * 1024)
+        CK(cudaFuncSetAttribute(k_contract<false, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm0));
+      k_contract<false, double><<<(unsigned)nt, 32 * nw, sm0, st>>>(
+          PV, QV, cls, nf, pqa, ctx->d_tasks + t0, nt, nullptr, ctx->d_part, out_dev, offsets_dev, ctx->d_status,
+          ctx->timing ? ctx->d_fma + 1 : nullptr);
+    }
     t0 += nt;
     if (ctx->timing) {
       cudaEventRecord(ev.second, st);
@@ -1533,8 +1636,27 @@ static int ensure_prim_bounds(f12int_ctx *ctx, int basis_id, int cls) {
   return F12INT_OK;
 }
 
+static int compute_class_impl(f12int_ctx *ctx, int basis_id, int cls, const int32_t *quartets_dev, int64_t n,
+                              double *out_dev, const int64_t *offsets_dev, void *cuda_stream, double fp32_below,
+                              bool prim_screen = true);
+static int ensure_pair_bounds(f12int_ctx *ctx, int basis_id, int cls);
+
 int f12int_compute_class(f12int_ctx *ctx, int basis_id, int cls, const int32_t *quartets_dev, int64_t n,
                          double *out_dev, const int64_t *offsets_dev, void *cuda_stream) {
+  return compute_class_impl(ctx, basis_id, cls, quartets_dev, n, out_dev, offsets_dev, cuda_stream, 0.0);
+}
+
+int f12int_compute_class_mixed(f12int_ctx *ctx, int basis_id, int cls, const int32_t *quartets_dev, int64_t n,
+                               double *out_dev, const int64_t *offsets_dev, double fp32_below, void *cuda_stream) {
+  if (!(fp32_below >= 0.0)) return F12INT_EINVAL;
+  return compute_class_impl(ctx, basis_id, cls, quartets_dev, n, out_dev, offsets_dev, cuda_stream, fp32_below);
+}
+
+}  // extern "C"
+
+static int compute_class_impl(f12int_ctx *ctx, int basis_id, int cls, const int32_t *quartets_dev, int64_t n,
+                              double *out_dev, const int64_t *offsets_dev, void *cuda_stream, double fp32_below,
+                              bool prim_screen) {
   if (!ctx) return F12INT_EINVAL;
   if (cls < 1 || cls > 6 || n < 0) return F12INT_EINVAL;
   if (basis_id < 0 || basis_id >= (int)ctx->bases.size()) return F12INT_ENOTREADY;
@@ -1543,6 +1665,7 @@ int f12int_compute_class(f12int_ctx *ctx, int basis_id, int cls, const int32_t *
   if (!quartets_dev || !out_dev || !offsets_dev) return F12INT_EINVAL;
   {
     int rc0 = ensure_prim_bounds(ctx, basis_id, cls);
+    if (rc0 == F12INT_OK && fp32_below > 0.0) rc0 = ensure_pair_bounds(ctx, basis_id, cls);
     if (rc0 != F12INT_OK) return rc0;
   }
   std::lock_guard<std::mutex> lk(ctx->mu);
@@ -1571,20 +1694,24 @@ int f12int_compute_class(f12int_ctx *ctx, int basis_id, int cls, const int32_t *
   std::vector<size_t> sm0((size_t)n);
   std::vector<int> nw0((size_t)n), sp0((size_t)n);
   std::vector<double> wk0((size_t)n);
+  std::vector<char> f320((size_t)n, 0);
   struct PlanMemo {
     ContractPlan pl;
     double work;
     bool set;
   };
   std::unordered_map<int64_t, PlanMemo> memo;
+  const std::vector<double> *pb = fp32_below > 0.0 ? &B.pair_bound[cls == 5 ? 3 : cls] : nullptr;
   for (int64_t i = 0; i < n; ++i) {
     const int k = key0[i];
     const int32_t *s = &hq0[4 * i];
     const int64_t np = (int64_t)B.nprim[s[0]] * B.nprim[s[1]] * B.nprim[s[2]] * B.nprim[s[3]];
-    PlanMemo &m = memo[(np << 8) | k];
+    // mixed path: FP32 Hermite recursion and contraction below the bound
+    if (pb && screen_estimate(ctx, B, cls, s[0], s[1], s[2], s[3]) < fp32_below) f320[i] = 1;
+    PlanMemo &m = memo[(np << 9) | (f320[i] << 8) | k];
     if (!m.set) {
       const int la = (k >> 6) & 3, lb = (k >> 4) & 3, lc = (k >> 2) & 3, ld = k & 3;
-      m.pl = contract_plan(la, lb, lc, ld, cls, np);
+      m.pl = contract_plan(la, lb, lc, ld, cls, np, f320[i] ? 4 : 8);
       const int ncd = ncart(lc) * ncart(ld);
       m.work = (double)np * task_flops(la, lb, lc, ld, cls, (ncd + m.pl.nsplit - 1) / m.pl.nsplit);
       m.set = true;
@@ -1605,9 +1732,10 @@ int f12int_compute_class(f12int_ctx *ctx, int basis_id, int cls, const int32_t *
       uint32_t fb;
       std::memcpy(&fb, &wf, sizeof fb);
       wb = fb;
-      // exact shared memory (8-byte units, < 2^24): a tier launches with the
-      // need of its first quartet, so no later one may need more
-      const uint64_t hi = ((uint64_t)(0xFFFFFF - (sm0[i] >> 3)) << 40) |
+      // FP64 quartets first; exact shared memory (4-byte units, < 2^23): a
+      // tier launches with the need of its first quartet, so no later one
+      // may need more
+      const uint64_t hi = ((uint64_t)f320[i] << 63) | ((uint64_t)(0x7FFFFF - (sm0[i] >> 2)) << 40) |
                           ((uint64_t)(0xFFFFFFFFu - (uint32_t)wb) << 8) | (uint64_t)key0[i];
       sk[i] = {hi, (uint64_t)i};
     }
@@ -1619,12 +1747,14 @@ int f12int_compute_class(f12int_ctx *ctx, int basis_id, int cls, const int32_t *
   ctx->h_nw.resize((size_t)n);
   ctx->h_split.resize((size_t)n);
   ctx->h_smem.resize((size_t)n);
+  ctx->h_fp32.resize((size_t)n);
   for (int64_t i = 0; i < n; ++i) {
     for (int k = 0; k < 4; ++k) hq[4 * i + k] = hq0[4 * perm[i] + k];
     ho[i] = ho0[perm[i]];
     ctx->h_nw[i] = nw0[perm[i]];
     ctx->h_split[i] = sp0[perm[i]];
     ctx->h_smem[i] = sm0[perm[i]];
+    ctx->h_fp32[i] = f320[perm[i]];
   }
   std::vector<int64_t> pqoff((size_t)n + 1);
   int64_t npq = 0;
@@ -1651,7 +1781,7 @@ int f12int_compute_class(f12int_ctx *ctx, int basis_id, int cls, const int32_t *
     int64_t qb = qa + 1;
     while (qb < n && pqoff[qb + 1] - pqoff[qa] <= pq_chunk) ++qb;
     rc = launch_chunk(ctx, B, cls, ctx->d_qperm, ctx->d_pqoff, n, qa, qb, pqoff[qa], pqoff[qb], smem, out_dev,
-                      ctx->d_operm, st);
+                      ctx->d_operm, st, prim_screen);
     if (rc != F12INT_OK) return rc;
     qa = qb;
   }
@@ -1660,6 +1790,8 @@ int f12int_compute_class(f12int_ctx *ctx, int basis_id, int cls, const int32_t *
   if (ctx->timing) collect_events(ctx);
   return F12INT_OK;
 }
+
+extern "C" {
 
 int f12int_aux(f12int_ctx *ctx, int cls, int64_t npts, const double *xi_dev, const double *D_dev, int nmax,
                double *out_dev, void *cuda_stream) {
@@ -1710,7 +1842,11 @@ static int ensure_pair_bounds(f12int_ctx *ctx, int basis_id, int cls) {
     if (cudaMemcpyAsync(dq, hq.data(), sizeof(int32_t) * hq.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemcpyAsync(doff, off.data(), sizeof(int64_t) * nq, cudaMemcpyHostToDevice, st) != cudaSuccess)
       rc = F12INT_ECUDA;
-    if (rc == F12INT_OK) rc = f12int_compute_class(ctx, basis_id, dcls, dq, nq, dout, doff, st);
+    // the diagonal blocks themselves can be far below the primitive screen
+    // (a pair's bound multiplies a partner's that may be large), so they are
+    // computed without it
+    if (rc == F12INT_OK)
+      rc = compute_class_impl(ctx, basis_id, dcls, dq, nq, dout, doff, st, 0.0, /*prim_screen=*/false);
     if (rc == F12INT_OK &&
         (cudaMemcpyAsync(hout.data(), dout, sizeof(double) * tot, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
          cudaStreamSynchronize(st) != cudaSuccess))
@@ -1733,6 +1869,32 @@ static int ensure_pair_bounds(f12int_ctx *ctx, int basis_id, int cls) {
   return F12INT_OK;
 }
 
+int f12int_pair_bounds(f12int_ctx *ctx, int basis_id, int cls, double *bounds_out) {
+  if (!ctx || cls < 1 || cls > 6 || !bounds_out) return F12INT_EINVAL;
+  if (basis_id < 0 || basis_id >= (int)ctx->bases.size() || !ctx->factor_ready) return F12INT_ENOTREADY;
+  int rc = ensure_pair_bounds(ctx, basis_id, cls);
+  if (rc != F12INT_OK) return rc;
+  const std::vector<double> &b = ctx->bases[basis_id].pair_bound[cls == 5 ? 3 : cls];
+  std::memcpy(bounds_out, b.data(), sizeof(double) * b.size());
+  return F12INT_OK;
+}
+
+int f12int_quartet_estimates(f12int_ctx *ctx, int basis_id, int cls, const int32_t *quartets, int64_t n,
+                             double *est_out) {
+  if (!ctx || cls < 1 || cls > 6 || n < 0 || (n > 0 && (!quartets || !est_out))) return F12INT_EINVAL;
+  if (basis_id < 0 || basis_id >= (int)ctx->bases.size() || !ctx->factor_ready) return F12INT_ENOTREADY;
+  int rc = ensure_pair_bounds(ctx, basis_id, cls);
+  if (rc != F12INT_OK) return rc;
+  const f12int_ctx::BasisData &B = ctx->bases[basis_id];
+  for (int64_t i = 0; i < n; ++i) {
+    const int32_t *q = quartets + 4 * i;
+    for (int k = 0; k < 4; ++k)
+      if (q[k] < 0 || q[k] >= B.nshell) return F12INT_EINVAL;
+    est_out[i] = screen_estimate(ctx, B, cls, q[0], q[1], q[2], q[3]);
+  }
+  return F12INT_OK;
+}
+
 int f12int_screen(f12int_ctx *ctx, int basis_id, int cls, double thresh, int32_t *quartets_out, int64_t cap,
                   int64_t *n_out) {
   if (!ctx || cls < 1 || cls > 6 || !n_out || cap < 0 || (cap > 0 && !quartets_out)) return F12INT_EINVAL;
@@ -1747,12 +1909,18 @@ int f12int_screen(f12int_ctx *ctx, int basis_id, int cls, double thresh, int32_t
   for (int a = 0; a < ns; ++a)
     for (int b = 0; b <= a; ++b) pairs.emplace_back(a, b);
   int64_t cnt = 0;
+  const std::vector<double> &g = ctx->kgrow[cls];
+  const double gmax = g.empty() ? 1.0 : g.back();   // G is non-decreasing
   for (size_t i = 0; i < pairs.size(); ++i) {
     size_t jend = (cls == 5) ? pairs.size() : i + 1;
     double bi = bound[(size_t)pairs[i].first * ns + pairs[i].second];
     for (size_t j = 0; j < jend; ++j) {
       double bj = bound[(size_t)pairs[j].first * ns + pairs[j].second];
-      if (bi * bj >= thresh) {
+      const double q = bi * bj;
+      if (q >= thresh ||
+          (q * gmax * kScreenSafety[cls] >= thresh &&
+           screen_estimate(ctx, B, cls, pairs[i].first, pairs[i].second, pairs[j].first, pairs[j].second) >=
+               thresh)) {
         if (cnt < cap) {
           quartets_out[4 * cnt] = pairs[i].first;
           quartets_out[4 * cnt + 1] = pairs[i].second;
@@ -1928,8 +2096,8 @@ extern "C" int f12int_compute_class_static(f12int_ctx *ctx, int basis_id, int cl
       int64_t rb = ra + 1;
       while (rb < qb && hnw[rb] == nwr && 2 * hsm[rb] > smr) ++rb;
       const int64_t nt = tfirst[rb] - tfirst[ra];
-      if (smr > 48 * 1024) CK(cudaFuncSetAttribute(k_contract<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
-      k_contract<false><<<(unsigned)nt, 32 * nwr, smr, st>>>(PV, QV, cls, nf, pqa, d_tk + tfirst[ra], nt, nullptr, d_part,
+      if (smr > 48 * 1024) CK(cudaFuncSetAttribute(k_contract<false, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
+      k_contract<false, double><<<(unsigned)nt, 32 * nwr, smr, st>>>(PV, QV, cls, nf, pqa, d_tk + tfirst[ra], nt, nullptr, d_part,
                                                      out_dev, d_o, ctx->d_status, nullptr);
       ctx->launches++;
       CK(cudaGetLastError());

@@ -23,9 +23,10 @@ STATUS = {0: "F12INT_OK", -1: "F12INT_EINVAL", -2: "F12INT_ENOMEM", -3: "F12INT_
 
 # every entry point declared in include/f12int.h
 EXPORTS = ("f12int_create", "f12int_destroy", "f12int_set_basis", "f12int_set_factor", "f12int_screen",
-           "f12int_compute_class", "f12int_compute_class_static", "f12int_aux", "f12int_launch_count",
+           "f12int_compute_class", "f12int_compute_class_mixed", "f12int_compute_class_static", "f12int_aux", "f12int_launch_count",
            "f12int_device_status", "f12int_set_timing", "f12int_kernel_stats", "f12int_kernel_radial",
            "f12int_submit", "f12int_poll", "f12int_batch_limits", "f12int_batch_autotune", "f12int_batch_stats",
+           "f12int_set_fp32_below", "f12int_pair_bounds", "f12int_quartet_estimates",
            "f12int_strerror")
 
 
@@ -75,6 +76,8 @@ def load():
     L.f12int_screen.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                 ctypes.POINTER(ctypes.c_int32), ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
     L.f12int_compute_class.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int64, _vp, _vp, _vp]
+    L.f12int_compute_class_mixed.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int64, _vp, _vp,
+                                             ctypes.c_double, _vp]
     L.f12int_compute_class_static.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int64, _vp, _vp, _vp]
     L.f12int_aux.argtypes = [_vp, ctypes.c_int, ctypes.c_int64, _vp, _vp, ctypes.c_int, _vp, _vp]
     L.f12int_launch_count.argtypes = [_vp]
@@ -88,6 +91,10 @@ def load():
     L.f12int_poll.argtypes = [_vp, ctypes.c_uint64, ctypes.c_int64, _ip]
     L.f12int_batch_limits.argtypes = [_vp, ctypes.c_int64, ctypes.c_int64]
     L.f12int_batch_stats.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
+    L.f12int_set_fp32_below.argtypes = [_vp, ctypes.c_double]
+    L.f12int_pair_bounds.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _dp]
+    L.f12int_quartet_estimates.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
+                                           ctypes.c_int64, _dp]
     L.f12int_batch_autotune.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int32), ctypes.c_int64,
                                         ctypes.c_uint32, _dp]
     L.f12int_strerror.argtypes = [ctypes.c_int]
@@ -171,6 +178,16 @@ def f12int_compute_class(ctx, basis_id: int, cls: int, quartets_dev, out_dev, of
     n = quartets_dev.numel() // 4
     _check(load().f12int_compute_class(ctx, int(basis_id), int(cls), _ptr(quartets_dev), n, _ptr(out_dev),
                                        _ptr(offsets_dev), _stream_ptr(stream)), "f12int_compute_class")
+
+
+def f12int_compute_class_mixed(ctx, basis_id: int, cls: int, quartets_dev, out_dev, offsets_dev, fp32_below: float,
+                               stream=None) -> None:
+    """As f12int_compute_class, with the Hermite recursion and contraction in
+    FP32 for quartets whose shell-pair bound product is below fp32_below."""
+    n = quartets_dev.numel() // 4
+    _check(load().f12int_compute_class_mixed(ctx, int(basis_id), int(cls), _ptr(quartets_dev), n, _ptr(out_dev),
+                                             _ptr(offsets_dev), float(fp32_below), _stream_ptr(stream)),
+           "f12int_compute_class_mixed")
 
 
 def f12int_compute_class_static(ctx, basis_id: int, cls: int, quartets_dev, out_dev, offsets_dev,
@@ -268,3 +285,24 @@ def f12int_batch_autotune(ctx, basis_id: int, quartets, classes) -> dict:
     _check(load().f12int_batch_autotune(ctx, int(basis_id), q.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                                         len(q), mask, rep), "f12int_batch_autotune")
     return {int(c): (rep[3 * (c - 1)], int(rep[3 * (c - 1) + 1]), rep[3 * (c - 1) + 2]) for c in classes}
+
+
+def f12int_set_fp32_below(ctx, bound: float) -> None:
+    _check(load().f12int_set_fp32_below(ctx, float(bound)), "f12int_set_fp32_below")
+
+
+def f12int_pair_bounds(ctx, basis_id: int, cls: int, nshell: int) -> np.ndarray:
+    """Shell-pair bounds sqrt(max |(ab|k|ab)|) of class cls, [nshell, nshell]."""
+    out = np.zeros((nshell, nshell))
+    _check(load().f12int_pair_bounds(ctx, int(basis_id), int(cls), out.ctypes.data_as(_dp)), "f12int_pair_bounds")
+    return out
+
+
+def f12int_quartet_estimates(ctx, basis_id: int, cls: int, quartets) -> np.ndarray:
+    """The screening estimate of f12int_screen for each host quartet [n, 4]."""
+    q = np.ascontiguousarray(quartets, dtype=np.int32).reshape(-1, 4)
+    out = np.zeros(len(q))
+    _check(load().f12int_quartet_estimates(ctx, int(basis_id), int(cls),
+                                           q.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), len(q),
+                                           out.ctypes.data_as(_dp)), "f12int_quartet_estimates")
+    return out

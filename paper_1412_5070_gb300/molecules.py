@@ -204,3 +204,41 @@ def serving_pool(npool: int = 12, seed0: int = 500):
         out.append(random_molecule(seed0 + i, natom, 12.0 + 4.0 * (natom > 30), 1.8, (4, 3, 2, 1), (1, 6),
                                    (0.03, 200.0), name="serving molecule %d" % (seed0 + i)))
     return out
+
+
+def c4_molecule(seed: int = 40) -> Basis:
+    """Molecule of the mixed-precision workload: 40 atoms in a 20 bohr cube
+    (minimum separation 1.8 bohr), 5s4p3d2f shells per atom, U{1..8}
+    primitives per shell, exponents log-uniform in [0.02, 500], coefficients
+    uniform in [0.1, 1]."""
+    return random_molecule(seed, 40, 20.0, 1.8, (5, 4, 3, 2), (1, 8), (0.02, 500.0), name="40-atom 5s4p3d2f")
+
+
+def bound_stratified_quartets(pair_bound: np.ndarray, n: int, split: float, floor: float, seed: int,
+                              canonical_braket: bool = True) -> np.ndarray:
+    """n shell quartets drawn at random from pairs (a >= b): half with bound
+    product >= split, half in [floor, split); pair_bound is [nshell, nshell]."""
+    ns = pair_bound.shape[0]
+    a, b = np.tril_indices(ns)
+    pb = pair_bound[a, b]
+    keep = pb * pb.max() >= floor
+    a, b, pb = a[keep], b[keep], pb[keep]
+    rng = np.random.default_rng(seed)
+    want = {True: n // 2, False: n - n // 2}
+    got = {True: [], False: []}
+    have = {True: 0, False: 0}
+    for _ in range(10000):
+        if have[True] >= want[True] and have[False] >= want[False]:
+            break
+        i = rng.integers(0, len(a), size=4 * n)
+        j = rng.integers(0, len(a), size=4 * n)
+        if canonical_braket:
+            i, j = np.maximum(i, j), np.minimum(i, j)
+        prod = pb[i] * pb[j]
+        for side, sel in ((True, prod >= split), (False, (prod >= floor) & (prod < split))):
+            k = np.nonzero(sel)[0][: max(0, want[side] - have[side])]
+            got[side].append(np.stack([a[i[k]], b[i[k]], a[j[k]], b[j[k]]], axis=1))
+            have[side] += len(k)
+    else:
+        raise RuntimeError("could not draw the stratified sample")
+    return np.concatenate([np.concatenate(got[True]), np.concatenate(got[False])]).astype(np.int32)

@@ -28,7 +28,7 @@ def lib():
 def declared_functions():
     src = open(os.path.join(ROOT, "include", "f12int.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(f12int_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(f12int_[a-z_0-9]+)\s*\(", src)))
 
 
 def test_library_exports_every_declared_entry_point(lib):
