@@ -16,9 +16,9 @@
 
 namespace {
 
-constexpr int kTiers = 4;                // shared-memory tiers per precision
-constexpr size_t kTierCap[kTiers] = {32 * 1024, 64 * 1024, 112 * 1024, 200 * 1024};
-constexpr int kTierWarps = 4;
+constexpr int kTiers = 5;                // shared-memory tiers per precision
+constexpr size_t kTierCap[kTiers] = {32 * 1024, 64 * 1024, 112 * 1024, 200 * 1024, 200 * 1024};
+constexpr int kTierWarps[kTiers] = {4, 4, 4, 4, 2};   // the last for quartets that need fewer warps
 constexpr int kLaunches = 2 * kTiers;     // FP64 tiers, then FP32 tiers (mixed requests)
 
 struct EngineReq {
@@ -55,18 +55,22 @@ static bool batch_plan(int la, int lb, int lc, int ld, int cls, int64_t nprimq, 
                        bool fp32 = false) {
   const int ncd = ncart(lc) * ncart(ld);
   const size_t esz = fp32 ? 4 : 8;
-  for (int ns = 1; ns <= ncd; ++ns) {
-    if (!valid_split(ncd, ns)) continue;
-    if (contract_smem(la, lb, lc, ld, cls, kTierWarps, ns, esz) > kTierCap[kTiers - 1]) continue;
-    const int nsw = work_split(la, lb, lc, ld, cls, nprimq, ns, target);
-    const size_t sm = contract_smem(la, lb, lc, ld, cls, kTierWarps, nsw, esz);
-    for (int t = 0; t < kTiers; ++t)
-      if (sm <= kTierCap[t]) {
-        bp->tier = t + (fp32 ? kTiers : 0);
-        bp->nsplit = nsw;
-        bp->work = (double)nprimq * task_flops(la, lb, lc, ld, cls, (ncd + nsw - 1) / nsw);
-        return true;
-      }
+  // 4-warp tiers first; the 2-warp tier only for what no 4-warp tier holds
+  for (int pass = 0; pass < 2; ++pass) {
+    const int nw = pass == 0 ? 4 : 2;
+    for (int ns = 1; ns <= ncd; ++ns) {
+      if (!valid_split(ncd, ns)) continue;
+      if (contract_smem(la, lb, lc, ld, cls, nw, ns, esz) > kTierCap[kTiers - 1]) continue;
+      const int nsw = work_split(la, lb, lc, ld, cls, nprimq, ns, target);
+      const size_t sm = contract_smem(la, lb, lc, ld, cls, nw, nsw, esz);
+      for (int t = 0; t < kTiers; ++t)
+        if (kTierWarps[t] == nw && sm <= kTierCap[t]) {
+          bp->tier = t + (fp32 ? kTiers : 0);
+          bp->nsplit = nsw;
+          bp->work = (double)nprimq * task_flops(la, lb, lc, ld, cls, (ncd + nsw - 1) / nsw);
+          return true;
+        }
+    }
   }
   return false;
 }
@@ -225,12 +229,13 @@ static int engine_capture(f12int_ctx *ctx, Engine &E) {
           ctx->tables, none, QV, cls, 0, 0, E.order[cls],
                                                                E.part[cls], E.status, nullptr);
       for (int t = 0; t < kLaunches; ++t) {
+        const int tt = t % kTiers;
         if (t < kTiers)
-          k_contract<true, double><<<E.tier_blocks[t], 32 * kTierWarps, kTierCap[t], bs>>>(
+          k_contract<true, double><<<E.tier_blocks[t], 32 * kTierWarps[tt], kTierCap[tt], bs>>>(
               none, QV, cls, nf, 0, L.tasks, 0, L.counts + 2 + 2 * t, E.part[cls], nullptr, L.offsets, E.status,
               nullptr);
         else
-          k_contract<true, float><<<E.tier_blocks[t], 32 * kTierWarps, kTierCap[t - kTiers], bs>>>(
+          k_contract<true, float><<<E.tier_blocks[t], 32 * kTierWarps[tt], kTierCap[tt], bs>>>(
               none, QV, cls, nf, 0, L.tasks, 0, L.counts + 2 + 2 * t, E.part[cls], nullptr, L.offsets, E.status,
               nullptr);
       }
@@ -303,9 +308,11 @@ static int engine_init(f12int_ctx *ctx, Engine &E) {
       CK(cudaFuncSetAttribute(k_contract<true, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTierCap[t]));
       CK(cudaFuncSetAttribute(k_contract<true, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTierCap[t]));
     }
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_contract<true, double>, 32 * kTierWarps, kTierCap[t]));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_contract<true, double>, 32 * kTierWarps[t],
+                                                     kTierCap[t]));
     E.tier_blocks[t] = nsm * std::max(per, 1);
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_contract<true, float>, 32 * kTierWarps, kTierCap[t]));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_contract<true, float>, 32 * kTierWarps[t],
+                                                     kTierCap[t]));
     E.tier_blocks[kTiers + t] = nsm * std::max(per, 1);
   }
   E.ready = true;

@@ -375,6 +375,9 @@ __global__ void k_aux_points(Tables T, int cls, int64_t npts, const double *xi, 
 // primitive pairs.  Below, ncd is the number of ket components of the block.
 // Shared memory (doubles):
 //   per warp: R0, R1  two levels of the Hermite recursion        2 * nh(L)
+//             Rc      the last level (n = 0) in a cube [t][u][v] of
+//                     pitch L+1, so that the index of R_{t+t',u+u',v+v'}
+//                     is a bra part plus a ket part                  (L+1)^3
 //             W       ket-contracted integrals, bra order <= lab
 //                     (+2 for I5), summed over the warp's ket
 //                     primitive pairs                             nh(Lb) * ncd
@@ -382,13 +385,15 @@ __global__ void k_aux_points(Tables T, int cls, int64_t npts, const double *xi, 
 //             E3cd    E^{cd}_{t'u'v'} = E_t' E_u' E_v' of the
 //                     current ket primitive pair, per component   ne3(lc, ld)
 //   block:    O       output accumulator                          nab * ncd
+//             ck, hb  (ints) cube offset of every ket Hermite product
+//                     and W offset hidx(t,u,v)*ncd of every bra one
 //             E3ab    E^{ab}_{tuv} of the current bra primitive
 //                     pair (times (a-b)/2p for I5), and for I5 the
 //                     three dE/dAB-weighted products              ne3(la, lb) (x4 for I5)
 // The per-warp W are summed in warp order, so results do not depend on
 // scheduling; the sum also applies the bra sign (-1)^{t+u+v} of Eq. ii.
-__host__ __device__ __forceinline__ size_t contract_warp_doubles(int nhL, int nhB, int ncd, int ne3cd) {
-  return (size_t)2 * nhL + (size_t)nhB * ncd + (LAUX + 1) + (size_t)ne3cd;
+__host__ __device__ __forceinline__ size_t contract_warp_doubles(int nhL, int nhB, int ncd, int ne3cd, int L) {
+  return (size_t)2 * nhL + (size_t)(L + 1) * (L + 1) * (L + 1) + (size_t)nhB * ncd + (LAUX + 1) + (size_t)ne3cd;
 }
 
 // number of Hermite products over all component pairs of shells (l1, l2)
@@ -465,15 +470,37 @@ __device__ __forceinline__ void contract_task(const PairView &PV0, const Quartet
   }
   __syncthreads();
   const int ne3cd = off_cd[ncd], ne3ab = off_ab[nab];
-  const size_t wsz = contract_warp_doubles(nhL, nhB, ncd, ne3cd);
+  const size_t wsz = contract_warp_doubles(nhL, nhB, ncd, ne3cd, L);
+  const int P = L + 1;   // cube pitch of Rc
   T *R0 = smem + warp * wsz;
   T *R1 = R0 + nhL;
-  T *W = R1 + nhL;
+  T *Rc = R1 + nhL;
+  T *W = Rc + (size_t)P * P * P;
   T *gw = W + (size_t)nhB * ncd;
   T *E3cd = gw + (LAUX + 1);
   T *Oacc = smem + nw * wsz;
   T *E3ab = Oacc + (size_t)nab * ncd;
   T *E3fx = E3ab + ne3ab, *E3fy = E3fx + ne3ab, *E3fz = E3fy + ne3ab;
+  int *ck = reinterpret_cast<int *>(E3ab + (size_t)ne3ab * (cls == 5 ? 4 : 1));
+  int *hb = ck + ne3cd;
+  // index tables of this task (same for every primitive quartet)
+  for (int j = tid; j < ncd; j += nthr) {
+    const unsigned char *ec = c_cart[lc][(j0 + j) / nd], *ed = c_cart[ld][(j0 + j) % nd];
+    const int tx = ec[0] + ed[0], ty = ec[1] + ed[1], tz = ec[2] + ed[2];
+    int m = off_cd[j];
+    for (int t2 = 0; t2 <= tx; ++t2)
+      for (int u2 = 0; u2 <= ty; ++u2)
+        for (int v2 = 0; v2 <= tz; ++v2) ck[m++] = (t2 * P + u2) * P + v2;
+  }
+  for (int c = tid; c < nab; c += nthr) {
+    const unsigned char *ea = c_cart[la][c / nb], *eb = c_cart[lb][c % nb];
+    const int tx = ea[0] + eb[0], ty = ea[1] + eb[1], tz = ea[2] + eb[2];
+    int m = off_ab[c];
+    for (int t = 0; t <= tx; ++t)
+      for (int u = 0; u <= ty; ++u)
+        for (int v = 0; v <= tz; ++v) hb[m++] = hidx(t, u, v) * ncd;
+  }
+  __syncthreads();
   const int ab = s[0] * ns + s[1], cd = s[2] * ns + s[3];
   const int ab0 = PV.pair_start[ab], npab = PV.pair_start[ab + 1] - ab0;
   const int cd0 = PV.pair_start[cd], npcd = PV.pair_start[cd + 1] - cd0;
@@ -522,7 +549,10 @@ __device__ __forceinline__ void contract_task(const PairView &PV0, const Quartet
       __syncwarp();
       // Hermite recursion from level n = L down to 0, ping-pong between R0/R1
       T *cur = R0, *nxt = R1;
-      if (lane == 0) cur[0] = gw[L];
+      if (lane == 0) {
+        cur[0] = gw[L];
+        if (L == 0) Rc[0] = gw[0];
+      }
       __syncwarp();
       for (int n = L - 1; n >= 0; --n) {
         const int cnt = nh_count(L - n);
@@ -541,7 +571,8 @@ __device__ __forceinline__ void contract_task(const PairView &PV0, const Quartet
             val = Z * cur[hidx(t, u, v - 1)];
             if (v > 1) val += (v - 1) * cur[hidx(t, u, v - 2)];
           }
-          nxt[idx] = val;
+          if (n > 0) nxt[idx] = val;
+          else Rc[(t * P + u) * P + v] = val;   // the last level, in the cube
         }
         __syncwarp();
         T *tmp = cur;
@@ -551,26 +582,21 @@ __device__ __forceinline__ void contract_task(const PairView &PV0, const Quartet
       // inner (ket) sum of Eq. ii:  W[tuv][cd] += sum E^{cd}_{t'u'v'} R_{t+t',u+u',v+v'}
       for (int i = lane; i < nhB * ncd; i += 32) {
         const int bi = i / ncd, j = i - bi * ncd;
-        const int ic = (j0 + j) / nd, id = (j0 + j) - ic * nd;
-        const int t = c_tuv[bi][0], u = c_tuv[bi][1], v = c_tuv[bi][2];
-        const unsigned char *ec = c_cart[lc][ic], *ed = c_cart[ld][id];
-        const int tx = ec[0] + ed[0], ty = ec[1] + ed[1], tz = ec[2] + ed[2];
-        const T *e = E3cd + off_cd[j];
+        const int cb = (c_tuv[bi][0] * P + c_tuv[bi][1]) * P + c_tuv[bi][2];
+        const int m0 = off_cd[j], m1 = off_cd[j + 1];
         T acc = 0;
-        int m = 0;
-        for (int t2 = 0; t2 <= tx; ++t2)
-          for (int u2 = 0; u2 <= ty; ++u2)
-            for (int v2 = 0; v2 <= tz; ++v2) acc = tfma(e[m++], cur[hidx(t + t2, u + u2, v + v2)], acc);
+        for (int m = m0; m < m1; ++m) acc = tfma(E3cd[m], Rc[cb + ck[m]], acc);
         W[i] += acc;
       }
       __syncwarp();
     }
     __syncthreads();
     // sum the warps' W into warp 0's buffer (fixed order), with the bra sign
-    T *W0 = smem + 2 * nhL;
+    const size_t woff = (size_t)2 * nhL + (size_t)P * P * P;   // W within a warp's region
+    T *W0 = smem + woff;
     for (int i = tid; i < nhB * ncd; i += nthr) {
       T acc = W0[i];
-      for (int w = 1; w < nw; ++w) acc += smem[w * wsz + 2 * nhL + i];
+      for (int w = 1; w < nw; ++w) acc += smem[w * wsz + woff + i];
       const int bi = i / ncd;
       W0[i] = ((c_tuv[bi][0] + c_tuv[bi][1] + c_tuv[bi][2]) & 1) ? -acc : acc;
     }
@@ -615,7 +641,7 @@ __device__ __forceinline__ void contract_task(const PairView &PV0, const Quartet
         for (int u = 0; u <= ty; ++u)
           for (int v = 0; v <= tz; ++v, ++m) {
             if (cls != 5) {
-              acc = tfma(E3ab[o + m], W0[hidx(t, u, v) * ncd + j], acc);
+              acc = tfma(E3ab[o + m], W0[hb[o + m] + j], acc);
             } else {
               // Eq. I5byI3_ with the second coefficient -1 (see the derivation note
               // below); W0 carries the bra sign, so the gradient term changes sign
@@ -1346,8 +1372,9 @@ static size_t contract_smem(int la, int lb, int lc, int ld, int cls, int nw, int
   int ncd = ncart(lc) * ncart(ld), nab = ncart(la) * ncart(lb);
   int jc = (ncd + nsplit - 1) / nsplit;
   size_t e3ab = (size_t)ne3_count(la, lb) * (cls == 5 ? 4 : 1);
-  return esz * ((size_t)nw * contract_warp_doubles(nhL, nhB, jc, ne3_chunk_max(lc, ld, jc)) +
-                 (size_t)nab * jc + e3ab);
+  const int ne3cd = ne3_chunk_max(lc, ld, jc), ne3ab = ne3_count(la, lb);
+  return esz * ((size_t)nw * contract_warp_doubles(nhL, nhB, jc, ne3cd, L) + (size_t)nab * jc + e3ab) +
+         sizeof(int) * ((size_t)ne3cd + ne3ab);
 }
 
 struct ContractPlan {
