@@ -249,23 +249,30 @@ __device__ __forceinline__ int64_t item_count(const QuartetView &QV, int nf, int
   return QV.count_dev ? (QV.count_dev[1] - pq0) * nf : nitems;
 }
 
-// Pass 1: key of every item and a histogram of the keys.
+// hist[key] += 1 for every active lane, one atomic per distinct key of the warp
+__device__ __forceinline__ void hist_add(unsigned int *hist, int key) {
+  const unsigned grp = __match_any_sync(__activemask(), key);
+  if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&hist[key], (unsigned)__popc(grp));
+}
+
+// Pass 1: key of every item and a histogram of the keys.  One thread per
+// primitive quartet (its geometry serves all of its families).
 template <bool BATCH>
 __global__ void k_items_classify(Tables T, PairView PV, QuartetView QV, int cls, int64_t pq0, int64_t nitems,
                                  int *keys, unsigned int *hist) {
   const int kcls = cls == 5 ? 3 : cls;
   const int nf = T.nfam[kcls];
-  const int64_t nit = item_count(QV, nf, pq0, nitems);
-  for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < nit;
-       it += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t pq = pq0 + it / nf;
-    const int f = (int)(it % nf);
-    ItemGeom g = item_geometry<BATCH>(PV, QV, cls, pq);
-    const FamDev &F = T.fam[T.fam0[kcls] + f];
-    int key = prim_negligible(*g.pv, g.iab, g.icd) ? SKIP_KEY
-                                                   : item_key(f, min(g.L, LAUX), item_bin(F, g.xi, g.D, g.L));
-    keys[it] = key;
-    atomicAdd(&hist[key], 1u);
+  const int64_t npq = item_count(QV, nf, pq0, nitems) / nf;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < npq;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    ItemGeom g = item_geometry<BATCH>(PV, QV, cls, pq0 + r);
+    const bool skip = prim_negligible(*g.pv, g.iab, g.icd);
+    for (int f = 0; f < nf; ++f) {
+      const FamDev &F = T.fam[T.fam0[kcls] + f];
+      const int key = skip ? SKIP_KEY : item_key(f, min(g.L, LAUX), item_bin(F, g.xi, g.D, g.L));
+      keys[r * nf + f] = key;
+      hist_add(hist, key);
+    }
   }
 }
 
@@ -300,10 +307,17 @@ __global__ void k_items_scan(unsigned int *hist, int nkeys) {
 __global__ void k_items_scatter(QuartetView QV, int nf, int64_t pq0, const int *keys, unsigned int *cursor,
                                 int64_t nitems, unsigned int *order) {
   const int64_t nit = item_count(QV, nf, pq0, nitems);
+  const int lane = threadIdx.x & 31;
   for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < nit;
        it += (int64_t)gridDim.x * blockDim.x) {
-    unsigned int pos = atomicAdd(&cursor[keys[it]], 1u);
-    order[pos] = (unsigned int)it;
+    // one atomic per distinct key of the warp; lanes take consecutive slots
+    const int key = keys[it];
+    const unsigned grp = __match_any_sync(__activemask(), key);
+    const int leader = __ffs(grp) - 1;
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(&cursor[key], (unsigned)__popc(grp));
+    base = __shfl_sync(grp, base, leader);
+    order[base + __popc(grp & ((1u << lane) - 1u))] = (unsigned int)it;
   }
 }
 
@@ -1488,7 +1502,9 @@ static int launch_chunk(f12int_ctx *ctx, const f12int_ctx::BasisData &B, int cls
     if (rc != F12INT_OK) return rc;
     CK(cudaMemsetAsync(ctx->d_hist, 0, sizeof(unsigned) * kNKeys, st));
     const unsigned nb = (unsigned)((nitems + BLOCK_AUX - 1) / BLOCK_AUX);
-    k_items_classify<false><<<nb, BLOCK_AUX, 0, st>>>(ctx->tables, PV, QV, cls, pqa, nitems, ctx->d_keys, ctx->d_hist);
+    const unsigned nbq = (unsigned)((pqb - pqa + BLOCK_AUX - 1) / BLOCK_AUX);
+    k_items_classify<false><<<nbq, BLOCK_AUX, 0, st>>>(ctx->tables, PV, QV, cls, pqa, nitems, ctx->d_keys,
+                                                       ctx->d_hist);
     k_items_scan<<<1, 1024, 0, st>>>(ctx->d_hist, kNKeys);
     k_items_scatter<<<nb, BLOCK_AUX, 0, st>>>(QV, nf, pqa, ctx->d_keys, ctx->d_hist, nitems, ctx->d_order);
     std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
@@ -2109,7 +2125,8 @@ extern "C" int f12int_compute_class_static(f12int_ctx *ctx, int basis_id, int cl
       // previous call's contents
       CK(cudaMemsetAsync(d_hist, 0, sizeof(unsigned) * kNKeys, st));
       const unsigned nb = (unsigned)((nitems + BLOCK_AUX - 1) / BLOCK_AUX);
-      k_items_classify<false><<<nb, BLOCK_AUX, 0, st>>>(ctx->tables, PV, QV, cls, pqa, nitems, d_keys, d_hist);
+      const unsigned nbq = (unsigned)((pqoff[qb] - pqa + BLOCK_AUX - 1) / BLOCK_AUX);
+      k_items_classify<false><<<nbq, BLOCK_AUX, 0, st>>>(ctx->tables, PV, QV, cls, pqa, nitems, d_keys, d_hist);
       k_items_scan<<<1, 1024, 0, st>>>(d_hist, kNKeys);
       k_items_scatter<<<nb, BLOCK_AUX, 0, st>>>(QV, nf, pqa, d_keys, d_hist, nitems, d_order);
       k_items_eval<false><<<nb, BLOCK_AUX, 0, st>>>(ctx->tables, PV, QV, cls, pqa, nitems, d_order, d_part, ctx->d_status,
