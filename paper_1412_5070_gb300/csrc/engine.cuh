@@ -577,6 +577,8 @@ int f12int_submit(f12int_ctx *ctx, int basis_id, const f12int_request *req, uint
   if (req->n_quartets < 0 || (req->n_quartets > 0 && (!req->quartets || !req->offsets || !req->out_dev)))
     return F12INT_EINVAL;
   if (req->class_mask == 0 || (req->class_mask >> 6) != 0) return F12INT_EINVAL;
+  for (int c = 1; c <= 6; ++c)
+    if (((req->class_mask >> (c - 1)) & 1) && !ctx->cls_ok[c]) return F12INT_EDOMAIN;
   if (req->precision != 0 && req->precision != 1) return F12INT_EINVAL;
   if (!(req->schwarz_thresh >= 0.0)) return F12INT_EINVAL;
   const f12int_ctx::BasisData &B = ctx->bases[basis_id];

@@ -262,6 +262,7 @@ __global__ void k_items_classify(Tables T, PairView PV, QuartetView QV, int cls,
                                  int *keys, unsigned int *hist) {
   const int kcls = cls == 5 ? 3 : cls;
   const int nf = T.nfam[kcls];
+  if (nf <= 0) return;   // a class the factor leaves out (never scheduled)
   const int64_t npq = item_count(QV, nf, pq0, nitems) / nf;
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < npq;
        r += (int64_t)gridDim.x * blockDim.x) {
@@ -777,6 +778,7 @@ struct f12int_ctx {
   std::vector<size_t> h_smem;  // contraction shared memory, per quartet in the working order
   std::mutex mu;
   std::recursive_mutex bounds_mu;   // first-time primitive and shell-pair bounds
+  bool cls_ok[7] = {false, false, false, false, false, false, false};   // classes the factor supports
   // growth of each class's kernel with distance (screening estimate):
   // kgrow[cls][i] = G(i * kGrowStep), see screen_estimate
   std::vector<double> kgrow[7];
@@ -1157,25 +1159,32 @@ int f12int_set_factor(f12int_ctx *ctx, const f12int_factor *f, const f12int_fact
   std::vector<FamDev> fams;
   std::vector<double> coef;
   Tables T{};
+  bool supported[7] = {false, true, true, true, true, true, true};
   for (int cls = 1; cls <= 6; ++cls) {
     T.fam0[cls] = (int)fams.size();
     T.nfam[cls] = 0;
     if (cls == 5) {
       T.fam0[cls] = T.fam0[3];
       T.nfam[cls] = T.nfam[3];
+      supported[5] = supported[3];
       continue;
     }
     f12::TermList kt = f12::kernel_terms(cls, F1, F2);
     std::vector<f12::Family> fl = f12::families(kt);
-    if ((int)fl.size() > MAXFAM) return F12INT_EDOMAIN;
+    // a class whose families need S(alpha) below alpha = -1 (other than the
+    // alpha = -1 finite part) is left out: its calls return F12INT_EDOMAIN
+    for (const f12::Family &fam0 : fl) {
+      const double a = fam0.a0 + 2.0;
+      if (a < -1.0 - 1e-9 || (a <= -1.0 && std::fabs(a + 1.0) >= 1e-9)) supported[cls] = false;
+    }
+    if ((int)fl.size() > MAXFAM) supported[cls] = false;
+    if (!supported[cls]) continue;
     for (const f12::Family &fam0 : fl) {
       FamDev d{};
       d.b = fam0.b;
       d.g = fam0.g;
       d.alpha0 = fam0.a0 + 2.0;   // F_l = x^{2l+2} D_r^l k: lowest power a0 + 2 for every l
-      if (d.alpha0 < -1.0 - 1e-9) return F12INT_EDOMAIN;       // not integrable even as finite part here
       d.fp_minus1 = std::fabs(d.alpha0 + 1.0) < 1e-9 ? 1 : 0;
-      if (!d.fp_minus1 && d.alpha0 <= -1.0) return F12INT_EDOMAIN;
       if (d.fp_minus1) d.alpha0 = -1.0;
       for (int j = 0; j < JMAX; ++j) {
         double arg = 0.5 * (d.alpha0 + 1.0 + j);
@@ -1215,6 +1224,7 @@ int f12int_set_factor(f12int_ctx *ctx, const f12int_factor *f, const f12int_fact
   T.fam = ctx->d_fam;
   T.coef = ctx->d_coef;
   ctx->tables = T;
+  for (int c = 1; c <= 6; ++c) ctx->cls_ok[c] = supported[c];
   for (auto &b : ctx->bases)   // the primitive bounds depend on the factor
     for (int c = 0; c < 7; ++c)
       if (b.d_qprim[c]) {
@@ -1704,6 +1714,7 @@ static int compute_class_impl(f12int_ctx *ctx, int basis_id, int cls, const int3
   if (cls < 1 || cls > 6 || n < 0) return F12INT_EINVAL;
   if (basis_id < 0 || basis_id >= (int)ctx->bases.size()) return F12INT_ENOTREADY;
   if (!ctx->factor_ready) return F12INT_ENOTREADY;
+  if (!ctx->cls_ok[cls]) return F12INT_EDOMAIN;
   if (n == 0) return F12INT_OK;
   if (!quartets_dev || !out_dev || !offsets_dev) return F12INT_EINVAL;
   {
@@ -1840,6 +1851,7 @@ int f12int_aux(f12int_ctx *ctx, int cls, int64_t npts, const double *xi_dev, con
                double *out_dev, void *cuda_stream) {
   if (!ctx || cls < 1 || cls > 6 || npts < 0 || nmax < 0 || nmax > LAUX) return F12INT_EINVAL;
   if (!ctx->factor_ready) return F12INT_ENOTREADY;
+  if (!ctx->cls_ok[cls]) return F12INT_EDOMAIN;
   if (npts == 0) return F12INT_OK;
   if (!xi_dev || !D_dev || !out_dev) return F12INT_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
@@ -2025,6 +2037,7 @@ extern "C" int f12int_compute_class_static(f12int_ctx *ctx, int basis_id, int cl
   if (cls < 1 || cls > 6 || n < 0) return F12INT_EINVAL;
   if (basis_id < 0 || basis_id >= (int)ctx->bases.size()) return F12INT_ENOTREADY;
   if (!ctx->factor_ready) return F12INT_ENOTREADY;
+  if (!ctx->cls_ok[cls]) return F12INT_EDOMAIN;
   if (n == 0) return F12INT_OK;
   if (!quartets_dev || !out_dev || !offsets_dev) return F12INT_EINVAL;
   // fixed part of the scratch: quartet list, offsets and primitive offsets in
