@@ -28,6 +28,9 @@ Two further workloads, each printing its own JSON line:
                       with Schwarz bound product >= 1e-4, half below), FP64 against
                       the mixed path (FP32 recursion and contraction below 1e-4):
                       time and the mixed path's max abs/rel difference.
+  --workload perl     the 12-atom workload split by class and (la, lb, lc, ld): shell and
+                      primitive quartets/s of every combination, with the FP64 rate of each
+                      kernel from the library's event timing and work counters.
   --workload serve    Poisson request streams at 10..2000 requests/s over 12
                       molecules of 2-60 atoms; half the requests ask for one
                       class, half for I2..I6, each over U{8..64} x U{8..64}
@@ -68,7 +71,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
-    ap.add_argument("--workload", default="spd12", choices=("spd12", "batch64", "serve", "mixed"))
+    ap.add_argument("--workload", default="spd12", choices=("spd12", "batch64", "serve", "mixed", "perl"))
     ap.add_argument("--fraction", type=float, default=1.0, help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu-baseline", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -665,6 +668,58 @@ def run_mixed(args):
     print(json.dumps(line), flush=True)
 
 
+def run_per_l(args):
+    """Per class and (la, lb, lc, ld): rates and kernel FP64 rates on the 12-atom workload."""
+    import torch
+    from paper_1412_5070_gb300 import build as B
+    from paper_1412_5070_gb300 import f12int as F
+    B.build()
+    basis = build_workload()
+    stream = torch.cuda.Stream()
+    ctx = F.f12int_create(0, 0, stream)
+    F.f12int_set_factor(ctx, M.P0)
+    bid = F.f12int_set_basis(ctx, basis)
+    lists, _ = screened_lists(F, ctx, bid, basis, 1.0)
+    rows = []
+    for c in CLASSES:
+        q = lists[c]
+        key = basis.l[q] @ np.array([1000, 100, 10, 1])
+        for k in np.unique(key):
+            sub = np.ascontiguousarray(q[key == k])
+            off = M.block_offsets(basis, sub)
+            dq = torch.from_numpy(sub).cuda()
+            doff = torch.from_numpy(off[:-1].copy()).cuda()
+            out = torch.empty(int(off[-1]), dtype=torch.float64, device="cuda")
+            F.f12int_compute_class(ctx, bid, c, dq, out, doff, stream)   # warm-up
+            stream.synchronize()
+            F.f12int_set_timing(ctx, True)
+            F.f12int_kernel_stats(ctx, reset=True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            F.f12int_compute_class(ctx, bid, c, dq, out, doff, stream)
+            e1.record(stream)
+            e1.synchronize()
+            st = F.f12int_kernel_stats(ctx, reset=True)
+            F.f12int_set_timing(ctx, False)
+            ms = e0.elapsed_time(e1)
+            npq = int(np.sum(np.prod(basis.nprim[sub], axis=1)))
+            rows.append({"class": "I%d" % c, "l": [int(x) for x in basis.l[sub[0]]], "shell_quartets": len(sub),
+                         "prim_quartets": npq, "ms": ms, "shell_quartets_per_s": len(sub) / (ms / 1e3),
+                         "prim_quartets_per_s": npq / (ms / 1e3),
+                         "aux_tflops": st["aux_flops"] / (st["aux_ms"] / 1e3) / 1e12 if st["aux_ms"] else 0.0,
+                         "contract_tflops": st["contract_flops"] / (st["contract_ms"] / 1e3) / 1e12
+                         if st["contract_ms"] else 0.0,
+                         "aux_share": st["aux_ms"] / max(st["aux_ms"] + st["contract_ms"], 1e-9)})
+            del out
+        print("perl: I%d done" % c, file=sys.stderr, flush=True)
+    F.f12int_device_status(ctx)
+    line = {"metric": "F12 quartets/s per class and (la,lb,lc,ld), with kernel FP64 rates", "unit": UNIT,
+            "n_gpus": 1, "dtype": "f64", "data": "synthetic", "config": {"workload": WORKLOAD},
+            "fp64_peak_tflops": FP64_PEAK_TFLOPS, "rows": rows}
+    F.f12int_destroy(ctx)
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -675,6 +730,8 @@ def main():
         run_serving(args)
     elif args.workload == "mixed":
         run_mixed(args)
+    elif args.workload == "perl":
+        run_per_l(args)
     else:
         run_ours(args)
 
