@@ -475,3 +475,131 @@ def test_term_magnitude_single_term():
     out, off, mag = O.shell_blocks(K, 3, basis, q, with_mag=True)
     assert mag[1] == pytest.approx(abs(out[1]), rel=1e-15)
     assert abs(out[0]) < 0.05 * mag[0]
+
+
+# --------------------------------------------------------- Hobson cross-check --
+
+def _laplacian_power(t, u, v, k):
+    """Delta^k of x^t y^u z^v as {(i, j, l): coefficient} (exact integers)."""
+    poly = {(t, u, v): 1}
+    for _ in range(k):
+        nxt = {}
+        for (i, j, l), c in poly.items():
+            for d, e in ((0, i), (1, j), (2, l)):
+                if e >= 2:
+                    key = [i, j, l]
+                    key[d] -= 2
+                    nxt[tuple(key)] = nxt.get(tuple(key), 0) + c * e * (e - 1)
+        poly = {key: c for key, c in nxt.items() if c}
+    return poly
+
+
+def hermite_r_hobson(X, g, L):
+    """R_tuv = d^t/dX^t d^u/dY^u d^v/dZ^v B(|X|) by Hobson's theorem (the
+    spherical route of App. A): for a monomial m of degree n,
+    m(grad) B = sum_k (Delta^k m)(X) / (2^k k!) g_{n-k}, g_j = (r^-1 d/dr)^j B."""
+    R = {}
+    for t in range(L + 1):
+        for u in range(L + 1 - t):
+            for v in range(L + 1 - t - u):
+                n = t + u + v
+                s = 0.0
+                for k in range(n // 2 + 1):
+                    lap = sum(c * X[0] ** i * X[1] ** j * X[2] ** l
+                              for (i, j, l), c in _laplacian_power(t, u, v, k).items())
+                    s += lap / (2.0 ** k * math.factorial(k)) * g[n - k]
+                R[(t, u, v)] = s
+    return R
+
+
+def hermite_r_recursion(X, g, L):
+    """R by the Cartesian recursion R^(n)_{t+1,u,v} = t R^(n+1)_{t-1,u,v} + X R^(n+1)_{tuv}."""
+    R = {(n, 0, 0, 0): g[n] for n in range(L + 1)}
+    for tot in range(1, L + 1):
+        for n in range(L - tot, -1, -1):
+            for t in range(tot, -1, -1):
+                for u in range(tot - t, -1, -1):
+                    v = tot - t - u
+                    if t > 0:
+                        val = X[0] * R[(n + 1, t - 1, u, v)] + ((t - 1) * R[(n + 1, t - 2, u, v)] if t > 1 else 0.0)
+                    elif u > 0:
+                        val = X[1] * R[(n + 1, t, u - 1, v)] + ((u - 1) * R[(n + 1, t, u - 2, v)] if u > 1 else 0.0)
+                    else:
+                        val = X[2] * R[(n + 1, t, u, v - 1)] + ((v - 1) * R[(n + 1, t, u, v - 2)] if v > 1 else 0.0)
+                    R[(n, t, u, v)] = val
+    return {(t, u, v): R[(0, t, u, v)] for (n, t, u, v) in R if n == 0}
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_hermite_recursion_matches_hobson(seed):
+    """The Cartesian recursion for R_tuv (used by the oracle and the kernels)
+    against Hobson's theorem, for arbitrary radial derivatives g_n and
+    separations, up to L = 14."""
+    rng = np.random.default_rng(seed)
+    X = rng.normal(size=3) * [0.7, 1.3, 0.4][seed % 3]
+    g = rng.normal(size=15)
+    L = 14
+    a = hermite_r_recursion(X, g, L)
+    b = hermite_r_hobson(X, g, L)
+    keys = sorted(b)
+    va, vb = np.array([a[k] for k in keys]), np.array([b[k] for k in keys])
+    np.testing.assert_allclose(va, vb, rtol=1e-11, atol=1e-13 * np.max(np.abs(vb)))
+
+
+def _e_direct(a, b, A, B, i, j):
+    """E_t^{ij}: x_A^i x_B^j e^{-a x_A^2 - b x_B^2} = sum_t E_t Lambda_t(x; p, P),
+    Lambda_t = (d/dP)^t e^{-p x_P^2}, by binomial expansion about P and
+    x_P^k = sum_t c_kt Lambda_t (Hermite inversion) -- written from the definition."""
+    p = a + b
+    P = (a * A + b * B) / p
+    K = math.exp(-a * b / p * (A - B) ** 2)
+    mono = np.zeros(i + j + 1)   # coefficients of x_P^k in x_A^i x_B^j
+    for r in range(i + 1):
+        for s in range(j + 1):
+            mono[r + s] += math.comb(i, r) * math.comb(j, s) * (P - A) ** (i - r) * (P - B) ** (j - s)
+    # x_P^k e^{-p x_P^2} = sum_t c_kt (d/dP)^t e^{-p x_P^2}: from x e^{-p x^2} = (1/2p) d/dP e^{-p x^2}
+    # and the product rule, c_{k+1,t} = c_{k,t-1}/(2p) + (t+1) c_{k,t+1}
+    n = i + j
+    c = np.zeros((n + 1, n + 2))
+    c[0, 0] = 1.0
+    for k in range(n):
+        for t in range(k + 2):
+            c[k + 1, t] = (c[k, t - 1] / (2 * p) if t > 0 else 0.0) + (t + 1) * c[k, t + 1]
+    return K * np.array([sum(mono[k] * c[k, t] for k in range(n + 1)) for t in range(n + 1)])
+
+
+def test_prim_block_through_hobson():
+    """A (p p|p d) primitive block of I3 assembled here from the oracle's radial
+    derivatives, Hobson's R, direct-expansion E and Eq. ii equals the oracle's."""
+    K = O.factor_kernel(P0)
+    ls = [1, 1, 1, 2]
+    ex = [0.9, 0.35, 1.4, 0.6]
+    cen = [np.array(c) for c in ([0.0, 0.0, 0.0], [0.4, -1.1, 0.7], [1.8, 0.3, -0.5], [1.2, 1.0, 0.2])]
+    p, q = ex[0] + ex[1], ex[2] + ex[3]
+    P = (ex[0] * cen[0] + ex[1] * cen[1]) / p
+    Q = (ex[2] * cen[2] + ex[3] * cen[3]) / q
+    X = Q - P
+    xi, D = p * q / (p + q), float(np.linalg.norm(X))
+    L = sum(ls)
+    g = math.pi ** 2.5 / (math.sqrt(p + q) * p * q) * O.radial(K, 3, xi, D, L)
+    R = hermite_r_hobson(X, g, L)
+    cart = lambda l: [(i, j, l - i - j) for i in range(l, -1, -1) for j in range(l - i, -1, -1)]
+    out = []
+    for ca in cart(ls[0]):
+        for cb in cart(ls[1]):
+            for cc in cart(ls[2]):
+                for cd in cart(ls[3]):
+                    Eab = [_e_direct(ex[0], ex[1], cen[0][k], cen[1][k], ca[k], cb[k]) for k in range(3)]
+                    Ecd = [_e_direct(ex[2], ex[3], cen[2][k], cen[3][k], cc[k], cd[k]) for k in range(3)]
+                    s = 0.0
+                    for t, et in enumerate(Eab[0]):
+                        for u, eu in enumerate(Eab[1]):
+                            for v, ev in enumerate(Eab[2]):
+                                for t2, ft in enumerate(Ecd[0]):
+                                    for u2, fu in enumerate(Ecd[1]):
+                                        for v2, fv in enumerate(Ecd[2]):
+                                            s += (-1) ** (t + u + v) * et * eu * ev * ft * fu * fv * \
+                                                 R[(t + t2, u + u2, v + v2)]
+                    out.append(s)
+    ref = O.prim_block(K, 3, ls, ex, cen).ravel()
+    np.testing.assert_allclose(np.array(out), ref, rtol=1e-11, atol=1e-13 * np.max(np.abs(ref)))
