@@ -146,7 +146,10 @@ int f12int_pair_bounds(f12int_ctx *ctx, int basis_id, int cls, double *bounds_ou
  *   quartets_dev[4n]  shell indices (a, b, c, d), device memory
  *   offsets_dev[n]    element offset of each block in out_dev, device memory
  *   out_dev           output, device memory, FP64
- * The work is queued on cuda_stream; the call returns once it is queued.
+ * The work runs on cuda_stream.  The call reads the quartet list back to
+ * plan its launches (which waits for earlier work on that stream) and
+ * returns when the blocks are written (it synchronises the stream); many
+ * small requests are better served by f12int_submit.
  * Scratch memory is allocated by the context (bounded by its budget).
  * Errors: F12INT_ENOTREADY without basis or factor, F12INT_EINVAL for bad
  * arguments, F12INT_ENOMEM when scratch would exceed the budget. */
