@@ -448,7 +448,7 @@ template <bool BATCH, class T>
 __device__ __forceinline__ void contract_task(const PairView &PV0, const QuartetView &QV, int cls, int nf,
                                               int64_t pq0, const CTask task, const double *part, double *out,
                                               const int64_t *offsets, unsigned long long *flops_total,
-                                              T *smem, int *off_ab, int *off_cd, int *jmap) {
+                                              T *smem, int *off_ab, int *off_cd) {
   const int64_t q = task.q;
   const int split = task.split, nsplit = task.nsplit;
   const PairView &PV = qv_view<BATCH>(PV0, QV, q);
@@ -468,26 +468,11 @@ __device__ __forceinline__ void contract_task(const PairView &PV0, const Quartet
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
   if (tid == 0) {
-    // the block's ket components in order of their number of Hermite
-    // products (a stable sort), so that the lanes of one pass of the ket sum
-    // run loops of equal length; jmap gives the actual component
-    auto nterm = [&](int comp) {
-      const unsigned char *ec = c_cart[lc][comp / nd], *ed = c_cart[ld][comp % nd];
-      return (ec[0] + ed[0] + 1) * (ec[1] + ed[1] + 1) * (ec[2] + ed[2] + 1);
-    };
-    for (int j = 0; j < ncd; ++j) {
-      const int v = j0 + j, cv = nterm(v);
-      int b = j - 1;
-      while (b >= 0 && nterm(jmap[b]) > cv) {
-        jmap[b + 1] = jmap[b];
-        --b;
-      }
-      jmap[b + 1] = v;
-    }
     int o = 0;
     for (int j = 0; j < ncd; ++j) {
       off_cd[j] = o;
-      o += nterm(jmap[j]);
+      const unsigned char *ec = c_cart[lc][(j0 + j) / nd], *ed = c_cart[ld][(j0 + j) % nd];
+      o += (ec[0] + ed[0] + 1) * (ec[1] + ed[1] + 1) * (ec[2] + ed[2] + 1);
     }
     off_cd[ncd] = o;
     o = 0;
@@ -515,7 +500,7 @@ __device__ __forceinline__ void contract_task(const PairView &PV0, const Quartet
   int *hb = ck + ne3cd;
   // index tables of this task (same for every primitive quartet)
   for (int j = tid; j < ncd; j += nthr) {
-    const unsigned char *ec = c_cart[lc][jmap[j] / nd], *ed = c_cart[ld][jmap[j] % nd];
+    const unsigned char *ec = c_cart[lc][(j0 + j) / nd], *ed = c_cart[ld][(j0 + j) % nd];
     const int tx = ec[0] + ed[0], ty = ec[1] + ed[1], tz = ec[2] + ed[2];
     int m = off_cd[j];
     for (int t2 = 0; t2 <= tx; ++t2)
@@ -563,7 +548,7 @@ __device__ __forceinline__ void contract_task(const PairView &PV0, const Quartet
       // E^{cd}_{t'u'v'} products of this ket primitive pair
       const double *Ecd = PV.epool + PV.pp_eoff[pcd];
       for (int j = lane; j < ncd; j += 32) {
-        const unsigned char *ec = c_cart[lc][jmap[j] / nd], *ed = c_cart[ld][jmap[j] % nd];
+        const unsigned char *ec = c_cart[lc][(j0 + j) / nd], *ed = c_cart[ld][(j0 + j) % nd];
         const double *ex = Ecd + (ec[0] * (ld + 1) + ed[0]) * ntcd;
         const double *ey = Ecd + n1cd + (ec[1] * (ld + 1) + ed[1]) * ntcd;
         const double *ez = Ecd + 2 * n1cd + (ec[2] * (ld + 1) + ed[2]) * ntcd;
@@ -692,7 +677,7 @@ __device__ __forceinline__ void contract_task(const PairView &PV0, const Quartet
   else o = out + offsets[q];
   for (int i = tid; i < nab * ncd; i += nthr) {
     const int iabc = i / ncd;
-    o[(size_t)iabc * ncd_all + jmap[i - iabc * ncd]] = (double)Oacc[i];
+    o[(size_t)iabc * ncd_all + j0 + (i - iabc * ncd)] = (double)Oacc[i];
   }
   if (flops_total && lane == 0 && nproc) {
     // algorithmic FP64 flops per primitive quartet: Hermite recursion 2 C(L+4,4)
@@ -712,19 +697,18 @@ k_contract(PairView PV0, QuartetView QV, int cls, int nf, int64_t pq0, const CTa
            unsigned int *status, unsigned long long *flops_total) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *smem = reinterpret_cast<T *>(smem_raw);
-  __shared__ int off_ab[101], off_cd[101], jmap[101];
+  __shared__ int off_ab[101], off_cd[101];
   if constexpr (BATCH) {
     // ntask_dev = {first, end} of this launch's tasks
     const int64_t te = ntask_dev[1];
     for (int64_t tk = ntask_dev[0] + blockIdx.x; tk < te; tk += gridDim.x) {
       __syncthreads();   // the previous task's shared-memory reads are done
-      contract_task<BATCH, T>(PV0, QV, cls, nf, pq0, tasks[tk], part, out, offsets, flops_total, smem, off_ab, off_cd,
-                              jmap);
+      contract_task<BATCH, T>(PV0, QV, cls, nf, pq0, tasks[tk], part, out, offsets, flops_total, smem, off_ab, off_cd);
     }
   } else {
     if (blockIdx.x < ntask)
       contract_task<BATCH, T>(PV0, QV, cls, nf, pq0, tasks[blockIdx.x], part, out, offsets, flops_total, smem, off_ab,
-                              off_cd, jmap);
+                           off_cd);
   }
 }
 // Derivation note for I5: with d/dA_x = (a/p) d/dP_x + d/dAB_x and
