@@ -86,18 +86,22 @@ int f12int_set_basis(f12int_ctx *ctx, int nshell, const double *centers, const i
  * f' = f).  Builds, on the host, the term lists of the kernels k1..k6
  * (Eqs. k1-k6) as sums of c x^a exp(b x - g x^2) and their radial
  * derivatives, and copies them to the device.
- * Errors: F12INT_EDOMAIN when mu <= 0, c0 < 0, B < 0, n < 0 or n > 20, a
- * value is not finite, or rho + 2n + 2 <= 0 (the damped long-range term must
- * be integrable at r = 0, Sec. 3.1).
+ * B may have either sign: B > 0 grows at long range, B < 0 decays (a
+ * Ten-no-like tail; its term families, b < 0, are integrated by a
+ * Gauss-Legendre quadrature in a second evaluation launch).
+ * Errors: F12INT_EDOMAIN when mu <= 0, c0 < 0, n < 0 or n > 20, a value is
+ * not finite, or rho + 2n + 2 <= 0 (the damped long-range term must be
+ * integrable at r = 0, Sec. 3.1).
  * Classes: the auxiliary stage evaluates S(alpha, beta, gamma) (Eq. sila)
- * for alpha > -1 and the alpha = -1 finite part (Sec. 3.3.2).  A class whose
- * kernel has a term family x^a e^{bx - gx^2} in x^2 k(x) with a <= -1,
- * other than exactly a = -1, is left out
- * of an accepted factor: every call for it (compute, aux, submit) returns
- * F12INT_EDOMAIN.  For f' = f and c0 > 0 the lowest powers are rho + 2
+ * for alpha > -1 and the alpha = -1 finite part (Sec. 3.3.2).  A class is
+ * left out of an accepted factor, and every call for it (compute, aux,
+ * submit) returns F12INT_EDOMAIN, when its kernel has a term family
+ * x^a e^{bx - gx^2} in x^2 k(x) with a <= -1 other than exactly a = -1, or
+ * a family with b < 0 whose power a is neither an integer nor a
+ * half-integer.  For f' = f and c0 > 0 the lowest powers are rho + 2
  * (I3, I5), rho + 1 (I2), 2 rho + 2 (I4) and 2 rho (I6), which keeps I3 and
  * I5 for rho >= -3, I2 for rho >= -2, I4 for rho >= -3/2 and I6 for
- * rho >= -1/2. */
+ * rho >= -1/2; with B < 0, 2 rho must moreover be an integer. */
 int f12int_set_factor(f12int_ctx *ctx, const f12int_factor *f, const f12int_factor *fprime);
 
 /* Host-only view of the term lists that f12int_set_factor uploads: writes

@@ -33,11 +33,42 @@
 //    peak x* = (b + 2 xi D)/(2 gamma) of e^{(b + 2 xi D) x - gamma x^2}
 //    (the moderate/large-Q case of Sec. 2.5.2; the r12 -> 0 end contributes
 //    below double precision there).
+//
+// Families with b < 0 (a factor that decays exponentially, B < 0 in Eq. rs12,
+// or a Ten-no-type term e^{-w r}): S(alpha, beta, gamma) with beta < 0 is the
+// minimal solution of the alpha recursion (the Tricomi-U case of App. B), so
+// the upward recursion above loses accuracy; their non-peak orders are
+// instead integrated directly by composite Gauss-Legendre quadrature of the
+// same integral (family_quad).
+//
+// The header also compiles as plain C++ (without nvcc) so that a CPU test can
+// evaluate this stage against the oracle; the library itself only runs it on
+// the GPU.
 #pragma once
 
+#ifdef __CUDACC__
 #include <cuda_runtime.h>
+#define F12_DEV __device__
+#define F12_CONST __constant__
+#define F12_GLOBAL __device__
+#else
+#include <cmath>
+#define F12_DEV
+#define F12_CONST
+#define F12_GLOBAL
+#endif
 
 namespace f12dev {
+
+#ifndef __CUDACC__
+inline double rsqrt(double x) { return 1.0 / std::sqrt(x); }
+using std::exp;
+using std::fabs;
+using std::fma;
+using std::log;
+using std::pow;
+using std::sqrt;
+#endif
 
 constexpr int LAUX = 14;     // highest radial order (f shells, I5: 3+3+3+3+2)
 constexpr int JMAX = 48;     // longest family polynomial
@@ -47,6 +78,8 @@ constexpr int NGH = 16;      // Gauss-Hermite nodes
 constexpr int KTAB = 320;    // tabulated series coefficient ratios
 constexpr int MAXFAM = 24;   // families per kernel
 constexpr int NCLASS = 7;    // index by class 1..6
+constexpr int NGL = 16;      // Gauss-Legendre nodes per panel (b < 0 families)
+constexpr int NPMAX = 40;    // panels at most (the rule of family_quad needs about 30)
 
 struct FamDev {
   double b, g;
@@ -67,22 +100,24 @@ struct Tables {
   const double *coef;
 };
 
-__constant__ double c_gh_x[NGH];
-__constant__ double c_gh_w[NGH];
+F12_CONST double c_gh_x[NGH];
+F12_CONST double c_gh_w[NGH];
+F12_CONST double c_gl_x[NGL];   // Gauss-Legendre on [-1, 1]
+F12_CONST double c_gl_w[NGL];
 // c_{l,k+1}/c_{l,k} = (k+l+1) / ((k+1)(2k+2l+2)(2k+2l+3)),  c_{l,k} = 2^l (k+l)!/(k!(2k+2l+1)!)
 // (the same ratios advance the power series of j_l)
-__constant__ double c_cratio[LAUX + 1][KTAB];
-__constant__ double c_inv_dfact[LAUX + 2];        // 1/(2l+1)!! = c_{l,0}
+F12_CONST double c_cratio[LAUX + 1][KTAB];
+F12_CONST double c_inv_dfact[LAUX + 2];        // 1/(2l+1)!! = c_{l,0}
 constexpr int NKUM = 512;
-__device__ double d_kum_inv[2][NKUM];             // 1/((b+n)(n+1)) for b = 1/2, 3/2
-__device__ double d_sm1_ratio[NKUM];              // Gamma((m+1)/2)/(Gamma(m/2)(m+1))
+F12_GLOBAL double d_kum_inv[2][NKUM];             // 1/((b+n)(n+1)) for b = 1/2, 3/2
+F12_GLOBAL double d_sm1_ratio[NKUM];              // Gamma((m+1)/2)/(Gamma(m/2)(m+1))
 
-__device__ __forceinline__ double threshold_z(int l) { return 36.0 + 4.5 * l; }
+F12_DEV inline double threshold_z(int l) { return 36.0 + 4.5 * l; }
 
 // e^{-z} j_l(z) for l = 0..N (N <= LAUX): power series for the top two orders
 // and the stable downward recurrence j_{l-1} = z^2 j_{l+1} + (2l+1) j_l for
 // small z; closed forms of j_0, j_1 and the upward recurrence for large z.
-__device__ inline void jhat_all(double z, int N, double *jh) {
+F12_DEV inline void jhat_all(double z, int N, double *jh) {
   if (z > 2.0 * N + 30.0) {
     double e2 = z < 40.0 ? exp(-2.0 * z) : 0.0, iz = 1.0 / z;
     jh[0] = 0.5 * (1.0 - e2) * iz;
@@ -105,7 +140,7 @@ __device__ inline void jhat_all(double z, int N, double *jh) {
 }
 
 // Kummer M(a, b, z), z >= 0, a > 0, b = 1/2 (ib = 0) or 3/2 (ib = 1) (App. B, Eq. msmallz).
-__device__ inline double kummer_m(double a, int ib, double z, int *bad) {
+F12_DEV inline double kummer_m(double a, int ib, double z, int *bad) {
   double t = 1.0, s = 1.0;
   if (z == 0.0) return 1.0;
   for (int n = 0; n < NKUM; ++n) {
@@ -122,7 +157,7 @@ __device__ inline double kummer_m(double a, int ib, double z, int *bad) {
 // from the Kummer form  J = 1/2 [Gamma((a+1)/2) M((a+1)/2, 1/2, y^2/4)
 //                               + y Gamma((a+2)/2) M((a+2)/2, 3/2, y^2/4)].
 // rho = Gamma((alpha+2)/2)/Gamma((alpha+1)/2).
-__device__ inline double jhat_start(double alpha, double rho, double y, int *bad) {
+F12_DEV inline double jhat_start(double alpha, double rho, double y, int *bad) {
   double z = 0.25 * y * y;
   if (y == 0.0) return 0.5;
   return 0.5 * (kummer_m(0.5 * (alpha + 1.0), 0, z, bad) + y * rho * kummer_m(0.5 * (alpha + 2.0), 1, z, bad));
@@ -130,7 +165,7 @@ __device__ inline double jhat_start(double alpha, double rho, double y, int *bad
 
 // Finite part S(-1, b, gamma) (Sec. 3.3.2, integer alpha; Eq. sila):
 //   = -gamma_E/2 - log(gamma)/2 + 1/2 sum_{m>=1} y^m Gamma(m/2)/m!,  y = b/sqrt(gamma) >= 0.
-__device__ inline double s_minus1(double b, double gam, int *bad) {
+F12_DEV inline double s_minus1(double b, double gam, int *bad) {
   const double euler = 0.57721566490153286061;
   double y = b / sqrt(gam);
   double s = -0.5 * euler - 0.5 * log(gam);
@@ -153,11 +188,119 @@ __device__ inline double s_minus1(double b, double gam, int *bad) {
   return s;
 }
 
+// Orders l = l0..L of a family with b < 0, added into out[l] times fct[l]:
+//   int_0^inf x^alpha0 P_l(x) e^{b x - g x^2 - xi (x - D)^2} jhat_l(2 xi D x) dx,
+// the integral of the header written with e^{-xi x^2 - xi D^2} j_l(2 xi D x)
+// = e^{-xi (x - D)^2} jhat_l(2 xi D x), by composite Gauss-Legendre quadrature.
+// With beta = b + 2 xi D, gamma = g + xi and d the highest power of the
+// integrand, the integrand is below e^{-40} of its largest value past
+//   beta > 0:  hi = beta/(2 gamma) + (sqrt(d/2) + 6.5)/sqrt(gamma)
+//              (about the peak of e^{beta x - gamma x^2}, moved out by x^d);
+//   beta <= 0: hi = (sqrt(d/2) + 6.5)/sqrt(gamma), and for beta < 0 at most
+//              (d + 9 sqrt(d) + 45)/|beta| (the tail of x^d e^{-|beta| x}).
+// A panel starting at a is 1.25/max(sqrt(gamma), |beta|/sqrt(max(1, |beta| a)))
+// wide: about two widths of the Gaussian, or of the bump x^m e^{-|beta| x}
+// that peaks near a (twice that width left errors up to 1e-8 at l = 5).  On the first panel a half-integer power x^{n+1/2} is
+// integrated in u = sqrt(x) (x^{n+1/2} dx = 2 u^{2n+2} du).  For alpha0 = -1
+// the j = 0 term P_0 x^{-1} H_l(x), H_l(0) = c_{l,0} e^{-xi D^2}, is the
+// finite part of Sec. 3.3.2 in the convention of s_minus1:
+//   int_0^inf [H_l(x) - H_l(0) e^{-gamma x^2}] / x dx + H_l(0) (-gamma_E - log gamma)/2.
+F12_DEV inline int family_quad(const Tables &T, const FamDev &F, double xi, double D, int l0, int L,
+                                 const double *fct, double *out, unsigned long long *nfma) {
+  const double gam = F.g + xi, sg = sqrt(gam);
+  const double beta = F.b + 2.0 * xi * D;
+  int spmax = 0;
+  for (int l = l0; l <= L; ++l) spmax = F.span[l] > spmax ? F.span[l] : spmax;
+  const double d = fmax(0.0, F.alpha0 + (double)(spmax - 1));
+  double hi;
+  if (beta > 0.0) {
+    hi = 0.5 * beta / gam + (sqrt(0.5 * d) + 6.5) / sg;
+  } else {
+    hi = (sqrt(0.5 * d) + 6.5) / sg;
+    if (beta < 0.0) hi = fmin(hi, (d + 9.0 * sqrt(d) + 45.0) / -beta);
+  }
+  const double edd = exp(-xi * D * D);
+  const double twoxd = 2.0 * xi * D;
+  double acc[LAUX + 1], jh[LAUX + 2];
+  for (int l = l0; l <= L; ++l) acc[l] = 0.0;
+  unsigned long long n = 0;
+  double a = 0.0;
+  int stretched = 0;
+  for (int p = 0; p < NPMAX && a < hi; ++p) {
+    double r = 0.0;
+    if (beta < 0.0) r = -beta / sqrt(fmax(1.0, -beta * a));
+    const double w = 1.25 / fmax(sg, r);
+    // the last panel reaches hi (flagged if that makes it wider than the rule)
+    if (p == NPMAX - 1 && hi - a > w) stretched = 1;
+    const double hw = 0.5 * (p == NPMAX - 1 ? fmax(w, hi - a) : w);
+    const bool usq = (p == 0 && F.pow_kind == 2);
+    const double su = usq ? sqrt(2.0 * hw) : 0.0;
+    for (int i = 0; i < NGL; ++i) {
+      double x, wt;
+      if (usq) {                       // x = u^2, u in [0, sqrt(2 hw)]
+        const double u = 0.5 * su * (c_gl_x[i] + 1.0);
+        x = u * u;
+        wt = 0.5 * su * c_gl_w[i] * 2.0 * u;
+      } else {
+        x = a + hw * (c_gl_x[i] + 1.0);
+        wt = hw * c_gl_w[i];
+      }
+      const double ex = exp(F.b * x - F.g * x * x - xi * (x - D) * (x - D));
+      jhat_all(twoxd * x, L, jh);
+      if (F.fp_minus1) {
+        const double es = edd * exp(-gam * x * x);
+        const double ix = 1.0 / x;
+        for (int l = l0; l <= L; ++l) {
+          const double *P = T.coef + F.coff[l];
+          const int sp = F.span[l];
+          double h = 0.0;
+          for (int j = sp - 1; j >= 1; --j) h = fma(h, x, P[j]);
+          const double Hl = ex * jh[l];
+          acc[l] = fma(wt, fma(Hl, h, P[0] * (Hl - c_inv_dfact[l] * es) * ix), acc[l]);
+          n += sp + 2;
+        }
+      } else {
+        double xa;
+        if (F.pow_kind == 1) {
+          xa = 1.0;
+          for (int k = 0; k < F.pow_int; ++k) xa *= x;
+        } else if (F.pow_kind == 2) {
+          xa = sqrt(x);
+          for (int k = 0; k < F.pow_int; ++k) xa *= x;
+          if (F.pow_int < 0) xa /= x;
+        } else {
+          xa = pow(x, F.alpha0);
+        }
+        const double e = wt * xa * ex;
+        for (int l = l0; l <= L; ++l) {
+          const double *P = T.coef + F.coff[l];
+          const int sp = F.span[l];
+          double h = 0.0;
+          for (int j = sp - 1; j >= 0; --j) h = fma(h, x, P[j]);
+          acc[l] = fma(e * jh[l], h, acc[l]);
+          n += sp + 1;
+        }
+      }
+    }
+    a += 2.0 * hw;
+  }
+  if (F.fp_minus1) {
+    const double fp0 = edd * (-0.5 * 0.57721566490153286061 - 0.5 * log(gam));
+    for (int l = l0; l <= L; ++l) acc[l] = fma(T.coef[F.coff[l]] * c_inv_dfact[l], fp0, acc[l]);
+  }
+  for (int l = l0; l <= L; ++l) out[l] += fct[l] * acc[l];
+  if (nfma) *nfma += n;
+  return stretched;
+}
+
 // Contribution of one family to hat g_l, l = 0..L, added into out[] with the
 // common factor 4 xi (2 xi)^l applied.  Returns nonzero if a series did not
-// converge within KMAX terms.
-__device__ inline int family_eval(const Tables &T, const FamDev &F, double xi, double D, int L, double *out,
-                                  unsigned long long *fma_count = nullptr) {
+// converge within KMAX terms.  NEGB: a family with b < 0, whose non-peak
+// orders go to family_quad (kept out of the b >= 0 instantiation, which the
+// main evaluation kernel uses, so that its register budget is unchanged).
+template <bool NEGB = false>
+F12_DEV inline int family_eval(const Tables &T, const FamDev &F, double xi, double D, int L, double *out,
+                               unsigned long long *fma_count = nullptr) {
   int bad = 0;
   unsigned long long nfma = 0;
   const double gam = F.g + xi;
@@ -165,7 +308,8 @@ __device__ inline int family_eval(const Tables &T, const FamDev &F, double xi, d
   const double z = beta * beta / (4.0 * gam);
   // orders l < ls use the quadrature about the peak, l >= ls the series
   int ls = 0;
-  while (ls <= L && z >= threshold_z(ls)) ++ls;
+  if (!NEGB || beta > 0.0)       // b < 0 and beta <= 0: no peak inside (0, inf)
+    while (ls <= L && z >= threshold_z(ls)) ++ls;
   double fct[LAUX + 1];
   fct[0] = 4.0 * xi;
   for (int l = 1; l <= L; ++l) fct[l] = fct[l - 1] * 2.0 * xi;
@@ -208,7 +352,9 @@ __device__ inline int family_eval(const Tables &T, const FamDev &F, double xi, d
     for (int l = 0; l < ls; ++l) out[l] += fct[l] * pre * acc[l];
   }
 
-  if (ls <= L) {
+  if constexpr (NEGB) {
+    if (ls <= L) bad |= family_quad(T, F, xi, D, ls, L, fct, out, &nfma);
+  } else if (ls <= L) {
     const double y = F.b * rsqrt(gam);
     const double v = 4.0 * xi * xi * D * D / gam;
     const double eT = exp(-xi * D * D);
@@ -312,19 +458,20 @@ __device__ inline int family_eval(const Tables &T, const FamDev &F, double xi, d
 }
 
 // hat g_l for l = 0..L of the kernel of class kcls (sum over its families).
-__device__ inline int aux_eval(const Tables &T, int kcls, double xi, double D, int L, double *out) {
+F12_DEV inline int aux_eval(const Tables &T, int kcls, double xi, double D, int L, double *out) {
   for (int l = 0; l <= L; ++l) out[l] = 0.0;
   int bad = 0;
   const int nf = T.nfam[kcls];
   const FamDev *fams = T.fam + T.fam0[kcls];
-  for (int f = 0; f < nf; ++f) bad |= family_eval(T, fams[f], xi, D, L, out);
+  for (int f = 0; f < nf; ++f)
+    bad |= fams[f].b < 0.0 ? family_eval<true>(T, fams[f], xi, D, L, out) : family_eval<false>(T, fams[f], xi, D, L, out);
   return bad;
 }
 
 // Work-item key used to order (primitive quartet, family) items so that a
 // warp runs the same branch with a similar series length: family, total
 // order L, and a bin of z (series by z/2, then the quadrature/series split).
-__device__ __forceinline__ int item_bin(const FamDev &F, double xi, double D, int L) {
+F12_DEV inline int item_bin(const FamDev &F, double xi, double D, int L) {
   const double gam = F.g + xi;
   const double beta = F.b + 2.0 * xi * D;
   const double z = beta * beta / (4.0 * gam);

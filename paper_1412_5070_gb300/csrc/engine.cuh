@@ -118,7 +118,7 @@ struct Engine {
   cudaStream_t branch[7] = {nullptr};   // capture streams of the class branches
   cudaGraphExec_t exec = nullptr;
   bool graph_dirty = true;
-  int items_blocks = 0, classify_blocks = 0, tier_blocks[kLaunches] = {0};
+  int items_blocks = 0, quad_blocks = 0, classify_blocks = 0, tier_blocks[kLaunches] = {0};
   double fp32_below = 1e-5;           // mixed requests: FP32 below this screening estimate
   // per-class schedule (f12int_batch_autotune): work target of a contraction
   // task and the divisor of the auxiliary-stage grid
@@ -228,6 +228,9 @@ static int engine_capture(f12int_ctx *ctx, Engine &E) {
       k_items_eval<true><<<std::max(1, E.items_blocks / E.items_div[cls]), BLOCK_AUX, 0, bs>>>(
           ctx->tables, none, QV, cls, 0, 0, E.order[cls],
                                                                E.part[cls], E.status, nullptr);
+      if (ctx->cls_negb[cls])   // families with b < 0 (a decaying factor)
+        k_items_eval<true, true><<<E.quad_blocks, BLOCK_AUX, 0, bs>>>(ctx->tables, none, QV, cls, 0, 0,
+                                                                       E.order[cls], E.part[cls], E.status, nullptr);
       for (int t = 0; t < kLaunches; ++t) {
         const int tt = t % kTiers;
         if (t < kTiers)
@@ -302,6 +305,8 @@ static int engine_init(f12int_ctx *ctx, Engine &E) {
   int per = 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_items_eval<true>, BLOCK_AUX, 0));
   E.items_blocks = nsm * std::max(per, 1);
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_items_eval<true, true>, BLOCK_AUX, 0));
+  E.quad_blocks = nsm * std::max(per, 1);
   E.classify_blocks = nsm * 8;
   for (int t = 0; t < kTiers; ++t) {
     if (kTierCap[t] > 48 * 1024) {

@@ -30,6 +30,7 @@
 
 #include "../../include/f12int.h"
 #include "aux.cuh"
+#include "auxtab.h"
 #include "termlist.h"
 
 using namespace f12dev;
@@ -323,8 +324,10 @@ __global__ void k_items_scatter(QuartetView QV, int nf, int64_t pq0, const int *
 }
 
 // Pass 4: one family's contribution to hat g_l (l <= L) per item, into
-// part[item * (LAUX+1) + l], in key order.
-template <bool BATCH>
+// part[item * (LAUX+1) + l], in key order.  The families with b < 0 (a
+// decaying factor) are left to a second launch of the same kernel with
+// NEGB = true (family_quad), made only when the factor has such families.
+template <bool BATCH, bool NEGB>
 __device__ __forceinline__ unsigned long long items_eval_one(Tables T, PairView PV, QuartetView QV, int cls,
                                                              int64_t pq0, int64_t it, double *part,
                                                              unsigned int *status) {
@@ -332,6 +335,8 @@ __device__ __forceinline__ unsigned long long items_eval_one(Tables T, PairView 
   const int nf = T.nfam[kcls];
   const int64_t pq = pq0 + it / nf;
   const int f = (int)(it % nf);
+  const FamDev &F = T.fam[T.fam0[kcls] + f];
+  if ((F.b < 0.0) != NEGB) return 0;   // the other launch's family
   ItemGeom g = item_geometry<BATCH>(PV, QV, cls, pq);
   if (prim_negligible(*g.pv, g.iab, g.icd)) return 0;   // never read by the contraction
   if (g.L > LAUX) {
@@ -341,14 +346,14 @@ __device__ __forceinline__ unsigned long long items_eval_one(Tables T, PairView 
   double out[LAUX + 1];
   for (int l = 0; l <= g.L; ++l) out[l] = 0.0;
   unsigned long long nfma = 0;
-  int bad = family_eval(T, T.fam[T.fam0[kcls] + f], g.xi, g.D, g.L, out, &nfma);
+  int bad = family_eval<NEGB>(T, F, g.xi, g.D, g.L, out, &nfma);
   if (bad) atomicOr(status, 1u);
   double *o = part + it * (LAUX + 1);
   for (int l = 0; l <= g.L; ++l) o[l] = out[l];
   return nfma;
 }
 
-template <bool BATCH>
+template <bool BATCH, bool NEGB = false>
 __global__ void k_items_eval(Tables T, PairView PV, QuartetView QV, int cls, int64_t pq0, int64_t nitems,
                              const unsigned int *order, double *part, unsigned int *status,
                              unsigned long long *fma_total) {
@@ -356,10 +361,10 @@ __global__ void k_items_eval(Tables T, PairView PV, QuartetView QV, int cls, int
   if constexpr (BATCH) {
     const int64_t nit = item_count(QV, T.nfam[cls == 5 ? 3 : cls], pq0, nitems);
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nit; t += (int64_t)gridDim.x * blockDim.x)
-      nfma += items_eval_one<BATCH>(T, PV, QV, cls, pq0, order[t], part, status);
+      nfma += items_eval_one<BATCH, NEGB>(T, PV, QV, cls, pq0, order[t], part, status);
   } else {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t < nitems) nfma = items_eval_one<BATCH>(T, PV, QV, cls, pq0, order[t], part, status);
+    if (t < nitems) nfma = items_eval_one<BATCH, NEGB>(T, PV, QV, cls, pq0, order[t], part, status);
   }
   // warp-aggregated count of the core multiply-adds (series terms and quadrature nodes)
   if (fma_total) {
@@ -779,6 +784,7 @@ struct f12int_ctx {
   std::mutex mu;
   std::recursive_mutex bounds_mu;   // first-time primitive and shell-pair bounds
   bool cls_ok[7] = {false, false, false, false, false, false, false};   // classes the factor supports
+  bool cls_negb[7] = {false, false, false, false, false, false, false};   // classes with b < 0 families
   // growth of each class's kernel with distance (screening estimate):
   // kgrow[cls][i] = G(i * kGrowStep), see screen_estimate
   std::vector<double> kgrow[7];
@@ -819,48 +825,6 @@ void dfree(f12int_ctx *ctx, T *&p, size_t bytes) {
 
 cudaStream_t pick_stream(f12int_ctx *ctx, void *s) { return s ? (cudaStream_t)s : ctx->stream; }
 
-// Gauss-Hermite nodes and weights (weight e^{-t^2}) from the orthonormal
-// Hermite recurrence: sign changes on a fine grid, then Newton.
-void gauss_hermite(int n, double *x, double *w) {
-  auto eval = [n](double t, double &pn, double &pn1) {
-    double p0 = 0.0, p1 = std::pow(M_PI, -0.25);
-    for (int k = 0; k < n; ++k) {
-      double p2 = t * std::sqrt(2.0 / (k + 1)) * p1 - std::sqrt((double)k / (k + 1)) * p0;
-      p0 = p1;
-      p1 = p2;
-    }
-    pn = p1;
-    pn1 = p0;
-  };
-  double lim = std::sqrt(2.0 * n + 1.0) + 1.0;
-  int found = 0;
-  const int grid = 200000;
-  double tprev = -lim, pprev, dummy;
-  eval(tprev, pprev, dummy);
-  for (int i = 1; i <= grid && found < n; ++i) {
-    double t = -lim + 2.0 * lim * i / grid, pc;
-    eval(t, pc, dummy);
-    if ((pc < 0) != (pprev < 0)) {
-      double r = 0.5 * (t + tprev);
-      for (int it = 0; it < 100; ++it) {
-        double pn, pn1;
-        eval(r, pn, pn1);
-        double dp = std::sqrt(2.0 * n) * pn1;
-        double dr = pn / dp;
-        r -= dr;
-        if (std::fabs(dr) < 1e-15 * (1.0 + std::fabs(r))) break;
-      }
-      double pn, pn1;
-      eval(r, pn, pn1);
-      x[found] = r;
-      w[found] = 1.0 / (n * pn1 * pn1);
-      ++found;
-    }
-    tprev = t;
-    pprev = pc;
-  }
-}
-
 bool g_const_ready = false;
 std::mutex g_const_mu;
 
@@ -889,30 +853,18 @@ int upload_constants() {
         ++k;
       }
   }
-  double gx[NGH], gw[NGH];
-  gauss_hermite(NGH, gx, gw);
-  static double cr[LAUX + 1][KTAB];
-  for (int l = 0; l <= LAUX; ++l)
-    for (int k = 0; k < KTAB; ++k)
-      cr[l][k] = (double)(k + l + 1) / ((double)(k + 1) * (2.0 * k + 2.0 * l + 2.0) * (2.0 * k + 2.0 * l + 3.0));
-  CK(cudaMemcpyToSymbol(c_cratio, cr, sizeof(cr)));
-  double idf[LAUX + 2];
-  idf[0] = 1.0;
-  for (int l = 1; l < LAUX + 2; ++l) idf[l] = idf[l - 1] / (2.0 * l + 1.0);
-  CK(cudaMemcpyToSymbol(c_inv_dfact, idf, sizeof(idf)));
-  static double kinv[2][NKUM], smr[NKUM];
-  for (int n = 0; n < NKUM; ++n) {
-    kinv[0][n] = 1.0 / ((0.5 + n) * (n + 1.0));
-    kinv[1][n] = 1.0 / ((1.5 + n) * (n + 1.0));
-    // Gamma((m+1)/2) / (Gamma(m/2) (m+1)); entry 0 unused
-    smr[n] = n == 0 ? 0.0 : std::exp(std::lgamma(0.5 * (n + 1.0)) - std::lgamma(0.5 * n)) / (n + 1.0);
-  }
-  CK(cudaMemcpyToSymbol(d_kum_inv, kinv, sizeof(kinv)));
-  CK(cudaMemcpyToSymbol(d_sm1_ratio, smr, sizeof(smr)));
+  static AuxConst ac;
+  fill_aux_const(ac);
+  CK(cudaMemcpyToSymbol(c_cratio, ac.cratio, sizeof(ac.cratio)));
+  CK(cudaMemcpyToSymbol(c_inv_dfact, ac.inv_dfact, sizeof(ac.inv_dfact)));
+  CK(cudaMemcpyToSymbol(d_kum_inv, ac.kum_inv, sizeof(ac.kum_inv)));
+  CK(cudaMemcpyToSymbol(d_sm1_ratio, ac.sm1_ratio, sizeof(ac.sm1_ratio)));
   CK(cudaMemcpyToSymbol(c_tuv, tuv, sizeof(tuv)));
   CK(cudaMemcpyToSymbol(c_cart, cart, sizeof(cart)));
-  CK(cudaMemcpyToSymbol(c_gh_x, gx, sizeof(gx)));
-  CK(cudaMemcpyToSymbol(c_gh_w, gw, sizeof(gw)));
+  CK(cudaMemcpyToSymbol(c_gh_x, ac.gh_x, sizeof(ac.gh_x)));
+  CK(cudaMemcpyToSymbol(c_gh_w, ac.gh_w, sizeof(ac.gh_w)));
+  CK(cudaMemcpyToSymbol(c_gl_x, ac.gl_x, sizeof(ac.gl_x)));
+  CK(cudaMemcpyToSymbol(c_gl_w, ac.gl_w, sizeof(ac.gl_w)));
   g_const_ready = true;
   return F12INT_OK;
 }
@@ -923,7 +875,7 @@ bool finite_factor(const f12int_factor &f) {
 
 int check_factor(const f12int_factor &f) {
   if (!finite_factor(f)) return F12INT_EDOMAIN;
-  if (!(f.mu > 0.0) || f.c0 < 0.0 || f.B < 0.0 || f.n < 0 || f.n > 20) return F12INT_EDOMAIN;
+  if (!(f.mu > 0.0) || f.c0 < 0.0 || f.n < 0 || f.n > 20) return F12INT_EDOMAIN;
   if (f.c0 > 0.0 && !(f.rho + 2.0 * f.n + 2.0 > 0.0)) return F12INT_EDOMAIN;
   return F12INT_OK;
 }
@@ -1156,60 +1108,17 @@ int f12int_set_factor(f12int_ctx *ctx, const f12int_factor *f, const f12int_fact
   std::lock_guard<std::mutex> lk(ctx->mu);
   CK(cudaSetDevice(ctx->device));
   f12::Factor F1{f->c0, f->rho, f->B, f->mu, f->n}, F2{fp.c0, fp.rho, fp.B, fp.mu, fp.n};
-  std::vector<FamDev> fams;
-  std::vector<double> coef;
+  f12::TermList kt[NCLASS];
+  for (int cls = 1; cls <= 6; ++cls)
+    if (cls != 5) kt[cls] = f12::kernel_terms(cls, F1, F2);
+  ClassTables ct;
+  if (!build_class_tables(kt, ct)) return F12INT_EDOMAIN;
+  const std::vector<FamDev> &fams = ct.fams;
+  const std::vector<double> &coef = ct.coef;
   Tables T{};
-  bool supported[7] = {false, true, true, true, true, true, true};
-  for (int cls = 1; cls <= 6; ++cls) {
-    T.fam0[cls] = (int)fams.size();
-    T.nfam[cls] = 0;
-    if (cls == 5) {
-      T.fam0[cls] = T.fam0[3];
-      T.nfam[cls] = T.nfam[3];
-      supported[5] = supported[3];
-      continue;
-    }
-    f12::TermList kt = f12::kernel_terms(cls, F1, F2);
-    std::vector<f12::Family> fl = f12::families(kt);
-    // a class whose families need S(alpha) below alpha = -1 (other than the
-    // alpha = -1 finite part) is left out: its calls return F12INT_EDOMAIN
-    for (const f12::Family &fam0 : fl) {
-      const double a = fam0.a0 + 2.0;
-      if (a < -1.0 - 1e-9 || (a <= -1.0 && std::fabs(a + 1.0) >= 1e-9)) supported[cls] = false;
-    }
-    if ((int)fl.size() > MAXFAM) supported[cls] = false;
-    if (!supported[cls]) continue;
-    for (const f12::Family &fam0 : fl) {
-      FamDev d{};
-      d.b = fam0.b;
-      d.g = fam0.g;
-      d.alpha0 = fam0.a0 + 2.0;   // F_l = x^{2l+2} D_r^l k: lowest power a0 + 2 for every l
-      d.fp_minus1 = std::fabs(d.alpha0 + 1.0) < 1e-9 ? 1 : 0;
-      if (d.fp_minus1) d.alpha0 = -1.0;
-      for (int j = 0; j < JMAX; ++j) {
-        double arg = 0.5 * (d.alpha0 + 1.0 + j);
-        d.gam_tab[j] = arg > 0.0 ? std::tgamma(arg) : 0.0;
-      }
-      {
-        double fl = std::floor(d.alpha0 + 1e-9);
-        double fr = d.alpha0 - fl;
-        d.pow_int = (int)fl;
-        d.pow_kind = (std::fabs(fr) < 1e-9) ? 1 : (std::fabs(fr - 0.5) < 1e-9 ? 2 : 0);
-        if (d.pow_kind == 1 && d.pow_int < -1) d.pow_kind = 0;
-      }
-      double as = d.fp_minus1 ? 0.0 : d.alpha0;
-      d.rho_start = std::exp(std::lgamma(0.5 * (as + 2.0)) - std::lgamma(0.5 * (as + 1.0)));
-      f12::Family cur = fam0;
-      for (int l = 0; l <= LAUX; ++l) {
-        if ((int)cur.poly.size() > JMAX) return F12INT_EDOMAIN;
-        d.coff[l] = (int)coef.size();
-        d.span[l] = (int)cur.poly.size();
-        coef.insert(coef.end(), cur.poly.begin(), cur.poly.end());
-        cur = f12::radial_derivative(cur);
-      }
-      fams.push_back(d);
-    }
-    T.nfam[cls] = (int)fl.size();
+  for (int c = 0; c < NCLASS; ++c) {
+    T.nfam[c] = ct.nfam[c];
+    T.fam0[c] = ct.fam0[c];
   }
   // upload
   dfree(ctx, ctx->d_fam, ctx->fam_bytes);
@@ -1224,7 +1133,10 @@ int f12int_set_factor(f12int_ctx *ctx, const f12int_factor *f, const f12int_fact
   T.fam = ctx->d_fam;
   T.coef = ctx->d_coef;
   ctx->tables = T;
-  for (int c = 1; c <= 6; ++c) ctx->cls_ok[c] = supported[c];
+  for (int c = 1; c <= 6; ++c) {
+    ctx->cls_ok[c] = ct.supported[c];
+    ctx->cls_negb[c] = ct.negb[c];
+  }
   for (auto &b : ctx->bases)   // the primitive bounds depend on the factor
     for (int c = 0; c < 7; ++c)
       if (b.d_qprim[c]) {
@@ -1524,6 +1436,12 @@ static int launch_chunk(f12int_ctx *ctx, const f12int_ctx::BasisData &B, int cls
     }
     k_items_eval<false><<<nb, BLOCK_AUX, 0, st>>>(ctx->tables, PV, QV, cls, pqa, nitems, ctx->d_order, ctx->d_part,
                                            ctx->d_status, ctx->timing ? ctx->d_fma : nullptr);
+    if (ctx->cls_negb[cls]) {
+      k_items_eval<false, true><<<nb, BLOCK_AUX, 0, st>>>(ctx->tables, PV, QV, cls, pqa, nitems, ctx->d_order,
+                                                          ctx->d_part, ctx->d_status,
+                                                          ctx->timing ? ctx->d_fma : nullptr);
+      ctx->launches++;
+    }
     if (ctx->timing) {
       cudaEventRecord(ev.second, st);
       ctx->ev_aux.push_back(ev);
@@ -2145,6 +2063,11 @@ extern "C" int f12int_compute_class_static(f12int_ctx *ctx, int basis_id, int cl
       k_items_eval<false><<<nb, BLOCK_AUX, 0, st>>>(ctx->tables, PV, QV, cls, pqa, nitems, d_order, d_part, ctx->d_status,
                                              nullptr);
       ctx->launches += 4;
+      if (ctx->cls_negb[cls]) {
+        k_items_eval<false, true><<<nb, BLOCK_AUX, 0, st>>>(ctx->tables, PV, QV, cls, pqa, nitems, d_order, d_part,
+                                                            ctx->d_status, nullptr);
+        ctx->launches++;
+      }
       CK(cudaGetLastError());
     }
     for (int64_t ra = qa; ra < qb;) {

@@ -1,0 +1,76 @@
+// aux_host.cpp -- CPU build of the library's auxiliary-function stage, for tests.
+//
+// Compiles paper_1412_5070_gb300/csrc/aux.cuh as plain C++ (no nvcc, no GPU)
+// with the tables filled by the library's own host code (auxtab.h,
+// termlist.cpp), so that tests without a GPU can compare the stage's
+// arithmetic, hat g_l(xi, D) for every class, with the oracle.  The library
+// never loads this file's build; on the GPU the same functions run inside
+// the kernels.
+#include <cstdint>
+#include <cstring>
+
+#include "../paper_1412_5070_gb300/csrc/aux.cuh"
+#include "../paper_1412_5070_gb300/csrc/auxtab.h"
+#include "../paper_1412_5070_gb300/csrc/termlist.h"
+
+using namespace f12dev;
+
+namespace {
+
+void load_constants() {
+  static bool done = false;
+  if (done) return;
+  static AuxConst ac;
+  fill_aux_const(ac);
+  std::memcpy(c_gh_x, ac.gh_x, sizeof(ac.gh_x));
+  std::memcpy(c_gh_w, ac.gh_w, sizeof(ac.gh_w));
+  std::memcpy(c_gl_x, ac.gl_x, sizeof(ac.gl_x));
+  std::memcpy(c_gl_w, ac.gl_w, sizeof(ac.gl_w));
+  std::memcpy(c_cratio, ac.cratio, sizeof(ac.cratio));
+  std::memcpy(c_inv_dfact, ac.inv_dfact, sizeof(ac.inv_dfact));
+  std::memcpy(d_kum_inv, ac.kum_inv, sizeof(ac.kum_inv));
+  std::memcpy(d_sm1_ratio, ac.sm1_ratio, sizeof(ac.sm1_ratio));
+  done = true;
+}
+
+int eval(const f12::TermList kt[NCLASS], int cls, int64_t n, const double *xi, const double *D, int nmax,
+         double *out) {
+  load_constants();
+  ClassTables ct;
+  if (!build_class_tables(kt, ct)) return -3;
+  if (!ct.supported[cls]) return -3;
+  Tables T{};
+  for (int c = 0; c < NCLASS; ++c) {
+    T.nfam[c] = ct.nfam[c];
+    T.fam0[c] = ct.fam0[c];
+  }
+  T.fam = ct.fams.data();
+  T.coef = ct.coef.data();
+  int bad = 0;
+  double g[LAUX + 1];
+  for (int64_t i = 0; i < n; ++i) {
+    bad |= aux_eval(T, cls == 5 ? 3 : cls, xi[i], D[i], nmax, g);
+    for (int l = 0; l <= nmax; ++l) out[i * (nmax + 1) + l] = g[l];
+  }
+  return bad ? 1 : 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+// hat g_l, l = 0..nmax, of class cls for the factor pair (f, fp) given as
+// {c0, rho, B, mu, n} (Eq. rs12).  Returns 0, 1 if a series or quadrature
+// reported a failure, -3 if the class is outside what the stage supports,
+// -1 for bad arguments.
+int aux_host_eval(const double *f, const double *fp, int cls, int64_t n, const double *xi, const double *D,
+                  int nmax, double *out) {
+  if (!f || !fp || cls < 1 || cls > 6 || nmax < 0 || nmax > LAUX || n < 0) return -1;
+  f12::Factor F1{f[0], f[1], f[2], f[3], (int)f[4]}, F2{fp[0], fp[1], fp[2], fp[3], (int)fp[4]};
+  f12::TermList kt[NCLASS];
+  for (int c = 1; c <= 6; ++c)
+    if (c != 5) kt[c] = f12::kernel_terms(c, F1, F2);
+  return eval(kt, cls, n, xi, D, nmax, out);
+}
+
+}  // extern "C"

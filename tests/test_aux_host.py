@@ -1,0 +1,125 @@
+"""The library's auxiliary-function stage compiled for the CPU (tests/aux_host.cpp
+builds paper_1412_5070_gb300/csrc/aux.cuh as plain C++ with the library's own
+table code) against the oracle, without a GPU.
+
+On the GPU the same functions run inside the kernels; these tests check the
+arithmetic of the stage, including the Gauss-Legendre branch for families
+with b < 0 (a factor that decays, B < 0 in Eq. rs12), on the grid of the GPU
+aux test and up to the highest order, 14.  The GPU tests repeat the
+comparison through the C ABI.
+"""
+import ctypes
+import os
+import shutil
+import subprocess
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1412_5070_gb300 import molecules as M
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(os.path.dirname(HERE), "paper_1412_5070_gb300", "csrc")
+SRC = [os.path.join(HERE, "aux_host.cpp"), os.path.join(CSRC, "termlist.cpp")]
+DEPS = SRC + [os.path.join(CSRC, f) for f in ("aux.cuh", "auxtab.h", "termlist.h")]
+LIB = os.path.join(HERE, "_build", "libauxhost.so")
+
+XI_D_GRID = [(xi, D) for xi in (0.025, 0.1, 0.5, 2.0, 10.0, 50.0) for D in (0.0, 0.05, 0.3, 1.0, 2.5, 5.0, 7.0,
+                                                                            10.0, 20.0)]
+FACTORS = {
+    "P0": M.P0,
+    "B<0 rho=-1/2": dict(c0=0.5, rho=-0.5, B=-0.8, mu=1.0, n=0),
+    "B<0 rho=0 n=1": dict(c0=1.0, rho=0.0, B=-1.3, mu=1.5, n=1),
+    "B<0 rho=-1 n=2": dict(c0=0.7, rho=-1.0, B=-4.0, mu=0.8, n=2),
+}
+
+
+@pytest.fixture(scope="module")
+def lib():
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("no C++ compiler")
+    os.makedirs(os.path.dirname(LIB), exist_ok=True)
+    if not os.path.exists(LIB) or any(os.path.getmtime(d) > os.path.getmtime(LIB) for d in DEPS):
+        tmp = LIB + ".tmp%d" % os.getpid()
+        subprocess.run([gxx, "-O2", "-std=c++17", "-fPIC", "-shared", "-o", tmp, *SRC], check=True)
+        os.replace(tmp, LIB)
+    L = ctypes.CDLL(LIB)
+    dp = ctypes.POINTER(ctypes.c_double)
+    L.aux_host_eval.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int64, dp, dp, ctypes.c_int, dp]
+    L.aux_host_eval.restype = ctypes.c_int
+    return L
+
+
+def host_aux(lib, f, fp, cls, pts, nmax):
+    dp = ctypes.POINTER(ctypes.c_double)
+    fa = np.array([f["c0"], f["rho"], f["B"], f["mu"], f["n"]], dtype=np.float64)
+    fb = np.array([fp["c0"], fp["rho"], fp["B"], fp["mu"], fp["n"]], dtype=np.float64)
+    xi = np.ascontiguousarray([p[0] for p in pts], dtype=np.float64)
+    D = np.ascontiguousarray([p[1] for p in pts], dtype=np.float64)
+    out = np.zeros(len(pts) * (nmax + 1))
+    rc = lib.aux_host_eval(fa.ctypes.data_as(dp), fb.ctypes.data_as(dp), cls, len(pts), xi.ctypes.data_as(dp),
+                           D.ctypes.data_as(dp), nmax, out.ctypes.data_as(dp))
+    return rc, out.reshape(len(pts), nmax + 1)
+
+
+def worst_relative(got, kern, cls, pts, nmax):
+    # the oracle's calls release the GIL: one point per thread
+    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        refs = list(ex.map(lambda p: O.radial(kern, cls, p[0], p[1], nmax), pts))
+    return max(float(np.max(np.abs(got[i] - ref) / np.abs(ref))) for i, ref in enumerate(refs))
+
+
+@pytest.mark.parametrize("name", list(FACTORS))
+@pytest.mark.parametrize("cls", [1, 2, 3, 4, 6])
+def test_aux_stage_on_cpu_against_oracle(lib, name, cls):
+    """hat g_n, n <= 10, on the (xi, D) grid of the GPU aux test: relative error
+    below 1e-8 (I6 at large xi is limited by cancellation between its
+    families, for either sign of B), below 1e-10 for the other classes."""
+    f = FACTORS[name]
+    if cls == 1 and name != "P0":
+        pytest.skip("I1 does not depend on the factor")
+    if name == "B<0 rho=-1 n=2" and cls == 6:
+        pytest.skip("rho + rho' = -2: k6 needs S(alpha) below alpha = -1")
+    rc, got = host_aux(lib, f, f, cls, XI_D_GRID, 10)
+    assert rc == 0
+    worst = worst_relative(got, O.factor_kernel(f), cls, XI_D_GRID, 10)
+    assert worst < (1e-8 if cls == 6 else 1e-10), worst
+
+
+@pytest.mark.parametrize("name", ["P0", "B<0 rho=-1/2", "B<0 rho=-1 n=2"])
+@pytest.mark.parametrize("cls", [2, 3, 4])
+def test_aux_stage_on_cpu_highest_order(lib, name, cls):
+    """All orders up to 14 (f-shell I5) on a coarser grid."""
+    f = FACTORS[name]
+    pts = XI_D_GRID[::4]
+    rc, got = host_aux(lib, f, f, cls, pts, 14)
+    assert rc == 0
+    assert worst_relative(got, O.factor_kernel(f), cls, pts, 14) < 1e-9
+
+
+def test_negative_B_with_a_general_power_is_refused(lib):
+    """A family with b < 0 and a power that is neither an integer nor a
+    half-integer is outside the quadrature's end-point forms: the class is
+    refused (-3), while the same power with B >= 0 is served."""
+    f = dict(c0=0.5, rho=-0.3, B=-0.8, mu=1.0, n=0)
+    for cls in (2, 3, 4, 6):
+        rc, _ = host_aux(lib, f, f, cls, XI_D_GRID[:3], 4)
+        assert rc == -3
+    rc, _ = host_aux(lib, dict(f, B=0.8), dict(f, B=0.8), 3, XI_D_GRID[:3], 4)
+    assert rc == 0
+    rc, _ = host_aux(lib, f, f, 1, XI_D_GRID[:3], 4)   # I1 does not use the factor
+    assert rc == 0
+
+
+def test_factor_pair_with_negative_B(lib):
+    """f' != f with B < 0 in one and B > 0 in the other: the product families
+    of I4 and I6 have b of either sign."""
+    f = dict(c0=0.5, rho=-0.5, B=-0.8, mu=1.0, n=0)
+    fp = dict(c0=0.3, rho=0.5, B=0.4, mu=0.7, n=0)
+    for cls in (4, 6):
+        rc, got = host_aux(lib, f, fp, cls, XI_D_GRID[1::3], 8)
+        assert rc == 0
+        assert worst_relative(got, O.factor_kernel(f, fp), cls, XI_D_GRID[1::3], 8) < 1e-8

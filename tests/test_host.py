@@ -54,13 +54,18 @@ def test_create_reports_missing_gpu(lib):
     assert e.value.status in (-1, -6)
 
 
+DECAYING = dict(c0=0.5, rho=-0.5, B=-0.8, mu=1.0, n=0)
+
+
+@pytest.mark.parametrize("f", [M.P0, DECAYING], ids=["P0", "B<0"])
 @pytest.mark.parametrize("cls", [1, 2, 3, 4, 6])
 @pytest.mark.parametrize("x", [0.03, 0.4, 1.1, 2.7, 6.5])
-def test_term_lists_reproduce_the_kernels(lib, cls, x):
+def test_term_lists_reproduce_the_kernels(lib, f, cls, x):
     """l = 0: x^2 k(x) from the generated families equals x^2 k(x) from the
-    oracle's pointwise kernel (separation of the damping, Eq. hj00eps)."""
-    got = F.f12int_kernel_radial(cls, M.P0, 0, x)
-    ref = x * x * O.kernel_value(O.factor_kernel(M.P0), cls, x)
+    oracle's pointwise kernel (separation of the damping, Eq. hj00eps), for a
+    growing (B > 0) and a decaying (B < 0) long-range part."""
+    got = F.f12int_kernel_radial(cls, f, 0, x)
+    ref = x * x * O.kernel_value(O.factor_kernel(f), cls, x)
     assert abs(got - ref) <= 1e-13 * abs(ref) + 1e-15
 
 
@@ -97,11 +102,12 @@ def test_factor_pair_with_different_parameters(lib):
 
 @pytest.mark.parametrize("bad", [dict(c0=0.5, rho=-0.5, B=0.5, mu=0.0, n=0),
                                  dict(c0=0.5, rho=-2.5, B=0.5, mu=1.0, n=0),
-                                 dict(c0=0.5, rho=-0.5, B=-0.5, mu=1.0, n=0),
+                                 dict(c0=-0.5, rho=-0.5, B=0.5, mu=1.0, n=0),
+                                 dict(c0=0.5, rho=-0.5, B=0.5, mu=1.0, n=21),
                                  dict(c0=float("nan"), rho=-0.5, B=0.5, mu=1.0, n=0)])
 def test_factor_domain_checks(lib, bad):
-    """mu > 0 and rho + 2n + 2 > 0 (Sec. 3.1); B >= 0 and finite values are
-    what the library supports."""
+    """mu > 0 and rho + 2n + 2 > 0 (Sec. 3.1); c0 >= 0, 0 <= n <= 20 and
+    finite values are what the library supports (B of either sign)."""
     with pytest.raises(F.F12IntError) as e:
         F.f12int_kernel_radial(3, bad, 0, 1.0)
     assert e.value.status == -3

@@ -121,6 +121,78 @@ def test_radial_two_forms_agree(cls, xi, D):
     assert np.all(np.abs(a - b) <= 1e-13 * scale + 1e-300), (a, b)
 
 
+# ---------------------------------------------------------- decaying factors --
+# Closed form for any kernel written as terms c r^a e^{b r - g r^2}, in
+# arbitrary precision (mpmath): each term of hat g_0 is
+#   c e^{-xi D^2} [S(a+1, b + 2 xi D, g + xi) - S(a+1, b - 2 xi D, g + xi)] / D
+# (the Gaussian bracket of Eq. bfinal completed into e^{+-2 xi D r}), with
+# S(alpha, beta, gamma) of Eq. sila summed from its power series in beta by
+# parity into Kummer functions, an identity for either sign of beta, and
+# D_Q^n = 2^n d^n/ds^n in s = D^2 by numerical differentiation.
+
+def _mp_S(mp, alpha, beta, gam):
+    z = beta * beta / (4 * gam)
+    return 0.5 * gam ** (-(alpha + 1) / 2) * (
+        mp.gamma((alpha + 1) / 2) * mp.hyp1f1((alpha + 1) / 2, 0.5, z)
+        + beta / mp.sqrt(gam) * mp.gamma((alpha + 2) / 2) * mp.hyp1f1((alpha + 2) / 2, 1.5, z))
+
+
+def _mp_rs12_terms(mp, f):
+    """Eq. rs12 with the damping of Eq. ttdamp written out,
+    S_n(x) = 1 - e^{-x} sum_{k<=n} x^k/k!, x = mu r^2."""
+    c0, rho, B, mu = (mp.mpf(f[k]) for k in ("c0", "rho", "B", "mu"))
+    t = [(mp.mpf(1), 0, 0, mu), (mp.mpf(0.5), 1, 0, mu), (c0, rho, B, 0)]
+    for k in range(f["n"] + 1):
+        t.append((-c0 * mu ** k / mp.factorial(k), rho + 2 * k, B, mu))
+    return t
+
+
+def _mp_hat_g(mp, terms, xi, D, nmax):
+    xi = mp.mpf(xi)
+
+    def g0(s):
+        d = mp.sqrt(s)
+        acc = 0
+        for c, a, b, g in terms:
+            acc += c * (_mp_S(mp, a + 1, b + 2 * xi * d, g + xi) - _mp_S(mp, a + 1, b - 2 * xi * d, g + xi))
+        return acc * mp.exp(-xi * s) / d
+
+    s0 = mp.mpf(D) ** 2
+    return np.array([float(2 ** n * mp.diff(g0, s0, n)) for n in range(nmax + 1)])
+
+
+NEG_B = [dict(c0=0.5, rho=-0.5, B=-0.8, mu=1.0, n=0), dict(c0=1.0, rho=0.0, B=-1.3, mu=1.5, n=1)]
+
+
+@pytest.mark.parametrize("fi", [0, 1])
+@pytest.mark.parametrize("cls", [2, 3])
+@pytest.mark.parametrize("xi,D", [(0.5, 1.2), (2.0, 0.7), (0.1, 3.0), (8.0, 0.4)])
+def test_radial_decaying_factor_closed_form(fi, cls, xi, D):
+    """B < 0 in Eq. rs12 (the long-range part decays): the oracle's hat g_n,
+    n <= 6, for k3 = f and k2 = f/r against the closed form above."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    f = NEG_B[fi]
+    terms = _mp_rs12_terms(mp, f)
+    if cls == 2:
+        terms = [(c, a - 1, b, g) for c, a, b, g in terms]
+    ref = _mp_hat_g(mp, terms, xi, D, 6)
+    got = O.radial(O.factor_kernel(f), cls, xi, D, 6)
+    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("om", [0.7, 1.5])
+@pytest.mark.parametrize("xi,D", [(0.5, 1.2), (3.0, 2.0), (0.05, 6.0)])
+def test_radial_slater_kernel_closed_form(om, xi, D):
+    """k = e^{-om r}, the Ten-no factor: the oracle's hat g_n, n <= 6,
+    against the closed form above (one term, b = -om)."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    ref = _mp_hat_g(mp, [(mp.mpf(1), 0, -mp.mpf(om), 0)], xi, D, 6)
+    got = O.radial(O.test_kernel(O.K_SLATER, om), 3, xi, D, 6)
+    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=0)
+
+
 def test_jhat_switch_continuity():
     """e^{-z} j_m(z) from the series and from the closed forms meet at the switch."""
     N = 10
