@@ -58,6 +58,15 @@ typedef struct {
   int n;
 } f12int_factor;
 
+/* One term c r^a exp(b r - g r^2) of a correlation factor given as a sum of
+ * terms: the general form the kernels of Eqs. k1-k6 are built from (the
+ * factor of Eq. rs12 expands into five or more such terms).  It covers the
+ * Ten-no factor exp(-w r) (one term, b = -w) and Gaussian-type geminals
+ * sum_i c_i exp(-g_i r^2) (Sec. 1 and the factors cited there). */
+typedef struct {
+  double c, a, b, g;
+} f12int_term;
+
 /* Create a context on CUDA device `device`.  hbm_budget_bytes caps the
  * device memory the context allocates (0 = no cap).  cuda_stream is the
  * default stream for the context (NULL = the legacy default stream).
@@ -112,6 +121,23 @@ int f12int_set_factor(f12int_ctx *ctx, const f12int_factor *f, const f12int_fact
  * F12INT_EDOMAIN as for f12int_set_factor. */
 int f12int_kernel_radial(int cls, const f12int_factor *f, const f12int_factor *fprime, int l, double x,
                          double *value);
+
+/* Set the correlation factors as sums of terms: f(r) = sum_{i<nf} f[i].c
+ * r^{f[i].a} exp(f[i].b r - f[i].g r^2), and f' likewise from fprime/nfp
+ * (fprime = NULL means f' = f).  Everything after the kernels' term lists is
+ * as for f12int_set_factor, which this call replaces.
+ * Arguments: host arrays, read during the call only; 1 <= nf, nfp <= 64.
+ * Errors: F12INT_EINVAL for a NULL f or a count out of range; F12INT_EDOMAIN
+ * when a value is not finite or some g < 0.
+ * Classes: the rules of f12int_set_factor, and one more that the damping of
+ * Eq. rs12 guarantees there: a class whose x^2 k(x) has a net x^-1 term at
+ * r -> 0 (a kernel like r^-3, whose integrals diverge) is left out. */
+int f12int_set_factor_terms(f12int_ctx *ctx, const f12int_term *f, int nf, const f12int_term *fprime, int nfp);
+
+/* Host-only view of f12int_kernel_radial for factors given as terms (the
+ * arguments of f12int_set_factor_terms).  Needs no GPU. */
+int f12int_kernel_radial_terms(int cls, const f12int_term *f, int nf, const f12int_term *fprime, int nfp, int l,
+                               double x, double *value);
 
 /* Schwarz-type screening for class cls: bound(ab) = sqrt(max |(ab|k|ab)|)
  * over the diagonal block (the I3 diagonal for I5), times a growth factor

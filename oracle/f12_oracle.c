@@ -78,9 +78,14 @@ typedef long double real;
 #define ORK_MAXL 5    /* highest shell angular momentum (f = 3, plus 2 for I5) */
 
 /* Kernel description.  id = 0 selects the range-separated factor pair (f, f')
- * of Eq. rs12; other ids select plain test kernels used to pin the oracle:
+ * of Eq. rs12; id = 20 a factor pair given as sums of terms
+ * c r^a exp(b r - g r^2) (t[i] = {c, a, b, g}), from which the kernels of the
+ * six classes are formed as for id 0 (Eqs. k1-k6, I6_); other ids select
+ * plain test kernels used to pin the oracle:
  *   10: k = 1          11: k = exp(-gam r^2)     12: k = r
  *   13: k = 1/r        14: k = exp(-gam r)                                     */
+#define ORK_TERMS 20
+#define ORK_MAXT 16
 typedef struct {
   int id;
   double c0, rho, B, mu;
@@ -88,6 +93,8 @@ typedef struct {
   double c0p, rhop, Bp, mup;
   int np;
   double gam;
+  int nt, ntp;
+  double t[ORK_MAXT][4], tp[ORK_MAXT][4];
 } ork_kernel;
 
 /* ---------------------------------------------------------------- kernels -- */
@@ -141,9 +148,34 @@ static void factor_eval(real r, double c0, double rho, double B, double mu, int 
   *fr = sr_r + lr_r;
 }
 
+/* f(r) and f_r(r) of a factor given as terms c r^a e^{b r - g r^2}. */
+static void terms_eval(const double (*t)[4], int nt, real r, real *f, real *fr) {
+  real s = 0, sr = 0;
+  for (int i = 0; i < nt; ++i) {
+    const real a = t[i][1], b = t[i][2], g = t[i][3];
+    const real v = (real)t[i][0] * R_POW(r, a) * R_EXP(b * r - g * r * r);
+    s += v;
+    sr += v * (a / r + b - 2 * g * r);
+  }
+  *f = s;
+  *fr = sr;
+}
+
+/* f (prime = 0) or f' (prime = 1) of the kernel's factor pair, and its derivative. */
+static void pair_eval(const ork_kernel *K, int prime, real r, real *f, real *fr) {
+  if (K->id == ORK_TERMS) {
+    if (prime) terms_eval(K->tp, K->ntp, r, f, fr);
+    else terms_eval(K->t, K->nt, r, f, fr);
+  } else if (prime) {
+    factor_eval(r, K->c0p, K->rhop, K->Bp, K->mup, K->np, f, fr);
+  } else {
+    factor_eval(r, K->c0, K->rho, K->B, K->mu, K->n, f, fr);
+  }
+}
+
 /* k_i(r) of Eqs. k1-k6 (class 5 uses the I3 kernel f, see Eq. I5_). */
 static real kernel_value(const ork_kernel *K, int cls, real r) {
-  if (K->id) {
+  if (K->id && K->id != ORK_TERMS) {
     switch (K->id) {
       case 10: return 1;
       case 11: return R_EXP(-(real)K->gam * r * r);
@@ -156,16 +188,16 @@ static real kernel_value(const ork_kernel *K, int cls, real r) {
   real f, fr, fp, frp;
   switch (cls) {
     case 1: return 1 / r;
-    case 2: factor_eval(r, K->c0, K->rho, K->B, K->mu, K->n, &f, &fr); return f / r;
+    case 2: pair_eval(K, 0, r, &f, &fr); return f / r;
     case 3:
-    case 5: factor_eval(r, K->c0, K->rho, K->B, K->mu, K->n, &f, &fr); return f;
+    case 5: pair_eval(K, 0, r, &f, &fr); return f;
     case 4:
-      factor_eval(r, K->c0, K->rho, K->B, K->mu, K->n, &f, &fr);
-      factor_eval(r, K->c0p, K->rhop, K->Bp, K->mup, K->np, &fp, &frp);
+      pair_eval(K, 0, r, &f, &fr);
+      pair_eval(K, 1, r, &fp, &frp);
       return f * fp;
     case 6:
-      factor_eval(r, K->c0, K->rho, K->B, K->mu, K->n, &f, &fr);
-      factor_eval(r, K->c0p, K->rhop, K->Bp, K->mup, K->np, &fp, &frp);
+      pair_eval(K, 0, r, &f, &fr);
+      pair_eval(K, 1, r, &fp, &frp);
       return fr * frp;
     default: return 0;
   }
@@ -275,11 +307,27 @@ static jet factor_jet(jet r, double c0, double rho, double B, double mu, int n) 
   return f;
 }
 
+/* A factor given as terms c r^a e^{b r - g r^2}, as a jet in r. */
+static jet terms_jet(jet r, const double (*t)[4], int nt) {
+  jet f = jet_cst(0, r.n);
+  for (int i = 0; i < nt; ++i) {
+    jet e = jet_exp(jet_add(jet_scale(r, (real)t[i][2]), jet_scale(jet_mul(r, r), -(real)t[i][3])));
+    f = jet_add(f, jet_scale(jet_mul(jet_pow(r, (real)t[i][1]), e), (real)t[i][0]));
+  }
+  return f;
+}
+
+static jet pair_jet(const ork_kernel *K, int prime, jet r) {
+  if (K->id == ORK_TERMS) return prime ? terms_jet(r, K->tp, K->ntp) : terms_jet(r, K->t, K->nt);
+  if (prime) return factor_jet(r, K->c0p, K->rhop, K->Bp, K->mup, K->np);
+  return factor_jet(r, K->c0, K->rho, K->B, K->mu, K->n);
+}
+
 /* x k_i(x) of Eqs. k1-k6 as a jet about x0 > 0 with coefficients up to order
  * nord (test kernels as in kernel_value); f_r takes one order more. */
 static jet phi_jet(const ork_kernel *K, int cls, real x0, int nord) {
   jet r = jet_var(x0, nord + 2), k;
-  if (K->id) {
+  if (K->id && K->id != ORK_TERMS) {
     switch (K->id) {
       case 10: k = jet_cst(1, r.n); break;
       case 11: k = jet_exp(jet_scale(jet_mul(r, r), -(real)K->gam)); break;
@@ -292,17 +340,11 @@ static jet phi_jet(const ork_kernel *K, int cls, real x0, int nord) {
   }
   switch (cls) {
     case 1: return jet_cst(1, r.n);
-    case 2: return factor_jet(r, K->c0, K->rho, K->B, K->mu, K->n);
+    case 2: return pair_jet(K, 0, r);
     case 3:
-    case 5: k = factor_jet(r, K->c0, K->rho, K->B, K->mu, K->n); break;
-    case 4:
-      k = jet_mul(factor_jet(r, K->c0, K->rho, K->B, K->mu, K->n),
-                  factor_jet(r, K->c0p, K->rhop, K->Bp, K->mup, K->np));
-      break;
-    case 6:
-      k = jet_mul(jet_der(factor_jet(r, K->c0, K->rho, K->B, K->mu, K->n)),
-                  jet_der(factor_jet(r, K->c0p, K->rhop, K->Bp, K->mup, K->np)));
-      break;
+    case 5: k = pair_jet(K, 0, r); break;
+    case 4: k = jet_mul(pair_jet(K, 0, r), pair_jet(K, 1, r)); break;
+    case 6: k = jet_mul(jet_der(pair_jet(K, 0, r)), jet_der(pair_jet(K, 1, r))); break;
     default: k = jet_cst(0, r.n);
   }
   return jet_mul(r, k);
@@ -310,9 +352,16 @@ static jet phi_jet(const ork_kernel *K, int cls, real x0, int nord) {
 
 /* Largest exponential growth rate of the kernel (the e^{B r} factors). */
 static double kernel_growth(const ork_kernel *K, int cls) {
-  if (K->id) return 0.0;
-  double b = K->c0 != 0.0 && K->B > 0 ? K->B : 0.0;
-  double bp = K->c0p != 0.0 && K->Bp > 0 ? K->Bp : 0.0;
+  double b = 0.0, bp = 0.0;
+  if (K->id == ORK_TERMS) {
+    for (int i = 0; i < K->nt; ++i) b = K->t[i][2] > b ? K->t[i][2] : b;
+    for (int i = 0; i < K->ntp; ++i) bp = K->tp[i][2] > bp ? K->tp[i][2] : bp;
+  } else if (K->id) {
+    return 0.0;
+  } else {
+    b = K->c0 != 0.0 && K->B > 0 ? K->B : 0.0;
+    bp = K->c0p != 0.0 && K->Bp > 0 ? K->Bp : 0.0;
+  }
   switch (cls) {
     case 2: case 3: case 5: return b;
     case 4: case 6: return b + bp;

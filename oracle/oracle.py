@@ -34,11 +34,15 @@ class OrkKernel(ctypes.Structure):
         ("c0p", ctypes.c_double), ("rhop", ctypes.c_double), ("Bp", ctypes.c_double), ("mup", ctypes.c_double),
         ("np", ctypes.c_int),
         ("gam", ctypes.c_double),
+        ("nt", ctypes.c_int), ("ntp", ctypes.c_int),
+        ("t", (ctypes.c_double * 4) * 16), ("tp", (ctypes.c_double * 4) * 16),
     ]
 
 
 # plain test kernels (id field of OrkKernel)
 K_ONE, K_GAUSS, K_R, K_COULOMB, K_SLATER = 10, 11, 12, 13, 14
+K_TERMS = 20        # factor pair given as term lists
+MAX_TERMS = 16
 
 
 def build(force: bool = False) -> str:
@@ -103,6 +107,27 @@ def factor_kernel(f, fprime=None) -> OrkKernel:
     fp = f if fprime is None else fprime
     return OrkKernel(0, f["c0"], f["rho"], f["B"], f["mu"], int(f["n"]),
                      fp["c0"], fp["rho"], fp["B"], fp["mu"], int(fp["n"]), 0.0)
+
+
+def factor_kernel_terms(terms, terms_prime=None) -> OrkKernel:
+    """Kernel record for a factor pair given as sums of terms c r^a e^{b r - g r^2}.
+
+    ``terms`` and ``terms_prime`` are sequences of (c, a, b, g) (at most 16
+    each); ``terms_prime`` defaults to ``terms``.  The classes' kernels are
+    formed from them as for the range-separated factor (Eqs. k1-k6, I6_).
+    """
+    tp = terms if terms_prime is None else terms_prime
+    if not (0 < len(terms) <= MAX_TERMS and 0 < len(tp) <= MAX_TERMS):
+        raise ValueError("1 to %d terms per factor" % MAX_TERMS)
+    k = OrkKernel(K_TERMS, 0.0, 0.0, 0.0, 1.0, 0, 0.0, 0.0, 0.0, 1.0, 0, 0.0)
+    k.nt, k.ntp = len(terms), len(tp)
+    for i, row in enumerate(terms):
+        for j in range(4):
+            k.t[i][j] = float(row[j])
+    for i, row in enumerate(tp):
+        for j in range(4):
+            k.tp[i][j] = float(row[j])
+    return k
 
 
 def test_kernel(kid: int, gam: float = 0.0) -> OrkKernel:

@@ -125,8 +125,10 @@ struct ClassTables {
 
 // kernels[cls] (cls = 1..6; entry 5 unused) are the kernel term lists.  A class
 // is left out (supported false) when a family needs S(alpha) below
-// alpha = -1 other than the alpha = -1 finite part, when it has more than
-// MAXFAM families, or when a family with b < 0 has a power that is neither an
+// alpha = -1 other than the alpha = -1 finite part, when the x^-1 terms of the
+// alpha = -1 families do not cancel (the kernel's integrals diverge at r = 0;
+// the damping of Eq. rs12 always cancels them), when it has more than MAXFAM
+// families, or when a family with b < 0 has a power that is neither an
 // integer nor a half-integer (the quadrature of family_quad handles those two
 // end-point forms only).  Returns false if a family polynomial is longer than
 // JMAX.
@@ -153,6 +155,15 @@ inline bool build_class_tables(const f12::TermList kernels[NCLASS], ClassTables 
       if (a < -1.0 - 1e-9 || (a <= -1.0 && std::fabs(a + 1.0) >= 1e-9)) ct.supported[cls] = false;
     }
     if ((int)fl.size() > MAXFAM) ct.supported[cls] = false;
+    // integrable at r = 0: the x^-1 terms of the alpha0 = -1 families (each
+    // taken as a finite part) must cancel between them
+    double fsum = 0.0, fabs_sum = 0.0;
+    for (const f12::Family &fam0 : fl)
+      if (std::fabs(fam0.a0 + 3.0) < 1e-9 && !fam0.poly.empty()) {
+        fsum += fam0.poly[0];
+        fabs_sum += std::fabs(fam0.poly[0]);
+      }
+    if (std::fabs(fsum) > 1e-10 * fabs_sum) ct.supported[cls] = false;
     if (!ct.supported[cls]) continue;
     std::vector<double> coef;
     for (const f12::Family &fam0 : fl) {

@@ -873,6 +873,20 @@ bool finite_factor(const f12int_factor &f) {
   return std::isfinite(f.c0) && std::isfinite(f.rho) && std::isfinite(f.B) && std::isfinite(f.mu);
 }
 
+// A factor given as terms: 1..64 finite terms with g >= 0, not all zero.
+int check_terms(const f12int_term *t, int n, f12::TermList &out) {
+  if (!t || n < 1 || n > 64) return F12INT_EINVAL;
+  out.clear();
+  for (int i = 0; i < n; ++i) {
+    const f12int_term &u = t[i];
+    if (!std::isfinite(u.c) || !std::isfinite(u.a) || !std::isfinite(u.b) || !std::isfinite(u.g) || u.g < 0.0)
+      return F12INT_EDOMAIN;
+    out.push_back({u.c, u.a, u.b, u.g});
+  }
+  f12::simplify(out);
+  return out.empty() ? F12INT_EDOMAIN : F12INT_OK;
+}
+
 int check_factor(const f12int_factor &f) {
   if (!finite_factor(f)) return F12INT_EDOMAIN;
   if (!(f.mu > 0.0) || f.c0 < 0.0 || f.n < 0 || f.n > 20) return F12INT_EDOMAIN;
@@ -1012,15 +1026,11 @@ int f12int_device_status(f12int_ctx *ctx) {
   return h ? F12INT_EDEVICE : F12INT_OK;
 }
 
-int f12int_kernel_radial(int cls, const f12int_factor *f, const f12int_factor *fprime, int l, double x,
-                         double *value) {
-  if (!f || !value || cls < 1 || cls > 6 || l < 0 || l > LAUX || !(x > 0.0)) return F12INT_EINVAL;
-  const f12int_factor &fp = fprime ? *fprime : *f;
-  int rc = check_factor(*f);
-  if (rc == F12INT_OK) rc = check_factor(fp);
-  if (rc != F12INT_OK) return rc;
-  f12::Factor F1{f->c0, f->rho, f->B, f->mu, f->n}, F2{fp.c0, fp.rho, fp.B, fp.mu, fp.n};
-  std::vector<f12::Family> fl = f12::families(f12::kernel_terms(cls, F1, F2));
+}  // extern "C"
+
+// x^{2l+2} (D_r^l k)(x) of a kernel from its families.
+static double kernel_radial_value(const f12::TermList &kt, int l, double x) {
+  std::vector<f12::Family> fl = f12::families(kt);
   double s = 0.0;
   for (const f12::Family &fam0 : fl) {
     f12::Family cur = fam0;
@@ -1030,7 +1040,31 @@ int f12int_kernel_radial(int cls, const f12int_factor *f, const f12int_factor *f
     for (size_t j = cur.poly.size(); j-- > 0;) poly = poly * x + cur.poly[j];
     s += poly * std::pow(x, fam0.a0 + 2.0) * std::exp(fam0.b * x - fam0.g * x * x);
   }
-  *value = s;
+  return s;
+}
+
+extern "C" {
+
+int f12int_kernel_radial(int cls, const f12int_factor *f, const f12int_factor *fprime, int l, double x,
+                         double *value) {
+  if (!f || !value || cls < 1 || cls > 6 || l < 0 || l > LAUX || !(x > 0.0)) return F12INT_EINVAL;
+  const f12int_factor &fp = fprime ? *fprime : *f;
+  int rc = check_factor(*f);
+  if (rc == F12INT_OK) rc = check_factor(fp);
+  if (rc != F12INT_OK) return rc;
+  f12::Factor F1{f->c0, f->rho, f->B, f->mu, f->n}, F2{fp.c0, fp.rho, fp.B, fp.mu, fp.n};
+  *value = kernel_radial_value(f12::kernel_terms(cls, F1, F2), l, x);
+  return F12INT_OK;
+}
+
+int f12int_kernel_radial_terms(int cls, const f12int_term *f, int nf, const f12int_term *fprime, int nfp, int l,
+                               double x, double *value) {
+  if (!value || cls < 1 || cls > 6 || l < 0 || l > LAUX || !(x > 0.0)) return F12INT_EINVAL;
+  f12::TermList T1, T2;
+  int rc = check_terms(f, nf, T1);
+  if (rc == F12INT_OK) rc = fprime ? check_terms(fprime, nfp, T2) : (T2 = T1, F12INT_OK);
+  if (rc != F12INT_OK) return rc;
+  *value = kernel_radial_value(f12::kernel_terms(cls, T1, T2), l, x);
   return F12INT_OK;
 }
 
@@ -1096,21 +1130,16 @@ static double screen_estimate(const f12int_ctx *ctx, const f12int_ctx::BasisData
   return q * gam * kScreenSafety[cls];
 }
 
-extern "C" {
-
-int f12int_set_factor(f12int_ctx *ctx, const f12int_factor *f, const f12int_factor *fprime) {
-  if (!ctx || !f) return F12INT_EINVAL;
-  const f12int_factor &fp = fprime ? *fprime : *f;
-  int rc = check_factor(*f);
-  if (rc == F12INT_OK) rc = check_factor(fp);
-  if (rc != F12INT_OK) return rc;
+// The part of f12int_set_factor(_terms) after validation: kernels, families,
+// upload, and the bounds and schedules that depend on the factor.
+static int set_factor_lists(f12int_ctx *ctx, const f12::TermList &T1, const f12::TermList &T2) {
   if (!engine_idle(ctx)) return F12INT_EINVAL;   // submitted requests still use the current factor
   std::lock_guard<std::mutex> lk(ctx->mu);
   CK(cudaSetDevice(ctx->device));
-  f12::Factor F1{f->c0, f->rho, f->B, f->mu, f->n}, F2{fp.c0, fp.rho, fp.B, fp.mu, fp.n};
+  int rc = F12INT_OK;
   f12::TermList kt[NCLASS];
   for (int cls = 1; cls <= 6; ++cls)
-    if (cls != 5) kt[cls] = f12::kernel_terms(cls, F1, F2);
+    if (cls != 5) kt[cls] = f12::kernel_terms(cls, T1, T2);
   ClassTables ct;
   if (!build_class_tables(kt, ct)) return F12INT_EDOMAIN;
   const std::vector<FamDev> &fams = ct.fams;
@@ -1145,10 +1174,31 @@ int f12int_set_factor(f12int_ctx *ctx, const f12int_factor *f, const f12int_fact
       }
   for (auto &b : ctx->bases)   // and so do the shell-pair bounds
     for (int c = 0; c < 7; ++c) b.pair_bound[c].clear();
-  for (int c = 1; c <= 6; ++c) ctx->kgrow[c] = growth_table(f12::kernel_terms(c == 5 ? 3 : c, F1, F2));
+  for (int c = 1; c <= 6; ++c) ctx->kgrow[c] = growth_table(kt[c == 5 ? 3 : c]);
   engine_factor_changed(ctx);
   ctx->factor_ready = true;
   return F12INT_OK;
+}
+
+extern "C" {
+
+int f12int_set_factor(f12int_ctx *ctx, const f12int_factor *f, const f12int_factor *fprime) {
+  if (!ctx || !f) return F12INT_EINVAL;
+  const f12int_factor &fp = fprime ? *fprime : *f;
+  int rc = check_factor(*f);
+  if (rc == F12INT_OK) rc = check_factor(fp);
+  if (rc != F12INT_OK) return rc;
+  f12::Factor F1{f->c0, f->rho, f->B, f->mu, f->n}, F2{fp.c0, fp.rho, fp.B, fp.mu, fp.n};
+  return set_factor_lists(ctx, f12::factor_terms(F1), f12::factor_terms(F2));
+}
+
+int f12int_set_factor_terms(f12int_ctx *ctx, const f12int_term *f, int nf, const f12int_term *fprime, int nfp) {
+  if (!ctx) return F12INT_EINVAL;
+  f12::TermList T1, T2;
+  int rc = check_terms(f, nf, T1);
+  if (rc == F12INT_OK) rc = fprime ? check_terms(fprime, nfp, T2) : (T2 = T1, F12INT_OK);
+  if (rc != F12INT_OK) return rc;
+  return set_factor_lists(ctx, T1, T2);
 }
 
 int f12int_set_basis(f12int_ctx *ctx, int nshell, const double *centers, const int *l, const int *nprim,

@@ -79,16 +79,20 @@ TermList times_power(const TermList &t, double m) {
   return r;
 }
 
-TermList kernel_terms(int cls, const Factor &f, const Factor &fp) {
+TermList kernel_terms(int cls, const TermList &f, const TermList &fp) {
   switch (cls) {
-    case 1: return TermList{{1.0, -1.0, 0.0, 0.0}};               // Eq. k1: 1/r
-    case 2: return times_power(factor_terms(f), -1.0);           // Eq. k2: f/r
+    case 1: return TermList{{1.0, -1.0, 0.0, 0.0}};    // Eq. k1: 1/r
+    case 2: return times_power(f, -1.0);              // Eq. k2: f/r
     case 3:
-    case 5: return factor_terms(f);                              // Eq. k3: f
-    case 4: return product(factor_terms(f), factor_terms(fp));   // Eq. k4: f f'
-    case 6: return product(derivative(factor_terms(f)), derivative(factor_terms(fp)));  // Eq. I6_
+    case 5: return f;                                 // Eq. k3: f
+    case 4: return product(f, fp);                    // Eq. k4: f f'
+    case 6: return product(derivative(f), derivative(fp));   // Eq. I6_
     default: return TermList{};
   }
+}
+
+TermList kernel_terms(int cls, const Factor &f, const Factor &fp) {
+  return kernel_terms(cls, factor_terms(f), factor_terms(fp));
 }
 
 std::vector<Family> families(const TermList &t) {

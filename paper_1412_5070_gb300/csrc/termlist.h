@@ -34,7 +34,9 @@ TermList product(const TermList &x, const TermList &y);
 TermList times_power(const TermList &t, double m);            // r^m * t
 void simplify(TermList &t);                                   // merge like terms, drop zeros
 
-// Kernel of class cls (1..6; class 5 uses the I3 kernel f, Eq. I5_).
+// Kernel of class cls (1..6; class 5 uses the I3 kernel f, Eq. I5_), from the
+// factor pair as term lists or as parameters of Eq. rs12.
+TermList kernel_terms(int cls, const TermList &f, const TermList &fp);
 TermList kernel_terms(int cls, const Factor &f, const Factor &fp);
 
 struct Family {

@@ -22,7 +22,8 @@ STATUS = {0: "F12INT_OK", -1: "F12INT_EINVAL", -2: "F12INT_ENOMEM", -3: "F12INT_
           -4: "F12INT_ENOTREADY", -5: "F12INT_ETIMEOUT", -6: "F12INT_ECUDA", -7: "F12INT_EDEVICE"}
 
 # every entry point declared in include/f12int.h
-EXPORTS = ("f12int_create", "f12int_destroy", "f12int_set_basis", "f12int_set_factor", "f12int_screen",
+EXPORTS = ("f12int_create", "f12int_destroy", "f12int_set_basis", "f12int_set_factor", "f12int_set_factor_terms",
+           "f12int_kernel_radial_terms", "f12int_screen",
            "f12int_compute_class", "f12int_compute_class_mixed", "f12int_compute_class_static", "f12int_aux", "f12int_launch_count",
            "f12int_device_status", "f12int_set_timing", "f12int_kernel_stats", "f12int_kernel_radial",
            "f12int_submit", "f12int_poll", "f12int_batch_limits", "f12int_batch_autotune", "f12int_batch_stats",
@@ -44,6 +45,17 @@ class Factor(ctypes.Structure):
     @classmethod
     def of(cls, d):
         return cls(float(d["c0"]), float(d["rho"]), float(d["B"]), float(d["mu"]), int(d["n"]))
+
+
+class Term(ctypes.Structure):
+    """c r^a exp(b r - g r^2)."""
+    _fields_ = [("c", ctypes.c_double), ("a", ctypes.c_double), ("b", ctypes.c_double), ("g", ctypes.c_double)]
+
+
+def _terms(rows):
+    rows = [tuple(float(v) for v in r) for r in rows]
+    arr = (Term * max(len(rows), 1))(*[Term(*r) for r in rows])
+    return arr, len(rows)
 
 
 class Request(ctypes.Structure):
@@ -73,6 +85,9 @@ def load():
     L.f12int_destroy.argtypes = [_vp]
     L.f12int_set_basis.argtypes = [_vp, ctypes.c_int, _dp, _ip, _ip, _dp, _dp, _ip]
     L.f12int_set_factor.argtypes = [_vp, ctypes.POINTER(Factor), ctypes.POINTER(Factor)]
+    L.f12int_set_factor_terms.argtypes = [_vp, ctypes.POINTER(Term), ctypes.c_int, ctypes.POINTER(Term), ctypes.c_int]
+    L.f12int_kernel_radial_terms.argtypes = [ctypes.c_int, ctypes.POINTER(Term), ctypes.c_int, ctypes.POINTER(Term),
+                                             ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp]
     L.f12int_screen.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                 ctypes.POINTER(ctypes.c_int32), ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
     L.f12int_compute_class.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int64, _vp, _vp, _vp]
@@ -162,6 +177,17 @@ def f12int_set_factor(ctx, f, fprime=None) -> None:
            "f12int_set_factor")
 
 
+def f12int_set_factor_terms(ctx, terms, terms_prime=None) -> None:
+    """Factors as sums of terms: ``terms`` (and ``terms_prime``, default the
+    same) are sequences of (c, a, b, g) for c r^a exp(b r - g r^2)."""
+    t, n = _terms(terms)
+    if terms_prime is None:
+        _check(load().f12int_set_factor_terms(ctx, t, n, None, 0), "f12int_set_factor_terms")
+    else:
+        tp, npr = _terms(terms_prime)
+        _check(load().f12int_set_factor_terms(ctx, t, n, tp, npr), "f12int_set_factor_terms")
+
+
 def f12int_screen(ctx, basis_id: int, cls: int, thresh: float, cap: int = 0) -> np.ndarray:
     """Canonical quartets surviving the Schwarz-type screen (host int32 [n, 4])."""
     L = load()
@@ -219,6 +245,19 @@ def f12int_kernel_radial(cls: int, f, l: int, x: float, fprime=None) -> float:
     v = ctypes.c_double(0.0)
     _check(load().f12int_kernel_radial(int(cls), ctypes.byref(F), ctypes.byref(Fp) if Fp is not None else None,
                                        int(l), float(x), ctypes.byref(v)), "f12int_kernel_radial")
+    return v.value
+
+
+def f12int_kernel_radial_terms(cls: int, terms, l: int, x: float, terms_prime=None) -> float:
+    """f12int_kernel_radial for factors given as terms (no GPU needed)."""
+    t, n = _terms(terms)
+    v = ctypes.c_double(0.0)
+    if terms_prime is None:
+        rc = load().f12int_kernel_radial_terms(int(cls), t, n, None, 0, int(l), float(x), ctypes.byref(v))
+    else:
+        tp, npr = _terms(terms_prime)
+        rc = load().f12int_kernel_radial_terms(int(cls), t, n, tp, npr, int(l), float(x), ctypes.byref(v))
+    _check(rc, "f12int_kernel_radial_terms")
     return v.value
 
 

@@ -73,4 +73,20 @@ int aux_host_eval(const double *f, const double *fp, int cls, int64_t n, const d
   return eval(kt, cls, n, xi, D, nmax, out);
 }
 
+// The same for factors given as terms: t[4 i + (0..3)] = c, a, b, g of
+// c r^a exp(b r - g r^2), nt terms in f and ntp in f'.
+int aux_host_eval_terms(const double *t, int nt, const double *tp, int ntp, int cls, int64_t n, const double *xi,
+                        const double *D, int nmax, double *out) {
+  if (!t || !tp || nt < 1 || ntp < 1 || cls < 1 || cls > 6 || nmax < 0 || nmax > LAUX || n < 0) return -1;
+  f12::TermList T1, T2;
+  for (int i = 0; i < nt; ++i) T1.push_back({t[4 * i], t[4 * i + 1], t[4 * i + 2], t[4 * i + 3]});
+  for (int i = 0; i < ntp; ++i) T2.push_back({tp[4 * i], tp[4 * i + 1], tp[4 * i + 2], tp[4 * i + 3]});
+  f12::simplify(T1);
+  f12::simplify(T2);
+  f12::TermList kt[NCLASS];
+  for (int c = 1; c <= 6; ++c)
+    if (c != 5) kt[c] = f12::kernel_terms(c, T1, T2);
+  return eval(kt, cls, n, xi, D, nmax, out);
+}
+
 }  // extern "C"

@@ -50,6 +50,9 @@ def lib():
     dp = ctypes.POINTER(ctypes.c_double)
     L.aux_host_eval.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int64, dp, dp, ctypes.c_int, dp]
     L.aux_host_eval.restype = ctypes.c_int
+    L.aux_host_eval_terms.argtypes = [dp, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int64, dp, dp,
+                                      ctypes.c_int, dp]
+    L.aux_host_eval_terms.restype = ctypes.c_int
     return L
 
 
@@ -62,6 +65,18 @@ def host_aux(lib, f, fp, cls, pts, nmax):
     out = np.zeros(len(pts) * (nmax + 1))
     rc = lib.aux_host_eval(fa.ctypes.data_as(dp), fb.ctypes.data_as(dp), cls, len(pts), xi.ctypes.data_as(dp),
                            D.ctypes.data_as(dp), nmax, out.ctypes.data_as(dp))
+    return rc, out.reshape(len(pts), nmax + 1)
+
+
+def host_aux_terms(lib, t, tp, cls, pts, nmax):
+    dp = ctypes.POINTER(ctypes.c_double)
+    a = np.ascontiguousarray(t, dtype=np.float64).ravel()
+    b = np.ascontiguousarray(tp, dtype=np.float64).ravel()
+    xi = np.ascontiguousarray([p[0] for p in pts], dtype=np.float64)
+    D = np.ascontiguousarray([p[1] for p in pts], dtype=np.float64)
+    out = np.zeros(len(pts) * (nmax + 1))
+    rc = lib.aux_host_eval_terms(a.ctypes.data_as(dp), len(t), b.ctypes.data_as(dp), len(tp), cls, len(pts),
+                                 xi.ctypes.data_as(dp), D.ctypes.data_as(dp), nmax, out.ctypes.data_as(dp))
     return rc, out.reshape(len(pts), nmax + 1)
 
 
@@ -123,3 +138,74 @@ def test_factor_pair_with_negative_B(lib):
         rc, got = host_aux(lib, f, fp, cls, XI_D_GRID[1::3], 8)
         assert rc == 0
         assert worst_relative(got, O.factor_kernel(f, fp), cls, XI_D_GRID[1::3], 8) < 1e-8
+
+
+# factors given as terms (c, a, b, g): c r^a exp(b r - g r^2)
+TERM_SETS = {
+    "Ten-no exp(-1.2 r)": [(1.0, 0, -1.2, 0)],
+    "three Gaussians": [(0.3, 0, 0, 0.2), (0.25, 0, 0, 1.1), (0.2, 0, 0, 4.0)],
+    "Ten-no + Gaussian + r exp": [(-1 / 1.2, 0, -1.2, 0), (0.1, 0, 0, 0.5), (0.05, 1, -0.7, 0.3)],
+    "r exp(-r)": [(1.0, 1, -1.0, 0)],
+    "half-integer powers": [(0.4, -0.5, -0.9, 0), (0.2, 0.5, 0.0, 0.8)],
+}
+
+
+@pytest.mark.parametrize("name", list(TERM_SETS))
+@pytest.mark.parametrize("cls", [2, 3, 4, 6])
+def test_term_list_factors_on_cpu_against_oracle(lib, name, cls):
+    """Factors given as term lists (the Ten-no factor, Gaussian geminals,
+    mixtures): hat g_n up to order 14 against the oracle's term-list kernel."""
+    t = TERM_SETS[name]
+    pts = XI_D_GRID[::2]
+    rc, got = host_aux_terms(lib, t, t, cls, pts, 14)
+    if name == "half-integer powers" and cls == 6:
+        assert rc == -3   # f_r^2 ~ r^-3: x^2 k has an x^-1 term that nothing cancels
+        return
+    assert rc == 0
+    assert worst_relative(got, O.factor_kernel_terms(t), cls, pts, 14) < 1e-11
+
+
+def test_term_list_pair(lib):
+    """f' != f as term lists (Ten-no and Gaussians) for I4 and I6."""
+    t, tp = TERM_SETS["Ten-no exp(-1.2 r)"], TERM_SETS["three Gaussians"]
+    for cls in (4, 6):
+        rc, got = host_aux_terms(lib, t, tp, cls, XI_D_GRID[1::3], 10)
+        assert rc == 0
+        assert worst_relative(got, O.factor_kernel_terms(t, tp), cls, XI_D_GRID[1::3], 10) < 1e-11
+
+
+def test_term_list_domain(lib):
+    """r^-3 diverges in every class and is refused; r^-3 (1 - e^{-0.7 r^2}) has
+    an integrable I3 kernel (its two alpha = -1 families cancel) and is served,
+    while its other classes need S(alpha) below -1 and are refused."""
+    bare = [(1.0, -3, 0, 0)]
+    damped = [(1.0, -3, 0, 0), (-1.0, -3, 0, 0.7)]
+    for cls in (2, 3, 4, 6):
+        assert host_aux_terms(lib, bare, bare, cls, XI_D_GRID[:2], 4)[0] == -3
+        assert host_aux_terms(lib, damped, damped, cls, XI_D_GRID[:2], 4)[0] == (0 if cls == 3 else -3)
+
+
+def test_cancelling_terms_against_quadrature(lib):
+    """I3 of k = r^-3 (1 - e^{-0.7 r^2}), evaluated through two finite-part
+    families, against 30-digit quadrature of the kernel itself (written with
+    expm1, so without the cancellation), hat g_n for n <= 3."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 30
+    damped = [(1.0, -3, 0, 0), (-1.0, -3, 0, 0.7)]
+    pts = [(0.5, 1.2), (2.0, 0.7)]
+    rc, got = host_aux_terms(lib, damped, damped, 3, pts, 3)
+    assert rc == 0
+
+    def k(r):
+        return -mp.expm1(-mp.mpf("0.7") * r * r) / r ** 3
+
+    for i, (x, d) in enumerate(pts):
+        x = mp.mpf(x)
+
+        def g0(s):
+            dd = mp.sqrt(s)
+            f = lambda r: k(r) * r * (mp.exp(-x * (r - dd) ** 2) - mp.exp(-x * (r + dd) ** 2)) / dd
+            return mp.quad(f, [0, dd, dd + 10 / mp.sqrt(x), mp.inf])
+
+        ref = np.array([float(2 ** n * mp.diff(g0, mp.mpf(d) ** 2, n)) for n in range(4)])
+        np.testing.assert_allclose(got[i], ref, rtol=1e-12, atol=0)

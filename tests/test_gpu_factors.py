@@ -196,3 +196,37 @@ def test_decaying_factor_batch_equals_per_call(dev):
             assert np.all(np.abs(got - ref) <= tol), (cls, float(np.max(np.abs(got - ref) - tol)))
     finally:
         F.f12int_destroy(ctx)
+
+
+TERM_SETS = {
+    "Ten-no exp(-1.2 r)": [(1.0, 0, -1.2, 0)],
+    "three Gaussians": [(0.3, 0, 0, 0.2), (0.25, 0, 0, 1.1), (0.2, 0, 0, 4.0)],
+    "Ten-no + Gaussian + r exp": [(-1 / 1.2, 0, -1.2, 0), (0.1, 0, 0, 0.5), (0.05, 1, -0.7, 0.3)],
+}
+
+
+@pytest.mark.parametrize("name", list(TERM_SETS))
+@pytest.mark.parametrize("cls", [2, 3, 4, 5, 6])
+def test_term_list_factors_two_centre(dev, name, cls):
+    """Factors given as term lists (f12int_set_factor_terms): the Ten-no
+    factor, a Gaussian geminal and a mixture, on the two-centre s/p basis."""
+    t = TERM_SETS[name]
+    ctx = F.f12int_create(0, 0, None)
+    try:
+        F.f12int_set_factor_terms(ctx, t)
+        basis = M.two_centre_sp()
+        bid = F.f12int_set_basis(ctx, basis)
+        q = M.canonical_quartets(basis, cls)[5::12]
+        off = M.block_offsets(basis, q)
+        out = torch.full((int(off[-1]),), float("nan"), dtype=torch.float64, device="cuda")
+        F.f12int_compute_class(ctx, bid, cls, torch.from_numpy(q).cuda(), out,
+                               torch.from_numpy(off[:-1].copy()).cuda())
+        torch.cuda.synchronize()
+        F.f12int_device_status(ctx)
+        got = out.cpu().numpy()
+    finally:
+        F.f12int_destroy(ctx)
+    ref, _, mag = O.shell_blocks(O.factor_kernel_terms(t), cls, basis, q, with_mag=True)
+    bad = close(got, ref, mag)
+    assert not np.isnan(got).any()
+    assert not bad.any(), report(got, ref, mag, bad)

@@ -113,6 +113,35 @@ def test_factor_domain_checks(lib, bad):
     assert e.value.status == -3
 
 
+TENNO = [(1.0, 0, -1.2, 0)]
+GAUSSIANS = [(0.3, 0, 0, 0.2), (0.25, 0, 0, 1.1), (0.2, 0, 0, 4.0)]
+
+
+@pytest.mark.parametrize("terms", [TENNO, GAUSSIANS], ids=["Ten-no", "Gaussians"])
+@pytest.mark.parametrize("cls", [1, 2, 3, 4, 6])
+@pytest.mark.parametrize("x", [0.05, 0.9, 3.0])
+def test_term_list_factors_reproduce_the_kernels(lib, terms, cls, x):
+    """Factors given as terms: x^2 k(x) from the library's term lists equals
+    the oracle's pointwise kernel of the same factor."""
+    got = F.f12int_kernel_radial_terms(cls, terms, 0, x)
+    ref = x * x * O.kernel_value(O.factor_kernel_terms(terms), cls, x)
+    assert abs(got - ref) <= 1e-13 * abs(ref) + 1e-15
+
+
+def test_term_list_pair_and_domain(lib):
+    """f' != f as term lists; g < 0, non-finite values, an empty or all-zero
+    list, and more than 64 terms are refused."""
+    x = 1.3
+    got = F.f12int_kernel_radial_terms(6, TENNO, 0, x, terms_prime=GAUSSIANS)
+    ref = x * x * O.kernel_value(O.factor_kernel_terms(TENNO, GAUSSIANS), 6, x)
+    assert abs(got - ref) <= 1e-13 * abs(ref)
+    for bad, status in (([(1.0, 0, 0, -0.5)], -3), ([(float("inf"), 0, 0, 1.0)], -3), ([], -1),
+                        ([(1.0, 0, 0, 1.0), (-1.0, 0, 0, 1.0)], -3), ([(1.0, 0, 0, 1.0)] * 65, -1)):
+        with pytest.raises(F.F12IntError) as e:
+            F.f12int_kernel_radial_terms(3, bad, 0, 1.0)
+        assert e.value.status == status
+
+
 def test_shard_partitions_every_list():
     lst = np.arange(103 * 4).reshape(103, 4)
     parts = [sharding.shard(lst, r, 3) for r in range(3)]

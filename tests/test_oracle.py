@@ -193,6 +193,36 @@ def test_radial_slater_kernel_closed_form(om, xi, D):
     np.testing.assert_allclose(got, ref, rtol=1e-12, atol=0)
 
 
+def _mp_kernel_terms(cls, t):
+    """Kernel of class cls (Eqs. k2, k3, k4, I6_ with f' = f) from a factor's
+    terms (c, a, b, g), written out: f/r, f, f f', f_r f'_r."""
+    def d(u):
+        out = []
+        for c, a, b, g in u:
+            out += [(c * a, a - 1, b, g), (c * b, a, b, g), (-2 * g * c, a + 1, b, g)]
+        return [x for x in out if x[0] != 0]
+
+    def prod(u, v):
+        return [(c1 * c2, a1 + a2, b1 + b2, g1 + g2) for c1, a1, b1, g1 in u for c2, a2, b2, g2 in v]
+
+    return {2: [(c, a - 1, b, g) for c, a, b, g in t], 3: t, 4: prod(t, t), 6: prod(d(t), d(t))}[cls]
+
+
+@pytest.mark.parametrize("name,terms", [("Ten-no", [(1.0, 0, -1.2, 0)]),
+                                        ("Gaussians", [(0.3, 0, 0, 0.2), (0.25, 0, 0, 1.1), (0.2, 0, 0, 4.0)])])
+@pytest.mark.parametrize("cls", [2, 3, 4, 6])
+@pytest.mark.parametrize("xi,D", [(0.5, 1.2), (3.0, 2.0)])
+def test_radial_term_list_factor_closed_form(name, terms, cls, xi, D):
+    """The oracle's term-list kernels (factors given as c r^a e^{b r - g r^2})
+    against the closed form above, hat g_n for n <= 6."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    kt = [(mp.mpf(c), a, mp.mpf(b), mp.mpf(g)) for c, a, b, g in _mp_kernel_terms(cls, terms)]
+    ref = _mp_hat_g(mp, kt, xi, D, 6)
+    got = O.radial(O.factor_kernel_terms(terms), cls, xi, D, 6)
+    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=0)
+
+
 def test_jhat_switch_continuity():
     """e^{-z} j_m(z) from the series and from the closed forms meet at the switch."""
     N = 10
