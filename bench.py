@@ -31,6 +31,11 @@ Two further workloads, each printing its own JSON line:
   --workload perl     the 12-atom workload split by class and (la, lb, lc, ld): shell and
                       primitive quartets/s of every combination, with the FP64 rate of each
                       kernel from the library's event timing and work counters.
+  --workload factors  the 12-atom workload (a seeded sample of 200k screened shell quartets
+                      per class, I2..I6) for four forms of the correlation factor: Eq. rs12
+                      with B = +0.5 and with B = -0.5 (a decaying long range, second
+                      evaluation launch), the Ten-no factor exp(-1.2 r) and a six-Gaussian
+                      geminal (both as term lists): shell quartets/s per class and launches.
   --workload serve    Poisson request streams at 10..2000 requests/s over 12
                       molecules of 2-60 atoms; half the requests ask for one
                       class, half for I2..I6, each over U{8..64} x U{8..64}
@@ -71,7 +76,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
-    ap.add_argument("--workload", default="spd12", choices=("spd12", "batch64", "serve", "mixed", "perl"))
+    ap.add_argument("--workload", default="spd12", choices=("spd12", "batch64", "serve", "mixed", "perl", "factors"))
     ap.add_argument("--fraction", type=float, default=1.0, help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu-baseline", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -720,6 +725,67 @@ def run_per_l(args):
     print(json.dumps(line), flush=True)
 
 
+FACTOR_FORMS = {
+    "rs12 B=+0.5": ("rs12", M.P0),
+    "rs12 B=-0.5": ("rs12", dict(M.P0, B=-0.5)),
+    "Ten-no exp(-1.2 r)": ("terms", [(1.0, 0, -1.2, 0)]),
+    "6 Gaussians": ("terms", [(0.5 / (i + 1), 0, 0, 0.2 * 2.5 ** i) for i in range(6)]),
+}
+
+
+def run_factors(args):
+    """Shell quartets/s per class for several forms of the correlation factor."""
+    import torch
+    from paper_1412_5070_gb300 import build as B
+    from paper_1412_5070_gb300 import f12int as F
+    B.build()
+    basis = build_workload()
+    stream = torch.cuda.Stream()
+    ctx = F.f12int_create(0, 0, stream)
+    bid = F.f12int_set_basis(ctx, basis)
+    rng = np.random.default_rng(11)
+    per = 200_000
+    steps = max(1, args.steps)
+    results = {}
+    for name, (kind, f) in FACTOR_FORMS.items():
+        if kind == "rs12":
+            F.f12int_set_factor(ctx, f)
+        else:
+            F.f12int_set_factor_terms(ctx, f)
+        row = {}
+        for c in (2, 3, 4, 5, 6):
+            q = F.f12int_screen(ctx, bid, c, THRESH)
+            q = np.ascontiguousarray(q[np.sort(rng.choice(len(q), size=min(per, len(q)), replace=False))])
+            off = M.block_offsets(basis, q)
+            dq = torch.from_numpy(q).cuda()
+            doff = torch.from_numpy(off[:-1].copy()).cuda()
+            out = torch.empty(int(off[-1]), dtype=torch.float64, device="cuda")
+            F.f12int_compute_class(ctx, bid, c, dq, out, doff, stream)   # warm-up
+            stream.synchronize()
+            n0 = F.f12int_launch_count(ctx)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                F.f12int_compute_class(ctx, bid, c, dq, out, doff, stream)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            row["I%d" % c] = {"shell_quartets": len(q), "ms": ms, "shell_quartets_per_s": len(q) / (ms / 1e3),
+                              "launches": (F.f12int_launch_count(ctx) - n0) // steps}
+            del out
+        F.f12int_device_status(ctx)
+        results[name] = row
+        print("factors: %s done" % name, file=sys.stderr, flush=True)
+    F.f12int_destroy(ctx)
+    line = {"metric": "F12 shell quartets/s per class for several correlation-factor forms", "unit": UNIT,
+            "n_gpus": 1, "steps": steps, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "12-atom 3s2p1d (seed 2), Schwarz 1e-12 per factor, seeded sample of "
+                                   "%d quartets per class" % per,
+                       "factors": {k: v[1] for k, v in FACTOR_FORMS.items()}},
+            "results": results}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -732,6 +798,8 @@ def main():
         run_mixed(args)
     elif args.workload == "perl":
         run_per_l(args)
+    elif args.workload == "factors":
+        run_factors(args)
     else:
         run_ours(args)
 
