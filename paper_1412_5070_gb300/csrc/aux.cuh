@@ -37,9 +37,12 @@
 // Families with b < 0 (a factor that decays exponentially, B < 0 in Eq. rs12,
 // or a Ten-no-type term e^{-w r}): S(alpha, beta, gamma) with beta < 0 is the
 // minimal solution of the alpha recursion (the Tricomi-U case of App. B), so
-// the upward recursion above loses accuracy; their non-peak orders are
-// instead integrated directly by composite Gauss-Legendre quadrature of the
-// same integral (family_quad).
+// the upward recursion above loses accuracy; and families whose lowest power
+// is below -1 (a singular factor whose damping makes only the kernel as a
+// whole integrable; the T_s functions of Sec. 3.3.1 for integer alpha): the
+// non-peak orders of both are instead integrated directly by composite
+// Gauss-Legendre quadrature of the same integral, each family as its
+// Hadamard finite part (family_quad).
 //
 // The header also compiles as plain C++ (without nvcc) so that a CPU test can
 // evaluate this stage against the oracle; the library itself only runs it on
@@ -88,7 +91,9 @@ struct FamDev {
   double rho_start;           // Gamma((as+2)/2) / Gamma((as+1)/2), as = first regular alpha
   int fp_minus1;              // alpha0 == -1: the j = 0 term needs the finite part S(-1,...)
   int pow_kind;               // x^alpha0: 1 integer, 2 half-integer, 0 general
-  int pow_int;                // integer part for pow_kind 1 and 2
+  int pow_int;                // integer part for pow_kind 1 and 2 (floor of alpha0)
+  int quad;                   // b < 0 or alpha0 < -1: evaluated by family_quad (second launch)
+  int nsing;                  // powers alpha0 + k <= -1 (k < nsing) taken as finite parts
   int span[LAUX + 1];
   int coff[LAUX + 1];         // offset of P_l in the coefficient pool
 };
@@ -188,8 +193,11 @@ F12_DEV inline double s_minus1(double b, double gam, int *bad) {
   return s;
 }
 
-// Orders l = l0..L of a family with b < 0, added into out[l] times fct[l]:
-//   int_0^inf x^alpha0 P_l(x) e^{b x - g x^2 - xi (x - D)^2} jhat_l(2 xi D x) dx,
+// Orders l = l0..L of a family evaluated by quadrature (b < 0, or a lowest
+// power alpha0 < -1), added into out[l] times fct[l]:
+//   I_l = int_0^inf x^alpha0 u_l(x) dx,
+//   u_l(x) = P_l(x) e^{b x - g x^2 - xi (x - D)^2} jhat_l(2 xi D x) = e^{-gamma x^2} v_l(x),
+//   v_l(x) = e^{-xi D^2} P_l(x) e^{b x} j_l(2 xi D x),
 // the integral of the header written with e^{-xi x^2 - xi D^2} j_l(2 xi D x)
 // = e^{-xi (x - D)^2} jhat_l(2 xi D x), by composite Gauss-Legendre quadrature.
 // With beta = b + 2 xi D, gamma = g + xi and d the highest power of the
@@ -200,13 +208,32 @@ F12_DEV inline double s_minus1(double b, double gam, int *bad) {
 //              (d + 9 sqrt(d) + 45)/|beta| (the tail of x^d e^{-|beta| x}).
 // A panel starting at a is 1.25/max(sqrt(gamma), |beta|/sqrt(max(1, |beta| a)))
 // wide: about two widths of the Gaussian, or of the bump x^m e^{-|beta| x}
-// that peaks near a (twice that width left errors up to 1e-8 at l = 5).  On the first panel a half-integer power x^{n+1/2} is
-// integrated in u = sqrt(x) (x^{n+1/2} dx = 2 u^{2n+2} du).  For alpha0 = -1
-// the j = 0 term P_0 x^{-1} H_l(x), H_l(0) = c_{l,0} e^{-xi D^2}, is the
-// finite part of Sec. 3.3.2 in the convention of s_minus1:
-//   int_0^inf [H_l(x) - H_l(0) e^{-gamma x^2}] / x dx + H_l(0) (-gamma_E - log gamma)/2.
+// that peaks near a (twice that width left errors up to 1e-8 at l = 5).  On
+// the first panel a half-integer power is integrated in u = sqrt(x)
+// (x^{n+1/2} dx = 2 u^{2n+2} du).
+// End point: the powers alpha0 + k <= -1 (k < K = nsing) are not integrable
+// one family at a time.  Their sum over the kernel's families cancels (the
+// host refuses a kernel where it does not), so each family's integral is
+// taken as its Hadamard finite part (Sec. 3.3.2 for alpha = -1; the integer
+// alpha <= -1 cases of Sec. 3.3.1), and the finite parts add up to the
+// kernel's integral:
+//   FP I_l = int_0^inf x^alpha0 [u_l(x) - e^{-lam x^2} sum_{k<K} t_k x^k] dx
+//            + sum_{k<K} t_k M(alpha0 + k),
+// t_k the Taylor coefficients of u_l(x) e^{lam x^2} = v_l(x) e^{(lam - gamma) x^2}
+// at 0, and M(beta) the finite part of int_0^inf x^beta e^{-lam x^2} dx:
+// Gamma((beta+1)/2) / (2 lam^{(beta+1)/2}), or for beta = -1 - 2m (a pole of
+// Gamma) (lam^m/2) ((-1)^m/m!) (psi(m+1) - log lam), what is left of
+// int_eps^inf after the powers of eps and log eps are dropped (m = 0 is the
+// convention of s_minus1).  The regulator e^{-lam x^2} is free; lam =
+// max(gamma, (6.5/hi)^2) makes the subtracted terms end with the range too
+// (with lam = gamma they would reach past hi where beta < 0 ends it early).
+// Singular powers per family at most: alpha0 >= -2.  Below that the per-family
+// finite parts cancel too strongly in FP64 (for alpha0 = -2.5 and -3 the
+// errors reached 1e-5 against the oracle), and the host refuses the class.
+constexpr int KSING = 2;
+
 F12_DEV inline int family_quad(const Tables &T, const FamDev &F, double xi, double D, int l0, int L,
-                                 const double *fct, double *out, unsigned long long *nfma) {
+                               const double *fct, double *out, unsigned long long *nfma) {
   const double gam = F.g + xi, sg = sqrt(gam);
   const double beta = F.b + 2.0 * xi * D;
   int spmax = 0;
@@ -221,15 +248,50 @@ F12_DEV inline int family_quad(const Tables &T, const FamDev &F, double xi, doub
   }
   const double edd = exp(-xi * D * D);
   const double twoxd = 2.0 * xi * D;
+  const int K = F.nsing < KSING ? F.nsing : KSING;
+  const double lam = K > 0 ? fmax(gam, (6.5 / hi) * (6.5 / hi)) : gam;
+  // Taylor coefficients t_k (k < K) of P_l e^{b x} e^{(lam - gamma) x^2} j_l(2 xi D x) e^{-xi D^2}
+  double tc[LAUX + 1][KSING];
+  if (K > 0) {
+    double eb[KSING];                        // e^{b x} e^{(lam - gamma) x^2}
+    {
+      double e1[KSING];
+      e1[0] = 1.0;
+      for (int k = 1; k < K; ++k) e1[k] = e1[k - 1] * F.b / k;
+      const double dl = lam - gam;
+      for (int k = 0; k < K; ++k) eb[k] = 0.0;
+      double em = 1.0;                       // (lam - gamma)^m / m!
+      for (int m = 0; 2 * m < K; ++m) {
+        for (int k = 2 * m; k < K; ++k) eb[k] = fma(em, e1[k - 2 * m], eb[k]);
+        em *= dl / (m + 1);
+      }
+    }
+    for (int l = l0; l <= L; ++l) {
+      double q[KSING];                       // eb times j_l(2 xi D x)
+      for (int k = 0; k < K; ++k) q[k] = 0.0;
+      double cj = c_inv_dfact[l];            // c_{l,m} (2 xi D)^{2m}
+      for (int m = 0; 2 * m < K; ++m) {
+        for (int k = 2 * m; k < K; ++k) q[k] = fma(cj, eb[k - 2 * m], q[k]);
+        cj *= c_cratio[l][m] * twoxd * twoxd;
+      }
+      const double *P = T.coef + F.coff[l];
+      for (int k = 0; k < K; ++k) {
+        double t = 0.0;
+        for (int i = 0; i <= k && i < F.span[l]; ++i) t = fma(P[i], q[k - i], t);
+        tc[l][k] = edd * t;
+      }
+    }
+  }
   double acc[LAUX + 1], jh[LAUX + 2];
   for (int l = l0; l <= L; ++l) acc[l] = 0.0;
   unsigned long long n = 0;
   double a = 0.0;
   int stretched = 0;
+  const double sl = sqrt(lam);
   for (int p = 0; p < NPMAX && a < hi; ++p) {
     double r = 0.0;
     if (beta < 0.0) r = -beta / sqrt(fmax(1.0, -beta * a));
-    const double w = 1.25 / fmax(sg, r);
+    const double w = 1.25 / fmax(sl, r);
     // the last panel reaches hi (flagged if that makes it wider than the rule)
     if (p == NPMAX - 1 && hi - a > w) stretched = 1;
     const double hw = 0.5 * (p == NPMAX - 1 ? fmax(w, hi - a) : w);
@@ -247,46 +309,54 @@ F12_DEV inline int family_quad(const Tables &T, const FamDev &F, double xi, doub
       }
       const double ex = exp(F.b * x - F.g * x * x - xi * (x - D) * (x - D));
       jhat_all(twoxd * x, L, jh);
-      if (F.fp_minus1) {
-        const double es = edd * exp(-gam * x * x);
-        const double ix = 1.0 / x;
-        for (int l = l0; l <= L; ++l) {
-          const double *P = T.coef + F.coff[l];
-          const int sp = F.span[l];
-          double h = 0.0;
-          for (int j = sp - 1; j >= 1; --j) h = fma(h, x, P[j]);
-          const double Hl = ex * jh[l];
-          acc[l] = fma(wt, fma(Hl, h, P[0] * (Hl - c_inv_dfact[l] * es) * ix), acc[l]);
-          n += sp + 2;
-        }
+      double xa;                       // x^alpha0
+      if (F.pow_kind == 0) {
+        xa = pow(x, F.alpha0);
       } else {
-        double xa;
-        if (F.pow_kind == 1) {
-          xa = 1.0;
+        xa = F.pow_kind == 2 ? sqrt(x) : 1.0;
+        if (F.pow_int >= 0) {
           for (int k = 0; k < F.pow_int; ++k) xa *= x;
-        } else if (F.pow_kind == 2) {
-          xa = sqrt(x);
-          for (int k = 0; k < F.pow_int; ++k) xa *= x;
-          if (F.pow_int < 0) xa /= x;
         } else {
-          xa = pow(x, F.alpha0);
+          const double ix = 1.0 / x;
+          for (int k = 0; k < -F.pow_int; ++k) xa *= ix;
         }
-        const double e = wt * xa * ex;
-        for (int l = l0; l <= L; ++l) {
-          const double *P = T.coef + F.coff[l];
-          const int sp = F.span[l];
-          double h = 0.0;
-          for (int j = sp - 1; j >= 0; --j) h = fma(h, x, P[j]);
-          acc[l] = fma(e * jh[l], h, acc[l]);
-          n += sp + 1;
+      }
+      const double es = K > 0 ? exp(-lam * x * x) : 0.0;
+      for (int l = l0; l <= L; ++l) {
+        const double *P = T.coef + F.coff[l];
+        const int sp = F.span[l];
+        double h = 0.0;
+        for (int j = sp - 1; j >= 0; --j) h = fma(h, x, P[j]);
+        double v = ex * jh[l] * h;
+        if (K > 0) {
+          double tk = 0.0;
+          for (int k = K - 1; k >= 0; --k) tk = fma(tk, x, tc[l][k]);
+          v = fma(-es, tk, v);
         }
+        acc[l] = fma(wt * xa, v, acc[l]);
+        n += sp + K + 1;
       }
     }
     a += 2.0 * hw;
   }
-  if (F.fp_minus1) {
-    const double fp0 = edd * (-0.5 * 0.57721566490153286061 - 0.5 * log(gam));
-    for (int l = l0; l <= L; ++l) acc[l] = fma(T.coef[F.coff[l]] * c_inv_dfact[l], fp0, acc[l]);
+  // finite parts of the subtracted terms
+  for (int k = 0; k < K; ++k) {
+    const double bk = F.alpha0 + k;
+    double M;
+    const double mm = -0.5 * (bk + 1.0);
+    if (F.pow_kind == 1 && mm >= 0.0 && fabs(mm - floor(mm + 0.5)) < 1e-9) {   // beta = -1 - 2m
+      const int m = (int)floor(mm + 0.5);
+      double psi = -0.57721566490153286061, fact = 1.0, gm = 1.0;
+      for (int i = 1; i <= m; ++i) {
+        psi += 1.0 / i;
+        fact *= i;
+        gm *= lam;
+      }
+      M = 0.5 * gm * ((m & 1) ? -1.0 : 1.0) / fact * (psi - log(lam));
+    } else {
+      M = 0.5 * F.gam_tab[k] * pow(lam, -0.5 * (bk + 1.0));
+    }
+    for (int l = l0; l <= L; ++l) acc[l] = fma(tc[l][k], M, acc[l]);
   }
   for (int l = l0; l <= L; ++l) out[l] += fct[l] * acc[l];
   if (nfma) *nfma += n;
@@ -295,10 +365,11 @@ F12_DEV inline int family_quad(const Tables &T, const FamDev &F, double xi, doub
 
 // Contribution of one family to hat g_l, l = 0..L, added into out[] with the
 // common factor 4 xi (2 xi)^l applied.  Returns nonzero if a series did not
-// converge within KMAX terms.  NEGB: a family with b < 0, whose non-peak
-// orders go to family_quad (kept out of the b >= 0 instantiation, which the
-// main evaluation kernel uses, so that its register budget is unchanged).
-template <bool NEGB = false>
+// converge within KMAX terms.  QUAD: a family with b < 0 or alpha0 < -1
+// (FamDev::quad), whose non-peak orders go to family_quad (kept out of the
+// other instantiation, which the main evaluation kernel uses, so that its
+// register budget is unchanged).
+template <bool QUAD = false>
 F12_DEV inline int family_eval(const Tables &T, const FamDev &F, double xi, double D, int L, double *out,
                                unsigned long long *fma_count = nullptr) {
   int bad = 0;
@@ -308,7 +379,7 @@ F12_DEV inline int family_eval(const Tables &T, const FamDev &F, double xi, doub
   const double z = beta * beta / (4.0 * gam);
   // orders l < ls use the quadrature about the peak, l >= ls the series
   int ls = 0;
-  if (!NEGB || beta > 0.0)       // b < 0 and beta <= 0: no peak inside (0, inf)
+  if (!QUAD || beta > 0.0)       // beta <= 0 (b < 0): no peak inside (0, inf)
     while (ls <= L && z >= threshold_z(ls)) ++ls;
   double fct[LAUX + 1];
   fct[0] = 4.0 * xi;
@@ -328,7 +399,19 @@ F12_DEV inline int family_eval(const Tables &T, const FamDev &F, double xi, doub
       if (x <= 0.0) continue;
       jhat_all(twoxd * x, ls - 1, jh);
       double xa;
-      if (F.pow_kind == 1) {          // alpha0 = integer n0
+      if constexpr (QUAD) {           // any power, alpha0 >= -KSING
+        if (F.pow_kind == 0) {
+          xa = pow(x, F.alpha0);
+        } else {
+          xa = F.pow_kind == 2 ? sqrt(x) : 1.0;
+          if (F.pow_int >= 0) {
+            for (int k = 0; k < F.pow_int; ++k) xa *= x;
+          } else {
+            const double ix = 1.0 / x;
+            for (int k = 0; k < -F.pow_int; ++k) xa *= ix;
+          }
+        }
+      } else if (F.pow_kind == 1) {   // alpha0 = integer n0
         xa = 1.0;
         for (int k = 0; k < F.pow_int; ++k) xa *= x;
         if (F.pow_int < 0) xa = 1.0 / x;  // only alpha0 = -1 occurs
@@ -352,7 +435,7 @@ F12_DEV inline int family_eval(const Tables &T, const FamDev &F, double xi, doub
     for (int l = 0; l < ls; ++l) out[l] += fct[l] * pre * acc[l];
   }
 
-  if constexpr (NEGB) {
+  if constexpr (QUAD) {
     if (ls <= L) bad |= family_quad(T, F, xi, D, ls, L, fct, out, &nfma);
   } else if (ls <= L) {
     const double y = F.b * rsqrt(gam);
@@ -464,7 +547,7 @@ F12_DEV inline int aux_eval(const Tables &T, int kcls, double xi, double D, int 
   const int nf = T.nfam[kcls];
   const FamDev *fams = T.fam + T.fam0[kcls];
   for (int f = 0; f < nf; ++f)
-    bad |= fams[f].b < 0.0 ? family_eval<true>(T, fams[f], xi, D, L, out) : family_eval<false>(T, fams[f], xi, D, L, out);
+    bad |= fams[f].quad ? family_eval<true>(T, fams[f], xi, D, L, out) : family_eval<false>(T, fams[f], xi, D, L, out);
   return bad;
 }
 

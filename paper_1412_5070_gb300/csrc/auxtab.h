@@ -6,6 +6,7 @@
 #pragma once
 
 #include <cmath>
+#include <map>
 #include <vector>
 
 #include "aux.cuh"
@@ -120,18 +121,17 @@ struct ClassTables {
   int nfam[NCLASS] = {};
   int fam0[NCLASS] = {};
   bool supported[NCLASS] = {};
-  bool negb[NCLASS] = {};        // the class has a family with b < 0
+  bool quad[NCLASS] = {};        // the class has a family evaluated by quadrature (FamDev::quad)
 };
 
 // kernels[cls] (cls = 1..6; entry 5 unused) are the kernel term lists.  A class
-// is left out (supported false) when a family needs S(alpha) below
-// alpha = -1 other than the alpha = -1 finite part, when the x^-1 terms of the
-// alpha = -1 families do not cancel (the kernel's integrals diverge at r = 0;
-// the damping of Eq. rs12 always cancels them), when it has more than MAXFAM
-// families, or when a family with b < 0 has a power that is neither an
-// integer nor a half-integer (the quadrature of family_quad handles those two
-// end-point forms only).  Returns false if a family polynomial is longer than
-// JMAX.
+// is left out (supported false) when x^2 k(x) is not integrable at r = 0 (the
+// families' coefficients of some power x^p, p <= -1, do not cancel; the
+// damping of Eq. rs12 always cancels them), when a family's lowest power is
+// below -KSING (= -2), when a family evaluated by quadrature (b < 0 or lowest power
+// below -1) has a power that is neither an integer nor a half-integer (the
+// end-point forms family_quad handles), or when it has more than MAXFAM
+// families.  Returns false if a family polynomial is longer than JMAX.
 inline bool build_class_tables(const f12::TermList kernels[NCLASS], ClassTables &ct) {
   ct.fams.clear();
   ct.coef.clear();
@@ -140,30 +140,42 @@ inline bool build_class_tables(const f12::TermList kernels[NCLASS], ClassTables 
     ct.fam0[cls] = (int)ct.fams.size();
     ct.nfam[cls] = 0;
     ct.supported[cls] = true;
-    ct.negb[cls] = false;
+    ct.quad[cls] = false;
     if (cls == 5) {
       ct.fam0[cls] = ct.fam0[3];
       ct.nfam[cls] = ct.nfam[3];
       ct.supported[5] = ct.supported[3];
-      ct.negb[5] = ct.negb[3];
+      ct.quad[5] = ct.quad[3];
       continue;
     }
     std::vector<f12::Family> fl = f12::families(kernels[cls]);
     std::vector<FamDev> mine;
+    // integrable at r = 0: for every power p <= -1 of x^2 k(x) near 0, the
+    // families' Taylor coefficients of x^alpha0 P(x) e^{bx - gx^2} at x^p
+    // (each family taken as a finite part) must cancel between them
+    std::map<long, std::pair<double, double>> sing;   // 2p -> (sum, sum of |.|)
     for (const f12::Family &fam0 : fl) {
       const double a = fam0.a0 + 2.0;
-      if (a < -1.0 - 1e-9 || (a <= -1.0 && std::fabs(a + 1.0) >= 1e-9)) ct.supported[cls] = false;
-    }
-    if ((int)fl.size() > MAXFAM) ct.supported[cls] = false;
-    // integrable at r = 0: the x^-1 terms of the alpha0 = -1 families (each
-    // taken as a finite part) must cancel between them
-    double fsum = 0.0, fabs_sum = 0.0;
-    for (const f12::Family &fam0 : fl)
-      if (std::fabs(fam0.a0 + 3.0) < 1e-9 && !fam0.poly.empty()) {
-        fsum += fam0.poly[0];
-        fabs_sum += std::fabs(fam0.poly[0]);
+      if (a < -(double)KSING - 1e-9) ct.supported[cls] = false;
+      if (a > -1.0 + 1e-9 || !ct.supported[cls]) continue;
+      const double twice = 2.0 * a;
+      if (std::fabs(twice - std::round(twice)) > 1e-9) {   // a general power below -1
+        ct.supported[cls] = false;
+        continue;
       }
-    if (std::fabs(fsum) > 1e-10 * fabs_sum) ct.supported[cls] = false;
+      double h[KSING + 1] = {1.0, fam0.b};                 // Taylor of e^{bx - gx^2}
+      for (int j = 2; j <= KSING; ++j) h[j] = (fam0.b * h[j - 1] - 2.0 * fam0.g * h[j - 2]) / j;
+      for (int k = 0; a + k <= -1.0 + 1e-9; ++k) {
+        double c = 0.0;
+        for (int i = 0; i <= k && i < (int)fam0.poly.size(); ++i) c += fam0.poly[(size_t)i] * h[k - i];
+        auto &e = sing[std::lround(twice) + 2 * k];
+        e.first += c;
+        e.second += std::fabs(c);
+      }
+    }
+    for (const auto &e : sing)
+      if (std::fabs(e.second.first) > 1e-10 * e.second.second) ct.supported[cls] = false;
+    if ((int)fl.size() > MAXFAM) ct.supported[cls] = false;
     if (!ct.supported[cls]) continue;
     std::vector<double> coef;
     for (const f12::Family &fam0 : fl) {
@@ -173,18 +185,20 @@ inline bool build_class_tables(const f12::TermList kernels[NCLASS], ClassTables 
       d.alpha0 = fam0.a0 + 2.0;   // F_l = x^{2l+2} D_r^l k: lowest power a0 + 2 for every l
       d.fp_minus1 = std::fabs(d.alpha0 + 1.0) < 1e-9 ? 1 : 0;
       if (d.fp_minus1) d.alpha0 = -1.0;
-      for (int j = 0; j < JMAX; ++j) {
+      for (int j = 0; j < JMAX; ++j) {   // Gamma((alpha0+1+j)/2); 0 at the poles
         double arg = 0.5 * (d.alpha0 + 1.0 + j);
-        d.gam_tab[j] = arg > 0.0 ? std::tgamma(arg) : 0.0;
+        const bool pole = arg <= 0.0 && std::fabs(arg - std::round(arg)) < 1e-9;
+        d.gam_tab[j] = pole ? 0.0 : std::tgamma(arg);
       }
       {
         double flo = std::floor(d.alpha0 + 1e-9);
         double fr = d.alpha0 - flo;
         d.pow_int = (int)flo;
         d.pow_kind = (std::fabs(fr) < 1e-9) ? 1 : (std::fabs(fr - 0.5) < 1e-9 ? 2 : 0);
-        if (d.pow_kind == 1 && d.pow_int < -1) d.pow_kind = 0;
       }
-      if (d.b < 0.0 && d.pow_kind == 0) ct.supported[cls] = false;
+      d.nsing = d.alpha0 <= -1.0 + 1e-9 ? (int)std::floor(-d.alpha0 + 1e-9) : 0;
+      d.quad = (d.b < 0.0 || d.alpha0 < -1.0 - 1e-9) ? 1 : 0;
+      if (d.quad && d.pow_kind == 0) ct.supported[cls] = false;
       double as = d.fp_minus1 ? 0.0 : d.alpha0;
       d.rho_start = std::exp(std::lgamma(0.5 * (as + 2.0)) - std::lgamma(0.5 * (as + 1.0)));
       f12::Family cur = fam0;
@@ -201,7 +215,7 @@ inline bool build_class_tables(const f12::TermList kernels[NCLASS], ClassTables 
     ct.fams.insert(ct.fams.end(), mine.begin(), mine.end());
     ct.coef.insert(ct.coef.end(), coef.begin(), coef.end());
     ct.nfam[cls] = (int)mine.size();
-    for (const FamDev &d : mine) ct.negb[cls] = ct.negb[cls] || d.b < 0.0;
+    for (const FamDev &d : mine) ct.quad[cls] = ct.quad[cls] || d.quad;
   }
   return true;
 }

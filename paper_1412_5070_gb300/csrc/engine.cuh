@@ -228,7 +228,7 @@ static int engine_capture(f12int_ctx *ctx, Engine &E) {
       k_items_eval<true><<<std::max(1, E.items_blocks / E.items_div[cls]), BLOCK_AUX, 0, bs>>>(
           ctx->tables, none, QV, cls, 0, 0, E.order[cls],
                                                                E.part[cls], E.status, nullptr);
-      if (ctx->cls_negb[cls])   // families with b < 0 (a decaying factor)
+      if (ctx->cls_quad[cls])   // families evaluated by quadrature (b < 0, alpha0 < -1)
         k_items_eval<true, true><<<E.quad_blocks, BLOCK_AUX, 0, bs>>>(ctx->tables, none, QV, cls, 0, 0,
                                                                        E.order[cls], E.part[cls], E.status, nullptr);
       for (int t = 0; t < kLaunches; ++t) {

@@ -324,10 +324,11 @@ __global__ void k_items_scatter(QuartetView QV, int nf, int64_t pq0, const int *
 }
 
 // Pass 4: one family's contribution to hat g_l (l <= L) per item, into
-// part[item * (LAUX+1) + l], in key order.  The families with b < 0 (a
-// decaying factor) are left to a second launch of the same kernel with
-// NEGB = true (family_quad), made only when the factor has such families.
-template <bool BATCH, bool NEGB>
+// part[item * (LAUX+1) + l], in key order.  The families evaluated by
+// quadrature (b < 0 or a lowest power below -1, FamDev::quad) are left to a
+// second launch of the same kernel with QUAD = true (family_quad), made only
+// when the factor has such families.
+template <bool BATCH, bool QUAD>
 __device__ __forceinline__ unsigned long long items_eval_one(Tables T, PairView PV, QuartetView QV, int cls,
                                                              int64_t pq0, int64_t it, double *part,
                                                              unsigned int *status) {
@@ -336,7 +337,7 @@ __device__ __forceinline__ unsigned long long items_eval_one(Tables T, PairView 
   const int64_t pq = pq0 + it / nf;
   const int f = (int)(it % nf);
   const FamDev &F = T.fam[T.fam0[kcls] + f];
-  if ((F.b < 0.0) != NEGB) return 0;   // the other launch's family
+  if ((F.quad != 0) != QUAD) return 0;   // the other launch's family
   ItemGeom g = item_geometry<BATCH>(PV, QV, cls, pq);
   if (prim_negligible(*g.pv, g.iab, g.icd)) return 0;   // never read by the contraction
   if (g.L > LAUX) {
@@ -346,14 +347,14 @@ __device__ __forceinline__ unsigned long long items_eval_one(Tables T, PairView 
   double out[LAUX + 1];
   for (int l = 0; l <= g.L; ++l) out[l] = 0.0;
   unsigned long long nfma = 0;
-  int bad = family_eval<NEGB>(T, F, g.xi, g.D, g.L, out, &nfma);
+  int bad = family_eval<QUAD>(T, F, g.xi, g.D, g.L, out, &nfma);
   if (bad) atomicOr(status, 1u);
   double *o = part + it * (LAUX + 1);
   for (int l = 0; l <= g.L; ++l) o[l] = out[l];
   return nfma;
 }
 
-template <bool BATCH, bool NEGB = false>
+template <bool BATCH, bool QUAD = false>
 __global__ void k_items_eval(Tables T, PairView PV, QuartetView QV, int cls, int64_t pq0, int64_t nitems,
                              const unsigned int *order, double *part, unsigned int *status,
                              unsigned long long *fma_total) {
@@ -361,10 +362,10 @@ __global__ void k_items_eval(Tables T, PairView PV, QuartetView QV, int cls, int
   if constexpr (BATCH) {
     const int64_t nit = item_count(QV, T.nfam[cls == 5 ? 3 : cls], pq0, nitems);
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nit; t += (int64_t)gridDim.x * blockDim.x)
-      nfma += items_eval_one<BATCH, NEGB>(T, PV, QV, cls, pq0, order[t], part, status);
+      nfma += items_eval_one<BATCH, QUAD>(T, PV, QV, cls, pq0, order[t], part, status);
   } else {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t < nitems) nfma = items_eval_one<BATCH, NEGB>(T, PV, QV, cls, pq0, order[t], part, status);
+    if (t < nitems) nfma = items_eval_one<BATCH, QUAD>(T, PV, QV, cls, pq0, order[t], part, status);
   }
   // warp-aggregated count of the core multiply-adds (series terms and quadrature nodes)
   if (fma_total) {
@@ -784,7 +785,7 @@ struct f12int_ctx {
   std::mutex mu;
   std::recursive_mutex bounds_mu;   // first-time primitive and shell-pair bounds
   bool cls_ok[7] = {false, false, false, false, false, false, false};   // classes the factor supports
-  bool cls_negb[7] = {false, false, false, false, false, false, false};   // classes with b < 0 families
+  bool cls_quad[7] = {false, false, false, false, false, false, false};   // classes with quadrature families
   // growth of each class's kernel with distance (screening estimate):
   // kgrow[cls][i] = G(i * kGrowStep), see screen_estimate
   std::vector<double> kgrow[7];
@@ -1164,7 +1165,7 @@ static int set_factor_lists(f12int_ctx *ctx, const f12::TermList &T1, const f12:
   ctx->tables = T;
   for (int c = 1; c <= 6; ++c) {
     ctx->cls_ok[c] = ct.supported[c];
-    ctx->cls_negb[c] = ct.negb[c];
+    ctx->cls_quad[c] = ct.quad[c];
   }
   for (auto &b : ctx->bases)   // the primitive bounds depend on the factor
     for (int c = 0; c < 7; ++c)
@@ -1486,7 +1487,7 @@ static int launch_chunk(f12int_ctx *ctx, const f12int_ctx::BasisData &B, int cls
     }
     k_items_eval<false><<<nb, BLOCK_AUX, 0, st>>>(ctx->tables, PV, QV, cls, pqa, nitems, ctx->d_order, ctx->d_part,
                                            ctx->d_status, ctx->timing ? ctx->d_fma : nullptr);
-    if (ctx->cls_negb[cls]) {
+    if (ctx->cls_quad[cls]) {
       k_items_eval<false, true><<<nb, BLOCK_AUX, 0, st>>>(ctx->tables, PV, QV, cls, pqa, nitems, ctx->d_order,
                                                           ctx->d_part, ctx->d_status,
                                                           ctx->timing ? ctx->d_fma : nullptr);
@@ -2113,7 +2114,7 @@ extern "C" int f12int_compute_class_static(f12int_ctx *ctx, int basis_id, int cl
       k_items_eval<false><<<nb, BLOCK_AUX, 0, st>>>(ctx->tables, PV, QV, cls, pqa, nitems, d_order, d_part, ctx->d_status,
                                              nullptr);
       ctx->launches += 4;
-      if (ctx->cls_negb[cls]) {
+      if (ctx->cls_quad[cls]) {
         k_items_eval<false, true><<<nb, BLOCK_AUX, 0, st>>>(ctx->tables, PV, QV, cls, pqa, nitems, d_order, d_part,
                                                             ctx->d_status, nullptr);
         ctx->launches++;

@@ -42,10 +42,18 @@ def dev():
     B.build()
 
 
+def lowest_power(f, fp, cls):
+    """Lowest power of x^2 k(x) among the kernel's long-range terms: rho + 2
+    (k3), rho + 1 (k2), rho + rho' + 2 (k4), rho + rho' (k6)."""
+    return {2: f["rho"] + 1, 3: f["rho"] + 2, 5: f["rho"] + 2,
+            4: (f["rho"] if f["c0"] else 0) + (fp["rho"] if fp["c0"] else 0) + 2,
+            6: (f["rho"] - 1 if f["c0"] else 0) + (fp["rho"] - 1 if fp["c0"] else 0) + 2}[cls]
+
+
 def supported(f, fp, cls):
-    """The auxiliary stage evaluates S(alpha) for alpha > -1 and the alpha = -1
-    finite part; the lowest power of x^2 k(x) among the kernel's long-range
-    terms is rho + 2 (k3), rho + 1 (k2), rho + rho' + 2 (k4), rho + rho' (k6)."""
+    """The auxiliary stage takes every family with a lowest power down to -2
+    as a finite part (below -1 only integer and half-integer powers); the
+    lowest power of x^2 k(x) is lowest_power()."""
     if f["c0"] == 0 and fp["c0"] == 0:
         return True
     # a term group with b < 0 must have an integer or half-integer power
@@ -60,10 +68,10 @@ def supported(f, fp, cls):
             groups.append((f["B"] + fp["B"], f["rho"] + fp["rho"]))
     if any(b < 0 and abs(2 * a - round(2 * a)) > 1e-9 for b, a in groups):
         return False
-    low = {2: f["rho"] + 1, 3: f["rho"] + 2, 5: f["rho"] + 2,
-           4: (f["rho"] if f["c0"] else 0) + (fp["rho"] if fp["c0"] else 0) + 2,
-           6: (f["rho"] - 1 if f["c0"] else 0) + (fp["rho"] - 1 if fp["c0"] else 0) + 2}[cls]
-    return low > -1 or low == -1
+    low = lowest_power(f, fp, cls)
+    if low < -1 and abs(2 * low - round(2 * low)) > 1e-9:
+        return False
+    return low >= -2
 
 
 @pytest.mark.parametrize("name", list(SETS))
@@ -102,8 +110,15 @@ def test_factor_sets_two_centre(dev, name, cls):
     finally:
         F.f12int_destroy(ctx)
     ref, _, mag = O.shell_blocks(O.factor_kernel(f, fp), cls, basis, q, with_mag=True)
-    bad = close(got, ref, mag)
     assert not np.isnan(got).any()
+    if (f["c0"] or fpp["c0"]) and lowest_power(f, fpp, cls) < -1:
+        # families below x^-1, each a finite part: the FP64 cancellation
+        # between them allows 1e-8 here (xi <= 2.7 on this basis)
+        big = np.abs(ref) > 1e-12
+        assert np.all(np.abs(got[big] - ref[big]) <= 1e-8 * np.abs(ref[big]))
+        assert np.all(np.abs(got[~big] - ref[~big]) <= 1e-12)
+        return
+    bad = close(got, ref, mag)
     assert not bad.any(), report(got, ref, mag, bad)
 
 
