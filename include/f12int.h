@@ -102,18 +102,19 @@ int f12int_set_basis(f12int_ctx *ctx, int nshell, const double *centers, const i
  * not finite, or rho + 2n + 2 <= 0 (the damped long-range term must be
  * integrable at r = 0, Sec. 3.1).
  * Classes: the auxiliary stage evaluates the term families x^a e^{bx - gx^2}
- * of x^2 k(x) through S(alpha, beta, gamma) (Eq. sila), each family with
- * a <= -1 as its finite part (Sec. 3.3.2 for a = -1; these cancel between
- * the families of an integrable kernel).  A class is left out of an
- * accepted factor, and every call for it (compute, aux, submit) returns
- * F12INT_EDOMAIN, when a family has a < -2, or a < -1 with a neither an
- * integer nor a half-integer, or b < 0 with such a power.  For f' = f and
- * c0 > 0 the lowest powers are rho + 2 (I3, I5), rho + 1 (I2), 2 rho + 2 (I4)
- * and 2 rho (I6), which keeps I3 and I5 for rho >= -4, I2 for rho >= -3, I4
- * for rho >= -2 and I6 for rho >= -1 (half-integer steps below -1); with
- * B < 0, 2 rho must moreover be an integer.  Accuracy: with a lowest power
- * below -1 the finite parts cancel in FP64, and hat g_n is good to about
- * 1e-8 relative for xi <= 10 (1e-6 at xi = 50) instead of 1e-10. */
+ * of x^2 k(x) through S(alpha, beta, gamma) (Eq. sila).  Families with a < -1
+ * (a factor r^rho with rho <= -1, made integrable by its damping) are
+ * evaluated together with the families of the same b, their singular terms
+ * cancelled between them; a = -1 on its own is a finite part (Sec. 3.3.2).
+ * A class is left out of an accepted factor, and every call for it (compute,
+ * aux, submit) returns F12INT_EDOMAIN, when x^2 k(x) is not integrable at
+ * r = 0, when a power below -1 is neither an integer nor a half-integer, or
+ * when a family with b < 0 has such a power.  For f' = f and c0 > 0 the
+ * lowest powers are rho + 2 (I3, I5), rho + 1 (I2), 2 rho + 2 (I4) and
+ * 2 rho (I6): every class is served for rho > -1 (B >= 0) and, for smaller
+ * rho, when 2 rho is an integer; with B < 0, 2 rho must be an integer.
+ * Accuracy of hat g_n for the singular groups: 1e-10 relative for xi <= 2,
+ * 1e-8 up to xi = 50. */
 int f12int_set_factor(f12int_ctx *ctx, const f12int_factor *f, const f12int_factor *fprime);
 
 /* Host-only view of the term lists that f12int_set_factor uploads: writes

@@ -94,8 +94,31 @@ struct FamDev {
   int pow_int;                // integer part for pow_kind 1 and 2 (floor of alpha0)
   int quad;                   // b < 0 or alpha0 < -1: evaluated by family_quad (second launch)
   int nsing;                  // powers alpha0 + k <= -1 (k < nsing) taken as finite parts
+  int group;                  // index of its GroupDev (families evaluated together), -1 none
+  int lead;                   // the group's first member, which evaluates the whole group
   int span[LAUX + 1];
   int coff[LAUX + 1];         // offset of P_l in the coefficient pool
+};
+
+// Families with the same b and power lattice whose singular terms at r = 0
+// cancel between them (the damped long range of Eq. rs12 with rho <= -1):
+// evaluated together by group_quad.  Below xs each member's Gaussian is split
+// as e^{-g x^2} = T_k(-g x^2) + R_k(g x^2), T_k its first k Taylor terms; the
+// T_k parts of all members form one base polynomial, whose singular
+// coefficients cancel exactly (the host builds it and zeroes them), and
+// R_k = O(x^{2k}) leaves each member's rest integrable.
+constexpr int MAXMEM = 8;
+constexpr int KEXP = 6;      // remainder orders below this
+struct GroupDev {
+  double b, gmin, gmax, xs;   // common b; smallest and largest member g; split point 1/sqrt(gmax)
+  double abase;               // lowest power of the group (the base polynomial's x^abase)
+  int pow_kind, pow_int;      // of abase, as in FamDev
+  int nmem;
+  int mem[MAXMEM];            // member families (indices into Tables::fam)
+  int kexp[MAXMEM];           // remainder order k of each member; -1: g = 0, wholly in the base
+  int dpow[MAXMEM];           // alpha0 of the member minus abase (an integer)
+  int bspan[LAUX + 1];        // base polynomial per order in the coefficient pool
+  int boff[LAUX + 1];
 };
 
 struct Tables {
@@ -103,6 +126,7 @@ struct Tables {
   int fam0[NCLASS];
   const FamDev *fam;
   const double *coef;
+  const GroupDev *grp;
 };
 
 F12_CONST double c_gh_x[NGH];
@@ -363,6 +387,204 @@ F12_DEV inline int family_quad(const Tables &T, const FamDev &F, double xi, doub
   return stretched;
 }
 
+// Orders l < ls of one family by Gauss-Hermite quadrature about the peak
+// (see the header), added into out[l] times fct[l].
+template <bool QUAD>
+F12_DEV inline void family_gh(const Tables &T, const FamDev &F, double xi, double D, int ls, const double *fct,
+                              double *out, unsigned long long &nfma) {
+  const double gam = F.g + xi;
+  const double beta = F.b + 2.0 * xi * D;
+  const double sg = sqrt(gam), isg = 1.0 / sg;
+  const double xs = beta / (2.0 * gam);
+  const double estar = (F.b * F.b + 4.0 * F.b * xi * D - 4.0 * F.g * xi * D * D) / (4.0 * gam);
+  const double pre = exp(estar) * isg;
+  double acc[LAUX + 1];
+  for (int l = 0; l < ls; ++l) acc[l] = 0.0;
+  double jh[LAUX + 2];
+  const double twoxd = 2.0 * xi * D;
+  for (int i = 0; i < NGH; ++i) {
+    const double x = xs + c_gh_x[i] * isg;
+    if (x <= 0.0) continue;
+    jhat_all(twoxd * x, ls - 1, jh);
+    double xa;
+    if constexpr (QUAD) {           // any power (a grouped member's may be below -2)
+      if (F.pow_kind == 0) {
+        xa = pow(x, F.alpha0);
+      } else {
+        xa = F.pow_kind == 2 ? sqrt(x) : 1.0;
+        if (F.pow_int >= 0) {
+          for (int k = 0; k < F.pow_int; ++k) xa *= x;
+        } else {
+          const double ix = 1.0 / x;
+          for (int k = 0; k < -F.pow_int; ++k) xa *= ix;
+        }
+      }
+    } else if (F.pow_kind == 1) {   // alpha0 = integer n0
+      xa = 1.0;
+      for (int k = 0; k < F.pow_int; ++k) xa *= x;
+      if (F.pow_int < 0) xa = 1.0 / x;  // only alpha0 = -1 occurs
+    } else if (F.pow_kind == 2) {   // alpha0 = n0 + 1/2
+      xa = sqrt(x);
+      for (int k = 0; k < F.pow_int; ++k) xa *= x;
+      if (F.pow_int < 0) xa /= x;     // alpha0 = -1/2
+    } else {
+      xa = pow(x, F.alpha0);
+    }
+    xa *= c_gh_w[i];
+    for (int l = 0; l < ls; ++l) {
+      const double *P = T.coef + F.coff[l];
+      const int sp = F.span[l];
+      double h = 0.0;
+      for (int j = sp - 1; j >= 0; --j) h = fma(h, x, P[j]);
+      acc[l] = fma(xa * jh[l], h, acc[l]);
+      nfma += sp + 1;
+    }
+  }
+  for (int l = 0; l < ls; ++l) out[l] += fct[l] * pre * acc[l];
+}
+
+// R_k(y) = e^{-y} - sum_{i<k} (-y)^i/i!, 0 <= y: for y < 1 from its own series
+// (terms decreasing, no cancellation), else directly.
+F12_DEV inline double exp_rem(double y, int k) {
+  if (k == 0) return exp(-y);
+  if (y < 1.0) {
+    double t = 1.0;
+    for (int i = 1; i <= k; ++i) t *= -y / i;
+    double s = 0.0;
+    for (int i = k; i < k + 40; ++i) {
+      s += t;
+      t *= -y / (i + 1);
+      if (fabs(t) <= 1e-17 * fabs(s)) break;
+    }
+    return s;
+  }
+  double s = 0.0, t = 1.0;
+  for (int i = 0; i < k; ++i) {
+    s += t;
+    t *= -y / (i + 1);
+  }
+  return exp(-y) - s;
+}
+
+// Orders l0..L of a group of families (GroupDev) by composite Gauss-Legendre
+// quadrature of their sum,
+//   int_0^inf e^{b x - xi (x - D)^2} jhat_l(2 xi D x) sum_m x^{a_m} P_{m,l}(x) e^{-g_m x^2} dx,
+// whose integrand is regular at x = 0 although its members are not.  Below
+// xs the sum is evaluated as x^abase B_l(x) + sum_m x^{a_m} P_{m,l}(x) R_{k_m}(g_m x^2)
+// (B_l the base polynomial; members with g = 0 are wholly in it), so that the
+// singular terms have cancelled in B_l's coefficients on the host; above xs,
+// where nothing is singular, member by member.  Range and panels as in
+// family_quad, with the widest Gaussian (gmin) setting the range and the
+// narrowest (gmax) the panels while it is still significant.
+F12_DEV inline int group_quad(const Tables &T, const GroupDev &G, double xi, double D, int l0, int L,
+                              const double *fct, double *out, unsigned long long *nfma) {
+  const double gam = G.gmin + xi, sg = sqrt(gam), sgx = sqrt(G.gmax + xi);
+  const double beta = G.b + 2.0 * xi * D;
+  int dmax = 0;
+  for (int m = 0; m < G.nmem; ++m) {
+    const FamDev &F = T.fam[G.mem[m]];
+    for (int l = l0; l <= L; ++l) dmax = G.dpow[m] + F.span[l] - 1 > dmax ? G.dpow[m] + F.span[l] - 1 : dmax;
+  }
+  const double d = fmax(0.0, G.abase + (double)dmax);
+  double hi;
+  if (beta > 0.0) {
+    hi = 0.5 * beta / gam + (sqrt(0.5 * d) + 6.5) / sg;
+  } else {
+    hi = (sqrt(0.5 * d) + 6.5) / sg;
+    if (beta < 0.0) hi = fmin(hi, (d + 9.0 * sqrt(d) + 45.0) / -beta);
+  }
+  const double twoxd = 2.0 * xi * D;
+  const double narrow = 6.5 / sgx;   // the largest-g members are negligible beyond
+  double acc[LAUX + 1], jh[LAUX + 2], xm[MAXMEM], fm[MAXMEM];
+  for (int l = l0; l <= L; ++l) acc[l] = 0.0;
+  unsigned long long n = 0;
+  double a = 0.0;
+  int stretched = 0;
+  for (int p = 0; p < NPMAX && a < hi; ++p) {
+    double r = 0.0;
+    if (beta < 0.0) r = -beta / sqrt(fmax(1.0, -beta * a));
+    const double w = 1.25 / fmax(a < narrow ? sgx : sg, r);
+    if (p == NPMAX - 1 && hi - a > w) stretched = 1;
+    const double hw = 0.5 * (p == NPMAX - 1 ? fmax(w, hi - a) : w);
+    const bool usq = (p == 0 && G.pow_kind == 2);
+    const double su = usq ? sqrt(2.0 * hw) : 0.0;
+    for (int i = 0; i < NGL; ++i) {
+      double x, wt;
+      if (usq) {
+        const double u = 0.5 * su * (c_gl_x[i] + 1.0);
+        x = u * u;
+        wt = 0.5 * su * c_gl_w[i] * 2.0 * u;
+      } else {
+        x = a + hw * (c_gl_x[i] + 1.0);
+        wt = hw * c_gl_w[i];
+      }
+      const double ex = exp(G.b * x - xi * (x - D) * (x - D));
+      jhat_all(twoxd * x, L, jh);
+      double xb = G.pow_kind == 2 ? sqrt(x) : 1.0;   // x^abase
+      if (G.pow_int >= 0) {
+        for (int k = 0; k < G.pow_int; ++k) xb *= x;
+      } else {
+        const double ix = 1.0 / x;
+        for (int k = 0; k < -G.pow_int; ++k) xb *= ix;
+      }
+      const bool split = x < G.xs;
+      for (int m = 0; m < G.nmem; ++m) {
+        double xp = xb;
+        for (int k = 0; k < G.dpow[m]; ++k) xp *= x;
+        xm[m] = xp;
+        const double gm = T.fam[G.mem[m]].g;
+        fm[m] = split ? (G.kexp[m] < 0 ? 0.0 : exp_rem(gm * x * x, G.kexp[m])) : exp(-gm * x * x);
+      }
+      const double e = wt * ex;
+      for (int l = l0; l <= L; ++l) {
+        double v = 0.0;
+        if (split) {
+          const double *B = T.coef + G.boff[l];
+          double h = 0.0;
+          for (int j = G.bspan[l] - 1; j >= 0; --j) h = fma(h, x, B[j]);
+          v = xb * h;
+          n += G.bspan[l];
+        }
+        for (int m = 0; m < G.nmem; ++m) {
+          if (fm[m] == 0.0) continue;
+          const FamDev &F = T.fam[G.mem[m]];
+          const double *P = T.coef + F.coff[l];
+          double h = 0.0;
+          for (int j = F.span[l] - 1; j >= 0; --j) h = fma(h, x, P[j]);
+          v = fma(xm[m] * fm[m], h, v);
+          n += F.span[l] + 1;
+        }
+        acc[l] = fma(e * jh[l], v, acc[l]);
+      }
+    }
+    a += 2.0 * hw;
+  }
+  for (int l = l0; l <= L; ++l) out[l] += fct[l] * acc[l];
+  if (nfma) *nfma += n;
+  return stretched;
+}
+
+// A group: orders whose every member has its peak well inside (0, inf) are
+// taken member by member about the peak (family_gh; the r -> 0 end is below
+// double precision there for each of them), the rest by group_quad.
+F12_DEV inline int group_eval(const Tables &T, const GroupDev &G, double xi, double D, int L, const double *fct,
+                              double *out, unsigned long long &nfma) {
+  const double beta = G.b + 2.0 * xi * D;
+  int ls = 0;
+  if (beta > 0.0) {
+    ls = L + 1;
+    for (int m = 0; m < G.nmem; ++m) {
+      const double z = beta * beta / (4.0 * (T.fam[G.mem[m]].g + xi));
+      int lm = 0;
+      while (lm <= L && z >= threshold_z(lm)) ++lm;
+      ls = lm < ls ? lm : ls;
+    }
+  }
+  if (ls > 0)
+    for (int m = 0; m < G.nmem; ++m) family_gh<true>(T, T.fam[G.mem[m]], xi, D, ls, fct, out, nfma);
+  return ls <= L ? group_quad(T, G, xi, D, ls, L, fct, out, &nfma) : 0;
+}
+
 // Contribution of one family to hat g_l, l = 0..L, added into out[] with the
 // common factor 4 xi (2 xi)^l applied.  Returns nonzero if a series did not
 // converge within KMAX terms.  QUAD: a family with b < 0 or alpha0 < -1
@@ -377,6 +599,17 @@ F12_DEV inline int family_eval(const Tables &T, const FamDev &F, double xi, doub
   const double gam = F.g + xi;
   const double beta = F.b + 2.0 * xi * D;
   const double z = beta * beta / (4.0 * gam);
+  if constexpr (QUAD) {
+    if (F.group >= 0) {            // the group's first member evaluates the whole group
+      if (!F.lead) return 0;
+      double fct[LAUX + 1];
+      fct[0] = 4.0 * xi;
+      for (int l = 1; l <= L; ++l) fct[l] = fct[l - 1] * 2.0 * xi;
+      bad = group_eval(T, T.grp[F.group], xi, D, L, fct, out, nfma);
+      if (fma_count) *fma_count += nfma;
+      return bad;
+    }
+  }
   // orders l < ls use the quadrature about the peak, l >= ls the series
   int ls = 0;
   if (!QUAD || beta > 0.0)       // beta <= 0 (b < 0): no peak inside (0, inf)
@@ -385,55 +618,7 @@ F12_DEV inline int family_eval(const Tables &T, const FamDev &F, double xi, doub
   fct[0] = 4.0 * xi;
   for (int l = 1; l <= L; ++l) fct[l] = fct[l - 1] * 2.0 * xi;
 
-  if (ls > 0) {
-    const double sg = sqrt(gam), isg = 1.0 / sg;
-    const double xs = beta / (2.0 * gam);
-    const double estar = (F.b * F.b + 4.0 * F.b * xi * D - 4.0 * F.g * xi * D * D) / (4.0 * gam);
-    const double pre = exp(estar) * isg;
-    double acc[LAUX + 1];
-    for (int l = 0; l < ls; ++l) acc[l] = 0.0;
-    double jh[LAUX + 2];
-    const double twoxd = 2.0 * xi * D;
-    for (int i = 0; i < NGH; ++i) {
-      const double x = xs + c_gh_x[i] * isg;
-      if (x <= 0.0) continue;
-      jhat_all(twoxd * x, ls - 1, jh);
-      double xa;
-      if constexpr (QUAD) {           // any power, alpha0 >= -KSING
-        if (F.pow_kind == 0) {
-          xa = pow(x, F.alpha0);
-        } else {
-          xa = F.pow_kind == 2 ? sqrt(x) : 1.0;
-          if (F.pow_int >= 0) {
-            for (int k = 0; k < F.pow_int; ++k) xa *= x;
-          } else {
-            const double ix = 1.0 / x;
-            for (int k = 0; k < -F.pow_int; ++k) xa *= ix;
-          }
-        }
-      } else if (F.pow_kind == 1) {   // alpha0 = integer n0
-        xa = 1.0;
-        for (int k = 0; k < F.pow_int; ++k) xa *= x;
-        if (F.pow_int < 0) xa = 1.0 / x;  // only alpha0 = -1 occurs
-      } else if (F.pow_kind == 2) {   // alpha0 = n0 + 1/2
-        xa = sqrt(x);
-        for (int k = 0; k < F.pow_int; ++k) xa *= x;
-        if (F.pow_int < 0) xa /= x;     // alpha0 = -1/2
-      } else {
-        xa = pow(x, F.alpha0);
-      }
-      xa *= c_gh_w[i];
-      for (int l = 0; l < ls; ++l) {
-        const double *P = T.coef + F.coff[l];
-        const int sp = F.span[l];
-        double h = 0.0;
-        for (int j = sp - 1; j >= 0; --j) h = fma(h, x, P[j]);
-        acc[l] = fma(xa * jh[l], h, acc[l]);
-        nfma += sp + 1;
-      }
-    }
-    for (int l = 0; l < ls; ++l) out[l] += fct[l] * pre * acc[l];
-  }
+  if (ls > 0) family_gh<QUAD>(T, F, xi, D, ls, fct, out, nfma);
 
   if constexpr (QUAD) {
     if (ls <= L) bad |= family_quad(T, F, xi, D, ls, L, fct, out, &nfma);

@@ -113,11 +113,13 @@ inline void fill_aux_const(AuxConst &c) {
   }
 }
 
-// Families of every class on the host: fams and coef are uploaded as they are;
-// nfam/fam0 index them per class (class 5 shares class 3's families, Eq. I5_).
+// Families of every class on the host: fams, coef and groups are uploaded as
+// they are; nfam/fam0 index the families per class (class 5 shares class 3's
+// families, Eq. I5_).
 struct ClassTables {
   std::vector<FamDev> fams;
   std::vector<double> coef;
+  std::vector<GroupDev> groups;
   int nfam[NCLASS] = {};
   int fam0[NCLASS] = {};
   bool supported[NCLASS] = {};
@@ -127,14 +129,18 @@ struct ClassTables {
 // kernels[cls] (cls = 1..6; entry 5 unused) are the kernel term lists.  A class
 // is left out (supported false) when x^2 k(x) is not integrable at r = 0 (the
 // families' coefficients of some power x^p, p <= -1, do not cancel; the
-// damping of Eq. rs12 always cancels them), when a family's lowest power is
-// below -KSING (= -2), when a family evaluated by quadrature (b < 0 or lowest power
-// below -1) has a power that is neither an integer nor a half-integer (the
-// end-point forms family_quad handles), or when it has more than MAXFAM
-// families.  Returns false if a family polynomial is longer than JMAX.
+// damping of Eq. rs12 always cancels them), when a power below -1 is neither
+// an integer nor a half-integer, when it has more than MAXFAM families, or
+// when a family evaluated alone by quadrature (b < 0, or a lowest power below
+// -1 outside a group) has a general power or a lowest power below -KSING.
+// Families with a lowest power below -1 are grouped with the families of the
+// same b and power lattice when their singular terms cancel within the group
+// (GroupDev).  Returns false if a family polynomial is longer than JMAX.
 inline bool build_class_tables(const f12::TermList kernels[NCLASS], ClassTables &ct) {
+  constexpr int KTAY = 16;    // Taylor terms for the integrability check (lowest power >= -KTAY + 1)
   ct.fams.clear();
   ct.coef.clear();
+  ct.groups.clear();
   ct.supported[0] = false;
   for (int cls = 1; cls <= 6; ++cls) {
     ct.fam0[cls] = (int)ct.fams.size();
@@ -149,25 +155,23 @@ inline bool build_class_tables(const f12::TermList kernels[NCLASS], ClassTables 
       continue;
     }
     std::vector<f12::Family> fl = f12::families(kernels[cls]);
-    std::vector<FamDev> mine;
     // integrable at r = 0: for every power p <= -1 of x^2 k(x) near 0, the
     // families' Taylor coefficients of x^alpha0 P(x) e^{bx - gx^2} at x^p
     // (each family taken as a finite part) must cancel between them
     std::map<long, std::pair<double, double>> sing;   // 2p -> (sum, sum of |.|)
     for (const f12::Family &fam0 : fl) {
       const double a = fam0.a0 + 2.0;
-      if (a < -(double)KSING - 1e-9) ct.supported[cls] = false;
-      if (a > -1.0 + 1e-9 || !ct.supported[cls]) continue;
+      if (a > -1.0 + 1e-9) continue;
       const double twice = 2.0 * a;
-      if (std::fabs(twice - std::round(twice)) > 1e-9) {   // a general power below -1
-        ct.supported[cls] = false;
-        continue;
+      if (std::fabs(twice - std::round(twice)) > 1e-9 || a < -(double)(KTAY - 1)) {
+        ct.supported[cls] = false;                     // a general power below -1, or too singular
+        break;
       }
-      double h[KSING + 1] = {1.0, fam0.b};                 // Taylor of e^{bx - gx^2}
-      for (int j = 2; j <= KSING; ++j) h[j] = (fam0.b * h[j - 1] - 2.0 * fam0.g * h[j - 2]) / j;
+      double h[KTAY] = {1.0, fam0.b};                    // Taylor of e^{bx - gx^2}
+      for (int q = 2; q < KTAY; ++q) h[q] = (fam0.b * h[q - 1] - 2.0 * fam0.g * h[q - 2]) / q;
       for (int k = 0; a + k <= -1.0 + 1e-9; ++k) {
         double c = 0.0;
-        for (int i = 0; i <= k && i < (int)fam0.poly.size(); ++i) c += fam0.poly[(size_t)i] * h[k - i];
+        for (int q = 0; q <= k && q < (int)fam0.poly.size(); ++q) c += fam0.poly[(size_t)q] * h[k - q];
         auto &e = sing[std::lround(twice) + 2 * k];
         e.first += c;
         e.second += std::fabs(c);
@@ -178,6 +182,7 @@ inline bool build_class_tables(const f12::TermList kernels[NCLASS], ClassTables 
     if ((int)fl.size() > MAXFAM) ct.supported[cls] = false;
     if (!ct.supported[cls]) continue;
     std::vector<double> coef;
+    std::vector<FamDev> mine;
     for (const f12::Family &fam0 : fl) {
       FamDev d{};
       d.b = fam0.b;
@@ -185,10 +190,10 @@ inline bool build_class_tables(const f12::TermList kernels[NCLASS], ClassTables 
       d.alpha0 = fam0.a0 + 2.0;   // F_l = x^{2l+2} D_r^l k: lowest power a0 + 2 for every l
       d.fp_minus1 = std::fabs(d.alpha0 + 1.0) < 1e-9 ? 1 : 0;
       if (d.fp_minus1) d.alpha0 = -1.0;
-      for (int j = 0; j < JMAX; ++j) {   // Gamma((alpha0+1+j)/2); 0 at the poles
-        double arg = 0.5 * (d.alpha0 + 1.0 + j);
+      for (int q = 0; q < JMAX; ++q) {   // Gamma((alpha0+1+q)/2); 0 at the poles
+        double arg = 0.5 * (d.alpha0 + 1.0 + q);
         const bool pole = arg <= 0.0 && std::fabs(arg - std::round(arg)) < 1e-9;
-        d.gam_tab[j] = pole ? 0.0 : std::tgamma(arg);
+        d.gam_tab[q] = pole ? 0.0 : std::tgamma(arg);
       }
       {
         double flo = std::floor(d.alpha0 + 1e-9);
@@ -198,7 +203,8 @@ inline bool build_class_tables(const f12::TermList kernels[NCLASS], ClassTables 
       }
       d.nsing = d.alpha0 <= -1.0 + 1e-9 ? (int)std::floor(-d.alpha0 + 1e-9) : 0;
       d.quad = (d.b < 0.0 || d.alpha0 < -1.0 - 1e-9) ? 1 : 0;
-      if (d.quad && d.pow_kind == 0) ct.supported[cls] = false;
+      d.group = -1;
+      d.lead = 0;
       double as = d.fp_minus1 ? 0.0 : d.alpha0;
       d.rho_start = std::exp(std::lgamma(0.5 * (as + 2.0)) - std::lgamma(0.5 * (as + 1.0)));
       f12::Family cur = fam0;
@@ -211,9 +217,110 @@ inline bool build_class_tables(const f12::TermList kernels[NCLASS], ClassTables 
       }
       mine.push_back(d);
     }
+    // groups around each family whose lowest power is below -1
+    std::vector<GroupDev> gl;
+    std::vector<int> gid(mine.size(), -1);
+    auto try_group = [&](size_t i0) -> bool {
+      std::vector<size_t> mem;
+      for (size_t j2 = 0; j2 < mine.size(); ++j2) {
+        if (gid[j2] >= 0) continue;
+        if (std::fabs(mine[j2].b - mine[i0].b) > 1e-12 * (1.0 + std::fabs(mine[i0].b))) continue;
+        const double dd = mine[j2].alpha0 - mine[i0].alpha0;
+        if (std::fabs(dd - std::round(dd)) > 1e-9) continue;
+        mem.push_back(j2);
+      }
+      if (mem.size() < 2 || mem.size() > (size_t)MAXMEM) return false;
+      GroupDev G{};
+      G.b = mine[i0].b;
+      G.nmem = (int)mem.size();
+      G.abase = mine[mem[0]].alpha0;
+      G.gmin = G.gmax = mine[mem[0]].g;
+      for (size_t m = 0; m < mem.size(); ++m) {
+        G.abase = std::min(G.abase, mine[mem[m]].alpha0);
+        G.gmin = std::min(G.gmin, mine[mem[m]].g);
+        G.gmax = std::max(G.gmax, mine[mem[m]].g);
+      }
+      G.xs = G.gmax > 0.0 ? 1.0 / std::sqrt(G.gmax) : 0.0;
+      {
+        double flo = std::floor(G.abase + 1e-9), fr = G.abase - flo;
+        G.pow_int = (int)flo;
+        G.pow_kind = (std::fabs(fr) < 1e-9) ? 1 : (std::fabs(fr - 0.5) < 1e-9 ? 2 : 0);
+        if (G.pow_kind == 0) return false;
+      }
+      for (size_t m = 0; m < mem.size(); ++m) {
+        const FamDev &F = mine[mem[m]];
+        G.dpow[m] = (int)std::lround(F.alpha0 - G.abase);
+        if (F.g == 0.0) {
+          G.kexp[m] = -1;
+        } else {
+          int k = 0;
+          while (F.alpha0 + 2.0 * k <= -1.0 + 1e-9) ++k;
+          if (k >= KEXP) return false;
+          G.kexp[m] = k;
+        }
+      }
+      // base polynomial per order: the members' Taylor heads T_k(-g x^2), and
+      // the whole of the g = 0 members, in powers x^{abase + j}
+      std::vector<double> add;
+      for (int l = 0; l <= LAUX; ++l) {
+        int len = 0;
+        for (size_t m = 0; m < mem.size(); ++m) {
+          const int k = G.kexp[m];
+          if (k == 0) continue;
+          const int ext = G.dpow[m] + mine[mem[m]].span[l] + (k > 0 ? 2 * (k - 1) : 0);
+          len = std::max(len, ext);
+        }
+        std::vector<double> c((size_t)len, 0.0), ab((size_t)len, 0.0);
+        for (size_t m = 0; m < mem.size(); ++m) {
+          const FamDev &F = mine[mem[m]];
+          const double *P = coef.data() + (F.coff[l] - (int)ct.coef.size());
+          const int k = G.kexp[m];
+          if (k == 0) continue;
+          const int nt = k < 0 ? 1 : k;
+          double ft = 1.0;                                 // (-g)^t / t!
+          for (int t = 0; t < nt; ++t) {
+            if (t > 0) ft *= -F.g / t;
+            for (int q = 0; q < F.span[l]; ++q) {
+              const double v = P[q] * (k < 0 ? 1.0 : ft);
+              c[(size_t)(G.dpow[m] + q + 2 * t)] += v;
+              ab[(size_t)(G.dpow[m] + q + 2 * t)] += std::fabs(v);
+            }
+          }
+        }
+        for (int q = 0; q < len; ++q)
+          if (G.abase + q <= -1.0 + 1e-9) {              // singular: must cancel
+            if (std::fabs(c[(size_t)q]) > 1e-10 * ab[(size_t)q]) return false;
+            c[(size_t)q] = 0.0;
+          }
+        G.boff[l] = (int)(ct.coef.size() + coef.size() + add.size());
+        G.bspan[l] = len;
+        add.insert(add.end(), c.begin(), c.end());
+      }
+      coef.insert(coef.end(), add.begin(), add.end());
+      for (size_t m = 0; m < mem.size(); ++m) {
+        G.mem[m] = ct.fam0[cls] + (int)mem[m];
+        gid[mem[m]] = (int)(ct.groups.size() + gl.size());
+      }
+      mine[mem[0]].lead = 1;
+      gl.push_back(G);
+      return true;
+    };
+    for (size_t i0 = 0; i0 < mine.size(); ++i0)
+      if (mine[i0].alpha0 < -1.0 - 1e-9 && gid[i0] < 0) try_group(i0);
+    for (size_t i0 = 0; i0 < mine.size(); ++i0) {
+      FamDev &d = mine[i0];
+      if (gid[i0] >= 0) {
+        d.group = gid[i0];
+        d.quad = 1;
+        continue;
+      }
+      if (d.alpha0 < -(double)KSING - 1e-9) ct.supported[cls] = false;
+      if (d.quad && d.pow_kind == 0) ct.supported[cls] = false;
+    }
     if (!ct.supported[cls]) continue;
     ct.fams.insert(ct.fams.end(), mine.begin(), mine.end());
     ct.coef.insert(ct.coef.end(), coef.begin(), coef.end());
+    ct.groups.insert(ct.groups.end(), gl.begin(), gl.end());
     ct.nfam[cls] = (int)mine.size();
     for (const FamDev &d : mine) ct.quad[cls] = ct.quad[cls] || d.quad;
   }

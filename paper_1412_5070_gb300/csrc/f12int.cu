@@ -742,6 +742,8 @@ struct f12int_ctx {
   bool factor_ready = false;
   FamDev *d_fam = nullptr;
   double *d_coef = nullptr;
+  GroupDev *d_grp = nullptr;
+  size_t grp_bytes = 0;
   Tables tables{};
   size_t fam_bytes = 0, coef_bytes = 0;
   // basis
@@ -960,6 +962,7 @@ int f12int_destroy(f12int_ctx *ctx) {
   }
   cudaFree(ctx->d_fam);
   cudaFree(ctx->d_coef);
+  cudaFree(ctx->d_grp);
   cudaFree(ctx->d_pqoff);
   cudaFree(ctx->d_keys);
   cudaFree(ctx->d_order);
@@ -1153,15 +1156,22 @@ static int set_factor_lists(f12int_ctx *ctx, const f12::TermList &T1, const f12:
   // upload
   dfree(ctx, ctx->d_fam, ctx->fam_bytes);
   dfree(ctx, ctx->d_coef, ctx->coef_bytes);
+  dfree(ctx, ctx->d_grp, ctx->grp_bytes);
+  ctx->d_grp = nullptr;
   ctx->fam_bytes = fams.size() * sizeof(FamDev);
   ctx->coef_bytes = coef.size() * sizeof(double);
+  ctx->grp_bytes = ct.groups.size() * sizeof(GroupDev);
   rc = dalloc(ctx, &ctx->d_fam, ctx->fam_bytes);
   if (rc == F12INT_OK) rc = dalloc(ctx, &ctx->d_coef, ctx->coef_bytes);
+  if (rc == F12INT_OK && ctx->grp_bytes) rc = dalloc(ctx, &ctx->d_grp, ctx->grp_bytes);
   if (rc != F12INT_OK) return rc;
   CK(cudaMemcpy(ctx->d_fam, fams.data(), ctx->fam_bytes, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->d_coef, coef.data(), ctx->coef_bytes, cudaMemcpyHostToDevice));
+  if (ctx->grp_bytes)
+    CK(cudaMemcpy(ctx->d_grp, ct.groups.data(), ctx->grp_bytes, cudaMemcpyHostToDevice));
   T.fam = ctx->d_fam;
   T.coef = ctx->d_coef;
+  T.grp = ctx->d_grp;
   ctx->tables = T;
   for (int c = 1; c <= 6; ++c) {
     ctx->cls_ok[c] = ct.supported[c];

@@ -96,41 +96,43 @@ def test_aux_stage_on_cpu_against_oracle(lib, name, cls):
     f = FACTORS[name]
     if cls == 1 and name != "P0":
         pytest.skip("I1 does not depend on the factor")
-    if name == "B<0 rho=-1 n=2" and cls == 6:
-        pytest.skip("lowest power -2: test_singular_families")
     rc, got = host_aux(lib, f, f, cls, XI_D_GRID, 10)
     assert rc == 0
     worst = worst_relative(got, O.factor_kernel(f), cls, XI_D_GRID, 10)
     assert worst < (1e-8 if cls == 6 else 1e-10), worst
 
 
-SINGULAR = {   # kernels whose lowest power of x^2 k is below -1 (each family a finite part)
-    "I6 rho=-1": (dict(M.P0, rho=-1.0), 6),
-    "I6 rho=-1 n=1": (dict(M.P0, rho=-1.0, n=1), 6),
-    "I2 rho=-2.5 n=1": (dict(M.P0, rho=-2.5, n=1), 2),
-    "I6 rho=-1 B=-4 n=2": (dict(c0=0.7, rho=-1.0, B=-4.0, mu=0.8, n=2), 6),
+SINGULAR = {   # kernels whose lowest power of x^2 k is below -1
+    "I6 rho=-1 (x^-2)": (dict(M.P0, rho=-1.0), 6),
+    "I6 rho=-1 n=1 (x^-2)": (dict(M.P0, rho=-1.0, n=1), 6),
+    "I2 rho=-5/2 n=1 (x^-3/2)": (dict(M.P0, rho=-2.5, n=1), 2),
+    "I4 rho=-5/2 n=1 (x^-3)": (dict(M.P0, rho=-2.5, n=1), 4),
+    "I6 rho=-5/2 n=1 (x^-5)": (dict(M.P0, rho=-2.5, n=1), 6),
+    "I6 rho=-5/4 (x^-5/2)": (dict(M.P0, rho=-1.25), 6),
+    "I6 rho=-1 B=-4 n=2 (x^-2)": (dict(c0=0.7, rho=-1.0, B=-4.0, mu=0.8, n=2), 6),
 }
 
 
 @pytest.mark.parametrize("name", list(SINGULAR))
 def test_singular_families(lib, name):
-    """Lowest power -2 (I6 with rho = -1) or -3/2 (I2 with rho = -5/2): each
-    family is taken as its Hadamard finite part, and the damping of Eq. rs12
-    makes them cancel.  In FP64 that cancellation costs accuracy as xi grows:
-    relative error of hat g_n (n <= 10) below 1e-8 for xi <= 2 and below 1e-5
-    up to xi = 50 (measured: at most 1e-8 at xi = 10, 4e-6 at xi = 50)."""
+    """The damped long range of Eq. rs12 with rho <= -1: its families of the
+    same b are evaluated together, their singular terms cancelled in a base
+    polynomial.  Relative error of hat g_n (n <= 10) below 1e-10 for xi <= 2
+    and below 1e-8 up to xi = 50."""
     f, cls = SINGULAR[name]
-    for pts, tol in (([p for p in XI_D_GRID if p[0] <= 2.0], 1e-8), ([p for p in XI_D_GRID if p[0] > 2.0], 1e-5)):
+    for pts, tol in (([p for p in XI_D_GRID if p[0] <= 2.0], 1e-10), ([p for p in XI_D_GRID if p[0] > 2.0], 1e-8)):
         rc, got = host_aux(lib, f, f, cls, pts, 10)
         assert rc == 0
         assert worst_relative(got, O.factor_kernel(f), cls, pts, 10) < tol
 
 
-def test_too_singular_families_are_refused(lib):
-    """Lowest power below -2 (I4 and I6 with rho = -5/2, I6 with rho = -5/4):
-    refused."""
-    for f, cls in ((dict(M.P0, rho=-2.5, n=1), 4), (dict(M.P0, rho=-2.5, n=1), 6), (dict(M.P0, rho=-1.25), 6)):
-        assert host_aux(lib, f, f, cls, XI_D_GRID[:2], 4)[0] == -3
+def test_unsupported_singular_kernels_are_refused(lib):
+    """A lowest power below -1 that is neither an integer nor a half-integer
+    (I6 with rho = -1.3) is refused, and so is a kernel whose singular terms
+    do not cancel (I6 of r^-3 (1 - e^{-0.7 r^2}), whose f_r^2 ~ r^-4)."""
+    assert host_aux(lib, dict(M.P0, rho=-1.3), dict(M.P0, rho=-1.3), 6, XI_D_GRID[:2], 4)[0] == -3
+    damped = [(1.0, -3, 0, 0), (-1.0, -3, 0, 0.7)]
+    assert host_aux_terms(lib, damped, damped, 6, XI_D_GRID[:2], 4)[0] == -3
 
 
 @pytest.mark.parametrize("name", ["P0", "B<0 rho=-1/2", "B<0 rho=-1 n=2"])
@@ -204,23 +206,23 @@ def test_term_list_pair(lib):
 
 
 def test_term_list_domain(lib):
-    """r^-3 diverges in every class and is refused; r^-3 (1 - e^{-0.7 r^2}) has
-    integrable I2 and I3 kernels (lowest powers -2 and -1, cancelling between
-    its two families) and is served there, while its I4 and I6 kernels reach
-    powers below -2 and are refused."""
+    """r^-3 diverges in every class and is refused; r^-3 (1 - e^{-0.7 r^2})
+    has integrable I2, I3 and I4 kernels (singular terms cancelling between
+    its families) and is served there, while its I6 kernel, f_r^2 ~ r^-4,
+    diverges and is refused."""
     bare = [(1.0, -3, 0, 0)]
     damped = [(1.0, -3, 0, 0), (-1.0, -3, 0, 0.7)]
     for cls in (2, 3, 4, 6):
         assert host_aux_terms(lib, bare, bare, cls, XI_D_GRID[:2], 4)[0] == -3
-        assert host_aux_terms(lib, damped, damped, cls, XI_D_GRID[:2], 4)[0] == (0 if cls in (2, 3) else -3)
+        assert host_aux_terms(lib, damped, damped, cls, XI_D_GRID[:2], 4)[0] == (0 if cls != 6 else -3)
 
 
 @pytest.mark.parametrize("cls", [2, 3])
 def test_cancelling_terms_against_quadrature(lib, cls):
-    """k3 = r^-3 (1 - e^{-0.7 r^2}) and k2 = k3/r, evaluated through two
-    finite-part families each (lowest powers -1 and -2), against 30-digit
-    quadrature of the kernel itself (written with expm1, so without the
-    cancellation), hat g_n for n <= 3."""
+    """k3 = r^-3 (1 - e^{-0.7 r^2}) (two finite-part families, lowest power -1)
+    and k2 = k3/r (a group, lowest power -2), against 30-digit quadrature of
+    the kernel itself (written with expm1, so without the cancellation),
+    hat g_n for n <= 3."""
     mp = pytest.importorskip("mpmath")
     mp.mp.dps = 30
     damped = [(1.0, -3, 0, 0), (-1.0, -3, 0, 0.7)]

@@ -51,9 +51,9 @@ def lowest_power(f, fp, cls):
 
 
 def supported(f, fp, cls):
-    """The auxiliary stage takes every family with a lowest power down to -2
-    as a finite part (below -1 only integer and half-integer powers); the
-    lowest power of x^2 k(x) is lowest_power()."""
+    """The auxiliary stage serves a lowest power of x^2 k(x) (lowest_power())
+    below -1 when it is an integer or a half-integer (the damping of Eq. rs12
+    makes the singular terms cancel)."""
     if f["c0"] == 0 and fp["c0"] == 0:
         return True
     # a term group with b < 0 must have an integer or half-integer power
@@ -69,9 +69,7 @@ def supported(f, fp, cls):
     if any(b < 0 and abs(2 * a - round(2 * a)) > 1e-9 for b, a in groups):
         return False
     low = lowest_power(f, fp, cls)
-    if low < -1 and abs(2 * low - round(2 * low)) > 1e-9:
-        return False
-    return low >= -2
+    return not (low < -1 and abs(2 * low - round(2 * low)) > 1e-9)
 
 
 @pytest.mark.parametrize("name", list(SETS))
@@ -112,10 +110,10 @@ def test_factor_sets_two_centre(dev, name, cls):
     ref, _, mag = O.shell_blocks(O.factor_kernel(f, fp), cls, basis, q, with_mag=True)
     assert not np.isnan(got).any()
     if (f["c0"] or fpp["c0"]) and lowest_power(f, fpp, cls) < -1:
-        # families below x^-1, each a finite part: the FP64 cancellation
-        # between them allows 1e-8 here (xi <= 2.7 on this basis)
+        # singular families evaluated as groups: hat g_n to 1e-10 on the CPU
+        # for xi <= 2; 1e-9 here leaves room for the GPU's rounding
         big = np.abs(ref) > 1e-12
-        assert np.all(np.abs(got[big] - ref[big]) <= 1e-8 * np.abs(ref[big]))
+        assert np.all(np.abs(got[big] - ref[big]) <= 1e-9 * np.abs(ref[big]))
         assert np.all(np.abs(got[~big] - ref[~big]) <= 1e-12)
         return
     bad = close(got, ref, mag)
