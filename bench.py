@@ -32,9 +32,10 @@ Two further workloads, each printing its own JSON line:
                       primitive quartets/s of every combination, with the FP64 rate of each
                       kernel from the library's event timing and work counters.
   --workload factors  the 12-atom workload (a seeded sample of 200k screened shell quartets
-                      per class, I2..I6) for four forms of the correlation factor: Eq. rs12
-                      with B = +0.5 and with B = -0.5 (a decaying long range, second
-                      evaluation launch), the Ten-no factor exp(-1.2 r) and a six-Gaussian
+                      per class, I2..I6) for five forms of the correlation factor: Eq. rs12
+                      with B = +0.5, with B = -0.5 (a decaying long range, second
+                      evaluation launch) and with rho = -1 (singular families, evaluated
+                      in groups), the Ten-no factor exp(-1.2 r) and a six-Gaussian
                       geminal (both as term lists): shell quartets/s per class and launches.
   --workload serve    Poisson request streams at 10..2000 requests/s over 12
                       molecules of 2-60 atoms; half the requests ask for one
@@ -728,6 +729,7 @@ def run_per_l(args):
 FACTOR_FORMS = {
     "rs12 B=+0.5": ("rs12", M.P0),
     "rs12 B=-0.5": ("rs12", dict(M.P0, B=-0.5)),
+    "rs12 rho=-1 (singular)": ("rs12", dict(M.P0, rho=-1.0)),
     "Ten-no exp(-1.2 r)": ("terms", [(1.0, 0, -1.2, 0)]),
     "6 Gaussians": ("terms", [(0.5 / (i + 1), 0, 0, 0.2 * 2.5 ** i) for i in range(6)]),
 }
