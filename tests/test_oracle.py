@@ -223,6 +223,48 @@ def test_radial_term_list_factor_closed_form(name, terms, cls, xi, D):
     np.testing.assert_allclose(got, ref, rtol=1e-12, atol=0)
 
 
+def _mp_rs12_kernel(mp, f, cls):
+    """Eq. rs12 pointwise in arbitrary precision, the damping S_n of Eq. ttdamp
+    as the regularized lower incomplete gamma P(n+1, x) (no cancellation at
+    small r), f_r from dS_n/dx = e^{-x} x^n/n!; k2, k3, k4, k6 with f' = f."""
+    c0, rho, B, mu, n = mp.mpf(f["c0"]), mp.mpf(f["rho"]), mp.mpf(f["B"]), mp.mpf(f["mu"]), f["n"]
+
+    def val(r):
+        x = mu * r * r
+        return (1 + r / 2) * mp.exp(-x) + c0 * mp.gammainc(n + 1, 0, x, regularized=True) * r ** rho * mp.exp(B * r)
+
+    def der(r):
+        x = mu * r * r
+        S = mp.gammainc(n + 1, 0, x, regularized=True)
+        dS = mp.exp(-x) * x ** n / mp.factorial(n) * 2 * mu * r
+        pw = r ** rho * mp.exp(B * r)
+        return (mp.mpf(0.5) - 2 * mu * r * (1 + r / 2)) * mp.exp(-x) + c0 * (dS * pw + S * pw * (rho / r + B))
+
+    return {2: lambda r: val(r) / r, 3: val, 4: lambda r: val(r) ** 2, 6: lambda r: der(r) ** 2}[cls]
+
+
+@pytest.mark.parametrize("rho,n,cls,xi,D", [(-1.0, 0, 6, 0.5, 1.2), (-2.5, 1, 2, 3.0, 0.6), (-2.5, 1, 4, 0.5, 1.2)])
+def test_radial_singular_factor_quadrature(rho, n, cls, xi, D):
+    """rho <= -1 in Eq. rs12: the damped kernel is integrable, its terms are
+    not (lowest powers of x^2 k: -2 for I6 with rho = -1, -3/2 and -3 for I2
+    and I4 with rho = -5/2).  The oracle's hat g_n (n <= 2) against 30-digit
+    quadrature of the kernel of Eq. bfinal, D_Q^n by differentiation in D^2."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 30
+    f = dict(P0, rho=rho, n=n)
+    k = _mp_rs12_kernel(mp, f, cls)
+    x = mp.mpf(xi)
+
+    def g0(s):
+        dd = mp.sqrt(s)
+        fn = lambda r: k(r) * r * (mp.exp(-x * (r - dd) ** 2) - mp.exp(-x * (r + dd) ** 2)) / dd
+        return mp.quad(fn, [0, dd / 2, dd, dd + 8 / mp.sqrt(x), mp.inf])
+
+    ref = np.array([float(2 ** m * mp.diff(g0, mp.mpf(D) ** 2, m)) for m in range(3)])
+    got = O.radial(O.factor_kernel(f), cls, xi, D, 2)
+    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=0)
+
+
 def test_jhat_switch_continuity():
     """e^{-z} j_m(z) from the series and from the closed forms meet at the switch."""
     N = 10
