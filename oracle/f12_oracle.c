@@ -17,7 +17,9 @@
  *     transform of I3 applied to the Cartesian functions themselves;
  *     I6 with the commutator reduced to f_r f'_r (Eq. I6_);
  *   - the correlation factor of Eq. rs12 with the Tang-Toennies damping of
- *     Eq. ttdamp, evaluated pointwise;
+ *     Eq. ttdamp, evaluated pointwise, or any factor given as a sum of terms
+ *     c r^a exp(b r - g r^2) (the Ten-no factor, Gaussian geminals), from
+ *     which the six kernels are formed as Eqs. k1-k6 and I6_ define them;
  *   - the Hermite expansion of Eq. AB / Eq. Lambda, with the E coefficients
  *     obtained by direct binomial expansion about P followed by the
  *     monomial -> Hermite-function conversion (not the recursions
