@@ -189,3 +189,38 @@ def test_two_rank_gloo_weak_scaling_split():
         assert p.exitcode == 0
     covered, sizes_ok, mx = q.get(timeout=10)
     assert covered and sizes_ok and mx == 2.5
+
+
+def _random_terms(rng):
+    n = int(rng.integers(1, 5))
+    return [(float(rng.uniform(-1, 1)), float(rng.choice([-1.0, -0.5, 0.0, 0.5, 1.0, 2.0])),
+             float(rng.uniform(-2.0, 1.0)), float(rng.choice([0.0, rng.uniform(0.1, 2.0)]))) for _ in range(n)]
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_random_term_lists_against_the_oracle_kernel(lib, seed):
+    """Seeded random factors of 1-4 terms: the library's term algebra (products,
+    derivatives, families, D_r) against the oracle's pointwise kernels; order 0
+    directly, orders 1 and 2 through finite differences of the oracle."""
+    rng = np.random.default_rng(seed)
+    t, tp = _random_terms(rng), _random_terms(rng)
+    K = O.factor_kernel_terms(t, tp)
+    for cls in (2, 3, 4, 6):
+        for x in (0.35, 1.1, 2.4):
+            got = F.f12int_kernel_radial_terms(cls, t, 0, x, terms_prime=tp)
+            ref = x * x * O.kernel_value(K, cls, x)
+            assert abs(got - ref) <= 1e-12 * abs(ref) + 1e-14, (cls, x)
+            k = lambda r: O.kernel_value(K, cls, r)
+            h = 1e-3 * x
+
+            def d1(fun, r):
+                return (fun(r - 2 * h) - 8 * fun(r - h) + 8 * fun(r + h) - fun(r + 2 * h)) / (12 * h)
+
+            dr1 = lambda r: d1(k, r) / r
+            v1 = x ** 4 * dr1(x)
+            v2 = x ** 6 * d1(dr1, x) / x
+            g1 = F.f12int_kernel_radial_terms(cls, t, 1, x, terms_prime=tp)
+            g2 = F.f12int_kernel_radial_terms(cls, t, 2, x, terms_prime=tp)
+            scale = max(abs(ref), abs(v1), abs(v2), 1e-3)
+            assert abs(g1 - v1) <= 1e-8 * scale, (cls, x, g1, v1)
+            assert abs(g2 - v2) <= 1e-6 * scale, (cls, x, g2, v2)
