@@ -257,3 +257,32 @@ def test_gpu_factor_sets_domain_matches_library(lib):
     for name, t in tg.TERM_SETS.items():
         for cls in (2, 3, 4, 5, 6):
             assert host_aux_terms(lib, t, t, cls, XI_D_GRID[:1], 2)[0] == 0, (name, cls)
+
+
+def _random_regular_terms(rng):
+    n = int(rng.integers(1, 4))
+    return [(float(rng.uniform(0.2, 1.0) * rng.choice([-1, 1])), float(rng.choice([0.0, 0.5, 1.0, 2.0])),
+             float(rng.uniform(-2.0, 1.0)), float(rng.choice([0.0, rng.uniform(0.1, 2.0)]))) for _ in range(n)]
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_random_term_lists_on_cpu_against_oracle(lib, seed):
+    """Seeded random factors of 1-3 terms (powers 0..2, b of either sign, with
+    and without a Gaussian) through every branch of the stage: hat g_n (n <= 10)
+    against the oracle, relative to |g_n| plus 1e-2 of the point's natural scale
+    (2 xi)^n max_m |g_m|/(2 xi)^m, for random coefficients can make one g_n
+    small by cancellation."""
+    rng = np.random.default_rng(seed)
+    t = _random_regular_terms(rng)
+    pts = XI_D_GRID[::2]
+    K = O.factor_kernel_terms(t)
+    for cls in (2, 3, 4, 6):
+        rc, got = host_aux_terms(lib, t, t, cls, pts, 10)
+        assert rc == 0
+        with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+            refs = list(ex.map(lambda p: O.radial(K, cls, p[0], p[1], 10), pts))
+        for i, (x, d) in enumerate(pts):
+            sc = (2.0 * x) ** np.arange(11)
+            nat = np.max(np.abs(refs[i]) / sc) * sc
+            err = np.abs(got[i] - refs[i]) / (np.abs(refs[i]) + 1e-2 * nat)
+            assert err.max() < 1e-9, (cls, x, d, float(err.max()))
