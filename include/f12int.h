@@ -135,7 +135,11 @@ int f12int_kernel_radial(int cls, const f12int_factor *f, const f12int_factor *f
  * when a value is not finite or some g < 0.
  * Classes: the rules of f12int_set_factor, and one more that the damping of
  * Eq. rs12 guarantees there: a class whose x^2 k(x) has a net x^-1 term at
- * r -> 0 (a kernel like r^-3, whose integrals diverge) is left out. */
+ * r -> 0 (a kernel like r^-3, whose integrals diverge) is left out.  A
+ * kernel holds at most 24 term families (distinct (b, g) and power
+ * lattice): a Gaussian geminal of six terms fits every class (I4 and I6 have
+ * one family per pair g_i + g_j), one of seven only I1-I3 and I5.  A family
+ * polynomial longer than 48 terms makes the call return F12INT_EDOMAIN. */
 int f12int_set_factor_terms(f12int_ctx *ctx, const f12int_term *f, int nf, const f12int_term *fprime, int nfp);
 
 /* Host-only view of f12int_kernel_radial for factors given as terms (the

@@ -286,3 +286,17 @@ def test_random_term_lists_on_cpu_against_oracle(lib, seed):
             nat = np.max(np.abs(refs[i]) / sc) * sc
             err = np.abs(got[i] - refs[i]) / (np.abs(refs[i]) + 1e-2 * nat)
             assert err.max() < 1e-9, (cls, x, d, float(err.max()))
+
+
+def test_family_limits(lib):
+    """At most MAXFAM = 24 families per kernel: a six-Gaussian geminal fits
+    every class, a seven-Gaussian one only I2 and I3 (I4 and I6 have a family
+    per pair sum of exponents); a family polynomial longer than 48 terms
+    refuses the whole factor."""
+    six = [(0.5 / (i + 1), 0, 0, 0.2 * 2.5 ** i) for i in range(6)]
+    seven = [(0.5 / (i + 1), 0, 0, 0.2 * 2.5 ** i) for i in range(7)]
+    for cls in (2, 3, 4, 6):
+        assert host_aux_terms(lib, six, six, cls, XI_D_GRID[:1], 2)[0] == 0
+        assert host_aux_terms(lib, seven, seven, cls, XI_D_GRID[:1], 2)[0] == (0 if cls in (2, 3) else -3)
+    long_poly = [(1.0 / (j + 1), float(j), 0.0, 1.0) for j in range(0, 60, 2)]
+    assert host_aux_terms(lib, long_poly, long_poly, 3, XI_D_GRID[:1], 2)[0] == -3
