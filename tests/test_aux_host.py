@@ -160,11 +160,12 @@ def test_negative_B_with_a_general_power_is_refused(lib):
     assert rc == 0
 
 
-def test_factor_pair_with_negative_B(lib):
-    """f' != f with B < 0 in one and B > 0 in the other: the product families
-    of I4 and I6 have b of either sign."""
-    f = dict(c0=0.5, rho=-0.5, B=-0.8, mu=1.0, n=0)
-    fp = dict(c0=0.3, rho=0.5, B=0.4, mu=0.7, n=0)
+@pytest.mark.parametrize("pair", [(dict(c0=0.5, rho=-0.5, B=-0.8, mu=1.0, n=0), dict(c0=0.3, rho=0.5, B=0.4, mu=0.7, n=0)),
+                                  (M.P0, dict(c0=0.3, rho=0.5, B=-1.2, mu=0.7, n=0))])
+def test_factor_pair_with_negative_B(lib, pair):
+    """f' != f with B < 0 in one and B > 0 in the other (either way round):
+    the product families of I4 and I6 have b of either sign."""
+    f, fp = pair
     for cls in (4, 6):
         rc, got = host_aux(lib, f, fp, cls, XI_D_GRID[1::3], 8)
         assert rc == 0
