@@ -91,3 +91,28 @@ def test_library_finite_parts_against_paper_omega(lib, y1, y2):  # noqa: F811
     assert rc == 0
     ref = paper_value(y1, y2)
     assert abs(got[0, 0] - ref) <= 1e-12 * abs(ref)
+
+
+# The worked example of Sec. 3.3: the finite part of S(-2, beta, 0), beta < 0,
+# is -beta [gamma_E + log(-beta) - 1].  For sum_i c_i x^-2 e^{b_i x} with
+# sum c_i = sum c_i b_i = 0 (the integral is then proper) the constants cancel:
+#   int_0^inf x^-2 sum_i c_i e^{b_i x} dx = -sum_i c_i b_i log(-b_i).
+EXAMPLES = [([(1.0, -1.0), (-2.0, -2.0), (1.0, -3.0)], 3 * np.log(3) - 4 * np.log(2)),
+            ([(2.0, -1.0), (-3.0, -2.0), (1.0, -4.0)], 2 * np.log(2))]
+
+
+@pytest.mark.parametrize("terms,value", EXAMPLES)
+def test_library_x2_finite_parts_against_paper_example(lib, terms, value):  # noqa: F811
+    """k3 = r^-4 sum_i c_i e^{b_i r}: three families of lowest power -2 with
+    different b, each taken as its own finite part (two subtracted Taylor
+    terms).  hat g_0 / (4 xi) at D = 0 tends to the integral above as xi -> 0;
+    the library's values at xi = 1e-6 and 2e-6, extrapolated to xi = 0 (the
+    xi-dependence is smooth), match the paper's example to 1e-10."""
+    assert abs(sum(c for c, _ in terms)) < 1e-15 and abs(sum(c * b for c, b in terms)) < 1e-15
+    t = [(c, -4.0, b, 0.0) for c, b in terms]
+    vals = []
+    for xi in (1e-6, 2e-6):
+        rc, got = host_aux_terms(lib, t, t, 3, [(xi, 0.0)], 0)
+        assert rc == 0
+        vals.append(got[0, 0] / (4.0 * xi))
+    assert abs(2.0 * vals[0] - vals[1] - value) <= 1e-10 * abs(value)
