@@ -747,3 +747,23 @@ def test_prim_block_through_hobson():
                     out.append(s)
     ref = O.prim_block(K, 3, ls, ex, cen).ravel()
     np.testing.assert_allclose(np.array(out), ref, rtol=1e-11, atol=1e-13 * np.max(np.abs(ref)))
+
+
+def _rs12_as_terms(f):
+    """Eq. rs12 with Eq. ttdamp expanded: (1 + r/2) e^{-mu r^2} + c0 r^rho e^{Br}
+    - c0 sum_{k<=n} mu^k/k! r^{rho+2k} e^{Br - mu r^2}."""
+    t = [(1.0, 0.0, 0.0, f["mu"]), (0.5, 1.0, 0.0, f["mu"]), (f["c0"], f["rho"], f["B"], 0.0)]
+    for k in range(f["n"] + 1):
+        t.append((-f["c0"] * f["mu"] ** k / math.factorial(k), f["rho"] + 2 * k, f["B"], f["mu"]))
+    return t
+
+
+@pytest.mark.parametrize("f", [P0, dict(P0, B=-0.8), dict(P0, rho=0.0, n=1)])
+@pytest.mark.parametrize("cls", [2, 3, 4, 6])
+def test_term_list_mode_matches_rs12_mode(f, cls):
+    """The oracle's two factor modes (Eq. rs12 pointwise with its damping, and
+    the same factor as a term list) agree where the expanded terms do not
+    cancel badly near r = 0 (n = 0, or rho >= 0)."""
+    a = O.radial(O.factor_kernel(f), cls, 0.7, 1.3, 8)
+    b = O.radial(O.factor_kernel_terms(_rs12_as_terms(f)), cls, 0.7, 1.3, 8)
+    np.testing.assert_allclose(b, a, rtol=1e-12, atol=0)
