@@ -305,8 +305,12 @@ inline bool build_class_tables(const f12::TermList kernels[NCLASS], ClassTables 
       gl.push_back(G);
       return true;
     };
+    // (the alpha0 = -1 families with b >= 0 stay in the series with their
+    // closed-form finite part; those with b < 0 are in the quadrature launch
+    // anyway, where a group is the more accurate form)
     for (size_t i0 = 0; i0 < mine.size(); ++i0)
-      if (mine[i0].alpha0 < -1.0 - 1e-9 && gid[i0] < 0) try_group(i0);
+      if ((mine[i0].alpha0 < -1.0 - 1e-9 || (mine[i0].alpha0 < -1.0 + 1e-9 && mine[i0].b < 0.0)) && gid[i0] < 0)
+        try_group(i0);
     for (size_t i0 = 0; i0 < mine.size(); ++i0) {
       FamDev &d = mine[i0];
       if (gid[i0] >= 0) {
