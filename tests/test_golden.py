@@ -19,6 +19,7 @@ with C cancelled: a value built from the paper's printed numbers alone.  The
 oracle integrates the kernel pointwise; the library takes each term as a
 finite part (b < 0, lowest power -1).  Both are checked against it.
 """
+import math
 import os
 
 import numpy as np
@@ -116,3 +117,44 @@ def test_library_x2_finite_parts_against_paper_example(lib, terms, value):  # no
         assert rc == 0
         vals.append(got[0, 0] / (4.0 * xi))
     assert abs(2.0 * vals[0] - vals[1] - value) <= 1e-10 * abs(value)
+
+
+def omega_small_x(k, x, terms=120):
+    """omega_k(x) from the small-x expansion of App. D, term-by-term integration
+    of e^{-x z}, with the factor 1/4 that int z^k log z e^{-z^2} dz =
+    Gamma((k+1)/2) psi((k+1)/2) / 4 carries (reading: the printed expansions
+    lack it and are 4 omega_k)."""
+    from scipy import special
+    s = 0.0
+    for j in range(terms):
+        a = (j + 1) / 2.0 if k == 0 else j / 2.0 + 1.0
+        s += (-x) ** j / math.factorial(j) * special.gamma(a) * special.digamma(a)
+    return 0.25 * s
+
+
+@pytest.mark.parametrize("y1,y2", [(0.5, 1.5), (1.0, 2.5), (0.3, 3.0)])
+def test_series_finite_parts_against_paper_omega_expansion(lib, y1, y2):  # noqa: F811
+    """b > 0: k = r^-3 (e^{y1 r} - e^{y2 r}); its two alpha = -1 families go
+    through the library's series route (the closed series for S(-1), b >= 0).
+    By parts, FP int z^-1 e^{y z - z^2} dz = -y omega_0(-y) + 2 omega_1(-y) + C,
+    with omega_k at negative argument from App. D's small-x expansion.  The
+    library and the oracle match it to 1e-12."""
+    ref = 4.0 * ((-y1 * omega_small_x(0, -y1) + 2 * omega_small_x(1, -y1))
+                 - (-y2 * omega_small_x(0, -y2) + 2 * omega_small_x(1, -y2)))
+    t = [(1.0, -3.0, y1, 0.0), (-1.0, -3.0, y2, 0.0)]
+    rc, got = host_aux_terms(lib, t, t, 3, [(1.0, 0.0)], 0)
+    assert rc == 0
+    assert abs(got[0, 0] - ref) <= 1e-12 * abs(ref)
+    orc = O.radial(O.factor_kernel_terms(t), 3, 1.0, 0.0, 0)[0]
+    assert abs(orc - ref) <= 1e-12 * abs(ref)
+
+
+@pytest.mark.parametrize("x", [0.5, 2.0, -1.0])
+def test_small_x_expansion_reading(x):
+    """Reading of App. D's small-x expansions: with the factor 1/4 they give
+    omega_k (30-digit quadrature of its definition)."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 30
+    for k in (0, 1):
+        ref = float(mp.quad(lambda z: z ** k * mp.log(z) * mp.exp(-mp.mpf(x) * z - z * z), [0, 1, mp.inf]))
+        assert abs(omega_small_x(k, x) - ref) <= 1e-12 * abs(ref)
