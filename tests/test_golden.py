@@ -158,3 +158,20 @@ def test_small_x_expansion_reading(x):
     for k in (0, 1):
         ref = float(mp.quad(lambda z: z ** k * mp.log(z) * mp.exp(-mp.mpf(x) * z - z * z), [0, 1, mp.inf]))
         assert abs(omega_small_x(k, x) - ref) <= 1e-12 * abs(ref)
+
+
+@pytest.mark.parametrize("x", [0.1, 0.5, 3.0, 7.0])   # x = 2 is where the two arguments coincide
+def test_T0_closed_form_reading(x):
+    """Reading of Eq. t0 (not used by the library, which never forms T_s):
+    T_0^{+-}(x) = int_0^inf e^{+-t - x t^2} dt = sqrt(pi/(4x)) e^{1/(4x)}
+    [1 +- erf(1/(2 sqrt x))] by completing the square, against quadrature;
+    the printed argument 1/(sqrt(2) x) does not reproduce it."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 30
+    xx = mp.mpf(x)
+    for sgn in (1, -1):
+        ref = mp.quad(lambda t: mp.exp(sgn * t - xx * t * t), [0, 1, mp.inf])
+        derived = mp.sqrt(mp.pi / (4 * xx)) * mp.exp(1 / (4 * xx)) * (1 + sgn * mp.erf(1 / (2 * mp.sqrt(xx))))
+        printed = mp.sqrt(mp.pi / (4 * xx)) * mp.exp(1 / (4 * xx)) * (1 + sgn * mp.erf(1 / (mp.sqrt(2) * xx)))
+        assert abs(derived - ref) <= mp.mpf(10) ** -25 * abs(ref)
+        assert abs(printed - ref) > 1e-3 * abs(ref)
