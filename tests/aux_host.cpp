@@ -90,4 +90,34 @@ int aux_host_eval_terms(const double *t, int nt, const double *tp, int ntp, int 
   return eval(kt, cls, n, xi, D, nmax, out);
 }
 
+// Single device functions of the stage, for unit tests.
+void aux_host_jhat(double z, int N, double *out) {
+  load_constants();
+  double jh[LAUX + 2];
+  jhat_all(z, N, jh);
+  for (int m = 0; m <= N; ++m) out[m] = jh[m];
+}
+
+double aux_host_kummer(double a, int ib, double z, int *bad) {
+  load_constants();
+  *bad = 0;
+  return kummer_m(a, ib, z, bad);
+}
+
+double aux_host_s_minus1(double b, double gam, int *bad) {
+  load_constants();
+  *bad = 0;
+  return s_minus1(b, gam, bad);
+}
+
+double aux_host_exp_rem(double y, int k) { return exp_rem(y, k); }
+
+void aux_host_gauss_legendre(double *x, double *w) {
+  load_constants();
+  for (int i = 0; i < NGL; ++i) {
+    x[i] = c_gl_x[i];
+    w[i] = c_gl_w[i];
+  }
+}
+
 }  // extern "C"

@@ -53,6 +53,15 @@ def lib():
     L.aux_host_eval_terms.argtypes = [dp, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int64, dp, dp,
                                       ctypes.c_int, dp]
     L.aux_host_eval_terms.restype = ctypes.c_int
+    ip = ctypes.POINTER(ctypes.c_int)
+    L.aux_host_jhat.argtypes = [ctypes.c_double, ctypes.c_int, dp]
+    L.aux_host_kummer.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.c_double, ip]
+    L.aux_host_kummer.restype = ctypes.c_double
+    L.aux_host_s_minus1.argtypes = [ctypes.c_double, ctypes.c_double, ip]
+    L.aux_host_s_minus1.restype = ctypes.c_double
+    L.aux_host_exp_rem.argtypes = [ctypes.c_double, ctypes.c_int]
+    L.aux_host_exp_rem.restype = ctypes.c_double
+    L.aux_host_gauss_legendre.argtypes = [dp, dp]
     return L
 
 
@@ -301,3 +310,72 @@ def test_family_limits(lib):
         assert host_aux_terms(lib, seven, seven, cls, XI_D_GRID[:1], 2)[0] == (0 if cls in (2, 3) else -3)
     long_poly = [(1.0 / (j + 1), float(j), 0.0, 1.0) for j in range(0, 60, 2)]
     assert host_aux_terms(lib, long_poly, long_poly, 3, XI_D_GRID[:1], 2)[0] == -3
+
+
+
+# ---------------------------------------------------------------- single device functions --
+
+@pytest.mark.parametrize("z", [0.0, 1e-3, 0.7, 5.0, 31.9, 45.0, 200.0])
+def test_jhat_against_definition(lib, z):
+    """e^{-z} j_m(z), j_m = (z^-1 d/dz)^m (sinh z / z), m <= 14: the series /
+    closed-form switch of jhat_all against 40-digit arithmetic of the
+    definition (differentiation of sinh z / z in z^2/2)."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    out = np.zeros(15)
+    lib.aux_host_jhat(z, 14, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    for m in range(15):
+        # j_m(z) = sum_k 2^m (k+m)!/(k! (2k+2m+1)!) z^{2k}
+        zz = mp.mpf(z)
+        ref = mp.nsum(lambda k: 2 ** m * mp.factorial(k + m) / (mp.factorial(k) * mp.factorial(2 * k + 2 * m + 1))
+                      * zz ** (2 * k), [0, mp.inf]) * mp.exp(-zz)
+        assert abs(out[m] - ref) <= 1e-13 * abs(ref), (m, out[m], ref)
+
+
+@pytest.mark.parametrize("a,ib,z", [(0.25, 0, 0.0), (0.75, 1, 0.3), (1.5, 0, 4.0), (0.25, 1, 20.0), (3.0, 0, 36.0)])
+def test_kummer_m_against_mpmath(lib, a, ib, z):
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 30
+    bad = ctypes.c_int(0)
+    got = lib.aux_host_kummer(a, ib, z, ctypes.byref(bad))
+    ref = mp.hyp1f1(a, 0.5 if ib == 0 else 1.5, z)
+    assert bad.value == 0 and abs(got - ref) <= 1e-14 * abs(ref)
+
+
+@pytest.mark.parametrize("b,gam", [(0.0, 1.0), (0.5, 0.3), (1.0, 2.5), (2.0, 0.05), (1.0, 0.01)])
+def test_s_minus1_against_finite_part_quadrature(lib, b, gam):
+    """The closed series for S(-1, b, gamma), b >= 0, against its definition
+    in the drop-log(eps) convention: int_0^inf (e^{bx} - 1) e^{-gamma x^2} / x dx
+    + (-gamma_E - log gamma)/2."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 30
+    bad = ctypes.c_int(0)
+    got = lib.aux_host_s_minus1(b, gam, ctypes.byref(bad))
+    bb, gg = mp.mpf(b), mp.mpf(gam)
+    ref = mp.quad(lambda x: mp.expm1(bb * x) * mp.exp(-gg * x * x) / x, [0, 1, mp.inf]) - (mp.euler + mp.log(gg)) / 2
+    assert bad.value == 0 and abs(got - ref) <= 1e-13 * max(abs(ref), 1.0)
+
+
+@pytest.mark.parametrize("k", [0, 1, 2, 3, 5])
+def test_exp_rem_against_mpmath(lib, k):
+    """R_k(y) = e^{-y} - sum_{i<k} (-y)^i / i! on both sides of its series /
+    direct switch at y = 1."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    for y in (0.0, 1e-8, 0.2, 0.999, 1.0, 3.0):
+        yy = mp.mpf(y)
+        # the remainder's own series: no cancellation even where it is ~y^k
+        ref = mp.nsum(lambda i: (-yy) ** int(i) / mp.factorial(int(i)), [k, mp.inf]) if y > 0 else (1 if k == 0 else 0)
+        got = lib.aux_host_exp_rem(y, k)
+        assert abs(got - ref) <= 1e-14 * abs(ref) + (0 if ref != 0 else 1e-300), (k, y, got, ref)
+
+
+def test_gauss_legendre_nodes(lib):
+    """The 16-point rule integrates x^j exactly for j <= 31 on [-1, 1]."""
+    dp = ctypes.POINTER(ctypes.c_double)
+    x, w = np.zeros(16), np.zeros(16)
+    lib.aux_host_gauss_legendre(x.ctypes.data_as(dp), w.ctypes.data_as(dp))
+    assert np.all(np.diff(x) > 0) and abs(w.sum() - 2.0) < 1e-14
+    for j in range(32):
+        exact = 0.0 if j % 2 else 2.0 / (j + 1)
+        assert abs(np.dot(w, x ** j) - exact) < 1e-14
