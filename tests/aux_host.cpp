@@ -112,6 +112,14 @@ double aux_host_s_minus1(double b, double gam, int *bad) {
 
 double aux_host_exp_rem(double y, int k) { return exp_rem(y, k); }
 
+// Jh_alpha(y) = [int_0^inf t^alpha e^{y t - t^2} dt] / Gamma((alpha+1)/2), y >= 0
+double aux_host_jhat_start(double alpha, double y, int *bad) {
+  load_constants();
+  *bad = 0;
+  const double rho = std::exp(std::lgamma(0.5 * (alpha + 2.0)) - std::lgamma(0.5 * (alpha + 1.0)));
+  return jhat_start(alpha, rho, y, bad);
+}
+
 void aux_host_gauss_legendre(double *x, double *w) {
   load_constants();
   for (int i = 0; i < NGL; ++i) {

@@ -62,6 +62,8 @@ def lib():
     L.aux_host_exp_rem.argtypes = [ctypes.c_double, ctypes.c_int]
     L.aux_host_exp_rem.restype = ctypes.c_double
     L.aux_host_gauss_legendre.argtypes = [dp, dp]
+    L.aux_host_jhat_start.argtypes = [ctypes.c_double, ctypes.c_double, ip]
+    L.aux_host_jhat_start.restype = ctypes.c_double
     return L
 
 
@@ -379,3 +381,18 @@ def test_gauss_legendre_nodes(lib):
     for j in range(32):
         exact = 0.0 if j % 2 else 2.0 / (j + 1)
         assert abs(np.dot(w, x ** j) - exact) < 1e-14
+
+
+
+@pytest.mark.parametrize("alpha", [-0.5, 0.0, 0.5, 1.5, 3.0])
+@pytest.mark.parametrize("y", [0.0, 0.4, 2.0, 6.0, 11.5])
+def test_jhat_start_against_definition(lib, alpha, y):
+    """Start values of the S recursion (Kummer form, Eq. msmallz for beta >= 0):
+    J_alpha(y) / Gamma((alpha+1)/2) against 30-digit quadrature."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 30
+    bad = ctypes.c_int(0)
+    got = lib.aux_host_jhat_start(alpha, y, ctypes.byref(bad))
+    a, yy = mp.mpf(alpha), mp.mpf(y)
+    ref = mp.quad(lambda t: t ** a * mp.exp(yy * t - t * t), [0, 1, yy / 2 + 1, mp.inf]) / mp.gamma((a + 1) / 2)
+    assert bad.value == 0 and abs(got - ref) <= 1e-14 * abs(ref), (got, ref)
