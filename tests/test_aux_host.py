@@ -396,3 +396,29 @@ def test_jhat_start_against_definition(lib, alpha, y):
     a, yy = mp.mpf(alpha), mp.mpf(y)
     ref = mp.quad(lambda t: t ** a * mp.exp(yy * t - t * t), [0, 1, yy / 2 + 1, mp.inf]) / mp.gamma((a + 1) / 2)
     assert bad.value == 0 and abs(got - ref) <= 1e-14 * abs(ref), (got, ref)
+
+
+@pytest.mark.parametrize("name", ["P0", "B<0 rho=-1/2", "B<0 rho=0 n=1"])
+def test_random_points_wide_range(lib, name):
+    """60 seeded random (xi, D) with xi log-uniform in [0.01, 2000] and D in
+    [0, 30] (a tenth at D = 0), orders <= 12, against the oracle relative to
+    |g_n| plus 1e-3 of the point's natural scale; I6 with B > 0 is limited by
+    its finite-part families at xi ~ 1000 (7e-9 there)."""
+    f = FACTORS[name]
+    rng = np.random.default_rng(123)
+    n = 60
+    xi = np.exp(rng.uniform(np.log(0.01), np.log(2000.0), n))
+    D = rng.uniform(0.0, 30.0, n) * rng.choice([0.0, 1.0], n, p=[0.1, 0.9])
+    pts = list(zip(xi, D))
+    K = O.factor_kernel(f)
+    for cls in (2, 3, 4, 6):
+        rc, got = host_aux(lib, f, f, cls, pts, 12)
+        assert rc == 0
+        with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+            refs = list(ex.map(lambda p: O.radial(K, cls, p[0], p[1], 12), pts))
+        tol = 2e-8 if cls == 6 else 1e-9
+        for i, (x, d) in enumerate(pts):
+            sc = (2.0 * x) ** np.arange(13)
+            nat = np.max(np.abs(refs[i]) / sc) * sc
+            err = np.abs(got[i] - refs[i]) / (np.abs(refs[i]) + 1e-3 * nat)
+            assert err.max() < tol, (cls, x, d, float(err.max()))
