@@ -142,6 +142,15 @@ int f12int_kernel_radial(int cls, const f12int_factor *f, const f12int_factor *f
  * polynomial longer than 48 terms makes the call return F12INT_EDOMAIN. */
 int f12int_set_factor_terms(f12int_ctx *ctx, const f12int_term *f, int nf, const f12int_term *fprime, int nfp);
 
+/* Host-only: which classes a factor pair serves, without a GPU or context.
+ * flags[c] for c = 1..6 (flags[0] unused) receives 0 when class c would be
+ * left out (its calls return F12INT_EDOMAIN), 1 when it is served by the
+ * series and peak quadrature alone, 3 when some of its families also need
+ * the quadrature launch (b < 0, or singular families).  fprime = NULL means
+ * f' = f.  Errors as for f12int_set_factor / f12int_set_factor_terms. */
+int f12int_factor_classes(const f12int_factor *f, const f12int_factor *fprime, int *flags);
+int f12int_factor_classes_terms(const f12int_term *f, int nf, const f12int_term *fprime, int nfp, int *flags);
+
 /* Host-only view of f12int_kernel_radial for factors given as terms (the
  * arguments of f12int_set_factor_terms).  Needs no GPU. */
 int f12int_kernel_radial_terms(int cls, const f12int_term *f, int nf, const f12int_term *fprime, int nfp, int l,

@@ -1061,6 +1061,40 @@ int f12int_kernel_radial(int cls, const f12int_factor *f, const f12int_factor *f
   return F12INT_OK;
 }
 
+}  // extern "C"
+
+static int factor_class_flags(const f12::TermList &T1, const f12::TermList &T2, int *flags) {
+  f12::TermList kt[NCLASS];
+  for (int cls = 1; cls <= 6; ++cls)
+    if (cls != 5) kt[cls] = f12::kernel_terms(cls, T1, T2);
+  ClassTables ct;
+  if (!build_class_tables(kt, ct)) return F12INT_EDOMAIN;
+  flags[0] = 0;
+  for (int c = 1; c <= 6; ++c) flags[c] = ct.supported[c] ? (ct.quad[c] ? 3 : 1) : 0;
+  return F12INT_OK;
+}
+
+extern "C" {
+
+int f12int_factor_classes(const f12int_factor *f, const f12int_factor *fprime, int *flags) {
+  if (!f || !flags) return F12INT_EINVAL;
+  const f12int_factor &fp = fprime ? *fprime : *f;
+  int rc = check_factor(*f);
+  if (rc == F12INT_OK) rc = check_factor(fp);
+  if (rc != F12INT_OK) return rc;
+  f12::Factor F1{f->c0, f->rho, f->B, f->mu, f->n}, F2{fp.c0, fp.rho, fp.B, fp.mu, fp.n};
+  return factor_class_flags(f12::factor_terms(F1), f12::factor_terms(F2), flags);
+}
+
+int f12int_factor_classes_terms(const f12int_term *f, int nf, const f12int_term *fprime, int nfp, int *flags) {
+  if (!flags) return F12INT_EINVAL;
+  f12::TermList T1, T2;
+  int rc = check_terms(f, nf, T1);
+  if (rc == F12INT_OK) rc = fprime ? check_terms(fprime, nfp, T2) : (T2 = T1, F12INT_OK);
+  if (rc != F12INT_OK) return rc;
+  return factor_class_flags(T1, T2, flags);
+}
+
 int f12int_kernel_radial_terms(int cls, const f12int_term *f, int nf, const f12int_term *fprime, int nfp, int l,
                                double x, double *value) {
   if (!value || cls < 1 || cls > 6 || l < 0 || l > LAUX || !(x > 0.0)) return F12INT_EINVAL;

@@ -23,7 +23,7 @@ STATUS = {0: "F12INT_OK", -1: "F12INT_EINVAL", -2: "F12INT_ENOMEM", -3: "F12INT_
 
 # every entry point declared in include/f12int.h
 EXPORTS = ("f12int_create", "f12int_destroy", "f12int_set_basis", "f12int_set_factor", "f12int_set_factor_terms",
-           "f12int_kernel_radial_terms", "f12int_screen",
+           "f12int_kernel_radial_terms", "f12int_factor_classes", "f12int_factor_classes_terms", "f12int_screen",
            "f12int_compute_class", "f12int_compute_class_mixed", "f12int_compute_class_static", "f12int_aux", "f12int_launch_count",
            "f12int_device_status", "f12int_set_timing", "f12int_kernel_stats", "f12int_kernel_radial",
            "f12int_submit", "f12int_poll", "f12int_batch_limits", "f12int_batch_autotune", "f12int_batch_stats",
@@ -88,6 +88,9 @@ def load():
     L.f12int_set_factor_terms.argtypes = [_vp, ctypes.POINTER(Term), ctypes.c_int, ctypes.POINTER(Term), ctypes.c_int]
     L.f12int_kernel_radial_terms.argtypes = [ctypes.c_int, ctypes.POINTER(Term), ctypes.c_int, ctypes.POINTER(Term),
                                              ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp]
+    L.f12int_factor_classes.argtypes = [ctypes.POINTER(Factor), ctypes.POINTER(Factor), _ip]
+    L.f12int_factor_classes_terms.argtypes = [ctypes.POINTER(Term), ctypes.c_int, ctypes.POINTER(Term), ctypes.c_int,
+                                              _ip]
     L.f12int_screen.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                 ctypes.POINTER(ctypes.c_int32), ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
     L.f12int_compute_class.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int64, _vp, _vp, _vp]
@@ -246,6 +249,30 @@ def f12int_kernel_radial(cls: int, f, l: int, x: float, fprime=None) -> float:
     _check(load().f12int_kernel_radial(int(cls), ctypes.byref(F), ctypes.byref(Fp) if Fp is not None else None,
                                        int(l), float(x), ctypes.byref(v)), "f12int_kernel_radial")
     return v.value
+
+
+def f12int_factor_classes(f, fprime=None) -> dict:
+    """{class: 0 left out / 1 served / 3 served, with the quadrature launch}
+    for an Eq. rs12 factor pair (no GPU needed)."""
+    F = Factor.of(f)
+    Fp = Factor.of(fprime) if fprime is not None else None
+    flags = (ctypes.c_int * 7)()
+    _check(load().f12int_factor_classes(ctypes.byref(F), ctypes.byref(Fp) if Fp is not None else None, flags),
+           "f12int_factor_classes")
+    return {c: flags[c] for c in range(1, 7)}
+
+
+def f12int_factor_classes_terms(terms, terms_prime=None) -> dict:
+    """f12int_factor_classes for factors given as terms."""
+    t, n = _terms(terms)
+    flags = (ctypes.c_int * 7)()
+    if terms_prime is None:
+        rc = load().f12int_factor_classes_terms(t, n, None, 0, flags)
+    else:
+        tp, npr = _terms(terms_prime)
+        rc = load().f12int_factor_classes_terms(t, n, tp, npr, flags)
+    _check(rc, "f12int_factor_classes_terms")
+    return {c: flags[c] for c in range(1, 7)}
 
 
 def f12int_kernel_radial_terms(cls: int, terms, l: int, x: float, terms_prime=None) -> float:

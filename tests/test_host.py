@@ -224,3 +224,31 @@ def test_random_term_lists_against_the_oracle_kernel(lib, seed):
             scale = max(abs(ref), abs(v1), abs(v2), 1e-3)
             assert abs(g1 - v1) <= 1e-8 * scale, (cls, x, g1, v1)
             assert abs(g2 - v2) <= 1e-6 * scale, (cls, x, g2, v2)
+
+
+def test_factor_classes_query(lib):
+    """The host-only class query: P0 is served everywhere without the
+    quadrature launch; B < 0 needs it in the F12 classes; rho = -5/2 needs it
+    for its singular classes I2, I4, I6; rho = -1.3 leaves I6 out (a general
+    power below -1); r^-3 leaves every F12 class out; seven Gaussians overflow
+    the family table in I4 and I6."""
+    assert F.f12int_factor_classes(M.P0) == {c: 1 for c in range(1, 7)}
+    assert F.f12int_factor_classes(dict(M.P0, B=-0.8)) == {1: 1, 2: 3, 3: 3, 4: 3, 5: 3, 6: 3}
+    assert F.f12int_factor_classes(dict(M.P0, rho=-2.5, n=1)) == {1: 1, 2: 3, 3: 1, 4: 3, 5: 1, 6: 3}
+    assert F.f12int_factor_classes(dict(M.P0, rho=-1.3))[6] == 0
+    assert F.f12int_factor_classes_terms([(1.0, -3, 0, 0)]) == {1: 1, 2: 0, 3: 0, 4: 0, 5: 0, 6: 0}
+    seven = [(0.5 / (i + 1), 0, 0, 0.2 * 2.5 ** i) for i in range(7)]
+    assert F.f12int_factor_classes_terms(seven) == {1: 1, 2: 1, 3: 1, 4: 0, 5: 1, 6: 0}
+    with pytest.raises(F.F12IntError):
+        F.f12int_factor_classes(dict(M.P0, mu=0.0))
+
+
+def test_factor_classes_query_matches_gpu_test_rule(lib):
+    """The GPU factor tests decide from their own rule which classes each
+    parameter set leaves out; the library's query must agree."""
+    tg = pytest.importorskip("test_gpu_factors")
+    for name, (f, fp) in tg.SETS.items():
+        flags = F.f12int_factor_classes(f, fp)
+        fpp = fp if fp is not None else f
+        for cls in (2, 3, 4, 5, 6):
+            assert (flags[cls] != 0) == tg.supported(f, fpp, cls), (name, cls)
