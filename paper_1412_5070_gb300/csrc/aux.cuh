@@ -41,8 +41,10 @@
 // is below -1 (a singular factor whose damping makes only the kernel as a
 // whole integrable; the T_s functions of Sec. 3.3.1 for integer alpha): the
 // non-peak orders of both are instead integrated directly by composite
-// Gauss-Legendre quadrature of the same integral, each family as its
-// Hadamard finite part (family_quad).
+// Gauss-Legendre quadrature of the same integral: singular families together
+// with the families of the same b whose singular terms they cancel
+// (group_quad), the others each as its Hadamard finite part (family_quad).
+// Both run only in a second launch of the evaluation kernel (QUAD).
 //
 // The header also compiles as plain C++ (without nvcc) so that a CPU test can
 // evaluate this stage against the oracle; the library itself only runs it on
