@@ -57,7 +57,9 @@
 #define F12_CONST __constant__
 #define F12_GLOBAL __device__
 #else
+#include <algorithm>
 #include <cmath>
+#include <cstring>
 #define F12_DEV
 #define F12_CONST
 #define F12_GLOBAL
@@ -67,6 +69,8 @@ namespace f12dev {
 
 #ifndef __CUDACC__
 inline double rsqrt(double x) { return 1.0 / std::sqrt(x); }
+using std::max;
+using std::min;
 using std::exp;
 using std::fabs;
 using std::fma;
@@ -80,11 +84,18 @@ constexpr int JMAX = 48;     // longest family polynomial
 constexpr int WIN = 64;      // circular window over the S sequence (> JMAX + 2)
 constexpr int KMAX = 1500;   // series length cap
 constexpr int NGH = 16;      // Gauss-Hermite nodes
+constexpr int NGHF = 10;     // the shorter Gauss-Hermite rule, far from r = 0 (stored after the first)
 constexpr int KTAB = 320;    // tabulated series coefficient ratios
 constexpr int MAXFAM = 24;   // families per kernel
 constexpr int NCLASS = 7;    // index by class 1..6
 constexpr int NGL = 16;      // Gauss-Legendre nodes per panel (b < 0 families)
 constexpr int NPMAX = 40;    // panels at most (the rule of family_quad needs about 30)
+// Start values of the series: per family a table of J_{as+k}(y_i)/k!, k < JT_NK,
+// on the grid y_i = i JT_DY, i < JT_NY (y = b/sqrt(gamma) <= 20 in the series
+// region), evaluated by Taylor steps from the nearest point
+constexpr int JT_NK = 17;
+constexpr int JT_NY = 321;
+constexpr double JT_DY = 1.0 / 16.0;
 
 struct FamDev {
   double b, g;
@@ -98,6 +109,8 @@ struct FamDev {
   int nsing;                  // powers alpha0 + k <= -1 (k < nsing) taken as finite parts
   int group;                  // index of its GroupDev (families evaluated together), -1 none
   int lead;                   // the group's first member, which evaluates the whole group
+  int jtab;                   // offset of its start-value table in Tables::jtab, -1 none
+  int jrow;                   // doubles per table row (JT_NK, or 2 JT_NK for a finite-part family)
   int span[LAUX + 1];
   int coff[LAUX + 1];         // offset of P_l in the coefficient pool
 };
@@ -129,10 +142,11 @@ struct Tables {
   const FamDev *fam;
   const double *coef;
   const GroupDev *grp;
+  const double *jtab;         // start-value tables (FamDev::jtab)
 };
 
-F12_CONST double c_gh_x[NGH];
-F12_CONST double c_gh_w[NGH];
+F12_CONST double c_gh_x[NGH + NGHF];
+F12_CONST double c_gh_w[NGH + NGHF];
 F12_CONST double c_gl_x[NGL];   // Gauss-Legendre on [-1, 1]
 F12_CONST double c_gl_w[NGL];
 // c_{l,k+1}/c_{l,k} = (k+l+1) / ((k+1)(2k+2l+2)(2k+2l+3)),  c_{l,k} = 2^l (k+l)!/(k!(2k+2l+1)!)
@@ -144,6 +158,34 @@ F12_GLOBAL double d_kum_inv[2][NKUM];             // 1/((b+n)(n+1)) for b = 1/2,
 F12_GLOBAL double d_sm1_ratio[NKUM];              // Gamma((m+1)/2)/(Gamma(m/2)(m+1))
 
 F12_DEV inline double threshold_z(int l) { return 36.0 + 4.5 * l; }
+// The peak quadrature's integrand is x^alpha0 P_l(x) e^{-z} j_l(z) about a
+// Gaussian of width 1/sqrt(gamma) centred at x*; relative to that width it
+// varies on the scale sqrt(z)/(l + 1), so that the shorter rule suffices for
+// orders l < ls once z is past this bound.
+#ifndef F12_GHF_A
+#define F12_GHF_A 60.0
+#define F12_GHF_B 12.0
+#endif
+F12_DEV inline double few_nodes_z(int l) { return F12_GHF_A + F12_GHF_B * l; }
+// ... and only up to this order: at higher orders the family sums cancel
+// (k2 at xi = 10, D = 20, order 13), and the shorter rule's different
+// rounding was measured to move the result by 1e-9 of itself there
+constexpr int FEW_NODES_LMAX = 3;
+
+// High 32 bits of a double (sign, exponent, top of the mantissa): integer
+// comparisons of these stand in for floating-point tests that would
+// otherwise take FP64 instructions.
+F12_DEV inline int hi_word(double x) {
+#ifdef __CUDA_ARCH__
+  return __double2hiint(x);
+#else
+  long long b;
+  std::memcpy(&b, &x, sizeof b);
+  return (int)(b >> 32);
+#endif
+}
+// biased binary exponent of |x| (0 for zero)
+F12_DEV inline int exp_bits(double x) { return (hi_word(x) >> 20) & 0x7FF; }
 
 // e^{-z} j_l(z) for l = 0..N (N <= LAUX): power series for the top two orders
 // and the stable downward recurrence j_{l-1} = z^2 j_{l+1} + (2l+1) j_l for
@@ -404,7 +446,10 @@ F12_DEV inline void family_gh(const Tables &T, const FamDev &F, double xi, doubl
   for (int l = 0; l < ls; ++l) acc[l] = 0.0;
   double jh[LAUX + 2];
   const double twoxd = 2.0 * xi * D;
-  for (int i = 0; i < NGH; ++i) {
+  // (not for the powers below -1 that the quadrature launch also takes here)
+  const bool few = !QUAD && ls <= FEW_NODES_LMAX + 1 && beta * beta / (4.0 * gam) >= few_nodes_z(ls - 1);
+  const int i0 = few ? NGH : 0, i1 = few ? NGH + NGHF : NGH;
+  for (int i = i0; i < i1; ++i) {
     const double x = xs + c_gh_x[i] * isg;
     if (x <= 0.0) continue;
     jhat_all(twoxd * x, ls - 1, jh);
@@ -632,10 +677,35 @@ F12_DEV inline int family_eval(const Tables &T, const FamDev &F, double xi, doub
     const int m0 = F.fp_minus1 ? 1 : 0;      // first regular index of the S family
     const double as = F.alpha0 + m0;
     // unnormalised start values J_{as}, J_{as+1} (J_alpha = int t^alpha e^{yt - t^2} dt)
-    const double rho1 = 0.5 * (as + 1.0) / F.rho_start;
-    const double J0 = jhat_start(as, F.rho_start, y, &bad) * F.gam_tab[m0];
-    const double J1 = jhat_start(as + 1.0, rho1, y, &bad) * F.gam_tab[m0 + 1];
-    const double sm1 = F.fp_minus1 ? s_minus1(F.b, gam, &bad) : 0.0;
+    double J0, J1, sm1 = 0.0;
+    const double yt = y * (1.0 / JT_DY);
+    if (F.jtab >= 0 && yt < JT_NY - 0.5) {
+      // Taylor steps from the nearest grid point: with e_k = J_{as+k}(y_i)/k!,
+      // J_{as}(y_i + h) = sum_k e_k h^k and J_{as+1} = dJ_{as}/dy its derivative
+      const double r = rint(yt);
+      const double h = (yt - r) * JT_DY;
+      const double *row = T.jtab + F.jtab + (int)r * F.jrow;
+      double p = row[JT_NK - 1], dp = 0.0;
+      for (int kk = JT_NK - 2; kk >= 0; --kk) {
+        dp = fma(dp, h, p);
+        p = fma(p, h, row[kk]);
+      }
+      J0 = p;
+      J1 = dp;
+      if (F.fp_minus1) {
+        // the y-series of S(-1, b, gamma) (s_minus1): its Taylor coefficients
+        // follow the J row (constant term, then JT_NK - 1 more)
+        const double *tr = row + JT_NK;
+        double t = tr[JT_NK - 1];
+        for (int kk = JT_NK - 2; kk >= 0; --kk) t = fma(t, h, tr[kk]);
+        sm1 = -0.5 * 0.57721566490153286061 - 0.5 * log(gam) + t;
+      }
+    } else {
+      const double rho1 = 0.5 * (as + 1.0) / F.rho_start;
+      J0 = jhat_start(as, F.rho_start, y, &bad) * F.gam_tab[m0];
+      J1 = jhat_start(as + 1.0, rho1, y, &bad) * F.gam_tab[m0 + 1];
+      if (F.fp_minus1) sm1 = s_minus1(F.b, gam, &bad);
+    }
     // gamma^{-(alpha0+1)/2}: products of rsqrt for integer and half-integer alpha0
     double gpow0;
     if (F.pow_kind == 1) {                 // (alpha0+1)/2 = (n0+1)/2: powers of gamma^{-1/2}
@@ -650,6 +720,7 @@ F12_DEV inline int family_eval(const Tables &T, const FamDev &F, double xi, doub
       gpow0 = pow(gam, -0.5 * (F.alpha0 + 1.0));
     }
     const double TWO600 = 4.149515568880993e+180, MTWO600 = 2.409919865102884e-181;
+    constexpr int HI_2P600 = (1023 + 600) << 20;   // high word of 2^600
 
     // all orders l = ls..L advance together over the series index k: the S
     // window is extended once per k, each order adds one FMA per coefficient
@@ -681,25 +752,35 @@ F12_DEV inline int family_eval(const Tables &T, const FamDev &F, double xi, doub
       win[m0 & (WIN - 1)] = J0;
       win[(m0 + 1) & (WIN - 1)] = J1;
       int mfill = m0 + 2;
-      double abs_lo = 0.0, abs_hi = 0.0;
+      // J_m = (y/2) J_{m-1} + ((alpha0 + m - 1)/2) J_{m-2}: hy and ha, the
+      // latter advanced by 1/2 per step (exact for integer and half-integer
+      // alpha0, recomputed otherwise)
+      const double hy = 0.5 * y;
+      double ha = 0.5 * (F.alpha0 + (double)(m0 + 1));
+      const bool ha_exact = F.pow_kind != 0;
+      // convergence: the terms of the lowest and highest order fall below
+      // 2^-56 of the largest term so far, twice (exponent comparisons)
+      int emax_lo = 0, emax_hi = 0;
       int small = 0;
       const int kmin = (int)(0.5 * v) + 2;   // past the largest term (terms ~ z^k/k!)
       int k;
       for (k = 0; k < KMAX; ++k) {
         const int need = spmax - 1 + 2 * k;
+        int hmax = 0;
         while (mfill <= need) {
-          const double a = F.alpha0 + (mfill - 1);
-          double jn = 0.5 * fma(y, win[(mfill - 1) & (WIN - 1)], a * win[(mfill - 2) & (WIN - 1)]);
+          const double jn = fma(hy, win[(mfill - 1) & (WIN - 1)], ha * win[(mfill - 2) & (WIN - 1)]);
           win[mfill & (WIN - 1)] = jn;
+          hmax = max(hmax, hi_word(jn));
           ++mfill;
-          if (fabs(jn) > TWO600) {   // keep the window in range; exact power-of-two rescale
-            for (int r = mfill - WIN; r < mfill; ++r)
-              if (r >= 0) win[r & (WIN - 1)] *= MTWO600;
-            for (int l = ls; l <= L; ++l) common[l] *= TWO600;
-          }
+          ha = ha_exact ? ha + 0.5 : 0.5 * (F.alpha0 + (double)(mfill - 1));
+        }
+        if (hmax > HI_2P600) {   // keep the window in range; exact power-of-two rescale
+          for (int r = mfill - WIN; r < mfill; ++r)
+            if (r >= 0) win[r & (WIN - 1)] *= MTWO600;
+          for (int l = ls; l <= L; ++l) common[l] *= TWO600;
         }
         const int jlo = (F.fp_minus1 && k == 0) ? 1 : 0;
-        double mag_lo = 0.0, mag_hi = 0.0;
+        int e_lo = 0, e_hi = 0;
         for (int l = ls; l <= L; ++l) {
           const double *q = qv + qoff[l];
           const int sp = F.span[l];
@@ -707,16 +788,17 @@ F12_DEV inline int family_eval(const Tables &T, const FamDev &F, double xi, doub
           for (int j = jlo; j < sp; ++j) part = fma(q[j], win[(j + 2 * k) & (WIN - 1)], part);
           const double term = common[l] * part;
           sum[l] += term;
-          if (l == ls) mag_lo = fabs(term);
-          if (l == L) mag_hi = fabs(term);
+          if (l == ls) e_lo = exp_bits(term);
+          if (l == L) e_hi = exp_bits(term);
           nfma += sp - jlo + 2;
           const double cr = k < KTAB ? c_cratio[l][k]
                                      : (double)(k + l + 1) / ((double)(k + 1) * (2.0 * k + 2.0 * l + 2.0) * (2.0 * k + 2.0 * l + 3.0));
           common[l] *= v * cr;
         }
-        abs_lo += mag_lo;
-        abs_hi += mag_hi;
-        small = (mag_lo <= 1e-17 * abs_lo && mag_hi <= 1e-17 * abs_hi) ? small + 1 : 0;
+        emax_lo = max(emax_lo, e_lo);
+        emax_hi = max(emax_hi, e_hi);
+        // (a zero or subnormal term counts as small)
+        small = ((e_lo + 56 < emax_lo || e_lo == 0) && (e_hi + 56 < emax_hi || e_hi == 0)) ? small + 1 : 0;
         if (small >= 2 && k >= kmin) break;
       }
       if (k == KMAX) bad = 1;

@@ -89,7 +89,7 @@ inline void gauss_legendre(int n, double *x, double *w) {
 }
 
 struct AuxConst {
-  double gh_x[NGH], gh_w[NGH];
+  double gh_x[NGH + NGHF], gh_w[NGH + NGHF];   // the NGH-node rule, then the NGHF-node one
   double gl_x[NGL], gl_w[NGL];
   double cratio[LAUX + 1][KTAB];
   double inv_dfact[LAUX + 2];
@@ -99,6 +99,7 @@ struct AuxConst {
 
 inline void fill_aux_const(AuxConst &c) {
   gauss_hermite(NGH, c.gh_x, c.gh_w);
+  gauss_hermite(NGHF, c.gh_x + NGH, c.gh_w + NGH);
   gauss_legendre(NGL, c.gl_x, c.gl_w);
   for (int l = 0; l <= LAUX; ++l)
     for (int k = 0; k < KTAB; ++k)
@@ -120,6 +121,7 @@ struct ClassTables {
   std::vector<FamDev> fams;
   std::vector<double> coef;
   std::vector<GroupDev> groups;
+  std::vector<double> jtab;      // start-value tables (FamDev::jtab)
   int nfam[NCLASS] = {};
   int fam0[NCLASS] = {};
   bool supported[NCLASS] = {};
@@ -136,6 +138,8 @@ struct ClassTables {
 // Families with a lowest power below -1 are grouped with the families of the
 // same b and power lattice when their singular terms cancel within the group
 // (GroupDev).  Returns false if a family polynomial is longer than JMAX.
+inline void build_start_tables(ClassTables &ct);
+
 inline bool build_class_tables(const f12::TermList kernels[NCLASS], ClassTables &ct) {
   constexpr int KTAY = 16;    // Taylor terms for the integrability check (lowest power >= -KTAY + 1)
   ct.fams.clear();
@@ -205,6 +209,8 @@ inline bool build_class_tables(const f12::TermList kernels[NCLASS], ClassTables 
       d.quad = (d.b < 0.0 || d.alpha0 < -1.0 - 1e-9) ? 1 : 0;
       d.group = -1;
       d.lead = 0;
+      d.jtab = -1;
+      d.jrow = 0;
       double as = d.fp_minus1 ? 0.0 : d.alpha0;
       d.rho_start = std::exp(std::lgamma(0.5 * (as + 2.0)) - std::lgamma(0.5 * (as + 1.0)));
       f12::Family cur = fam0;
@@ -328,7 +334,79 @@ inline bool build_class_tables(const f12::TermList kernels[NCLASS], ClassTables 
     ct.nfam[cls] = (int)mine.size();
     for (const FamDev &d : mine) ct.quad[cls] = ct.quad[cls] || d.quad;
   }
+  build_start_tables(ct);
   return true;
+}
+
+// J_a(y) = int_0^inf t^a e^{y t - t^2} dt, a > -1, y >= 0, in long double from
+// the Kummer form (Eq. msmallz of App. B, valid for y >= 0; every term
+// positive):  J = 1/2 [Gamma((a+1)/2) M((a+1)/2, 1/2, y^2/4)
+//                     + y Gamma((a+2)/2) M((a+2)/2, 3/2, y^2/4)].
+inline long double kummer_host(long double a, long double b, long double z) {
+  long double t = 1.0L, s = 1.0L;
+  for (int n = 0; n < 4000; ++n) {
+    t *= (a + n) * z / ((b + n) * (n + 1));
+    s += t;
+    if (t <= 1e-21L * s) break;
+  }
+  return s;
+}
+
+inline long double jstart_host(long double a, long double y) {
+  const long double z = 0.25L * y * y;
+  return 0.5L * (std::tgamma(0.5L * (a + 1.0L)) * kummer_host(0.5L * (a + 1.0L), 0.5L, z) +
+                 y * std::tgamma(0.5L * (a + 2.0L)) * kummer_host(0.5L * (a + 2.0L), 1.5L, z));
+}
+
+// Start-value tables of the series families with b > 0 (FamDev::jtab): at
+// y_i = i JT_DY, row i holds e_k = J_{as+k}(y_i)/k! for k < JT_NK (as = alpha0,
+// or 0 for the finite-part family alpha0 = -1), J_{as+k} from J_{as},
+// J_{as+1} by the upward recursion J_{a+1} = (y J_a + a J_{a-1})/2 (positive
+// terms).  A finite-part family's rows carry, after the J part, the Taylor
+// coefficients of the y-series of S(-1, b, gamma): T(y) = 1/2 sum_{m>=1}
+// y^m Gamma(m/2)/m!, whose derivative is J_0(y), so T(y_i + h) = T(y_i) +
+// sum_{k>=1} e_{k-1} h^k / k.
+inline void build_start_tables(ClassTables &ct) {
+  ct.jtab.clear();
+  for (FamDev &d : ct.fams) {
+    d.jtab = -1;
+    d.jrow = 0;
+    if (d.quad || !(d.b > 0.0) || d.group >= 0) continue;
+    const long double as = d.fp_minus1 ? 0.0L : (long double)d.alpha0;
+    d.jrow = d.fp_minus1 ? 2 * JT_NK : JT_NK;
+    d.jtab = (int)ct.jtab.size();
+    for (int i = 0; i < JT_NY; ++i) {
+      const long double y = (long double)i * (long double)JT_DY;
+      long double J[JT_NK + 1];
+      J[0] = jstart_host(as, y);
+      J[1] = jstart_host(as + 1.0L, y);
+      for (int k = 2; k <= JT_NK; ++k) J[k] = 0.5L * (y * J[k - 1] + (as + k - 1) * J[k - 2]);
+      long double fk = 1.0L;
+      long double e[JT_NK];
+      for (int k = 0; k < JT_NK; ++k) {
+        if (k > 0) fk *= k;
+        e[k] = J[k] / fk;
+        ct.jtab.push_back((double)e[k]);
+      }
+      if (d.fp_minus1) {
+        // t_m = y^m Gamma(m/2) / (2 m!): t_1 = y sqrt(pi)/2, t_{m+1} = t_m y g_m/(m+1)
+        // with g_m = Gamma((m+1)/2)/Gamma(m/2), g_1 = 1/sqrt(pi), g_{m+1} = (m/2)/g_m
+        long double T = 0.0L;
+        if (y > 0.0L) {
+          const long double sqpi = 1.772453850905516027298167483341145182798L;
+          long double t = 0.5L * y * sqpi, g = 1.0L / sqpi;
+          for (int m = 1; m < 4000; ++m) {
+            T += t;
+            t *= y * g / (m + 1);
+            g = 0.5L * m / g;
+            if (m > 2.0L * y * y + 10 && t <= 1e-21L * T) break;
+          }
+        }
+        ct.jtab.push_back((double)T);
+        for (int k = 1; k < JT_NK; ++k) ct.jtab.push_back((double)(e[k - 1] / k));
+      }
+    }
+  }
 }
 
 }  // namespace f12dev

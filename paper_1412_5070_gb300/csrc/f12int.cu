@@ -744,6 +744,8 @@ struct f12int_ctx {
   double *d_coef = nullptr;
   GroupDev *d_grp = nullptr;
   size_t grp_bytes = 0;
+  double *d_jtab = nullptr;   // start-value tables of the series families
+  size_t jtab_bytes = 0;
   Tables tables{};
   size_t fam_bytes = 0, coef_bytes = 0;
   // basis
@@ -963,6 +965,7 @@ int f12int_destroy(f12int_ctx *ctx) {
   cudaFree(ctx->d_fam);
   cudaFree(ctx->d_coef);
   cudaFree(ctx->d_grp);
+  cudaFree(ctx->d_jtab);
   cudaFree(ctx->d_pqoff);
   cudaFree(ctx->d_keys);
   cudaFree(ctx->d_order);
@@ -1191,21 +1194,28 @@ static int set_factor_lists(f12int_ctx *ctx, const f12::TermList &T1, const f12:
   dfree(ctx, ctx->d_fam, ctx->fam_bytes);
   dfree(ctx, ctx->d_coef, ctx->coef_bytes);
   dfree(ctx, ctx->d_grp, ctx->grp_bytes);
+  dfree(ctx, ctx->d_jtab, ctx->jtab_bytes);
   ctx->d_grp = nullptr;
+  ctx->d_jtab = nullptr;
   ctx->fam_bytes = fams.size() * sizeof(FamDev);
   ctx->coef_bytes = coef.size() * sizeof(double);
   ctx->grp_bytes = ct.groups.size() * sizeof(GroupDev);
+  ctx->jtab_bytes = ct.jtab.size() * sizeof(double);
   rc = dalloc(ctx, &ctx->d_fam, ctx->fam_bytes);
   if (rc == F12INT_OK) rc = dalloc(ctx, &ctx->d_coef, ctx->coef_bytes);
   if (rc == F12INT_OK && ctx->grp_bytes) rc = dalloc(ctx, &ctx->d_grp, ctx->grp_bytes);
+  if (rc == F12INT_OK && ctx->jtab_bytes) rc = dalloc(ctx, &ctx->d_jtab, ctx->jtab_bytes);
   if (rc != F12INT_OK) return rc;
   CK(cudaMemcpy(ctx->d_fam, fams.data(), ctx->fam_bytes, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->d_coef, coef.data(), ctx->coef_bytes, cudaMemcpyHostToDevice));
   if (ctx->grp_bytes)
     CK(cudaMemcpy(ctx->d_grp, ct.groups.data(), ctx->grp_bytes, cudaMemcpyHostToDevice));
+  if (ctx->jtab_bytes)
+    CK(cudaMemcpy(ctx->d_jtab, ct.jtab.data(), ctx->jtab_bytes, cudaMemcpyHostToDevice));
   T.fam = ctx->d_fam;
   T.coef = ctx->d_coef;
   T.grp = ctx->d_grp;
+  T.jtab = ctx->d_jtab;
   ctx->tables = T;
   for (int c = 1; c <= 6; ++c) {
     ctx->cls_ok[c] = ct.supported[c];
@@ -2053,22 +2063,14 @@ extern "C" int f12int_compute_class_static(f12int_ctx *ctx, int basis_id, int cl
   if (!ctx->cls_ok[cls]) return F12INT_EDOMAIN;
   if (n == 0) return F12INT_OK;
   if (!quartets_dev || !out_dev || !offsets_dev) return F12INT_EINVAL;
-  // fixed part of the scratch: quartet list, offsets and primitive offsets in
-  // the working order, and the key histogram; the rest holds the work items
-  const size_t fixed = align256(sizeof(int32_t) * 4 * (size_t)n) + align256(sizeof(int64_t) * (size_t)n) +
-                       align256(sizeof(int64_t) * ((size_t)n + 1)) + align256(sizeof(unsigned) * kNKeys) +
-                       align256(sizeof(CTask) * (size_t)n);
-  if (fixed + ((size_t)1 << 20) > F12INT_STATIC_SCRATCH_BYTES) return F12INT_EINVAL;  // too many quartets
+  // a first bound on the list length, before anything is read back
+  const size_t per_quartet = sizeof(int32_t) * 4 + sizeof(int64_t) * 2 + sizeof(CTask);
+  if ((size_t)n > F12INT_STATIC_SCRATCH_BYTES / per_quartet) return F12INT_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
   CK(cudaSetDevice(ctx->device));
   unsigned char *base = nullptr;
   int rc = static_scratch_address(ctx->device, &base);
   if (rc != F12INT_OK) return rc;
-  int32_t *d_q = (int32_t *)base;
-  int64_t *d_o = (int64_t *)(base + align256(sizeof(int32_t) * 4 * (size_t)n));
-  int64_t *d_pq = (int64_t *)((unsigned char *)d_o + align256(sizeof(int64_t) * (size_t)n));
-  unsigned *d_hist = (unsigned *)((unsigned char *)d_pq + align256(sizeof(int64_t) * ((size_t)n + 1)));
-  unsigned char *after_hist = (unsigned char *)d_hist + align256(sizeof(unsigned) * kNKeys);
   const size_t item_bytes = sizeof(int) + sizeof(unsigned) + sizeof(double) * (LAUX + 1);
 
   const f12int_ctx::BasisData &B = ctx->bases[basis_id];
@@ -2088,7 +2090,7 @@ extern "C" int f12int_compute_class_static(f12int_ctx *ctx, int basis_id, int cl
     key0[i] = (B.l[s[0]] << 6) | (B.l[s[1]] << 4) | (B.l[s[2]] << 2) | B.l[s[3]];
     const ContractPlan pl = contract_plan(B.l[s[0]], B.l[s[1]], B.l[s[2]], B.l[s[3]], cls,
                                           (int64_t)B.nprim[s[0]] * B.nprim[s[1]] * B.nprim[s[2]] * B.nprim[s[3]]);
-    if (pl.smem == 0) return F12INT_EINVAL;
+    if (pl.smem == 0 || pl.smem > 227 * 1024) return F12INT_EINVAL;
     nw0[i] = pl.nw;
     sp0[i] = pl.nsplit;
     sm0[i] = pl.smem;
@@ -2113,7 +2115,6 @@ extern "C" int f12int_compute_class_static(f12int_ctx *ctx, int basis_id, int cl
     const int32_t *s = &hq[4 * i];
     pqoff[i] = npq;
     npq += (int64_t)B.nprim[s[0]] * B.nprim[s[1]] * B.nprim[s[2]] * B.nprim[s[3]];
-    if (hsm[i] > 227 * 1024) return F12INT_EINVAL;
   }
   pqoff[n] = npq;
   // contraction tasks (one per quartet and ket range), then the work items
@@ -2122,25 +2123,39 @@ extern "C" int f12int_compute_class_static(f12int_ctx *ctx, int basis_id, int cl
     for (int sp = 0; sp < hsp[i]; ++sp) tasks.push_back(CTask{(int32_t)i, (int16_t)sp, (int16_t)hsp[i]});
   std::vector<int64_t> tfirst((size_t)n + 1, 0);
   for (int64_t i = 0; i < n; ++i) tfirst[i + 1] = tfirst[i] + hsp[i];
-  CTask *d_tk = (CTask *)after_hist;
-  unsigned char *items_base = after_hist + align256(sizeof(CTask) * tasks.size());
+  // layout of the array: quartets, offsets and primitive offsets in the
+  // working order, the key histogram and the task list (all sized exactly
+  // now), then the work items of one chunk.  Every size check happens here,
+  // before anything is queued, so that an F12INT_EINVAL leaves the array and
+  // the output untouched.
+  int32_t *d_q = (int32_t *)base;
+  int64_t *d_o = (int64_t *)(base + align256(sizeof(int32_t) * 4 * (size_t)n));
+  int64_t *d_pq = (int64_t *)((unsigned char *)d_o + align256(sizeof(int64_t) * (size_t)n));
+  unsigned *d_hist = (unsigned *)((unsigned char *)d_pq + align256(sizeof(int64_t) * ((size_t)n + 1)));
+  CTask *d_tk = (CTask *)((unsigned char *)d_hist + align256(sizeof(unsigned) * kNKeys));
+  unsigned char *items_base = (unsigned char *)d_tk + align256(sizeof(CTask) * tasks.size());
   const size_t used_fixed = (size_t)(items_base - base);
   if (used_fixed + 3 * 256 + item_bytes > F12INT_STATIC_SCRATCH_BYTES) return F12INT_EINVAL;
   const int64_t max_items = (int64_t)((F12INT_STATIC_SCRATCH_BYTES - used_fixed - 3 * 256) / item_bytes);
+  const int kcls = cls == 5 ? 3 : cls;
+  const int nf = ctx->tables.nfam[kcls];
+  const int64_t pq_chunk = std::max<int64_t>(1, max_items / std::max(nf, 1));
+  for (int64_t i = 0; i < n; ++i)
+    if (pqoff[i + 1] - pqoff[i] > pq_chunk) return F12INT_EINVAL;   // one quartet larger than the scratch
   CK(cudaMemcpyAsync(d_tk, tasks.data(), sizeof(CTask) * tasks.size(), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(d_q, hq.data(), sizeof(int32_t) * 4 * n, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(d_o, ho.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(d_pq, pqoff.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, st));
 
+  // the primitive screen of f12int_compute_class when its table for this
+  // (basis, class) exists already (building it would allocate); without it
+  // every primitive quartet is evaluated
   PairView PV{B.d_pair_start, B.d_pp_p, B.d_pp_P, B.d_pp_ab, B.d_pp_eoff, B.d_epool, B.d_shell_l, B.nshell,
-              nullptr};
+              B.prim_screen ? B.d_qprim[cls] : nullptr};
   QuartetView QV{d_q, d_pq, n, nullptr, nullptr, nullptr, nullptr};
-  const int kcls = cls == 5 ? 3 : cls;
-  const int nf = ctx->tables.nfam[kcls];
-  const int64_t pq_chunk = std::max<int64_t>(1, max_items / std::max(nf, 1));
-  for (int64_t qa = 0; qa < n;) {
+  int rc_launch = F12INT_OK;
+  for (int64_t qa = 0; qa < n && rc_launch == F12INT_OK;) {
     int64_t qb = qa + 1;
-    if (pqoff[qb] - pqoff[qa] > pq_chunk) return F12INT_EINVAL;  // one quartet larger than the scratch
     while (qb < n && pqoff[qb + 1] - pqoff[qa] <= pq_chunk) ++qb;
     const int64_t pqa = pqoff[qa], nitems = (pqoff[qb] - pqa) * nf;
     int *d_keys = (int *)items_base;
@@ -2149,7 +2164,10 @@ extern "C" int f12int_compute_class_static(f12int_ctx *ctx, int basis_id, int cl
     if (nitems > 0) {
       // the histogram must start at zero on every call: the array keeps the
       // previous call's contents
-      CK(cudaMemsetAsync(d_hist, 0, sizeof(unsigned) * kNKeys, st));
+      if (cudaMemsetAsync(d_hist, 0, sizeof(unsigned) * kNKeys, st) != cudaSuccess) {
+        rc_launch = F12INT_ECUDA;
+        break;
+      }
       const unsigned nb = (unsigned)((nitems + BLOCK_AUX - 1) / BLOCK_AUX);
       const unsigned nbq = (unsigned)((pqoff[qb] - pqa + BLOCK_AUX - 1) / BLOCK_AUX);
       k_items_classify<false><<<nbq, BLOCK_AUX, 0, st>>>(ctx->tables, PV, QV, cls, pqa, nitems, d_keys, d_hist);
@@ -2163,25 +2181,33 @@ extern "C" int f12int_compute_class_static(f12int_ctx *ctx, int basis_id, int cl
                                                             ctx->d_status, nullptr);
         ctx->launches++;
       }
-      CK(cudaGetLastError());
+      if (cudaGetLastError() != cudaSuccess) rc_launch = F12INT_ECUDA;
     }
-    for (int64_t ra = qa; ra < qb;) {
+    for (int64_t ra = qa; ra < qb && rc_launch == F12INT_OK;) {
       const int nwr = hnw[ra];
       const size_t smr = hsm[ra];
       int64_t rb = ra + 1;
       while (rb < qb && hnw[rb] == nwr && 2 * hsm[rb] > smr) ++rb;
       const int64_t nt = tfirst[rb] - tfirst[ra];
-      if (smr > 48 * 1024) CK(cudaFuncSetAttribute(k_contract<false, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
+      if (smr > 48 * 1024 &&
+          cudaFuncSetAttribute(k_contract<false, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr) !=
+              cudaSuccess) {
+        rc_launch = F12INT_ECUDA;
+        break;
+      }
       k_contract<false, double><<<(unsigned)nt, 32 * nwr, smr, st>>>(PV, QV, cls, nf, pqa, d_tk + tfirst[ra], nt, nullptr, d_part,
                                                      out_dev, d_o, ctx->d_status, nullptr);
       ctx->launches++;
-      CK(cudaGetLastError());
+      if (cudaGetLastError() != cudaSuccess) rc_launch = F12INT_ECUDA;
       ra = rb;
     }
     qa = qb;
   }
-  // the host vectors above stay alive until the queued copies are consumed
-  CK(cudaStreamSynchronize(st));
+  // the host vectors above stay alive until the queued copies are consumed,
+  // and on an error nothing of this call is still running when it returns
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (rc_launch != F12INT_OK) return rc_launch;
+  if (e != cudaSuccess) return cuda_fail(e);
   return F12INT_OK;
 }
 

@@ -47,6 +47,7 @@ int eval(const f12::TermList kt[NCLASS], int cls, int64_t n, const double *xi, c
   T.fam = ct.fams.data();
   T.coef = ct.coef.data();
   T.grp = ct.groups.data();
+  T.jtab = ct.jtab.data();
   int bad = 0;
   double g[LAUX + 1];
   for (int64_t i = 0; i < n; ++i) {

@@ -4,11 +4,12 @@ Every comparison goes through the C ABI (paper_1412_5070_gb300.f12int) and
 the oracle (oracle/oracle.py) on the same seeded inputs.
 
 Tolerance (FP64 path): relative 1e-10 where |I_ref| > 1e-12, absolute 1e-12
-elsewhere.  An element whose sum of terms cancels by more than about 1e5
-(|I| much smaller than M, the magnitude of the terms Eq. ii adds for it,
-computed by the oracle) cannot be resolved to 1e-10 relative by any FP64
-evaluation: one rounding of an input g_n already moves it by u M.  For
-those the bound is 32 u M (u = 2^-53), the FP64 resolution of the sum.
+elsewhere.  An element whose sum of terms cancels by more than 1e5 (|I| far
+below M, the magnitude of the terms Eq. ii adds for it, computed by the
+oracle) cannot be resolved to 1e-10 relative by any FP64 evaluation: one
+rounding of an input g_n already moves it by u M (u = 2^-53).  Only such an
+element may pass on the FP64 resolution of its sum instead, 4 u M; every
+element that does is counted and printed, per class and test.
 """
 import numpy as np
 import pytest
@@ -22,17 +23,26 @@ from paper_1412_5070_gb300 import f12int as F
 from paper_1412_5070_gb300 import molecules as M
 
 RTOL, ATOL_SMALL, SMALL = 1e-10, 1e-12, 1e-12
-KAPPA, U64 = 32.0, 2.0 ** -53
+KAPPA, U64, CANCEL = 4.0, 2.0 ** -53, 1e5
 
 
-def close(got, ref, mag):
+def close(got, ref, mag, label=""):
     """Mask of elements outside the FP64 tolerance (mag: the oracle's term
-    magnitude per element)."""
+    magnitude per element).  Elements within 4 u M but not within 1e-10
+    relative pass only if M/|I| > 1e5; they are printed."""
     big = np.abs(ref) > SMALL
     bad = np.zeros(ref.shape, dtype=bool)
-    tol = np.maximum(RTOL * np.abs(ref[big]), KAPPA * U64 * mag[big])
-    bad[big] = np.abs(got[big] - ref[big]) > tol
-    bad[~big] = np.abs(got[~big] - ref[~big]) > ATOL_SMALL
+    err = np.abs(got - ref)
+    rel_ok = err <= RTOL * np.abs(ref)
+    cancels = mag > CANCEL * np.abs(ref)
+    allow = cancels & (err <= KAPPA * U64 * mag)
+    bad[big] = ~(rel_ok[big] | allow[big])
+    bad[~big] = err[~big] > ATOL_SMALL
+    hits = np.nonzero(big & ~rel_ok & allow)[0]
+    print("%s: %d of %d elements above 1e-12; %d pass only on the resolution of their cancelling sum%s" % (
+        label, int(big.sum()), ref.size, len(hits),
+        "".join(" [ref %.3e rel %.2g M/|I| %.2g err/uM %.2f]" % (ref[i], err[i] / abs(ref[i]), mag[i] / abs(ref[i]),
+                                                                 err[i] / (U64 * mag[i])) for i in hits[:20])))
     return bad
 
 
@@ -103,7 +113,7 @@ def test_two_centre_sp_all_classes(ctx, cls):
     sel = q[::4]
     got, off = gpu_blocks(ctx, bid, cls, basis, sel)
     ref, _, mag = O.shell_blocks(O.factor_kernel(M.P0), cls, basis, sel, with_mag=True)
-    bad = close(got, ref, mag)
+    bad = close(got, ref, mag, "I%d %s" % (cls, basis.name))
     assert not np.isnan(got).any()
     assert not bad.any(), report(got, ref, mag, bad)
 
@@ -130,7 +140,7 @@ def test_twelve_atom_spd_stratified(ctx, cls):
     sel = stratified(basis, cls, 1, 20 + cls)
     got, off = gpu_blocks(ctx, bid, cls, basis, sel)
     ref, _, mag = O.shell_blocks(O.factor_kernel(M.P0), cls, basis, sel, with_mag=True)
-    bad = close(got, ref, mag)
+    bad = close(got, ref, mag, "I%d %s" % (cls, basis.name))
     assert not np.isnan(got).any()
     assert not bad.any(), report(got, ref, mag, bad)
 
@@ -159,6 +169,6 @@ def test_f_shells_stratified(ctx, cls):
     sel = q[np.sort(np.array(pick))][::2 if cls != 5 else 3]
     got, off = gpu_blocks(ctx, bid, cls, basis, sel)
     ref, _, mag = O.shell_blocks(O.factor_kernel(M.P0), cls, basis, sel, with_mag=True)
-    bad = close(got, ref, mag)
+    bad = close(got, ref, mag, "I%d %s" % (cls, basis.name))
     assert not np.isnan(got).any()
     assert not bad.any(), report(got, ref, mag, bad)
