@@ -37,6 +37,13 @@ Two further workloads, each printing its own JSON line:
                       evaluation launch) and with rho = -1 (singular families, evaluated
                       in groups), the Ten-no factor exp(-1.2 r) and a six-Gaussian
                       geminal (both as term lists): shell quartets/s per class and launches.
+  --workload slice    the first --fraction of the 12-atom lists of one class (--cls N) or of
+                      all six: one untimed pass, then one pass inside an NVTX range named
+                      "profiled" (a profiler can restrict its capture to it with --nvtx
+                      --nvtx-include "profiled/"), with the library's per-kernel event
+                      timing and work counters: the case every ncu summary names.
+  --workload peak     the device's measured FP64 FMA, FP64 matrix (mma.sync) and FP32 FMA
+                      peaks (f12int_measure_peak), each twice.
   --workload serve    Poisson request streams at 10..2000 requests/s over 12
                       molecules of 2-60 atoms; half the requests ask for one
                       class, half for I2..I6, each over U{8..64} x U{8..64}
@@ -68,7 +75,8 @@ UNIT = "shell quartets/s"
 CLASSES = (1, 2, 3, 4, 5, 6)
 THRESH = 1e-12
 WORKLOAD = "12-atom 3s2p1d (3 prims/shell, seed 2), Schwarz 1e-12, classes I1..I6, dense FP64 blocks"
-FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate of the profiling recipe's table (no measured FP64 peak)
+SLICE_FACTORS = {"P0": M.P0, "Bneg": dict(M.P0, B=-0.5)}
+KST_KEYS = ("aux_ms", "aux_launches", "contract_ms", "contract_launches", "aux_flops", "contract_flops")
 
 
 def parse():
@@ -77,9 +85,17 @@ def parse():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
-    ap.add_argument("--workload", default="spd12", choices=("spd12", "batch64", "serve", "mixed", "perl", "factors"))
-    ap.add_argument("--fraction", type=float, default=1.0, help=argparse.SUPPRESS)
+    ap.add_argument("--workload", default="spd12",
+                    choices=("spd12", "batch64", "serve", "mixed", "perl", "factors", "slice", "peak"))
+    ap.add_argument("--fraction", type=float, default=1.0,
+                    help="spd12/slice: the first fraction of each screened list")
+    ap.add_argument("--cls", type=int, default=0, help="slice: one class (0: all six)")
+    ap.add_argument("--factor", default="P0", choices=tuple(SLICE_FACTORS),
+                    help="slice: correlation factor (P0: Eq. rs12 with B = +0.5; Bneg: B = -0.5, whose "
+                         "families with b < 0 go through the quadrature launch)")
     ap.add_argument("--no-cpu-baseline", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--no-legs", action="store_true",
+                    help="default workload: skip the reduced batched and served measurements")
     return ap.parse_args()
 
 
@@ -182,6 +198,25 @@ def screened_lists(F, ctx, bid, basis, fraction):
     return lists, time.time() - t0
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip() + " (%s)" % os.uname().machine
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return os.uname().machine
+
+
 def cpu_oracle_sample(basis, lists, target_seconds=15.0, impl_line=False):
     """Time the oracle on a bounded sample of each class's quartet list.
     Returns (quartets/s over all classes weighted like the workload, info)."""
@@ -209,7 +244,8 @@ def cpu_oracle_sample(basis, lists, target_seconds=15.0, impl_line=False):
     step_time = sum(len(lists[c]) / per[c] for c in CLASSES)
     value = total_q / step_time
     threads = os.cpu_count()
-    return value, {"cores": threads, "per_class_quartets_per_s": {("I%d" % c): per[c] for c in CLASSES},
+    return value, {"cores": threads, "cpu_model": cpu_model(),
+                   "per_class_quartets_per_s": {("I%d" % c): per[c] for c in CLASSES},
                    "sample": "seeded random canonical shell quartets of each class (all six), ~%.0f s of "
                              "oracle work; quartets/s over the mix" % target_seconds}
 
@@ -235,7 +271,7 @@ def run_reference(args):
             "steps": steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total_q / value,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "quartets_per_step": total_q},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": info["cores"], "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": info["cores"], "cpu_model": info["cpu_model"], "kind": "oracle",
                              "sample": info["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -288,19 +324,33 @@ def run_ours(args):
     F.f12int_set_timing(ctx, True)
     F.f12int_kernel_stats(ctx, reset=True)
     n_launch0 = F.f12int_launch_count(ctx)
+    # per class: the library's kernel stats (event-timed launches, work counters),
+    # read after each class (a host synchronisation between classes)
+    cls_kst = {c: {k: 0.0 for k in KST_KEYS + ("plan_ms",)} for c in CLASSES}
+    F.f12int_host_stats(ctx, reset=True)
+
+    def step_with_stats(ev):
+        for i, c in enumerate(CLASSES):
+            F.f12int_compute_class(ctx, bid, c, dq[c], out[c], doff[c], stream)
+            ev[i + 1].record(stream)
+            st = F.f12int_kernel_stats(ctx, reset=True)
+            for k in KST_KEYS:
+                cls_kst[c][k] += st[k]
+            cls_kst[c]["plan_ms"] += F.f12int_host_stats(ctx, reset=True)["plan_ms"]
+
     with ClockSampler(local) as clk:
         for _ in range(args.steps):
             with torch.cuda.stream(stream):
                 flush.zero_()
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(CLASSES) + 1)]
             ev[0].record(stream)
-            step(ev)
+            step_with_stats(ev)
             ev[-1].synchronize()
             times.append(ev[0].elapsed_time(ev[-1]))
             for i, c in enumerate(CLASSES):
                 class_ms[c].append(ev[i].elapsed_time(ev[i + 1]))
     n_launch = F.f12int_launch_count(ctx) - n_launch0
-    kst = F.f12int_kernel_stats(ctx, reset=True)
+    kst = {k: sum(cls_kst[c][k] for c in CLASSES) for k in KST_KEYS}
     F.f12int_set_timing(ctx, False)
     torch.cuda.synchronize()
     F.f12int_device_status(ctx)
@@ -331,12 +381,22 @@ def run_ours(args):
         e2e_times.append(time.perf_counter() - t)
     e2e_value = total_q / float(np.median(e2e_times))
 
+    # measured arithmetic peaks of this device (the roofline denominators)
+    peaks = {k: F.f12int_measure_peak(local, k) for k in ("fp64_fma", "fp64_mma_m8n8k4", "fp32_fma")}
+    peak64 = peaks["fp64_fma"]
     per_class = {}
     for c in CLASSES:
         t_ms = float(np.mean(class_ms[c]))
+        ks = cls_kst[c]
+        a_t = ks["aux_flops"] / (ks["aux_ms"] / 1e3) / 1e12 if ks["aux_ms"] > 0 else 0.0
+        c_t = ks["contract_flops"] / (ks["contract_ms"] / 1e3) / 1e12 if ks["contract_ms"] > 0 else 0.0
         per_class["I%d" % c] = {"shell_quartets": len(my[c]), "prim_quartets": nprimq[c], "ms": t_ms,
                                 "shell_quartets_per_s": len(my[c]) / (t_ms / 1000.0),
-                                "prim_quartets_per_s": nprimq[c] / (t_ms / 1000.0)}
+                                "prim_quartets_per_s": nprimq[c] / (t_ms / 1000.0),
+                                "aux": {"ms": ks["aux_ms"] / args.steps, "tflops": a_t, "frac": a_t / peak64},
+                                "contract": {"ms": ks["contract_ms"] / args.steps, "tflops": c_t,
+                                             "frac": c_t / peak64},
+                                "host_plan_ms": ks["plan_ms"] / args.steps}
     # roofline of the dominant kernel, from its own launch durations (CUDA events
     # on the launching stream, recorded by the library during the timed steps)
     aux_ach = kst["aux_flops"] / (kst["aux_ms"] / 1e3) / 1e12 if kst["aux_ms"] > 0 else 0.0
@@ -361,20 +421,37 @@ def run_ours(args):
             "gpu_launches": int(n_launch),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "roofline": {"bound": "alu", "kernel": "k_items_eval" if dom == "aux" else "k_contract",
-                         "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-                         "note": "FP64 pipe; achieved = counted algorithmic FP64 flops of the kernel / its event-timed "
-                                 "launch durations; peak = nominal GB300 FP64 rate (recipe table), "
-                                 "1.195 TFLOP/s measured by an FMA microbenchmark"},
+                         "achieved": ach, "peak": peak64, "unit": "TFLOP/s",
+                         "frac": ach / peak64, "traffic": None,
+                         "note": "FP64 pipe; achieved = counted FP64 flops of the kernel (series and quadrature "
+                                 "multiply-adds for k_items_eval, the algorithmic count for k_contract) / its "
+                                 "event-timed launch durations; peak = FP64 FMA rate measured in this run "
+                                 "(f12int_measure_peak), of measured"},
+            "peaks_tflops": peaks,
             "kernels": kernels,
             "clocks": clk.summary()}
     if rank == 0 and not args.no_cpu_baseline:
         # the oracle samples from the canonical lists: its inputs never come from the CUDA path
         canon = {c: M.canonical_quartets(basis, c) for c in CLASSES}
         v, info = cpu_oracle_sample(basis, canon, target_seconds=15.0)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": info["cores"], "kind": "oracle",
-                                "sample": info["sample"]}
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": info["cores"], "cpu_model": info["cpu_model"],
+                                "kind": "oracle", "sample": info["sample"]}
     F.f12int_destroy(ctx)
+    del out, dq, doff, flush
+    torch.cuda.empty_cache()
+    # the batched and served forms on reduced workloads (rank 0 at N = 1 only)
+    if rank == 0 and world == 1 and not args.no_legs:
+        b = batching_measure(16, 1, 1)
+        line["batched"] = {"workload": b["workload"] + " (the first 16 of the 64-molecule batching workload)",
+                           "shell_quartets_per_pass": b["shell_quartets_per_pass"],
+                           "batched": b["batched"], "plain": b["plain"], "speedup": b["speedup"],
+                           "schedule": b["schedule"]}
+        r = serving_measure(6, rates=(20, 200), nreq=lambda lam: 300, plain_cap_s=20.0, verbose=False)
+        line["served"] = {"workload": r["workload"] + " (6 of the 48 molecules of the serving workload, "
+                                                      "2 rates, 300 requests each)",
+                          "rates": [{"rate_per_s": x["rate_per_s"], "requests": x["requests"],
+                                     "requests_path": x["requests_path"], "plain_serial": x["plain_serial"]}
+                                    for x in r["rates"]]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -394,13 +471,15 @@ def _request_layout(basis, quartets, classes):
     return np.stack([first + k * per for k in range(len(classes))]), per * len(classes)
 
 
-def run_batching(args):
-    """64 uneven molecules, all six classes: batched requests vs plain launches."""
+def batching_measure(nmol=64, steps=1, warmup=1):
+    """Batched requests (f12int_submit, graph replays) against one plain
+    f12int_compute_class per class and molecule, over nmol uneven molecules
+    (all six classes): seconds per pass and quartets/s of each path."""
     import torch
     from paper_1412_5070_gb300 import build as B
     from paper_1412_5070_gb300 import f12int as F
     B.build()
-    work = M.batching_workload(64)
+    work = M.batching_workload(nmol)
     stream = torch.cuda.Stream()
     ctx = F.f12int_create(0, 0, stream)
     F.f12int_set_factor(ctx, M.P0)
@@ -435,13 +514,13 @@ def run_batching(args):
     t0 = time.time()
     tuned = F.f12int_batch_autotune(ctx, bids[0], work[0][1], CLASSES)
     t_tune = time.time() - t0
-    for _ in range(max(0, args.warmup - 1)):
+    for _ in range(max(0, warmup - 1)):
         batched()
         plain()
     res = {}
     for name, fn in (("batched", batched), ("plain", plain)):
         ts = []
-        for _ in range(max(1, args.steps)):
+        for _ in range(max(1, steps)):
             torch.cuda.synchronize()
             l0 = F.f12int_launch_count(ctx)
             b0 = F.f12int_batch_stats(ctx)["batches"]
@@ -456,29 +535,45 @@ def run_batching(args):
                      "graph_replays": batches if name == "batched" else 0,
                      "plain_launches": launches if name == "plain" else 0}
     F.f12int_device_status(ctx)
-    line = {"metric": "F12 quartets/s over an uneven 64-molecule batch, graph-replayed requests vs plain launches",
-            "value": res["batched"]["shell_quartets_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "64 molecules (seeds 1000-1063, 2-30 atoms, 4s3p2d1f, 1-6 primitives, "
-                                   "exponents [0.03, 200]); 64 x 64 significant shell pairs each; I1..I6",
-                       "shell_quartets_per_pass": nq, "prim_quartets_per_pass": npq,
-                       "batch_limits": {"quartets_per_class": 1 << 19, "items_per_class": 1 << 26}},
+    F.f12int_destroy(ctx)
+    return {"workload": "%d molecules (seeds 1000-%d, 2-30 atoms, 4s3p2d1f, 1-6 primitives, exponents "
+                        "[0.03, 200]); 64 x 64 significant shell pairs each; I1..I6" % (nmol, 999 + nmol),
+            "shell_quartets_per_pass": nq, "prim_quartets_per_pass": npq,
             "batched": res["batched"], "plain": res["plain"],
             "speedup": res["plain"]["s_per_pass"] / res["batched"]["s_per_pass"],
-            "setup_s": {"set_basis_64": t_basis, "first_pass_with_bounds": t_first, "autotune": t_tune},
+            "setup_s": {"set_basis": t_basis, "first_pass_with_bounds": t_first, "autotune": t_tune},
             "schedule": {"I%d" % c: {"task_flops": v[0], "aux_grid_divisor": v[1]} for c, v in tuned.items()},
             "timing": "wall clock from first submit to last completion (host list building included)"}
-    F.f12int_destroy(ctx)
+
+
+def run_batching(args):
+    """64 uneven molecules, all six classes: batched requests vs plain launches."""
+    r = batching_measure(64, args.steps, args.warmup)
+    line = {"metric": "F12 quartets/s over an uneven 64-molecule batch, graph-replayed requests vs plain launches",
+            "value": r["batched"]["shell_quartets_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": r["workload"], "shell_quartets_per_pass": r["shell_quartets_per_pass"],
+                       "prim_quartets_per_pass": r["prim_quartets_per_pass"],
+                       "batch_limits": {"quartets_per_class": 1 << 19, "items_per_class": 1 << 26}},
+            **{k: r[k] for k in ("batched", "plain", "speedup", "setup_s", "schedule", "timing")}}
     print(json.dumps(line), flush=True)
 
 
-def run_serving(args):
-    """Poisson request streams: latency and throughput, requests vs serial plain launches."""
+def serving_measure(pool_n=12, rates=(10, 20, 50, 100, 200, 500, 1000, 2000), nreq=None, plain_cap_s=90.0,
+                    verbose=True):
+    """Poisson request streams over a pool of seeded molecules: p50/p99
+    latency (arrival to completion seen by poll) and shell quartets/s of the
+    request path (f12int_submit / f12int_poll, continuous batching), against
+    the same requests run one after another with plain f12int_compute_class
+    calls (capped at plain_cap_s per rate).  nreq(rate) gives the requests per
+    rate (default: one minute of arrivals, at most 2000)."""
     import torch
     from paper_1412_5070_gb300 import build as B
     from paper_1412_5070_gb300 import f12int as F
     B.build()
-    pool = M.serving_pool(12)
+    if nreq is None:
+        nreq = lambda lam: int(min(2000, 60 * lam))
+    pool = M.serving_pool(pool_n)
     stream = torch.cuda.Stream()
     ctx = F.f12int_create(0, 0, stream)
     F.f12int_set_factor(ctx, M.P0)
@@ -495,24 +590,21 @@ def run_serving(args):
     for _, t in warm:
         while not F.f12int_poll(ctx, t, 1000):
             pass
-    t_setup = time.time() - t0
+    t_bounds = time.time() - t0
     # per-class schedules measured on one request-sized block (40 x 40 pairs of a mid-size molecule)
     mid = int(np.argsort([b.nshell for b in pool])[len(pool) // 2])
     tuned = F.f12int_batch_autotune(ctx, bids[mid], M.pair_block(pool[mid], 40, 40, 3), (2, 3, 4, 5, 6))
     t_setup = time.time() - t0
-    print("serving: setup %.1f s" % t_setup, file=sys.stderr, flush=True)
-    rates = (10, 20, 50, 100, 200, 500, 1000, 2000)
+    if verbose:
+        print("serving: setup %.1f s (bounds %.1f s)" % (t_setup, t_bounds), file=sys.stderr, flush=True)
     rows = []
     for lam in rates:
-        n = int(min(200, max(40, lam * 8)))
-        reqs = M.serving_requests(n, float(lam), pool, seed=5 + lam)
+        reqs = M.serving_requests(nreq(lam), float(lam), pool, seed=5 + lam)
         prep = []
         for (ta, m, classes, q) in reqs:
             off, tot = _request_layout(pool[m], q, classes)
             o = torch.empty(tot, dtype=torch.float64, device="cuda")
-            dq = torch.from_numpy(np.ascontiguousarray(q)).cuda()
-            doff = [torch.from_numpy(off[k].copy()).cuda() for k in range(len(classes))]
-            prep.append((ta, m, classes, q, off, o, dq, doff))
+            prep.append((ta, m, classes, q, off, o))
         nq = sum(len(r[3]) * len(r[2]) for r in prep)
         torch.cuda.synchronize()
         # request path: submit at the arrival times, a poller records completions
@@ -538,7 +630,7 @@ def run_serving(args):
         start = time.perf_counter()
         th.start()
         sub = {}
-        for k, (ta, m, classes, q, off, o, dq, doff) in enumerate(prep):
+        for k, (ta, m, classes, q, off, o) in enumerate(prep):
             wait_s = start + ta - time.perf_counter()
             if wait_s > 0:
                 time.sleep(wait_s)
@@ -551,21 +643,23 @@ def run_serving(args):
         lat = np.array([done[k] - sub[k] for k in range(len(prep))]) * 1e3
         span = max(done.values()) - start
         eng = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-               "shell_quartets_per_s": nq / span}
-        print("serving: rate %d/s, %d requests: requests path p50 %.1f ms p99 %.1f ms" % (
-            lam, len(prep), eng["p50_ms"], eng["p99_ms"]), file=sys.stderr, flush=True)
-        # serial plain launches in arrival order (capped at 90 s per rate)
+               "shell_quartets_per_s": nq / span, "requests_per_s": len(prep) / span}
+        if verbose:
+            print("serving: rate %d/s, %d requests: requests path p50 %.1f ms p99 %.1f ms" % (
+                lam, len(prep), eng["p50_ms"], eng["p99_ms"]), file=sys.stderr, flush=True)
+        # serial plain launches in arrival order (capped)
         lat2 = []
         nq2 = 0
         start = time.perf_counter()
-        for (ta, m, classes, q, off, o, dq, doff) in prep:
-            if time.perf_counter() - start > 90.0:
+        for (ta, m, classes, q, off, o) in prep:
+            if time.perf_counter() - start > plain_cap_s:
                 break
             wait_s = start + ta - time.perf_counter()
             if wait_s > 0:
                 time.sleep(wait_s)
+            dq = torch.from_numpy(np.ascontiguousarray(q)).cuda()
             for k, c in enumerate(classes):
-                F.f12int_compute_class(ctx, bids[m], c, dq, o, doff[k], stream)
+                F.f12int_compute_class(ctx, bids[m], c, dq, o, torch.from_numpy(off[k].copy()).cuda(), stream)
             stream.synchronize()
             lat2.append(time.perf_counter() - (start + ta))
             nq2 += len(q) * len(classes)
@@ -574,23 +668,30 @@ def run_serving(args):
         plain = {"p50_ms": float(np.percentile(lat2, 50)), "p99_ms": float(np.percentile(lat2, 99)),
                  "shell_quartets_per_s": nq2 / span2, "requests_completed": len(lat2),
                  "truncated": len(lat2) < len(prep)}
-        print("serving: rate %d/s: plain p50 %.1f ms p99 %.1f ms (%d of %d)" % (
-            lam, plain["p50_ms"], plain["p99_ms"], len(lat2), len(prep)), file=sys.stderr, flush=True)
+        if verbose:
+            print("serving: rate %d/s: plain p50 %.1f ms p99 %.1f ms (%d of %d)" % (
+                lam, plain["p50_ms"], plain["p99_ms"], len(lat2), len(prep)), file=sys.stderr, flush=True)
         rows.append({"rate_per_s": lam, "requests": len(prep), "shell_quartets": nq, "requests_path": eng,
                      "plain_serial": plain})
         del prep
     F.f12int_device_status(ctx)
-    best = max(r["requests_path"]["shell_quartets_per_s"] for r in rows)
+    F.f12int_destroy(ctx)
+    return {"workload": "%d molecules (seeds 500-%d, 2-60 atoms, 4s3p2d1f, 1-6 primitives); Poisson arrivals; "
+                        "half one class of I2..I6, half all five; U{8..64} x U{8..64} significant shell pairs "
+                        "per request" % (pool_n, 499 + pool_n),
+            "batch_limits": {"quartets_per_class": 1 << 18, "items_per_class": 1 << 25},
+            "rates": rows, "setup_s": t_setup, "bounds_s": t_bounds,
+            "schedule": {"I%d" % c: {"task_flops": v[0], "aux_grid_divisor": v[1]} for c, v in tuned.items()}}
+
+
+def run_serving(args):
+    """Poisson request streams: latency and throughput, requests vs serial plain launches."""
+    r = serving_measure(48)
+    best = max(x["requests_path"]["shell_quartets_per_s"] for x in r["rates"])
     line = {"metric": "served p50/p99 latency (submit to done) and quartets/s, requests vs serial plain launches",
             "value": best, "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": "12 molecules (seeds 500-511, 2-60 atoms, 4s3p2d1f, 1-6 primitives); Poisson "
-                                   "arrivals; half one class of I2..I6, half all five; U{8..64} x U{8..64} "
-                                   "significant shell pairs per request",
-                       "batch_limits": {"quartets_per_class": 1 << 18, "items_per_class": 1 << 25}},
-            "rates": rows, "setup_s": t_setup,
-            "schedule": {"I%d" % c: {"task_flops": v[0], "aux_grid_divisor": v[1]} for c, v in tuned.items()}}
-    F.f12int_destroy(ctx)
+            "data": "synthetic", "config": {"workload": r["workload"], "batch_limits": r["batch_limits"]},
+            **{k: r[k] for k in ("rates", "setup_s", "bounds_s", "schedule")}}
     print(json.dumps(line), flush=True)
 
 
@@ -721,7 +822,7 @@ def run_per_l(args):
     F.f12int_device_status(ctx)
     line = {"metric": "F12 quartets/s per class and (la,lb,lc,ld), with kernel FP64 rates", "unit": UNIT,
             "n_gpus": 1, "dtype": "f64", "data": "synthetic", "config": {"workload": WORKLOAD},
-            "fp64_peak_tflops": FP64_PEAK_TFLOPS, "rows": rows}
+            "fp64_peak_tflops": F.f12int_measure_peak(0, "fp64_fma"), "rows": rows}
     F.f12int_destroy(ctx)
     print(json.dumps(line), flush=True)
 
@@ -788,6 +889,61 @@ def run_factors(args):
     print(json.dumps(line), flush=True)
 
 
+def run_slice(args):
+    """One class (or all) on a slice of the 12-atom lists, for profilers."""
+    import torch
+    from paper_1412_5070_gb300 import build as B
+    from paper_1412_5070_gb300 import f12int as F
+    B.build()
+    basis = build_workload()
+    stream = torch.cuda.Stream()
+    ctx = F.f12int_create(0, 0, stream)
+    F.f12int_set_factor(ctx, SLICE_FACTORS[args.factor])
+    bid = F.f12int_set_basis(ctx, basis)
+    classes = CLASSES if args.cls == 0 else (args.cls,)
+    lists, _ = screened_lists(F, ctx, bid, basis, args.fraction)
+    rows = {}
+    for c in classes:
+        q = np.ascontiguousarray(lists[c])
+        off = M.block_offsets(basis, q)
+        dq = torch.from_numpy(q).cuda()
+        doff = torch.from_numpy(off[:-1].copy()).cuda()
+        out = torch.empty(int(off[-1]), dtype=torch.float64, device="cuda")
+        F.f12int_compute_class(ctx, bid, c, dq, out, doff, stream)   # warm-up (and primitive bounds)
+        stream.synchronize()
+        F.f12int_set_timing(ctx, True)
+        F.f12int_kernel_stats(ctx, reset=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("profiled")
+        e0.record(stream)
+        F.f12int_compute_class(ctx, bid, c, dq, out, doff, stream)
+        e1.record(stream)
+        torch.cuda.nvtx.range_pop()
+        e1.synchronize()
+        st = F.f12int_kernel_stats(ctx, reset=True)
+        F.f12int_set_timing(ctx, False)
+        npq = int(np.sum(np.prod(basis.nprim[q], axis=1)))
+        rows["I%d" % c] = {"shell_quartets": len(q), "prim_quartets": npq, "ms": e0.elapsed_time(e1),
+                           "aux_ms": st["aux_ms"], "aux_launches": st["aux_launches"],
+                           "contract_ms": st["contract_ms"], "contract_launches": st["contract_launches"],
+                           "aux_counted_tflops": st["aux_flops"] / (st["aux_ms"] / 1e3) / 1e12 if st["aux_ms"] else 0,
+                           "contract_tflops": st["contract_flops"] / (st["contract_ms"] / 1e3) / 1e12
+                           if st["contract_ms"] else 0}
+        del out
+    F.f12int_device_status(ctx)
+    F.f12int_destroy(ctx)
+    print(json.dumps({"workload": "slice", "fraction": args.fraction, "factor": args.factor, "classes": rows}),
+          flush=True)
+
+
+def run_peak(args):
+    from paper_1412_5070_gb300 import build as B
+    from paper_1412_5070_gb300 import f12int as F
+    B.build()
+    res = {k: [F.f12int_measure_peak(0, k) for _ in range(2)] for k in F.PEAK_KINDS}
+    print(json.dumps({"workload": "peak", "unit": "TFLOP/s", "peaks": res}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -802,6 +958,10 @@ def main():
         run_per_l(args)
     elif args.workload == "factors":
         run_factors(args)
+    elif args.workload == "slice":
+        run_slice(args)
+    elif args.workload == "peak":
+        run_peak(args)
     else:
         run_ours(args)
 

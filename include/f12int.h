@@ -228,7 +228,7 @@ int f12int_compute_class_mixed(f12int_ctx *ctx, int basis_id, int cls, const int
 int f12int_aux(f12int_ctx *ctx, int cls, int64_t npts, const double *xi_dev, const double *D_dev,
                int nmax, double *out_dev, void *cuda_stream);
 
-/* Same blocks as f12int_compute_class, but the call allocates no device
+/* The blocks of f12int_compute_class, from a call that allocates no device
  * memory: every scratch buffer comes from one file-scope device array of
  * F12INT_STATIC_SCRATCH_BYTES (64 MiB) that each GPU which loads the library
  * holds until the process exits.  It is meant for callers that cannot call
@@ -244,9 +244,24 @@ int f12int_aux(f12int_ctx *ctx, int cls, int64_t npts, const double *xi_dev, con
  *     call's contents (the call clears what must start at zero).  Calls whose
  *     work overlaps on the GPU (other streams, other contexts of the same
  *     device) race on it and must be serialised by the caller.
- *   - Errors: F12INT_EINVAL when the quartet list (about 1.6M quartets at most)
- *     or one shell quartet's primitive work does not fit in the array; the
- *     other errors as for f12int_compute_class. */
+ *   - Primitive screening: the call uses the primitive-quartet screen of
+ *     f12int_compute_class when that table exists for the (basis, class),
+ *     i.e. after one allocating call of the class on the basis (or a
+ *     f12int_submit of it); the blocks are then bitwise those of
+ *     f12int_compute_class.  Without the table (building it allocates) every
+ *     primitive quartet is evaluated: more work, and blocks that differ from
+ *     f12int_compute_class's by the screened contributions only (below the
+ *     absolute accuracy the FP64 tolerance asks of elements near 1e-12).
+ *   - Limits: the list itself takes 40 bytes per quartet plus 8 bytes per
+ *     contraction task, one task per range of ket components (quartets of
+ *     high angular momentum, or with many primitive quartets, are split into
+ *     several ranges, up to 100): about 1.4M quartets of one range each, far
+ *     fewer when most are split.  Per shell quartet, its primitive quartets
+ *     times the kernel's term families must fit in the rest (about 500k work
+ *     items).  Every size check is made before any work is queued.
+ *   - Errors: F12INT_EINVAL when the list or one shell quartet's primitive
+ *     work does not fit in the array (nothing is then queued or written);
+ *     the other errors as for f12int_compute_class. */
 int f12int_compute_class_static(f12int_ctx *ctx, int basis_id, int cls, const int32_t *quartets_dev,
                                 int64_t n, double *out_dev, const int64_t *offsets_dev, void *cuda_stream);
 
@@ -286,8 +301,10 @@ int f12int_submit(f12int_ctx *ctx, int basis_id, const f12int_request *req, uint
 /* Wait at most timeout_us microseconds (0: do not wait) for a request.
  * *done = 1 once it has finished; the call then returns the request's status
  * (F12INT_OK, or F12INT_EDEVICE if a device-side check of its batch failed)
- * and forgets the ticket.  *done = 0 and F12INT_OK while it is queued or
- * running.  F12INT_EINVAL for an unknown or already reported ticket. */
+ * and forgets the ticket.  While it is queued or running, *done = 0 and the
+ * call returns F12INT_OK for timeout_us = 0 (a query) and F12INT_ETIMEOUT when
+ * a wait of timeout_us > 0 ran out (the ticket stays valid).  F12INT_EINVAL
+ * for an unknown or already reported ticket. */
 int f12int_poll(f12int_ctx *ctx, uint64_t ticket, int64_t timeout_us, int *done);
 
 /* Capacity of one batch, per class: max_quartets shell quartets and
@@ -341,6 +358,34 @@ int f12int_set_timing(f12int_ctx *ctx, int on);
  *       + 2 Nab nh(lab) Ncd per primitive quartet; bra step x4 and L+2 for I5).
  * reset != 0 clears them.  Synchronises the context's stream. */
 int f12int_kernel_stats(f12int_ctx *ctx, int reset, double *stats);
+
+/* Host-side planning time of f12int_compute_class calls since the last reset:
+ * stats[0] milliseconds (wall clock, from the call's entry to its first
+ * launch: reading the list, ordering the quartets, uploading the plan),
+ * stats[1] the number of calls.  reset != 0 clears them.  Measurement aid;
+ * the paper has no counterpart. */
+int f12int_host_stats(f12int_ctx *ctx, int reset, double *stats);
+
+/* Measured arithmetic peak of CUDA device `device`, in TFLOP/s, written to
+ * *tflops: the denominators of the library's roofline figures.  kind 0: FP64
+ * fused multiply-add (the DFMA pipe); 1, 2, 3: FP64 matrix multiply-accumulate
+ * (mma.sync, shapes m8n8k4, m16n8k4, m16n8k16); 4: FP32 fused multiply-add.
+ * Independent instruction chains on SMs x 8 blocks of 256 threads, one
+ * warm-up launch, CUDA events around one launch of a few hundred ms; 2 flops
+ * per FMA and 2 m n k per matrix instruction.  Allocates and frees a small
+ * device buffer; needs no context.  Measurement aid; the paper has no
+ * counterpart.  Errors: F12INT_EINVAL for a bad kind or device. */
+int f12int_measure_peak(int device, int kind, double *tflops);
+
+/* Cap on the length of the auxiliary stage's series (default and maximum 400
+ * terms; the longest series of the supported range needs about 200).  An
+ * item whose series has not converged at the cap sets bit 1 of the device
+ * status word, which f12int_device_status and f12int_poll report as
+ * F12INT_EDEVICE; no kernel faults or waits.  Lowering the cap is a way to
+ * exercise that path in tests; 0 restores the default.  Takes effect for
+ * later launches (the batch graph is captured again).  Errors: F12INT_EINVAL
+ * for a negative cap.  Test aid; the paper has no counterpart. */
+int f12int_set_series_cap(f12int_ctx *ctx, int kmax);
 
 /* Read and clear the device status word (a device-side check failing sets
  * it).  Synchronises the context's stream.  Returns F12INT_OK or

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libf12int.so")
-SOURCES = [os.path.join(CSRC, "f12int.cu"), os.path.join(CSRC, "termlist.cpp")]
+SOURCES = [os.path.join(CSRC, "f12int.cu"), os.path.join(CSRC, "peak.cu"), os.path.join(CSRC, "termlist.cpp")]
 DEPS = SOURCES + [os.path.join(CSRC, f) for f in ("aux.cuh", "auxtab.h", "engine.cuh", "termlist.h")] + \
     [os.path.join(os.path.dirname(HERE), "include", "f12int.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

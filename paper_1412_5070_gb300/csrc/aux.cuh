@@ -82,7 +82,7 @@ using std::sqrt;
 constexpr int LAUX = 14;     // highest radial order (f shells, I5: 3+3+3+3+2)
 constexpr int JMAX = 48;     // longest family polynomial
 constexpr int WIN = 64;      // circular window over the S sequence (> JMAX + 2)
-constexpr int KMAX = 1500;   // series length cap
+constexpr int KMAX = 400;    // series length cap (the longest series in use needs about 200 terms)
 constexpr int NGH = 16;      // Gauss-Hermite nodes
 constexpr int NGHF = 10;     // the shorter Gauss-Hermite rule, far from r = 0 (stored after the first)
 constexpr int KTAB = 320;    // tabulated series coefficient ratios
@@ -110,6 +110,8 @@ struct FamDev {
   int group;                  // index of its GroupDev (families evaluated together), -1 none
   int lead;                   // the group's first member, which evaluates the whole group
   int jtab;                   // offset of its start-value table in Tables::jtab, -1 none
+  int ha_base;                // 2 alpha0 - 2: index of (alpha0 + m - 1)/2 in d_quarter is ha_base + 2m
+  int ha_tab;                 // 1: that index stays inside d_quarter for every m of the series
   int jrow;                   // doubles per table row (JT_NK, or 2 JT_NK for a finite-part family)
   int span[LAUX + 1];
   int coff[LAUX + 1];         // offset of P_l in the coefficient pool
@@ -143,6 +145,7 @@ struct Tables {
   const double *coef;
   const GroupDev *grp;
   const double *jtab;         // start-value tables (FamDev::jtab)
+  int kcap;                   // series length cap (KMAX; lowered only to test the status word)
 };
 
 F12_CONST double c_gh_x[NGH + NGHF];
@@ -156,6 +159,17 @@ F12_CONST double c_inv_dfact[LAUX + 2];        // 1/(2l+1)!! = c_{l,0}
 constexpr int NKUM = 512;
 F12_GLOBAL double d_kum_inv[2][NKUM];             // 1/((b+n)(n+1)) for b = 1/2, 3/2
 F12_GLOBAL double d_sm1_ratio[NKUM];              // Gamma((m+1)/2)/(Gamma(m/2)(m+1))
+// The series coefficients c_{l,k} = 2^l (k+l)!/(k!(2k+2l+1)!) with a power of
+// two that depends on k alone split off: c_{l,k} = d_cser[l][k] 2^{-E_k},
+// E_k = -floor(log2 c_{0,k}) (so d_cser[0][k] lies in [1, 2)), and the step
+// d_vstep[k] = 2^{E_k - E_{k+1}}.  Built in long double by the ratio
+// recursion c_{l,k+1}/c_{l,k} = (k+l+1)/((k+1)(2k+2l+2)(2k+2l+3)).
+F12_GLOBAL double d_cser[LAUX + 1][KMAX];
+F12_GLOBAL double d_vstep[KMAX];
+// d_quarter[i] = i/4: the coefficients (alpha0 + m - 1)/2 of the S recursion
+// for integer and half-integer alpha0, read instead of being accumulated
+constexpr int NQUARTER = 2 * (JMAX + 2 * KMAX) + 16;
+F12_GLOBAL double d_quarter[NQUARTER];
 
 F12_DEV inline double threshold_z(int l) { return 36.0 + 4.5 * l; }
 // The peak quadrature's integrand is x^alpha0 P_l(x) e^{-z} j_l(z) about a
@@ -727,7 +741,7 @@ F12_DEV inline int family_eval(const Tables &T, const FamDev &F, double xi, doub
     constexpr int QMAX = 512;
     double qv[QMAX];
     int qoff[LAUX + 2];
-    double common[LAUX + 1], sum[LAUX + 1];
+    double sum[LAUX + 1];
     int tot = 0;
     for (int l = ls; l <= L; ++l) {
       qoff[l] = tot;
@@ -744,8 +758,7 @@ F12_DEV inline int family_eval(const Tables &T, const FamDev &F, double xi, doub
           qv[qoff[l] + j] = P[j] * gp;
           gp *= rgam;
         }
-        common[l] = c_inv_dfact[l] * eT;   // c_{l,0} e^{-xi D^2}
-        sum[l] = F.fp_minus1 ? qv[qoff[l]] * common[l] * sm1 : 0.0;
+        sum[l] = F.fp_minus1 ? qv[qoff[l]] * (c_inv_dfact[l] * eT) * sm1 : 0.0;   // c_{l,0} e^{-xi D^2} S(-1)
       }
       const int spmax = F.span[L];
       double win[WIN];
@@ -756,28 +769,31 @@ F12_DEV inline int family_eval(const Tables &T, const FamDev &F, double xi, doub
       // latter advanced by 1/2 per step (exact for integer and half-integer
       // alpha0, recomputed otherwise)
       const double hy = 0.5 * y;
-      double ha = 0.5 * (F.alpha0 + (double)(m0 + 1));
-      const bool ha_exact = F.pow_kind != 0;
+      // the k-dependence every order shares: Vk = e^{-xi D^2} v^k 2^{-E_k}, so
+      // that term_{l,k} = d_cser[l][k] Vk sum_j q_j J_{j+2k}
+      double Vk = eT;
       // convergence: the terms of the lowest and highest order fall below
       // 2^-56 of the largest term so far, twice (exponent comparisons)
       int emax_lo = 0, emax_hi = 0;
       int small = 0;
       const int kmin = (int)(0.5 * v) + 2;   // past the largest term (terms ~ z^k/k!)
       int k;
-      for (k = 0; k < KMAX; ++k) {
+      const int kcap = T.kcap > 0 && T.kcap < KMAX ? T.kcap : KMAX;
+      for (k = 0; k < kcap; ++k) {
         const int need = spmax - 1 + 2 * k;
         int hmax = 0;
         while (mfill <= need) {
+          // J_m = (y/2) J_{m-1} + ((alpha0 + m - 1)/2) J_{m-2}
+          const double ha = F.ha_tab ? d_quarter[F.ha_base + 2 * mfill] : 0.5 * (F.alpha0 + (double)(mfill - 1));
           const double jn = fma(hy, win[(mfill - 1) & (WIN - 1)], ha * win[(mfill - 2) & (WIN - 1)]);
           win[mfill & (WIN - 1)] = jn;
           hmax = max(hmax, hi_word(jn));
           ++mfill;
-          ha = ha_exact ? ha + 0.5 : 0.5 * (F.alpha0 + (double)(mfill - 1));
         }
         if (hmax > HI_2P600) {   // keep the window in range; exact power-of-two rescale
           for (int r = mfill - WIN; r < mfill; ++r)
             if (r >= 0) win[r & (WIN - 1)] *= MTWO600;
-          for (int l = ls; l <= L; ++l) common[l] *= TWO600;
+          Vk *= TWO600;
         }
         const int jlo = (F.fp_minus1 && k == 0) ? 1 : 0;
         int e_lo = 0, e_hi = 0;
@@ -786,22 +802,23 @@ F12_DEV inline int family_eval(const Tables &T, const FamDev &F, double xi, doub
           const int sp = F.span[l];
           double part = 0.0;
           for (int j = jlo; j < sp; ++j) part = fma(q[j], win[(j + 2 * k) & (WIN - 1)], part);
-          const double term = common[l] * part;
-          sum[l] += term;
-          if (l == ls) e_lo = exp_bits(term);
-          if (l == L) e_hi = exp_bits(term);
+          const double cv = d_cser[l][k] * Vk;
+          sum[l] = fma(cv, part, sum[l]);
+          // binary exponent of the term cv part (within one), 0 for a zero part
+          const int ep = exp_bits(part);
+          const int e = ep ? ep + exp_bits(cv) : 0;
+          if (l == ls) e_lo = e;
+          if (l == L) e_hi = e;
           nfma += sp - jlo + 2;
-          const double cr = k < KTAB ? c_cratio[l][k]
-                                     : (double)(k + l + 1) / ((double)(k + 1) * (2.0 * k + 2.0 * l + 2.0) * (2.0 * k + 2.0 * l + 3.0));
-          common[l] *= v * cr;
         }
+        Vk *= v * d_vstep[k];
         emax_lo = max(emax_lo, e_lo);
         emax_hi = max(emax_hi, e_hi);
         // (a zero or subnormal term counts as small)
-        small = ((e_lo + 56 < emax_lo || e_lo == 0) && (e_hi + 56 < emax_hi || e_hi == 0)) ? small + 1 : 0;
+        small = ((e_lo + 57 < emax_lo || e_lo == 0) && (e_hi + 57 < emax_hi || e_hi == 0)) ? small + 1 : 0;
         if (small >= 2 && k >= kmin) break;
       }
-      if (k == KMAX) bad = 1;
+      if (k == kcap) bad = 1;
       for (int l = ls; l <= L; ++l) out[l] += fct[l] * sum[l];
     }
   }

@@ -95,6 +95,9 @@ struct AuxConst {
   double inv_dfact[LAUX + 2];
   double kum_inv[2][NKUM];
   double sm1_ratio[NKUM];
+  double cser[LAUX + 1][KMAX];   // d_cser
+  double vstep[KMAX];            // d_vstep
+  double quarter[NQUARTER];      // d_quarter
 };
 
 inline void fill_aux_const(AuxConst &c) {
@@ -106,6 +109,35 @@ inline void fill_aux_const(AuxConst &c) {
       c.cratio[l][k] = (double)(k + l + 1) / ((double)(k + 1) * (2.0 * k + 2.0 * l + 2.0) * (2.0 * k + 2.0 * l + 3.0));
   c.inv_dfact[0] = 1.0;
   for (int l = 1; l < LAUX + 2; ++l) c.inv_dfact[l] = c.inv_dfact[l - 1] / (2.0 * l + 1.0);
+  {
+    // c_{l,k} as a long double mantissa times 2^ex (frexp after every step)
+    int E[KMAX];
+    long double m0 = 1.0L;   // c_{0,k} = m0 2^x0
+    int x0 = 0;
+    for (int k = 0; k < KMAX; ++k) {
+      int e = 0;
+      const long double f = std::frexp(m0, &e);   // c_{0,k} = f 2^{x0 + e}, f in [1/2, 1)
+      E[k] = -(x0 + e - 1);                        // c_{0,k} 2^{E_k} = 2 f in [1, 2)
+      m0 = f;
+      x0 += e;
+      m0 *= (long double)(k + 1) / ((long double)(k + 1) * (2.0L * k + 2.0L) * (2.0L * k + 3.0L));
+    }
+    for (int l = 0; l <= LAUX; ++l) {
+      long double m = 1.0L;   // c_{l,0} = 2^l l!/(2l+1)! = 1/(2l+1)!!
+      for (int i = 1; i <= l; ++i) m /= (2.0L * i + 1.0L);
+      int x = 0;
+      for (int k = 0; k < KMAX; ++k) {
+        int e = 0;
+        m = std::frexp(m, &e);
+        x += e;
+        c.cser[l][k] = (double)std::ldexp(m, x + E[k]);
+        m *= (long double)(k + l + 1) / ((long double)(k + 1) * (2.0L * k + 2.0L * l + 2.0L) * (2.0L * k + 2.0L * l + 3.0L));
+      }
+    }
+    for (int k = 0; k + 1 < KMAX; ++k) c.vstep[k] = std::ldexp(1.0, E[k] - E[k + 1]);
+    c.vstep[KMAX - 1] = 0.0;
+    for (int i = 0; i < NQUARTER; ++i) c.quarter[i] = 0.25 * i;
+  }
   for (int n = 0; n < NKUM; ++n) {
     c.kum_inv[0][n] = 1.0 / ((0.5 + n) * (n + 1.0));
     c.kum_inv[1][n] = 1.0 / ((1.5 + n) * (n + 1.0));
@@ -211,6 +243,8 @@ inline bool build_class_tables(const f12::TermList kernels[NCLASS], ClassTables 
       d.lead = 0;
       d.jtab = -1;
       d.jrow = 0;
+      d.ha_base = (int)std::lround(2.0 * d.alpha0) - 2;
+      d.ha_tab = (d.pow_kind != 0 && d.ha_base >= -4 && d.ha_base + 2 * (JMAX + 2 * KMAX) < NQUARTER) ? 1 : 0;
       double as = d.fp_minus1 ? 0.0 : d.alpha0;
       d.rho_start = std::exp(std::lgamma(0.5 * (as + 2.0)) - std::lgamma(0.5 * (as + 1.0)));
       f12::Family cur = fam0;

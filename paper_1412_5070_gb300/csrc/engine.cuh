@@ -383,8 +383,7 @@ static int engine_launch(f12int_ctx *ctx, Engine &E, const std::vector<EngineReq
         items.push_back(Item{n, bp.tier, bp.nsplit, bp.work});
         ++n;
       }
-      S.views[r] = PairView{B.d_pair_start, B.d_pp_p, B.d_pp_P, B.d_pp_ab, B.d_pp_eoff, B.d_epool, B.d_shell_l,
-                            B.nshell, B.prim_screen ? B.d_qprim[cls] : nullptr};
+      S.views[r] = pair_view(ctx, B, cls, B.prim_screen);
       S.outs[r] = R.out;
     }
     // working order: by tier, then decreasing work per task (the longest
@@ -691,7 +690,7 @@ int f12int_poll(f12int_ctx *ctx, uint64_t ticket, int64_t timeout_us, int *done)
         return rc;
       }
     }
-    if (std::chrono::steady_clock::now() >= deadline) return F12INT_OK;
+    if (std::chrono::steady_clock::now() >= deadline) return timeout_us > 0 ? F12INT_ETIMEOUT : F12INT_OK;
     std::this_thread::sleep_for(std::chrono::microseconds(20));
   }
 }

@@ -22,11 +22,14 @@
 #include <cstdio>
 #include <cstring>
 #include <deque>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <thread>
 #include <unordered_map>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/f12int.h"
 #include "aux.cuh"
@@ -66,18 +69,47 @@ struct PairView {
   const int *shell_l;
   int nshell;
   const double *qprim;       // [npp] primitive Schwarz factors of the class, or null
+  const double *grow;        // [ngrow] growth G(i kGrowStep) of the class's kernel, or null (no growth)
+  int ngrow;
 };
 
-// Primitive quartets whose Schwarz product is below this are skipped: the
-// skipped contributions stay below the absolute accuracy that elements just
-// above 1e-12 need for a relative error of 1e-10.
-__device__ __forceinline__ bool prim_negligible(const PairView &PV, int pab, int pcd) {
-  return PV.qprim && PV.qprim[pab] * PV.qprim[pcd] < 1e-26;
-}
+// Growth of a kernel with distance, tabulated at this step (screening).
+constexpr double kGrowStep = 0.05, kGrowMax = 120.0;
+constexpr double kPrimScreen = 1e-26;
 
 // X_PQ component k = Q - P = (H_cd - H_ab) + (offset_cd - offset_ab).
 __device__ __forceinline__ double pair_sep(const double *ppP, int pab, int pcd, int k) {
   return (ppP[6 * pcd + k] - ppP[6 * pab + k]) + (ppP[6 * pcd + 3 + k] - ppP[6 * pab + 3 + k]);
+}
+
+// Primitive quartets whose Schwarz product is below kPrimScreen are skipped:
+// the skipped contributions stay below the absolute accuracy that elements
+// just above 1e-12 need for a relative error of 1e-10.  The diagonal
+// integrals behind qprim sample the kernel at short range; a kernel that
+// grows with r (Eq. rs12 with B > 0: I2, I3 like e^{Br}, k4 = f f' and
+// k6 = f_r f'_r like e^{2Br}) is larger at the separation R = |P - Q| of the
+// two charge distributions, whose overlap e^{-xi w^2} reaches out to R + w.
+// A candidate is weighed, as the shell screen weighs a shell quartet, by
+//   Gamma = max over w = 0, 0.5, .., 3 (units of 1/sqrt(xi)) of G(R + w) e^{-xi w^2}
+// (e^{-xi w^2} = e^{-k^2/4} at the k-th sample).
+__device__ __forceinline__ bool prim_negligible(const PairView &PV, int pab, int pcd) {
+  if (!PV.qprim) return false;
+  const double v = PV.qprim[pab] * PV.qprim[pcd];
+  if (v >= kPrimScreen) return false;
+  if (!PV.grow) return true;
+  const double X = pair_sep(PV.pp_P, pab, pcd, 0), Y = pair_sep(PV.pp_P, pab, pcd, 1),
+               Z = pair_sep(PV.pp_P, pab, pcd, 2);
+  const double p = PV.pp_p[pab], q = PV.pp_p[pcd];
+  const double R = sqrt(X * X + Y * Y + Z * Z), hw = 0.5 * sqrt((p + q) / (p * q));
+  constexpr double kOverlap[7] = {1.0, 0.77880078307140487, 0.36787944117144233, 0.10539922456186433,
+                                  0.018315638888734179, 0.0019304541362277093, 0.00012340980408667956};
+  double gam = 0.0;
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    const int i = min(PV.ngrow - 1, (int)((R + k * hw) * (1.0 / kGrowStep)) + 1);
+    gam = fmax(gam, PV.grow[i] * kOverlap[k]);
+  }
+  return v * gam < kPrimScreen;
 }
 
 // ------------------------------------------------------------ pair builder --
@@ -793,6 +825,15 @@ struct f12int_ctx {
   // growth of each class's kernel with distance (screening estimate):
   // kgrow[cls][i] = G(i * kGrowStep), see screen_estimate
   std::vector<double> kgrow[7];
+  // the same tables on the device for the primitive screen ([7][kgrow_n]);
+  // grows[cls]: the kernel of cls grows (G > 1 somewhere)
+  double *d_kgrow = nullptr;
+  size_t kgrow_bytes = 0;
+  int kgrow_n = 0;
+  bool grows[7] = {false, false, false, false, false, false, false};
+  int series_cap = KMAX;   // f12int_set_series_cap
+  double plan_ms = 0.0;    // host planning of compute_class calls (f12int_host_stats)
+  int64_t plan_calls = 0;
   Engine *engine = nullptr;
 };
 
@@ -830,6 +871,31 @@ void dfree(f12int_ctx *ctx, T *&p, size_t bytes) {
 
 cudaStream_t pick_stream(f12int_ctx *ctx, void *s) { return s ? (cudaStream_t)s : ctx->stream; }
 
+// NVTX range over a host scope (the stages of a call, visible in a profiler's
+// timeline; free when no tool is attached)
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
+// The pair data of a basis as the kernels see it, for class cls: with the
+// primitive screen (its Schwarz factors and the kernel's growth table) when
+// screen is set and the factors exist.
+PairView pair_view(const f12int_ctx *ctx, const f12int_ctx::BasisData &B, int cls, bool screen) {
+  PairView v{B.d_pair_start, B.d_pp_p, B.d_pp_P, B.d_pp_ab, B.d_pp_eoff, B.d_epool, B.d_shell_l, B.nshell,
+             nullptr, nullptr, 0};
+  if (screen && B.d_qprim[cls]) {
+    v.qprim = B.d_qprim[cls];
+    if (ctx->grows[cls] && ctx->d_kgrow) {
+      v.grow = ctx->d_kgrow + (size_t)cls * ctx->kgrow_n;
+      v.ngrow = ctx->kgrow_n;
+    }
+  }
+  return v;
+}
+
 bool g_const_ready = false;
 std::mutex g_const_mu;
 
@@ -864,6 +930,9 @@ int upload_constants() {
   CK(cudaMemcpyToSymbol(c_inv_dfact, ac.inv_dfact, sizeof(ac.inv_dfact)));
   CK(cudaMemcpyToSymbol(d_kum_inv, ac.kum_inv, sizeof(ac.kum_inv)));
   CK(cudaMemcpyToSymbol(d_sm1_ratio, ac.sm1_ratio, sizeof(ac.sm1_ratio)));
+  CK(cudaMemcpyToSymbol(d_cser, ac.cser, sizeof(ac.cser)));
+  CK(cudaMemcpyToSymbol(d_vstep, ac.vstep, sizeof(ac.vstep)));
+  CK(cudaMemcpyToSymbol(d_quarter, ac.quarter, sizeof(ac.quarter)));
   CK(cudaMemcpyToSymbol(c_tuv, tuv, sizeof(tuv)));
   CK(cudaMemcpyToSymbol(c_cart, cart, sizeof(cart)));
   CK(cudaMemcpyToSymbol(c_gh_x, ac.gh_x, sizeof(ac.gh_x)));
@@ -966,6 +1035,7 @@ int f12int_destroy(f12int_ctx *ctx) {
   cudaFree(ctx->d_coef);
   cudaFree(ctx->d_grp);
   cudaFree(ctx->d_jtab);
+  cudaFree(ctx->d_kgrow);
   cudaFree(ctx->d_pqoff);
   cudaFree(ctx->d_keys);
   cudaFree(ctx->d_order);
@@ -1018,6 +1088,28 @@ int f12int_kernel_stats(f12int_ctx *ctx, int reset, double *stats) {
     ctx->aux_launches = ctx->contract_launches = 0;
     if (ctx->d_fma) CK(cudaMemset(ctx->d_fma, 0, sizeof(cnt)));
   }
+  return F12INT_OK;
+}
+
+int f12int_host_stats(f12int_ctx *ctx, int reset, double *stats) {
+  if (!ctx || !stats) return F12INT_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  stats[0] = ctx->plan_ms;
+  stats[1] = (double)ctx->plan_calls;
+  if (reset) {
+    ctx->plan_ms = 0.0;
+    ctx->plan_calls = 0;
+  }
+  return F12INT_OK;
+}
+
+int f12int_set_series_cap(f12int_ctx *ctx, int kmax) {
+  if (!ctx || kmax < 0) return F12INT_EINVAL;
+  if (!engine_idle(ctx)) return F12INT_EINVAL;   // submitted requests use the current tables
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  ctx->series_cap = kmax == 0 ? KMAX : std::min(kmax, KMAX);
+  ctx->tables.kcap = ctx->series_cap;
+  engine_factor_changed(ctx);
   return F12INT_OK;
 }
 
@@ -1126,8 +1218,6 @@ int f12int_kernel_radial_terms(int cls, const f12int_term *f, int nf, const f12i
 // at short range) carry a further factor 8; on the 12-atom s/p/d sample the
 // largest ratio of a quartet to its unscaled estimate was 55 (I5) and 49 (I6).
 constexpr double kScreenSafety[7] = {1.0, 1.0, 1.0, 1.0, 1.0, 8.0, 8.0};
-constexpr double kGrowStep = 0.05, kGrowMax = 120.0;
-
 static std::vector<double> growth_table(const f12::TermList &t) {
   auto kval = [&](double x) {
     double v = 0.0;
@@ -1216,6 +1306,7 @@ static int set_factor_lists(f12int_ctx *ctx, const f12::TermList &T1, const f12:
   T.coef = ctx->d_coef;
   T.grp = ctx->d_grp;
   T.jtab = ctx->d_jtab;
+  T.kcap = ctx->series_cap;
   ctx->tables = T;
   for (int c = 1; c <= 6; ++c) {
     ctx->cls_ok[c] = ct.supported[c];
@@ -1230,6 +1321,23 @@ static int set_factor_lists(f12int_ctx *ctx, const f12::TermList &T1, const f12:
   for (auto &b : ctx->bases)   // and so do the shell-pair bounds
     for (int c = 0; c < 7; ++c) b.pair_bound[c].clear();
   for (int c = 1; c <= 6; ++c) ctx->kgrow[c] = growth_table(kt[c == 5 ? 3 : c]);
+  {
+    dfree(ctx, ctx->d_kgrow, ctx->kgrow_bytes);
+    ctx->d_kgrow = nullptr;
+    ctx->kgrow_n = (int)ctx->kgrow[1].size();
+    std::vector<double> all((size_t)7 * ctx->kgrow_n, 1.0);
+    for (int c = 1; c <= 6; ++c) {
+      ctx->grows[c] = false;
+      for (int i = 0; i < ctx->kgrow_n; ++i) {
+        all[(size_t)c * ctx->kgrow_n + i] = ctx->kgrow[c][i];
+        ctx->grows[c] = ctx->grows[c] || ctx->kgrow[c][i] > 1.0;
+      }
+    }
+    ctx->kgrow_bytes = sizeof(double) * all.size();
+    rc = dalloc(ctx, &ctx->d_kgrow, ctx->kgrow_bytes);
+    if (rc != F12INT_OK) return rc;
+    CK(cudaMemcpy(ctx->d_kgrow, all.data(), ctx->kgrow_bytes, cudaMemcpyHostToDevice));
+  }
   engine_factor_changed(ctx);
   ctx->factor_ready = true;
   return F12INT_OK;
@@ -1515,8 +1623,7 @@ static int launch_chunk(f12int_ctx *ctx, const f12int_ctx::BasisData &B, int cls
                         const int64_t *d_pqoff, int64_t n, int64_t qa, int64_t qb, int64_t pqa, int64_t pqb,
                         size_t smem, double *out_dev, const int64_t *offsets_dev, cudaStream_t st,
                         bool prim_screen = true) {
-  PairView PV{B.d_pair_start, B.d_pp_p, B.d_pp_P, B.d_pp_ab, B.d_pp_eoff, B.d_epool, B.d_shell_l, B.nshell,
-              (B.prim_screen && prim_screen) ? B.d_qprim[cls] : nullptr};
+  PairView PV = pair_view(ctx, B, cls, B.prim_screen && prim_screen);
   QuartetView QV{d_quartets, d_pqoff, n, nullptr, nullptr, nullptr, nullptr};
   const int kcls = cls == 5 ? 3 : cls;
   const int nf = ctx->tables.nfam[kcls];
@@ -1749,6 +1856,9 @@ static int compute_class_impl(f12int_ctx *ctx, int basis_id, int cls, const int3
   CK(cudaSetDevice(ctx->device));
   const f12int_ctx::BasisData &B = ctx->bases[basis_id];
   cudaStream_t st = pick_stream(ctx, cuda_stream);
+  NvtxRange call_range("f12int.compute_class");
+  const auto t_plan0 = std::chrono::steady_clock::now();
+  std::unique_ptr<NvtxRange> plan_range(new NvtxRange("f12int.plan"));
   // quartet metadata: order by (la, lb, lc, ld), primitive-quartet offsets
   std::vector<int32_t> hq0((size_t)4 * n);
   std::vector<int64_t> ho0((size_t)n);
@@ -1763,62 +1873,89 @@ static int compute_class_impl(f12int_ctx *ctx, int basis_id, int cls, const int3
       if (s[k] < 0 || s[k] >= ns) return F12INT_EINVAL;
     key0[i] = (B.l[s[0]] << 6) | (B.l[s[1]] << 4) | (B.l[s[2]] << 2) | B.l[s[3]];
   }
-  std::vector<int64_t> perm((size_t)n);
-  for (int64_t i = 0; i < n; ++i) perm[i] = i;
-  // decreasing shared-memory need, then decreasing work per task (long
-  // blocks first), then by class key; plans are memoised per (key, number of
-  // primitive quartets)
-  std::vector<size_t> sm0((size_t)n);
-  std::vector<int> nw0((size_t)n), sp0((size_t)n);
-  std::vector<double> wk0((size_t)n);
-  std::vector<char> f320((size_t)n, 0);
-  struct PlanMemo {
+  // Every quartet with the same (primitive quartets, FP32 or not, class key)
+  // has the same plan: the distinct ones ("plan groups") are planned once,
+  // ordered -- FP64 first, decreasing shared-memory need (a tier launches
+  // with the need of its first quartet, so no later one may need more),
+  // decreasing work per task (the longest blocks start first), class key --
+  // and the quartets are placed group by group in their list order (a
+  // counting sort: linear in n).
+  struct PlanGroup {
     ContractPlan pl;
     double work;
-    bool set;
+    int64_t key;
+    int64_t count, first;
   };
-  std::unordered_map<int64_t, PlanMemo> memo;
-  const std::vector<double> *pb = fp32_below > 0.0 ? &B.pair_bound[cls == 5 ? 3 : cls] : nullptr;
-  for (int64_t i = 0; i < n; ++i) {
-    const int k = key0[i];
-    const int32_t *s = &hq0[4 * i];
-    const int64_t np = (int64_t)B.nprim[s[0]] * B.nprim[s[1]] * B.nprim[s[2]] * B.nprim[s[3]];
-    // mixed path: FP32 Hermite recursion and contraction below the bound
-    if (pb && screen_estimate(ctx, B, cls, s[0], s[1], s[2], s[3]) < fp32_below) f320[i] = 1;
-    PlanMemo &m = memo[(np << 9) | (f320[i] << 8) | k];
-    if (!m.set) {
-      const int la = (k >> 6) & 3, lb = (k >> 4) & 3, lc = (k >> 2) & 3, ld = k & 3;
-      m.pl = contract_plan(la, lb, lc, ld, cls, np, f320[i] ? 4 : 8);
-      const int ncd = ncart(lc) * ncart(ld);
-      m.work = (double)np * task_flops(la, lb, lc, ld, cls, (ncd + m.pl.nsplit - 1) / m.pl.nsplit);
-      m.set = true;
+  std::vector<PlanGroup> groups;
+  std::vector<int32_t> gid((size_t)n);
+  {
+    // open-addressing map from the group key to its index
+    std::vector<int64_t> slot_key(4096, -1);
+    std::vector<int32_t> slot_val(4096, -1);
+    size_t mask = slot_key.size() - 1;
+    const std::vector<double> *pb = fp32_below > 0.0 ? &B.pair_bound[cls == 5 ? 3 : cls] : nullptr;
+    for (int64_t i = 0; i < n; ++i) {
+      const int k = key0[i];
+      const int32_t *s = &hq0[4 * i];
+      const int64_t np = (int64_t)B.nprim[s[0]] * B.nprim[s[1]] * B.nprim[s[2]] * B.nprim[s[3]];
+      // mixed path: FP32 Hermite recursion and contraction below the bound
+      const int f32 = (pb && screen_estimate(ctx, B, cls, s[0], s[1], s[2], s[3]) < fp32_below) ? 1 : 0;
+      const int64_t gk = (np << 9) | (f32 << 8) | k;
+      size_t h = (size_t)((uint64_t)gk * 0x9E3779B97F4A7C15ull >> 40) & mask;
+      while (slot_key[h] != -1 && slot_key[h] != gk) h = (h + 1) & mask;
+      if (slot_key[h] == -1) {
+        if (groups.size() * 2 >= slot_key.size()) {   // grow and rehash
+          std::vector<int64_t> nk(slot_key.size() * 2, -1);
+          std::vector<int32_t> nv(slot_key.size() * 2, -1);
+          const size_t nm = nk.size() - 1;
+          for (size_t t = 0; t < slot_key.size(); ++t)
+            if (slot_key[t] != -1) {
+              size_t g = (size_t)((uint64_t)slot_key[t] * 0x9E3779B97F4A7C15ull >> 40) & nm;
+              while (nk[g] != -1) g = (g + 1) & nm;
+              nk[g] = slot_key[t];
+              nv[g] = slot_val[t];
+            }
+          slot_key.swap(nk);
+          slot_val.swap(nv);
+          mask = nm;
+          h = (size_t)((uint64_t)gk * 0x9E3779B97F4A7C15ull >> 40) & mask;
+          while (slot_key[h] != -1 && slot_key[h] != gk) h = (h + 1) & mask;
+        }
+        const int la = (k >> 6) & 3, lb = (k >> 4) & 3, lc = (k >> 2) & 3, ld = k & 3;
+        PlanGroup g{};
+        g.pl = contract_plan(la, lb, lc, ld, cls, np, f32 ? 4 : 8);
+        if (g.pl.smem == 0) return F12INT_EINVAL;
+        const int ncd = ncart(lc) * ncart(ld);
+        g.work = (double)np * task_flops(la, lb, lc, ld, cls, (ncd + g.pl.nsplit - 1) / g.pl.nsplit);
+        g.key = gk;
+        slot_key[h] = gk;
+        slot_val[h] = (int32_t)groups.size();
+        groups.push_back(g);
+      }
+      const int32_t g = slot_val[h];
+      gid[i] = g;
+      groups[g].count++;
     }
-    if (m.pl.smem == 0) return F12INT_EINVAL;
-    nw0[i] = m.pl.nw;
-    sp0[i] = m.pl.nsplit;
-    sm0[i] = m.pl.smem;
-    wk0[i] = m.work;
   }
   {
-    // one 64-bit key per quartet: shared memory (desc), work (desc, as the
-    // order-preserving bits of a positive double), then the class key
-    std::vector<std::pair<uint64_t, uint64_t>> sk((size_t)n);
-    for (int64_t i = 0; i < n; ++i) {
-      uint64_t wb;
-      float wf = (float)wk0[i];
-      uint32_t fb;
-      std::memcpy(&fb, &wf, sizeof fb);
-      wb = fb;
-      // FP64 quartets first; exact shared memory (4-byte units, < 2^23): a
-      // tier launches with the need of its first quartet, so no later one
-      // may need more
-      const uint64_t hi = ((uint64_t)f320[i] << 63) | ((uint64_t)(0x7FFFFF - (sm0[i] >> 2)) << 40) |
-                          ((uint64_t)(0xFFFFFFFFu - (uint32_t)wb) << 8) | (uint64_t)key0[i];
-      sk[i] = {hi, (uint64_t)i};
+    std::vector<int32_t> order(groups.size());
+    for (size_t g = 0; g < groups.size(); ++g) order[g] = (int32_t)g;
+    std::sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+      const PlanGroup &A = groups[x], &Bg = groups[y];
+      const int fa = (int)((A.key >> 8) & 1), fb = (int)((Bg.key >> 8) & 1);
+      if (fa != fb) return fa < fb;
+      if (A.pl.smem != Bg.pl.smem) return A.pl.smem > Bg.pl.smem;
+      if (A.work != Bg.work) return A.work > Bg.work;
+      return (A.key & 0xFF) < (Bg.key & 0xFF) || ((A.key & 0xFF) == (Bg.key & 0xFF) && A.key < Bg.key);
+    });
+    int64_t run = 0;
+    for (int32_t g : order) {
+      groups[g].first = run;
+      run += groups[g].count;
     }
-    std::sort(sk.begin(), sk.end());
-    for (int64_t i = 0; i < n; ++i) perm[i] = (int64_t)sk[i].second;
   }
+  std::vector<int64_t> perm((size_t)n);
+  for (int64_t i = 0; i < n; ++i) perm[groups[gid[i]].first++] = i;
   std::vector<int32_t> hq((size_t)4 * n);
   std::vector<int64_t> ho((size_t)n);
   ctx->h_nw.resize((size_t)n);
@@ -1826,12 +1963,14 @@ static int compute_class_impl(f12int_ctx *ctx, int basis_id, int cls, const int3
   ctx->h_smem.resize((size_t)n);
   ctx->h_fp32.resize((size_t)n);
   for (int64_t i = 0; i < n; ++i) {
-    for (int k = 0; k < 4; ++k) hq[4 * i + k] = hq0[4 * perm[i] + k];
-    ho[i] = ho0[perm[i]];
-    ctx->h_nw[i] = nw0[perm[i]];
-    ctx->h_split[i] = sp0[perm[i]];
-    ctx->h_smem[i] = sm0[perm[i]];
-    ctx->h_fp32[i] = f320[perm[i]];
+    const int64_t j = perm[i];
+    for (int k = 0; k < 4; ++k) hq[4 * i + k] = hq0[4 * j + k];
+    ho[i] = ho0[j];
+    const PlanGroup &g = groups[gid[j]];
+    ctx->h_nw[i] = g.pl.nw;
+    ctx->h_split[i] = g.pl.nsplit;
+    ctx->h_smem[i] = g.pl.smem;
+    ctx->h_fp32[i] = (char)((g.key >> 8) & 1);
   }
   std::vector<int64_t> pqoff((size_t)n + 1);
   int64_t npq = 0;
@@ -1854,6 +1993,9 @@ static int compute_class_impl(f12int_ctx *ctx, int basis_id, int cls, const int3
   const int kcls = cls == 5 ? 3 : cls;
   const int64_t nf = ctx->tables.nfam[kcls];
   const int64_t pq_chunk = std::max<int64_t>(1, kItemChunk / std::max<int64_t>(nf, 1));
+  plan_range.reset();
+  ctx->plan_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_plan0).count();
+  ctx->plan_calls++;
   for (int64_t qa = 0; qa < n;) {
     int64_t qb = qa + 1;
     while (qb < n && pqoff[qb + 1] - pqoff[qa] <= pq_chunk) ++qb;
@@ -2150,8 +2292,7 @@ extern "C" int f12int_compute_class_static(f12int_ctx *ctx, int basis_id, int cl
   // the primitive screen of f12int_compute_class when its table for this
   // (basis, class) exists already (building it would allocate); without it
   // every primitive quartet is evaluated
-  PairView PV{B.d_pair_start, B.d_pp_p, B.d_pp_P, B.d_pp_ab, B.d_pp_eoff, B.d_epool, B.d_shell_l, B.nshell,
-              B.prim_screen ? B.d_qprim[cls] : nullptr};
+  PairView PV = pair_view(ctx, B, cls, B.prim_screen);
   QuartetView QV{d_q, d_pq, n, nullptr, nullptr, nullptr, nullptr};
   int rc_launch = F12INT_OK;
   for (int64_t qa = 0; qa < n && rc_launch == F12INT_OK;) {

@@ -18,6 +18,7 @@ import numpy as np
 from . import build as _build
 
 F12INT_I1, F12INT_I2, F12INT_I3, F12INT_I4, F12INT_I5, F12INT_I6 = 1, 2, 3, 4, 5, 6
+OK, EINVAL, ENOMEM, EDOMAIN, ENOTREADY, ETIMEOUT, ECUDA, EDEVICE = 0, -1, -2, -3, -4, -5, -6, -7
 STATUS = {0: "F12INT_OK", -1: "F12INT_EINVAL", -2: "F12INT_ENOMEM", -3: "F12INT_EDOMAIN",
           -4: "F12INT_ENOTREADY", -5: "F12INT_ETIMEOUT", -6: "F12INT_ECUDA", -7: "F12INT_EDEVICE"}
 
@@ -28,7 +29,7 @@ EXPORTS = ("f12int_create", "f12int_destroy", "f12int_set_basis", "f12int_set_fa
            "f12int_device_status", "f12int_set_timing", "f12int_kernel_stats", "f12int_kernel_radial",
            "f12int_submit", "f12int_poll", "f12int_batch_limits", "f12int_batch_autotune", "f12int_batch_stats",
            "f12int_set_fp32_below", "f12int_pair_bounds", "f12int_quartet_estimates",
-           "f12int_strerror")
+           "f12int_measure_peak", "f12int_host_stats", "f12int_set_series_cap", "f12int_strerror")
 
 
 class F12IntError(RuntimeError):
@@ -115,6 +116,9 @@ def load():
                                            ctypes.c_int64, _dp]
     L.f12int_batch_autotune.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int32), ctypes.c_int64,
                                         ctypes.c_uint32, _dp]
+    L.f12int_measure_peak.argtypes = [ctypes.c_int, ctypes.c_int, _dp]
+    L.f12int_host_stats.argtypes = [_vp, ctypes.c_int, _dp]
+    L.f12int_set_series_cap.argtypes = [_vp, ctypes.c_int]
     L.f12int_strerror.argtypes = [ctypes.c_int]
     L.f12int_strerror.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -323,10 +327,21 @@ def f12int_submit(ctx, basis_id: int, quartets, classes, out_dev, offsets, schwa
 
 def f12int_poll(ctx, ticket: int, timeout_us: int = 0) -> bool:
     """True once the request has finished (its status is checked: a failed
-    request raises F12IntError); False while it is queued or running."""
+    request raises F12IntError); False while it is queued or running (the
+    library's F12INT_ETIMEOUT of a wait that ran out)."""
     done = ctypes.c_int(0)
-    _check(load().f12int_poll(ctx, ctypes.c_uint64(ticket), int(timeout_us), ctypes.byref(done)), "f12int_poll")
+    rc = load().f12int_poll(ctx, ctypes.c_uint64(ticket), int(timeout_us), ctypes.byref(done))
+    if rc == ETIMEOUT and not done.value:
+        return False
+    _check(rc, "f12int_poll")
     return bool(done.value)
+
+
+def f12int_poll_status(ctx, ticket: int, timeout_us: int = 0):
+    """(status, done) exactly as the C call returns them."""
+    done = ctypes.c_int(0)
+    rc = load().f12int_poll(ctx, ctypes.c_uint64(ticket), int(timeout_us), ctypes.byref(done))
+    return rc, bool(done.value)
 
 
 def f12int_batch_limits(ctx, max_quartets: int, max_items: int) -> None:
@@ -372,3 +387,28 @@ def f12int_quartet_estimates(ctx, basis_id: int, cls: int, quartets) -> np.ndarr
                                            q.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), len(q),
                                            out.ctypes.data_as(_dp)), "f12int_quartet_estimates")
     return out
+
+
+PEAK_KINDS = {"fp64_fma": 0, "fp64_mma_m8n8k4": 1, "fp64_mma_m16n8k4": 2, "fp64_mma_m16n8k16": 3, "fp32_fma": 4}
+
+
+def f12int_measure_peak(device: int, kind) -> float:
+    """Measured peak of one instruction kind on a device, TFLOP/s (kind: a key
+    of PEAK_KINDS or its number)."""
+    k = PEAK_KINDS[kind] if isinstance(kind, str) else int(kind)
+    v = ctypes.c_double(0.0)
+    _check(load().f12int_measure_peak(int(device), k, ctypes.byref(v)), "f12int_measure_peak")
+    return v.value
+
+
+def f12int_host_stats(ctx, reset: bool = False) -> dict:
+    """Host planning time of f12int_compute_class calls: {"plan_ms", "calls"}."""
+    st = (ctypes.c_double * 2)()
+    _check(load().f12int_host_stats(ctx, 1 if reset else 0, st), "f12int_host_stats")
+    return {"plan_ms": st[0], "calls": int(st[1])}
+
+
+def f12int_set_series_cap(ctx, kmax: int) -> None:
+    """Cap on the auxiliary series length (0 restores the default); a series
+    that reaches it sets the device status word (F12INT_EDEVICE)."""
+    _check(load().f12int_set_series_cap(ctx, int(kmax)), "f12int_set_series_cap")

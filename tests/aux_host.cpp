@@ -30,6 +30,9 @@ void load_constants() {
   std::memcpy(c_inv_dfact, ac.inv_dfact, sizeof(ac.inv_dfact));
   std::memcpy(d_kum_inv, ac.kum_inv, sizeof(ac.kum_inv));
   std::memcpy(d_sm1_ratio, ac.sm1_ratio, sizeof(ac.sm1_ratio));
+  std::memcpy(d_cser, ac.cser, sizeof(ac.cser));
+  std::memcpy(d_vstep, ac.vstep, sizeof(ac.vstep));
+  std::memcpy(d_quarter, ac.quarter, sizeof(ac.quarter));
   done = true;
 }
 
