@@ -226,21 +226,22 @@ static int engine_capture(f12int_ctx *ctx, Engine &E) {
       k_items_scatter<<<E.classify_blocks, BLOCK_AUX, 0, bs>>>(QV, nf, 0, E.keys[cls], E.hist[cls], 0,
                                                                E.order[cls]);
       k_items_eval<true><<<std::max(1, E.items_blocks / E.items_div[cls]), BLOCK_AUX, 0, bs>>>(
-          ctx->tables, none, QV, cls, 0, 0, E.order[cls],
+          ctx->tables, none, QV, cls, 0, 0, E.order[cls], E.keys[cls],
                                                                E.part[cls], E.status, nullptr);
       if (ctx->cls_quad[cls])   // families evaluated by quadrature (b < 0, alpha0 < -1)
         k_items_eval<true, true><<<E.quad_blocks, BLOCK_AUX, 0, bs>>>(ctx->tables, none, QV, cls, 0, 0,
-                                                                       E.order[cls], E.part[cls], E.status, nullptr);
+                                                                       E.order[cls], E.keys[cls], E.part[cls],
+                                                                       E.status, nullptr);
       for (int t = 0; t < kLaunches; ++t) {
         const int tt = t % kTiers;
         if (t < kTiers)
           k_contract<true, double><<<E.tier_blocks[t], 32 * kTierWarps[tt], kTierCap[tt], bs>>>(
-              none, QV, cls, nf, 0, L.tasks, 0, L.counts + 2 + 2 * t, E.part[cls], nullptr, L.offsets, E.status,
-              nullptr);
+              none, QV, cls, nf, 0, L.tasks, 0, L.counts + 2 + 2 * t, E.keys[cls], E.part[cls], nullptr, L.offsets,
+              E.status, nullptr);
         else
           k_contract<true, float><<<E.tier_blocks[t], 32 * kTierWarps[tt], kTierCap[tt], bs>>>(
-              none, QV, cls, nf, 0, L.tasks, 0, L.counts + 2 + 2 * t, E.part[cls], nullptr, L.offsets, E.status,
-              nullptr);
+              none, QV, cls, nf, 0, L.tasks, 0, L.counts + 2 + 2 * t, E.keys[cls], E.part[cls], nullptr, L.offsets,
+              E.status, nullptr);
       }
       cudaEventRecord(join[cls], bs);
       cudaStreamWaitEvent(cs, join[cls], 0);

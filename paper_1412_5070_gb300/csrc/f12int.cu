@@ -362,8 +362,11 @@ __global__ void k_items_scatter(QuartetView QV, int nf, int64_t pq0, const int *
 // when the factor has such families.
 template <bool BATCH, bool QUAD>
 __device__ __forceinline__ unsigned long long items_eval_one(Tables T, PairView PV, QuartetView QV, int cls,
-                                                             int64_t pq0, int64_t it, double *part,
+                                                             int64_t pq0, int64_t it, const int *keys, double *part,
                                                              unsigned int *status) {
+  // a primitive quartet the screen dropped (decided once, by the classify
+  // pass) is never read by the contraction
+  if (keys[it] == SKIP_KEY) return 0;
   const int kcls = cls == 5 ? 3 : cls;
   const int nf = T.nfam[kcls];
   const int64_t pq = pq0 + it / nf;
@@ -371,7 +374,6 @@ __device__ __forceinline__ unsigned long long items_eval_one(Tables T, PairView 
   const FamDev &F = T.fam[T.fam0[kcls] + f];
   if ((F.quad != 0) != QUAD) return 0;   // the other launch's family
   ItemGeom g = item_geometry<BATCH>(PV, QV, cls, pq);
-  if (prim_negligible(*g.pv, g.iab, g.icd)) return 0;   // never read by the contraction
   if (g.L > LAUX) {
     atomicOr(status, 4u);
     return 0;
@@ -388,16 +390,16 @@ __device__ __forceinline__ unsigned long long items_eval_one(Tables T, PairView 
 
 template <bool BATCH, bool QUAD = false>
 __global__ void k_items_eval(Tables T, PairView PV, QuartetView QV, int cls, int64_t pq0, int64_t nitems,
-                             const unsigned int *order, double *part, unsigned int *status,
+                             const unsigned int *order, const int *keys, double *part, unsigned int *status,
                              unsigned long long *fma_total) {
   unsigned long long nfma = 0;
   if constexpr (BATCH) {
     const int64_t nit = item_count(QV, T.nfam[cls == 5 ? 3 : cls], pq0, nitems);
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nit; t += (int64_t)gridDim.x * blockDim.x)
-      nfma += items_eval_one<BATCH, QUAD>(T, PV, QV, cls, pq0, order[t], part, status);
+      nfma += items_eval_one<BATCH, QUAD>(T, PV, QV, cls, pq0, order[t], keys, part, status);
   } else {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t < nitems) nfma = items_eval_one<BATCH, QUAD>(T, PV, QV, cls, pq0, order[t], part, status);
+    if (t < nitems) nfma = items_eval_one<BATCH, QUAD>(T, PV, QV, cls, pq0, order[t], keys, part, status);
   }
   // warp-aggregated count of the core multiply-adds (series terms and quadrature nodes)
   if (fma_total) {
@@ -484,7 +486,8 @@ __device__ __forceinline__ float tfma(float a, float b, float c) { return fmaf(a
 // (double, or float on the mixed path); g_n are always summed in double.
 template <bool BATCH, class T>
 __device__ __forceinline__ void contract_task(const PairView &PV0, const QuartetView &QV, int cls, int nf,
-                                              int64_t pq0, const CTask task, const double *part, double *out,
+                                              int64_t pq0, const CTask task, const int *keys, const double *part,
+                                              double *out,
                                               const int64_t *offsets, unsigned long long *flops_total,
                                               T *smem, int *off_ab, int *off_cd) {
   const int64_t q = task.q;
@@ -571,9 +574,9 @@ __device__ __forceinline__ void contract_task(const PairView &PV0, const Quartet
     __syncwarp();
     for (int icd = warp; icd < npcd; icd += nw) {
       const int pcd = cd0 + icd;
-      if (prim_negligible(PV, pab, pcd)) continue;   // warp-uniform
-      ++nproc;
       const int64_t pq = QV.pq_off[q] + (int64_t)iab * npcd + icd - pq0;
+      if (keys[pq * nf] == SKIP_KEY) continue;   // dropped by the primitive screen; warp-uniform
+      ++nproc;
       const T X = (T)pair_sep(PV.pp_P, pab, pcd, 0), Y = (T)pair_sep(PV.pp_P, pab, pcd, 1),
                    Z = (T)pair_sep(PV.pp_P, pab, pcd, 2);
       // g_n = sqrt(pi^5/(p+q))/(pq) * sum over families (fixed order)
@@ -728,10 +731,201 @@ __device__ __forceinline__ void contract_task(const PairView &PV0, const Quartet
   }
 }
 
+// ---------------------------------------------------- thin contraction --
+// Quartets of low total order (L = la+lb+lc+ld <= kThinL, classes other than
+// I5, FP64): the block has at most 9 elements and R at most 10 values, so one
+// warp takes a whole shell quartet and each lane one primitive quartet at a
+// time (the general kernel would keep 31 of 32 lanes idle on an (ss|ss)
+// quartet).  A lane forms g_n, R_tuv and the E products in registers and
+// accumulates every element of the block (Eq. ii, bra sign (-1)^{t+u+v});
+// the lanes' sums are then added by a fixed butterfly, so the result does not
+// depend on scheduling.
+constexpr int kThinL = 2;
+constexpr int kThinWarps = 4;
+
+__host__ __device__ constexpr int cart_i(int l, int k) {   // x exponent of component k of shell l
+  int n = 0;
+  for (int i = l; i >= 0; --i)
+    for (int j = l - i; j >= 0; --j, ++n)
+      if (n == k) return i;
+  return 0;
+}
+__host__ __device__ constexpr int cart_j(int l, int k) {   // y exponent
+  int n = 0;
+  for (int i = l; i >= 0; --i)
+    for (int j = l - i; j >= 0; --j, ++n)
+      if (n == k) return j;
+  return 0;
+}
+
+template <int LA, int LB, int LC, int LD>
+__global__ void __launch_bounds__(32 * kThinWarps)
+k_contract_thin(PairView PV, QuartetView QV, int nf, int64_t pq0, const CTask *tasks, int64_t ntask,
+                const int *keys, const double *part, double *out, const int64_t *offsets,
+                unsigned long long *flops_total) {
+  constexpr int L = LA + LB + LC + LD;
+  constexpr int NA = (LA + 1) * (LA + 2) / 2, NB = (LB + 1) * (LB + 2) / 2;
+  constexpr int NC = (LC + 1) * (LC + 2) / 2, ND = (LD + 1) * (LD + 2) / 2;
+  constexpr int NE = NA * NB * NC * ND;
+  constexpr int NTAB = LA + LB + 1, NTCD = LC + LD + 1;
+  constexpr int N1AB = (LA + 1) * (LB + 1) * NTAB, N1CD = (LC + 1) * (LD + 1) * NTCD;
+  constexpr int NH = (L + 1) * (L + 2) * (L + 3) / 6;
+  const int lane = threadIdx.x & 31;
+  const int64_t task = (int64_t)blockIdx.x * kThinWarps + (threadIdx.x >> 5);
+  if (task >= ntask) return;   // warp-uniform
+  const int64_t q = tasks[task].q;
+  const int32_t *s = QV.quartets + 4 * q;
+  const int ns = PV.nshell;
+  const int ab = s[0] * ns + s[1], cd = s[2] * ns + s[3];
+  const int ab0 = PV.pair_start[ab], npab = PV.pair_start[ab + 1] - ab0;
+  const int cd0 = PV.pair_start[cd], npcd = PV.pair_start[cd + 1] - cd0;
+  const int np = npab * npcd;
+  const double pi52 = 17.493418327624862846;  // pi^{5/2}
+  double O[NE];
+#pragma unroll
+  for (int i = 0; i < NE; ++i) O[i] = 0.0;
+  unsigned nproc = 0;
+  for (int r = lane; r < np; r += 32) {
+    const int iab = r / npcd, icd = r - iab * npcd;
+    const int pab = ab0 + iab, pcd = cd0 + icd;
+    const int64_t pq = QV.pq_off[q] + r - pq0;
+    if (keys[pq * nf] == SKIP_KEY) continue;   // dropped by the primitive screen
+    ++nproc;
+    // g_n = sqrt(pi^5/(p+q))/(pq) * sum over families (fixed order)
+    const double p = PV.pp_p[pab], qq = PV.pp_p[pcd];
+    const double pref = pi52 / (sqrt(p + qq) * p * qq);
+    double g[L + 1];
+#pragma unroll
+    for (int n = 0; n <= L; ++n) g[n] = 0.0;
+    for (int f = 0; f < nf; ++f) {
+      const double *pp = part + (pq * nf + f) * (LAUX + 1);
+#pragma unroll
+      for (int n = 0; n <= L; ++n) g[n] += pp[n];
+    }
+#pragma unroll
+    for (int n = 0; n <= L; ++n) g[n] *= pref;
+    const double X = pair_sep(PV.pp_P, pab, pcd, 0), Y = pair_sep(PV.pp_P, pab, pcd, 1),
+                 Z = pair_sep(PV.pp_P, pab, pcd, 2);
+    // Hermite recursion, levels n = L .. 0, in registers (every index is a
+    // compile-time constant after unrolling)
+    double R[NH], Rn[NH];
+    R[0] = g[L];
+#pragma unroll
+    for (int n = L - 1; n >= 0; --n) {
+#pragma unroll
+      for (int S = 0; S <= L - n; ++S)
+#pragma unroll
+        for (int t = S; t >= 0; --t)
+#pragma unroll
+          for (int v = 0; v <= S - t; ++v) {
+            const int u = S - t - v;
+            double val;
+            if (S == 0) val = g[n];
+            else if (t > 0) val = X * R[hidx(t - 1, u, v)] + (t > 1 ? (t - 1) * R[hidx(t - 2, u, v)] : 0.0);
+            else if (u > 0) val = Y * R[hidx(t, u - 1, v)] + (u > 1 ? (u - 1) * R[hidx(t, u - 2, v)] : 0.0);
+            else val = Z * R[hidx(t, u, v - 1)] + (v > 1 ? (v - 1) * R[hidx(t, u, v - 2)] : 0.0);
+            Rn[hidx(t, u, v)] = val;
+          }
+#pragma unroll
+      for (int i = 0; i < NH; ++i) R[i] = Rn[i];
+    }
+    const double *Eab = PV.epool + PV.pp_eoff[pab];
+    const double *Ecd = PV.epool + PV.pp_eoff[pcd];
+#pragma unroll
+    for (int ia = 0; ia < NA; ++ia)
+#pragma unroll
+      for (int ib = 0; ib < NB; ++ib)
+#pragma unroll
+        for (int ic = 0; ic < NC; ++ic)
+#pragma unroll
+          for (int id = 0; id < ND; ++id) {
+            const int ax = cart_i(LA, ia), ay = cart_j(LA, ia), az = LA - ax - ay;
+            const int bx = cart_i(LB, ib), by = cart_j(LB, ib), bz = LB - bx - by;
+            const int cx = cart_i(LC, ic), cy = cart_j(LC, ic), cz = LC - cx - cy;
+            const int dx = cart_i(LD, id), dy = cart_j(LD, id), dz = LD - dx - dy;
+            const double *ex = Eab + (ax * (LB + 1) + bx) * NTAB;
+            const double *ey = Eab + N1AB + (ay * (LB + 1) + by) * NTAB;
+            const double *ez = Eab + 2 * N1AB + (az * (LB + 1) + bz) * NTAB;
+            const double *fx = Ecd + (cx * (LD + 1) + dx) * NTCD;
+            const double *fy = Ecd + N1CD + (cy * (LD + 1) + dy) * NTCD;
+            const double *fz = Ecd + 2 * N1CD + (cz * (LD + 1) + dz) * NTCD;
+            double acc = 0.0;
+#pragma unroll
+            for (int t = 0; t <= ax + bx; ++t)
+#pragma unroll
+              for (int u = 0; u <= ay + by; ++u)
+#pragma unroll
+                for (int v = 0; v <= az + bz; ++v) {
+                  double w = 0.0;
+#pragma unroll
+                  for (int t2 = 0; t2 <= cx + dx; ++t2)
+#pragma unroll
+                    for (int u2 = 0; u2 <= cy + dy; ++u2)
+#pragma unroll
+                      for (int v2 = 0; v2 <= cz + dz; ++v2)
+                        w = fma(fx[t2] * fy[u2] * fz[v2], R[hidx(t + t2, u + u2, v + v2)], w);
+                  const double e = ex[t] * ey[u] * ez[v];
+                  acc = fma((t + u + v) & 1 ? -e : e, w, acc);
+                }
+            const int idx = ((ia * NB + ib) * NC + ic) * ND + id;
+            O[idx] += acc;
+          }
+  }
+  // the lanes' sums, by a fixed butterfly (every lane ends with the total)
+#pragma unroll
+  for (int i = 0; i < NE; ++i) {
+    double v = O[i];
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    O[i] = v;
+  }
+  if (lane == 0) {
+    double *o = out + offsets[q];
+#pragma unroll
+    for (int i = 0; i < NE; ++i) o[i] = O[i];
+  }
+  if (flops_total) {
+    // the same algorithmic count per primitive quartet as the general kernel
+    unsigned tot = nproc;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    if (lane == 0 && tot) {
+      const unsigned long long r = 2ull * (L + 1) * (L + 2) * (L + 3) * (L + 4) / 24;
+      const unsigned long long ket = 2ull * nh_count(LA + LB) * nh_count(LC + LD) * (NC * ND);
+      const unsigned long long bra = 2ull * (NA * NB) * nh_count(LA + LB) * (NC * ND);
+      atomicAdd(flops_total, (unsigned long long)tot * (r + ket + bra));
+    }
+  }
+}
+
+// Class key (la << 6 | lb << 4 | lc << 2 | ld) of a thin quartet -> launch of its instance.
+using ThinKernel = void (*)(PairView, QuartetView, int, int64_t, const CTask *, int64_t, const int *, const double *,
+                            double *, const int64_t *, unsigned long long *);
+template <int K>
+constexpr ThinKernel thin_entry() {
+  return &k_contract_thin<(K >> 6) & 3, (K >> 4) & 3, (K >> 2) & 3, K & 3>;
+}
+__host__ inline ThinKernel thin_kernel(int key) {
+  switch (key) {
+#define F12_THIN(K) \
+  case K: return thin_entry<K>();
+    // every (la, lb, lc, ld) with la + lb + lc + ld <= 2
+    F12_THIN(0x00) F12_THIN(0x01) F12_THIN(0x04) F12_THIN(0x10) F12_THIN(0x40)
+    F12_THIN(0x02) F12_THIN(0x08) F12_THIN(0x20) F12_THIN(0x80)
+    F12_THIN(0x05) F12_THIN(0x11) F12_THIN(0x41) F12_THIN(0x14) F12_THIN(0x44) F12_THIN(0x50)
+#undef F12_THIN
+    default: return nullptr;
+  }
+}
+__host__ __device__ inline bool thin_quartet(int key, int cls, bool fp32) {
+  const int L = ((key >> 6) & 3) + ((key >> 4) & 3) + ((key >> 2) & 3) + (key & 3);
+  return !fp32 && cls != 5 && L <= kThinL;
+}
+
 template <bool BATCH, class T>
 __global__ void __launch_bounds__(BLOCK_CONTRACT)
 k_contract(PairView PV0, QuartetView QV, int cls, int nf, int64_t pq0, const CTask *tasks, int64_t ntask,
-           const int64_t *ntask_dev, const double *part, double *out, const int64_t *offsets,
+           const int64_t *ntask_dev, const int *keys, const double *part, double *out, const int64_t *offsets,
            unsigned int *status, unsigned long long *flops_total) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *smem = reinterpret_cast<T *>(smem_raw);
@@ -741,12 +935,13 @@ k_contract(PairView PV0, QuartetView QV, int cls, int nf, int64_t pq0, const CTa
     const int64_t te = ntask_dev[1];
     for (int64_t tk = ntask_dev[0] + blockIdx.x; tk < te; tk += gridDim.x) {
       __syncthreads();   // the previous task's shared-memory reads are done
-      contract_task<BATCH, T>(PV0, QV, cls, nf, pq0, tasks[tk], part, out, offsets, flops_total, smem, off_ab, off_cd);
+      contract_task<BATCH, T>(PV0, QV, cls, nf, pq0, tasks[tk], keys, part, out, offsets, flops_total, smem, off_ab,
+                              off_cd);
     }
   } else {
     if (blockIdx.x < ntask)
-      contract_task<BATCH, T>(PV0, QV, cls, nf, pq0, tasks[blockIdx.x], part, out, offsets, flops_total, smem, off_ab,
-                           off_cd);
+      contract_task<BATCH, T>(PV0, QV, cls, nf, pq0, tasks[blockIdx.x], keys, part, out, offsets, flops_total, smem,
+                              off_ab, off_cd);
   }
 }
 // Derivation note for I5: with d/dA_x = (a/p) d/dP_x + d/dAB_x and
@@ -818,6 +1013,7 @@ struct f12int_ctx {
   std::vector<int> h_split;    // ket-component ranges (blocks) per quartet, same order
   std::vector<char> h_fp32;    // 1: Hermite recursion and contraction in FP32 (mixed path), same order
   std::vector<size_t> h_smem;  // contraction shared memory, per quartet in the working order
+  std::vector<int16_t> h_thin; // class key of a quartet for k_contract_thin, -1: the general kernel; same order
   std::mutex mu;
   std::recursive_mutex bounds_mu;   // first-time primitive and shell-pair bounds
   bool cls_ok[7] = {false, false, false, false, false, false, false};   // classes the factor supports
@@ -1646,11 +1842,11 @@ static int launch_chunk(f12int_ctx *ctx, const f12int_ctx::BasisData &B, int cls
       ev = take_events(ctx);
       cudaEventRecord(ev.first, st);
     }
-    k_items_eval<false><<<nb, BLOCK_AUX, 0, st>>>(ctx->tables, PV, QV, cls, pqa, nitems, ctx->d_order, ctx->d_part,
-                                           ctx->d_status, ctx->timing ? ctx->d_fma : nullptr);
+    k_items_eval<false><<<nb, BLOCK_AUX, 0, st>>>(ctx->tables, PV, QV, cls, pqa, nitems, ctx->d_order, ctx->d_keys,
+                                                  ctx->d_part, ctx->d_status, ctx->timing ? ctx->d_fma : nullptr);
     if (ctx->cls_quad[cls]) {
       k_items_eval<false, true><<<nb, BLOCK_AUX, 0, st>>>(ctx->tables, PV, QV, cls, pqa, nitems, ctx->d_order,
-                                                          ctx->d_part, ctx->d_status,
+                                                          ctx->d_keys, ctx->d_part, ctx->d_status,
                                                           ctx->timing ? ctx->d_fma : nullptr);
       ctx->launches++;
     }
@@ -1674,12 +1870,15 @@ static int launch_chunk(f12int_ctx *ctx, const f12int_ctx::BasisData &B, int cls
     CK(cudaMemcpyAsync(ctx->d_tasks, tasks.data(), sizeof(CTask) * tasks.size(), cudaMemcpyHostToDevice, st));
   }
   int64_t t0 = 0;
-  for (int64_t ra = qa; ra < qb;) {
+  // the thin quartets are a suffix of the working order
+  int64_t qthin = qb;
+  while (qthin > qa && ctx->h_thin[qthin - 1] >= 0) --qthin;
+  for (int64_t ra = qa; ra < qthin;) {
     const int nw = ctx->h_nw[ra];
     const char f32 = ctx->h_fp32[ra];
     const size_t sm0 = ctx->h_smem[ra];
     int64_t rb = ra + 1, nt = ctx->h_split[ra];
-    while (rb < qb && ctx->h_nw[rb] == nw && ctx->h_fp32[rb] == f32 && 2 * ctx->h_smem[rb] > sm0)
+    while (rb < qthin && ctx->h_nw[rb] == nw && ctx->h_fp32[rb] == f32 && 2 * ctx->h_smem[rb] > sm0)
       nt += ctx->h_split[rb++];
     std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
     if (ctx->timing) {
@@ -1690,15 +1889,43 @@ static int launch_chunk(f12int_ctx *ctx, const f12int_ctx::BasisData &B, int cls
       if (sm0 > 48 * 1024)
         CK(cudaFuncSetAttribute(k_contract<false, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm0));
       k_contract<false, float><<<(unsigned)nt, 32 * nw, sm0, st>>>(
-          PV, QV, cls, nf, pqa, ctx->d_tasks + t0, nt, nullptr, ctx->d_part, out_dev, offsets_dev, ctx->d_status,
+          PV, QV, cls, nf, pqa, ctx->d_tasks + t0, nt, nullptr, ctx->d_keys, ctx->d_part, out_dev, offsets_dev,
+          ctx->d_status,
           ctx->timing ? ctx->d_fma + 1 : nullptr);
     } else {
       if (sm0 > 48 * 1024)
         CK(cudaFuncSetAttribute(k_contract<false, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm0));
       k_contract<false, double><<<(unsigned)nt, 32 * nw, sm0, st>>>(
-          PV, QV, cls, nf, pqa, ctx->d_tasks + t0, nt, nullptr, ctx->d_part, out_dev, offsets_dev, ctx->d_status,
+          PV, QV, cls, nf, pqa, ctx->d_tasks + t0, nt, nullptr, ctx->d_keys, ctx->d_part, out_dev, offsets_dev,
+          ctx->d_status,
           ctx->timing ? ctx->d_fma + 1 : nullptr);
     }
+    t0 += nt;
+    if (ctx->timing) {
+      cudaEventRecord(ev.second, st);
+      ctx->ev_con.push_back(ev);
+      ctx->contract_launches++;
+    }
+    ctx->launches++;
+    CK(cudaGetLastError());
+    ra = rb;
+  }
+  // thin quartets: one launch per (la, lb, lc, ld), one warp per quartet
+  for (int64_t ra = qthin; ra < qb;) {
+    const int key = ctx->h_thin[ra];
+    int64_t rb = ra + 1;
+    while (rb < qb && ctx->h_thin[rb] == key) ++rb;
+    const int64_t nt = rb - ra;   // one task each
+    const ThinKernel kern = thin_kernel(key);
+    if (!kern) return F12INT_EINVAL;
+    std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+    if (ctx->timing) {
+      ev = take_events(ctx);
+      cudaEventRecord(ev.first, st);
+    }
+    kern<<<(unsigned)((nt + kThinWarps - 1) / kThinWarps), 32 * kThinWarps, 0, st>>>(
+        PV, QV, nf, pqa, ctx->d_tasks + t0, nt, ctx->d_keys, ctx->d_part, out_dev, offsets_dev,
+        ctx->timing ? ctx->d_fma + 1 : nullptr);
     t0 += nt;
     if (ctx->timing) {
       cudaEventRecord(ev.second, st);
@@ -1885,6 +2112,7 @@ static int compute_class_impl(f12int_ctx *ctx, int basis_id, int cls, const int3
     double work;
     int64_t key;
     int64_t count, first;
+    bool thin;   // contracted by k_contract_thin
   };
   std::vector<PlanGroup> groups;
   std::vector<int32_t> gid((size_t)n);
@@ -1925,6 +2153,8 @@ static int compute_class_impl(f12int_ctx *ctx, int basis_id, int cls, const int3
         PlanGroup g{};
         g.pl = contract_plan(la, lb, lc, ld, cls, np, f32 ? 4 : 8);
         if (g.pl.smem == 0) return F12INT_EINVAL;
+        g.thin = thin_quartet(k, cls, f32 != 0);
+        if (g.thin) g.pl = ContractPlan{1, 1, 0};   // one warp of the thin kernel, no shared memory
         const int ncd = ncart(lc) * ncart(ld);
         g.work = (double)np * task_flops(la, lb, lc, ld, cls, (ncd + g.pl.nsplit - 1) / g.pl.nsplit);
         g.key = gk;
@@ -1942,6 +2172,8 @@ static int compute_class_impl(f12int_ctx *ctx, int basis_id, int cls, const int3
     for (size_t g = 0; g < groups.size(); ++g) order[g] = (int32_t)g;
     std::sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
       const PlanGroup &A = groups[x], &Bg = groups[y];
+      if (A.thin != Bg.thin) return Bg.thin;   // the thin quartets last, by class key
+      if (A.thin) return (A.key & 0xFF) < (Bg.key & 0xFF) || ((A.key & 0xFF) == (Bg.key & 0xFF) && A.key < Bg.key);
       const int fa = (int)((A.key >> 8) & 1), fb = (int)((Bg.key >> 8) & 1);
       if (fa != fb) return fa < fb;
       if (A.pl.smem != Bg.pl.smem) return A.pl.smem > Bg.pl.smem;
@@ -1962,6 +2194,7 @@ static int compute_class_impl(f12int_ctx *ctx, int basis_id, int cls, const int3
   ctx->h_split.resize((size_t)n);
   ctx->h_smem.resize((size_t)n);
   ctx->h_fp32.resize((size_t)n);
+  ctx->h_thin.resize((size_t)n);
   for (int64_t i = 0; i < n; ++i) {
     const int64_t j = perm[i];
     for (int k = 0; k < 4; ++k) hq[4 * i + k] = hq0[4 * j + k];
@@ -1971,6 +2204,7 @@ static int compute_class_impl(f12int_ctx *ctx, int basis_id, int cls, const int3
     ctx->h_split[i] = g.pl.nsplit;
     ctx->h_smem[i] = g.pl.smem;
     ctx->h_fp32[i] = (char)((g.key >> 8) & 1);
+    ctx->h_thin[i] = g.thin ? (int16_t)(g.key & 0xFF) : (int16_t)-1;
   }
   std::vector<int64_t> pqoff((size_t)n + 1);
   int64_t npq = 0;
@@ -2236,6 +2470,11 @@ extern "C" int f12int_compute_class_static(f12int_ctx *ctx, int basis_id, int cl
     nw0[i] = pl.nw;
     sp0[i] = pl.nsplit;
     sm0[i] = pl.smem;
+    if (thin_quartet(key0[i], cls, false)) {   // k_contract_thin: sorted last (no shared memory), by key
+      nw0[i] = 1;
+      sp0[i] = 1;
+      sm0[i] = 0;
+    }
   }
   std::vector<int64_t> perm((size_t)n);
   for (int64_t i = 0; i < n; ++i) perm[i] = i;
@@ -2314,12 +2553,12 @@ extern "C" int f12int_compute_class_static(f12int_ctx *ctx, int basis_id, int cl
       k_items_classify<false><<<nbq, BLOCK_AUX, 0, st>>>(ctx->tables, PV, QV, cls, pqa, nitems, d_keys, d_hist);
       k_items_scan<<<1, 1024, 0, st>>>(d_hist, kNKeys);
       k_items_scatter<<<nb, BLOCK_AUX, 0, st>>>(QV, nf, pqa, d_keys, d_hist, nitems, d_order);
-      k_items_eval<false><<<nb, BLOCK_AUX, 0, st>>>(ctx->tables, PV, QV, cls, pqa, nitems, d_order, d_part, ctx->d_status,
-                                             nullptr);
+      k_items_eval<false><<<nb, BLOCK_AUX, 0, st>>>(ctx->tables, PV, QV, cls, pqa, nitems, d_order, d_keys, d_part,
+                                                    ctx->d_status, nullptr);
       ctx->launches += 4;
       if (ctx->cls_quad[cls]) {
-        k_items_eval<false, true><<<nb, BLOCK_AUX, 0, st>>>(ctx->tables, PV, QV, cls, pqa, nitems, d_order, d_part,
-                                                            ctx->d_status, nullptr);
+        k_items_eval<false, true><<<nb, BLOCK_AUX, 0, st>>>(ctx->tables, PV, QV, cls, pqa, nitems, d_order, d_keys,
+                                                            d_part, ctx->d_status, nullptr);
         ctx->launches++;
       }
       if (cudaGetLastError() != cudaSuccess) rc_launch = F12INT_ECUDA;
@@ -2328,6 +2567,26 @@ extern "C" int f12int_compute_class_static(f12int_ctx *ctx, int basis_id, int cl
       const int nwr = hnw[ra];
       const size_t smr = hsm[ra];
       int64_t rb = ra + 1;
+      if (smr == 0) {   // thin quartets: one launch per class key
+        const int key = (B.l[hq[4 * ra]] << 6) | (B.l[hq[4 * ra + 1]] << 4) | (B.l[hq[4 * ra + 2]] << 2) |
+                        B.l[hq[4 * ra + 3]];
+        auto key_of = [&](int64_t i) {
+          return (B.l[hq[4 * i]] << 6) | (B.l[hq[4 * i + 1]] << 4) | (B.l[hq[4 * i + 2]] << 2) | B.l[hq[4 * i + 3]];
+        };
+        while (rb < qb && hsm[rb] == 0 && key_of(rb) == key) ++rb;
+        const int64_t nt = tfirst[rb] - tfirst[ra];
+        const ThinKernel kern = thin_kernel(key);
+        if (!kern) {
+          rc_launch = F12INT_EINVAL;
+          break;
+        }
+        kern<<<(unsigned)((nt + kThinWarps - 1) / kThinWarps), 32 * kThinWarps, 0, st>>>(
+            PV, QV, nf, pqa, d_tk + tfirst[ra], nt, d_keys, d_part, out_dev, d_o, nullptr);
+        ctx->launches++;
+        if (cudaGetLastError() != cudaSuccess) rc_launch = F12INT_ECUDA;
+        ra = rb;
+        continue;
+      }
       while (rb < qb && hnw[rb] == nwr && 2 * hsm[rb] > smr) ++rb;
       const int64_t nt = tfirst[rb] - tfirst[ra];
       if (smr > 48 * 1024 &&
@@ -2336,8 +2595,8 @@ extern "C" int f12int_compute_class_static(f12int_ctx *ctx, int basis_id, int cl
         rc_launch = F12INT_ECUDA;
         break;
       }
-      k_contract<false, double><<<(unsigned)nt, 32 * nwr, smr, st>>>(PV, QV, cls, nf, pqa, d_tk + tfirst[ra], nt, nullptr, d_part,
-                                                     out_dev, d_o, ctx->d_status, nullptr);
+      k_contract<false, double><<<(unsigned)nt, 32 * nwr, smr, st>>>(PV, QV, cls, nf, pqa, d_tk + tfirst[ra], nt, nullptr,
+                                                                     d_keys, d_part, out_dev, d_o, ctx->d_status, nullptr);
       ctx->launches++;
       if (cudaGetLastError() != cudaSuccess) rc_launch = F12INT_ECUDA;
       ra = rb;
