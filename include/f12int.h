@@ -207,7 +207,9 @@ int f12int_compute_class(f12int_ctx *ctx, int basis_id, int cls, const int32_t *
  * bound product (as in f12int_screen) is below fp32_below run the Hermite
  * recursion and the contraction in FP32 with FP32 accumulation; the
  * auxiliary functions g_n, the shell-pair data and every other quartet stay
- * FP64.  fp32_below = 0 is f12int_compute_class.  Meant for quartets whose
+ * FP64, and so do the quartets of total angular momentum <= 3 (<= 2 for I5),
+ * whose one-lane-per-primitive-quartet FP64 contraction is faster than the
+ * FP32 form of the general one.  fp32_below = 0 is f12int_compute_class.  Meant for quartets whose
  * blocks are small in absolute terms: the error is bounded by about 1e-7
  * times the magnitude of the terms an element sums, not relative to the
  * element.  The first call of a (basis, class) computes its shell-pair
@@ -295,7 +297,10 @@ typedef struct {
  * buffers (see f12int_batch_limits) and starts the worker.
  * Errors: F12INT_EINVAL for bad arguments (shell index out of range, empty or
  * unknown class mask, precision not 0 or 1), F12INT_ENOTREADY without basis or
- * factor, F12INT_ENOMEM when the request alone exceeds one batch (split it). */
+ * factor, F12INT_ENOMEM when the request alone exceeds one batch (split it)
+ * or when the first request of a (basis, class) would need more device
+ * memory for that class's bounds than is free on the device at submit (or
+ * than the context's budget leaves): admission by free device memory. */
 int f12int_submit(f12int_ctx *ctx, int basis_id, const f12int_request *req, uint64_t *ticket);
 
 /* Wait at most timeout_us microseconds (0: do not wait) for a request.

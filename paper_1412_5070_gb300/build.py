@@ -14,8 +14,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libf12int.so")
-SOURCES = [os.path.join(CSRC, "f12int.cu"), os.path.join(CSRC, "peak.cu"), os.path.join(CSRC, "termlist.cpp")]
-DEPS = SOURCES + [os.path.join(CSRC, f) for f in ("aux.cuh", "auxtab.h", "engine.cuh", "termlist.h")] + \
+SOURCES = [os.path.join(CSRC, f) for f in ("f12int.cu", "thin_l2.cu", "thin_l3.cu", "thin_i5.cu", "peak.cu",
+                                            "termlist.cpp")]
+DEPS = SOURCES + [os.path.join(CSRC, f) for f in ("aux.cuh", "auxtab.h", "engine.cuh", "termlist.h",
+                                                  "kernel_common.cuh", "thin.cuh")] + \
     [os.path.join(os.path.dirname(HERE), "include", "f12int.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -35,15 +37,37 @@ def up_to_date() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
+    """Compile every source to an object in parallel (one nvcc process each),
+    then link the shared library."""
     if not force and up_to_date():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
-    tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [nvcc_path(), "-O3", "-lineinfo", "-std=c++17", *ARCH, "-Xcompiler", "-fPIC", "-shared",
-           "-o", tmp, *SOURCES, "-lcudart", *extra]
+    nvcc = nvcc_path()
+    tag = ".tmp%d" % os.getpid()
+    objs, procs = [], []
+    for src in SOURCES:
+        obj = os.path.join(BUILD, os.path.basename(src) + tag + ".o")
+        cmd = [nvcc, "-O3", "-lineinfo", "-std=c++17", *ARCH, "-Xcompiler", "-fPIC", "-c", "-o", obj, src, *extra]
+        if verbose:
+            print(" ".join(cmd), file=sys.stderr)
+        objs.append(obj)
+        procs.append((cmd, subprocess.Popen(cmd)))
+    failed = [cmd for cmd, p in procs if p.wait() != 0]
+    if failed:
+        for o in objs:
+            if os.path.exists(o):
+                os.remove(o)
+        raise subprocess.CalledProcessError(1, failed[0])
+    tmp = LIB + tag
+    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
     if verbose:
         print(" ".join(cmd), file=sys.stderr)
-    subprocess.run(cmd, check=True)
+    try:
+        subprocess.run(cmd, check=True)
+    finally:
+        for o in objs:
+            if os.path.exists(o):
+                os.remove(o)
     os.replace(tmp, LIB)
     return LIB
 

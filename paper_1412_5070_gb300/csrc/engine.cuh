@@ -576,6 +576,29 @@ int f12int_batch_limits(f12int_ctx *ctx, int64_t max_quartets, int64_t max_items
   return F12INT_OK;
 }
 
+// Device memory the one-time primitive bounds of (basis, class) take at most:
+// the per-primitive basis's pair data (E and F tables of every primitive
+// pair), the diagonal blocks of every primitive pair and the work items of
+// one call over them (the buffers of ensure_prim_bounds).
+static size_t prim_bounds_bytes(const f12int_ctx *ctx, const f12int_ctx::BasisData &B, int cls) {
+  std::vector<int> lp;
+  for (int s = 0; s < B.nshell; ++s)
+    for (int k = 0; k < B.nprim[s]; ++k) lp.push_back(B.l[s]);
+  const size_t np = lp.size();
+  size_t pair_data = 0, diag = 0;
+  for (size_t a = 0; a < np; ++a)
+    for (size_t b = 0; b <= a; ++b) {
+      const size_t la = (size_t)lp[a], lb = (size_t)lp[b];
+      pair_data += 2 * (6 * (la + 1) * (lb + 1) * (la + lb + 1) + 16) * sizeof(double);
+      const size_t nab = (size_t)ncart((int)la) * ncart((int)lb);
+      diag += nab * nab * sizeof(double) + 3 * sizeof(int64_t) + 4 * sizeof(int32_t);
+    }
+  const size_t npairs = np * (np + 1) / 2;
+  const size_t nf = (size_t)std::max(1, ctx->tables.nfam[cls == 5 ? 3 : cls]);
+  const size_t items = npairs * nf * (sizeof(int) + sizeof(unsigned) + sizeof(double) * (LAUX + 1));
+  return pair_data + diag + items;
+}
+
 int f12int_submit(f12int_ctx *ctx, int basis_id, const f12int_request *req, uint64_t *ticket) {
   if (!ctx || !req || !ticket) return F12INT_EINVAL;
   if (basis_id < 0 || basis_id >= (int)ctx->bases.size() || !ctx->factor_ready) return F12INT_ENOTREADY;
@@ -622,6 +645,18 @@ int f12int_submit(f12int_ctx *ctx, int basis_id, const f12int_request *req, uint
         return F12INT_EINVAL;
       }
       R->tasks[c] += bp.nsplit;
+    }
+    // admission by free device memory: the one-time bounds allocate, so a
+    // request whose bounds would not fit in what is free now (or in the
+    // context's budget) is refused before anything is allocated
+    if (B.prim_screen && !B.d_qprim[c]) {
+      size_t free_b = 0, total_b = 0;
+      const size_t need = prim_bounds_bytes(ctx, B, c);
+      if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess &&
+          (need > free_b || (ctx->budget && ctx->used + need > ctx->budget))) {
+        delete R;
+        return F12INT_ENOMEM;
+      }
     }
     int rc = ensure_prim_bounds(ctx, basis_id, c);
     if (rc == F12INT_OK && (R->thresh > 0.0 || R->precision == 1)) rc = ensure_pair_bounds(ctx, basis_id, c);

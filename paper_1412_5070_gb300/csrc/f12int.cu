@@ -33,10 +33,12 @@
 
 #include "../../include/f12int.h"
 #include "aux.cuh"
+#include "kernel_common.cuh"
 #include "auxtab.h"
 #include "termlist.h"
 
 using namespace f12dev;
+using namespace f12k;
 
 namespace {
 
@@ -48,39 +50,16 @@ constexpr int BLOCK_AUX = 64;
 __constant__ unsigned char c_tuv[NHMAX][3];   // Hermite index -> (t, u, v)
 __constant__ unsigned char c_cart[LSH + 3][28][3];  // shell l (<= 5) -> component exponents
 
-__host__ __device__ __forceinline__ int nh_count(int L) { return (L + 1) * (L + 2) * (L + 3) / 6; }
-__host__ __device__ __forceinline__ int ncart(int l) { return (l + 1) * (l + 2) / 2; }
-__host__ __device__ __forceinline__ int hidx(int t, int u, int v) {
-  int s = t + u + v, w = s - t;
-  return s * (s + 1) * (s + 2) / 6 + w * (w + 1) / 2 + v;
-}
 
 // ---------------------------------------------------------------------------
 // device status word bits: 1 = an auxiliary series hit its length cap,
 // 4 = a quartet needs a radial order above LAUX
 
-struct PairView {
-  const int *pair_start;     // [nshell*nshell + 1] first primitive pair of shell pair (i,j)
-  const double *pp_p;        // exponent sum p
-  const double *pp_P;        // [6*npp] centre P as heavy centre H (3) + offset P - H (3)
-  const double *pp_ab;       // [2*npp] exponents a, b
-  const int64_t *pp_eoff;    // offset into epool of this primitive pair's tables
-  const double *epool;       // E (3 dims) then F (3 dims), each (la+1)(lb+1)(la+lb+1)
-  const int *shell_l;
-  int nshell;
-  const double *qprim;       // [npp] primitive Schwarz factors of the class, or null
-  const double *grow;        // [ngrow] growth G(i kGrowStep) of the class's kernel, or null (no growth)
-  int ngrow;
-};
 
 // Growth of a kernel with distance, tabulated at this step (screening).
 constexpr double kGrowStep = 0.05, kGrowMax = 120.0;
 constexpr double kPrimScreen = 1e-26;
 
-// X_PQ component k = Q - P = (H_cd - H_ab) + (offset_cd - offset_ab).
-__device__ __forceinline__ double pair_sep(const double *ppP, int pab, int pcd, int k) {
-  return (ppP[6 * pcd + k] - ppP[6 * pab + k]) + (ppP[6 * pcd + 3 + k] - ppP[6 * pab + 3 + k]);
-}
 
 // Primitive quartets whose Schwarz product is below kPrimScreen are skipped:
 // the skipped contributions stay below the absolute accuracy that elements
@@ -200,21 +179,6 @@ __global__ void k_build_pairs(int npp, const int *pp_shell_a, const int *pp_shel
 }
 
 // ------------------------------------------------------------------- aux --
-// A list of shell quartets.  In a batch (qslot != null) every quartet names a
-// slot, which gives the pair data of its basis and the output array of its
-// request; counts then live in device memory (count_dev[0] quartets,
-// count_dev[1] primitive quartets), so one captured launch sequence serves
-// every batch.
-struct QuartetView {
-  const int32_t *quartets;     // [n][4]
-  const int64_t *pq_off;       // [n+1] first primitive quartet of each shell quartet
-  int64_t n;
-  const int64_t *count_dev;    // batch: {n, pq_off[n]} on the device, else null
-  const int32_t *qslot;        // batch: slot of each quartet, else null
-  const PairView *slot_view;   // batch: pair data per slot
-  double *const *slot_out;     // batch: output array per slot
-};
-
 __device__ __forceinline__ int64_t qv_count(const QuartetView &QV) { return QV.count_dev ? QV.count_dev[0] : QV.n; }
 
 // Pair data of quartet q: the kernel's own view, or the slot's in a batch
@@ -226,12 +190,6 @@ __device__ __forceinline__ const PairView &qv_view(const PairView &PV, const Qua
   else return PV;
 }
 
-// One block of contraction work: quartet q (index into the list), ket range
-// split of nsplit.
-struct CTask {
-  int32_t q;
-  int16_t split, nsplit;
-};
 
 __device__ __forceinline__ int64_t find_quartet(const int64_t *off, int64_t n, int64_t pq) {
   int64_t lo = 0, hi = n - 1;
@@ -274,7 +232,9 @@ __device__ __forceinline__ ItemGeom item_geometry(const PairView &PV0, const Qua
 }
 
 __device__ __forceinline__ int item_key(int f, int L, int bin) { return (f * (LAUX + 1) + L) * NZBIN + bin; }
-constexpr int SKIP_KEY = MAXFAM * (LAUX + 1) * NZBIN;   // last key: negligible primitive quartets
+constexpr int SKIP_KEY = kSkipKey;   // last key: negligible primitive quartets
+static_assert(kSkipKey == MAXFAM * (LAUX + 1) * NZBIN, "the skip key follows the item keys");
+static_assert(kLaux == LAUX, "one highest radial order");
 
 // Pass 1: key of every item and a histogram of the keys.
 // Items of a list: (pq_off[n] - pq0) * nf, from the device counts in a batch.
@@ -729,197 +689,6 @@ __device__ __forceinline__ void contract_task(const PairView &PV0, const Quartet
     const unsigned long long bra = 2ull * nab * nh_count(lab) * ncd * (cls == 5 ? 4 : 1);
     atomicAdd(flops_total, nproc * (r + ket + bra));
   }
-}
-
-// ---------------------------------------------------- thin contraction --
-// Quartets of low total order (L = la+lb+lc+ld <= kThinL, classes other than
-// I5, FP64): the block has at most 9 elements and R at most 10 values, so one
-// warp takes a whole shell quartet and each lane one primitive quartet at a
-// time (the general kernel would keep 31 of 32 lanes idle on an (ss|ss)
-// quartet).  A lane forms g_n, R_tuv and the E products in registers and
-// accumulates every element of the block (Eq. ii, bra sign (-1)^{t+u+v});
-// the lanes' sums are then added by a fixed butterfly, so the result does not
-// depend on scheduling.
-constexpr int kThinL = 2;
-constexpr int kThinWarps = 4;
-
-__host__ __device__ constexpr int cart_i(int l, int k) {   // x exponent of component k of shell l
-  int n = 0;
-  for (int i = l; i >= 0; --i)
-    for (int j = l - i; j >= 0; --j, ++n)
-      if (n == k) return i;
-  return 0;
-}
-__host__ __device__ constexpr int cart_j(int l, int k) {   // y exponent
-  int n = 0;
-  for (int i = l; i >= 0; --i)
-    for (int j = l - i; j >= 0; --j, ++n)
-      if (n == k) return j;
-  return 0;
-}
-
-template <int LA, int LB, int LC, int LD>
-__global__ void __launch_bounds__(32 * kThinWarps)
-k_contract_thin(PairView PV, QuartetView QV, int nf, int64_t pq0, const CTask *tasks, int64_t ntask,
-                const int *keys, const double *part, double *out, const int64_t *offsets,
-                unsigned long long *flops_total) {
-  constexpr int L = LA + LB + LC + LD;
-  constexpr int NA = (LA + 1) * (LA + 2) / 2, NB = (LB + 1) * (LB + 2) / 2;
-  constexpr int NC = (LC + 1) * (LC + 2) / 2, ND = (LD + 1) * (LD + 2) / 2;
-  constexpr int NE = NA * NB * NC * ND;
-  constexpr int NTAB = LA + LB + 1, NTCD = LC + LD + 1;
-  constexpr int N1AB = (LA + 1) * (LB + 1) * NTAB, N1CD = (LC + 1) * (LD + 1) * NTCD;
-  constexpr int NH = (L + 1) * (L + 2) * (L + 3) / 6;
-  const int lane = threadIdx.x & 31;
-  const int64_t task = (int64_t)blockIdx.x * kThinWarps + (threadIdx.x >> 5);
-  if (task >= ntask) return;   // warp-uniform
-  const int64_t q = tasks[task].q;
-  const int32_t *s = QV.quartets + 4 * q;
-  const int ns = PV.nshell;
-  const int ab = s[0] * ns + s[1], cd = s[2] * ns + s[3];
-  const int ab0 = PV.pair_start[ab], npab = PV.pair_start[ab + 1] - ab0;
-  const int cd0 = PV.pair_start[cd], npcd = PV.pair_start[cd + 1] - cd0;
-  const int np = npab * npcd;
-  const double pi52 = 17.493418327624862846;  // pi^{5/2}
-  double O[NE];
-#pragma unroll
-  for (int i = 0; i < NE; ++i) O[i] = 0.0;
-  unsigned nproc = 0;
-  for (int r = lane; r < np; r += 32) {
-    const int iab = r / npcd, icd = r - iab * npcd;
-    const int pab = ab0 + iab, pcd = cd0 + icd;
-    const int64_t pq = QV.pq_off[q] + r - pq0;
-    if (keys[pq * nf] == SKIP_KEY) continue;   // dropped by the primitive screen
-    ++nproc;
-    // g_n = sqrt(pi^5/(p+q))/(pq) * sum over families (fixed order)
-    const double p = PV.pp_p[pab], qq = PV.pp_p[pcd];
-    const double pref = pi52 / (sqrt(p + qq) * p * qq);
-    double g[L + 1];
-#pragma unroll
-    for (int n = 0; n <= L; ++n) g[n] = 0.0;
-    for (int f = 0; f < nf; ++f) {
-      const double *pp = part + (pq * nf + f) * (LAUX + 1);
-#pragma unroll
-      for (int n = 0; n <= L; ++n) g[n] += pp[n];
-    }
-#pragma unroll
-    for (int n = 0; n <= L; ++n) g[n] *= pref;
-    const double X = pair_sep(PV.pp_P, pab, pcd, 0), Y = pair_sep(PV.pp_P, pab, pcd, 1),
-                 Z = pair_sep(PV.pp_P, pab, pcd, 2);
-    // Hermite recursion, levels n = L .. 0, in registers (every index is a
-    // compile-time constant after unrolling)
-    double R[NH], Rn[NH];
-    R[0] = g[L];
-#pragma unroll
-    for (int n = L - 1; n >= 0; --n) {
-#pragma unroll
-      for (int S = 0; S <= L - n; ++S)
-#pragma unroll
-        for (int t = S; t >= 0; --t)
-#pragma unroll
-          for (int v = 0; v <= S - t; ++v) {
-            const int u = S - t - v;
-            double val;
-            if (S == 0) val = g[n];
-            else if (t > 0) val = X * R[hidx(t - 1, u, v)] + (t > 1 ? (t - 1) * R[hidx(t - 2, u, v)] : 0.0);
-            else if (u > 0) val = Y * R[hidx(t, u - 1, v)] + (u > 1 ? (u - 1) * R[hidx(t, u - 2, v)] : 0.0);
-            else val = Z * R[hidx(t, u, v - 1)] + (v > 1 ? (v - 1) * R[hidx(t, u, v - 2)] : 0.0);
-            Rn[hidx(t, u, v)] = val;
-          }
-#pragma unroll
-      for (int i = 0; i < NH; ++i) R[i] = Rn[i];
-    }
-    const double *Eab = PV.epool + PV.pp_eoff[pab];
-    const double *Ecd = PV.epool + PV.pp_eoff[pcd];
-#pragma unroll
-    for (int ia = 0; ia < NA; ++ia)
-#pragma unroll
-      for (int ib = 0; ib < NB; ++ib)
-#pragma unroll
-        for (int ic = 0; ic < NC; ++ic)
-#pragma unroll
-          for (int id = 0; id < ND; ++id) {
-            const int ax = cart_i(LA, ia), ay = cart_j(LA, ia), az = LA - ax - ay;
-            const int bx = cart_i(LB, ib), by = cart_j(LB, ib), bz = LB - bx - by;
-            const int cx = cart_i(LC, ic), cy = cart_j(LC, ic), cz = LC - cx - cy;
-            const int dx = cart_i(LD, id), dy = cart_j(LD, id), dz = LD - dx - dy;
-            const double *ex = Eab + (ax * (LB + 1) + bx) * NTAB;
-            const double *ey = Eab + N1AB + (ay * (LB + 1) + by) * NTAB;
-            const double *ez = Eab + 2 * N1AB + (az * (LB + 1) + bz) * NTAB;
-            const double *fx = Ecd + (cx * (LD + 1) + dx) * NTCD;
-            const double *fy = Ecd + N1CD + (cy * (LD + 1) + dy) * NTCD;
-            const double *fz = Ecd + 2 * N1CD + (cz * (LD + 1) + dz) * NTCD;
-            double acc = 0.0;
-#pragma unroll
-            for (int t = 0; t <= ax + bx; ++t)
-#pragma unroll
-              for (int u = 0; u <= ay + by; ++u)
-#pragma unroll
-                for (int v = 0; v <= az + bz; ++v) {
-                  double w = 0.0;
-#pragma unroll
-                  for (int t2 = 0; t2 <= cx + dx; ++t2)
-#pragma unroll
-                    for (int u2 = 0; u2 <= cy + dy; ++u2)
-#pragma unroll
-                      for (int v2 = 0; v2 <= cz + dz; ++v2)
-                        w = fma(fx[t2] * fy[u2] * fz[v2], R[hidx(t + t2, u + u2, v + v2)], w);
-                  const double e = ex[t] * ey[u] * ez[v];
-                  acc = fma((t + u + v) & 1 ? -e : e, w, acc);
-                }
-            const int idx = ((ia * NB + ib) * NC + ic) * ND + id;
-            O[idx] += acc;
-          }
-  }
-  // the lanes' sums, by a fixed butterfly (every lane ends with the total)
-#pragma unroll
-  for (int i = 0; i < NE; ++i) {
-    double v = O[i];
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    O[i] = v;
-  }
-  if (lane == 0) {
-    double *o = out + offsets[q];
-#pragma unroll
-    for (int i = 0; i < NE; ++i) o[i] = O[i];
-  }
-  if (flops_total) {
-    // the same algorithmic count per primitive quartet as the general kernel
-    unsigned tot = nproc;
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
-    if (lane == 0 && tot) {
-      const unsigned long long r = 2ull * (L + 1) * (L + 2) * (L + 3) * (L + 4) / 24;
-      const unsigned long long ket = 2ull * nh_count(LA + LB) * nh_count(LC + LD) * (NC * ND);
-      const unsigned long long bra = 2ull * (NA * NB) * nh_count(LA + LB) * (NC * ND);
-      atomicAdd(flops_total, (unsigned long long)tot * (r + ket + bra));
-    }
-  }
-}
-
-// Class key (la << 6 | lb << 4 | lc << 2 | ld) of a thin quartet -> launch of its instance.
-using ThinKernel = void (*)(PairView, QuartetView, int, int64_t, const CTask *, int64_t, const int *, const double *,
-                            double *, const int64_t *, unsigned long long *);
-template <int K>
-constexpr ThinKernel thin_entry() {
-  return &k_contract_thin<(K >> 6) & 3, (K >> 4) & 3, (K >> 2) & 3, K & 3>;
-}
-__host__ inline ThinKernel thin_kernel(int key) {
-  switch (key) {
-#define F12_THIN(K) \
-  case K: return thin_entry<K>();
-    // every (la, lb, lc, ld) with la + lb + lc + ld <= 2
-    F12_THIN(0x00) F12_THIN(0x01) F12_THIN(0x04) F12_THIN(0x10) F12_THIN(0x40)
-    F12_THIN(0x02) F12_THIN(0x08) F12_THIN(0x20) F12_THIN(0x80)
-    F12_THIN(0x05) F12_THIN(0x11) F12_THIN(0x41) F12_THIN(0x14) F12_THIN(0x44) F12_THIN(0x50)
-#undef F12_THIN
-    default: return nullptr;
-  }
-}
-__host__ __device__ inline bool thin_quartet(int key, int cls, bool fp32) {
-  const int L = ((key >> 6) & 3) + ((key >> 4) & 3) + ((key >> 2) & 3) + (key & 3);
-  return !fp32 && cls != 5 && L <= kThinL;
 }
 
 template <bool BATCH, class T>
@@ -1916,7 +1685,7 @@ static int launch_chunk(f12int_ctx *ctx, const f12int_ctx::BasisData &B, int cls
     int64_t rb = ra + 1;
     while (rb < qb && ctx->h_thin[rb] == key) ++rb;
     const int64_t nt = rb - ra;   // one task each
-    const ThinKernel kern = thin_kernel(key);
+    const ThinKernel kern = thin_kernel(key, cls == 5);
     if (!kern) return F12INT_EINVAL;
     std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
     if (ctx->timing) {
@@ -2153,7 +1922,7 @@ static int compute_class_impl(f12int_ctx *ctx, int basis_id, int cls, const int3
         PlanGroup g{};
         g.pl = contract_plan(la, lb, lc, ld, cls, np, f32 ? 4 : 8);
         if (g.pl.smem == 0) return F12INT_EINVAL;
-        g.thin = thin_quartet(k, cls, f32 != 0);
+        g.thin = thin_quartet(k, cls);
         if (g.thin) g.pl = ContractPlan{1, 1, 0};   // one warp of the thin kernel, no shared memory
         const int ncd = ncart(lc) * ncart(ld);
         g.work = (double)np * task_flops(la, lb, lc, ld, cls, (ncd + g.pl.nsplit - 1) / g.pl.nsplit);
@@ -2203,7 +1972,7 @@ static int compute_class_impl(f12int_ctx *ctx, int basis_id, int cls, const int3
     ctx->h_nw[i] = g.pl.nw;
     ctx->h_split[i] = g.pl.nsplit;
     ctx->h_smem[i] = g.pl.smem;
-    ctx->h_fp32[i] = (char)((g.key >> 8) & 1);
+    ctx->h_fp32[i] = (char)(g.thin ? 0 : (g.key >> 8) & 1);   // the thin kernel is FP64
     ctx->h_thin[i] = g.thin ? (int16_t)(g.key & 0xFF) : (int16_t)-1;
   }
   std::vector<int64_t> pqoff((size_t)n + 1);
@@ -2470,7 +2239,7 @@ extern "C" int f12int_compute_class_static(f12int_ctx *ctx, int basis_id, int cl
     nw0[i] = pl.nw;
     sp0[i] = pl.nsplit;
     sm0[i] = pl.smem;
-    if (thin_quartet(key0[i], cls, false)) {   // k_contract_thin: sorted last (no shared memory), by key
+    if (thin_quartet(key0[i], cls)) {   // k_contract_thin: sorted last (no shared memory), by key
       nw0[i] = 1;
       sp0[i] = 1;
       sm0[i] = 0;
@@ -2575,7 +2344,7 @@ extern "C" int f12int_compute_class_static(f12int_ctx *ctx, int basis_id, int cl
         };
         while (rb < qb && hsm[rb] == 0 && key_of(rb) == key) ++rb;
         const int64_t nt = tfirst[rb] - tfirst[ra];
-        const ThinKernel kern = thin_kernel(key);
+        const ThinKernel kern = thin_kernel(key, cls == 5);
         if (!kern) {
           rc_launch = F12INT_EINVAL;
           break;
