@@ -44,12 +44,17 @@ Two further workloads, each printing its own JSON line:
                       timing and work counters: the case every ncu summary names.
   --workload peak     the device's measured FP64 FMA, FP64 matrix (mma.sync) and FP32 FMA
                       peaks (f12int_measure_peak), each twice.
-  --workload serve    Poisson request streams at 10..2000 requests/s over 12
-                      molecules of 2-60 atoms; half the requests ask for one
+  --workload serve    Poisson request streams at 10..2000 requests/s over 24
+                      molecules of 2-60 atoms (one minute of arrivals per rate,
+                      at most 2000 requests); half the requests ask for one
                       class, half for I2..I6, each over U{8..64} x U{8..64}
                       significant shell pairs: p50/p99 latency (submit to done)
                       and throughput of the request path against serial plain
-                      launches in arrival order.
+                      launches in arrival order (capped at 45 s per rate).
+
+The default line also carries reduced forms of the last two: "batched" (the
+first 16 molecules of batch64) and "served" (6 molecules, 2 rates, 300
+requests each); --no-legs leaves them out.
 """
 from __future__ import annotations
 
@@ -447,7 +452,7 @@ def run_ours(args):
                            "batched": b["batched"], "plain": b["plain"], "speedup": b["speedup"],
                            "schedule": b["schedule"]}
         r = serving_measure(6, rates=(20, 200), nreq=lambda lam: 300, plain_cap_s=20.0, verbose=False)
-        line["served"] = {"workload": r["workload"] + " (6 of the 48 molecules of the serving workload, "
+        line["served"] = {"workload": r["workload"] + " (6 of the 24 molecules of the serving workload, "
                                                       "2 rates, 300 requests each)",
                           "rates": [{"rate_per_s": x["rate_per_s"], "requests": x["requests"],
                                      "requests_path": x["requests_path"], "plain_serial": x["plain_serial"]}
@@ -482,6 +487,14 @@ def batching_measure(nmol=64, steps=1, warmup=1):
     work = M.batching_workload(nmol)
     stream = torch.cuda.Stream()
     ctx = F.f12int_create(0, 0, stream)
+    try:
+        return _batching_measure(F, torch, ctx, stream, work, steps, warmup)
+    finally:
+        F.f12int_destroy(ctx)   # waits for the engine's work in flight, also on an error
+
+
+def _batching_measure(F, torch, ctx, stream, work, steps, warmup):
+    nmol = len(work)
     F.f12int_set_factor(ctx, M.P0)
     F.f12int_batch_limits(ctx, 1 << 19, 1 << 26)
     t0 = time.time()
@@ -535,7 +548,6 @@ def batching_measure(nmol=64, steps=1, warmup=1):
                      "graph_replays": batches if name == "batched" else 0,
                      "plain_launches": launches if name == "plain" else 0}
     F.f12int_device_status(ctx)
-    F.f12int_destroy(ctx)
     return {"workload": "%d molecules (seeds 1000-%d, 2-30 atoms, 4s3p2d1f, 1-6 primitives, exponents "
                         "[0.03, 200]); 64 x 64 significant shell pairs each; I1..I6" % (nmol, 999 + nmol),
             "shell_quartets_per_pass": nq, "prim_quartets_per_pass": npq,
@@ -576,6 +588,13 @@ def serving_measure(pool_n=12, rates=(10, 20, 50, 100, 200, 500, 1000, 2000), nr
     pool = M.serving_pool(pool_n)
     stream = torch.cuda.Stream()
     ctx = F.f12int_create(0, 0, stream)
+    try:
+        return _serving_measure(F, torch, ctx, stream, pool, pool_n, rates, nreq, plain_cap_s, verbose)
+    finally:
+        F.f12int_destroy(ctx)   # waits for the engine's work in flight, also on an error
+
+
+def _serving_measure(F, torch, ctx, stream, pool, pool_n, rates, nreq, plain_cap_s, verbose):
     F.f12int_set_factor(ctx, M.P0)
     F.f12int_batch_limits(ctx, 1 << 18, 1 << 25)
     bids = [F.f12int_set_basis(ctx, b) for b in pool]
@@ -675,7 +694,6 @@ def serving_measure(pool_n=12, rates=(10, 20, 50, 100, 200, 500, 1000, 2000), nr
                      "plain_serial": plain})
         del prep
     F.f12int_device_status(ctx)
-    F.f12int_destroy(ctx)
     return {"workload": "%d molecules (seeds 500-%d, 2-60 atoms, 4s3p2d1f, 1-6 primitives); Poisson arrivals; "
                         "half one class of I2..I6, half all five; U{8..64} x U{8..64} significant shell pairs "
                         "per request" % (pool_n, 499 + pool_n),
@@ -686,7 +704,7 @@ def serving_measure(pool_n=12, rates=(10, 20, 50, 100, 200, 500, 1000, 2000), nr
 
 def run_serving(args):
     """Poisson request streams: latency and throughput, requests vs serial plain launches."""
-    r = serving_measure(48)
+    r = serving_measure(24, plain_cap_s=45.0)
     best = max(x["requests_path"]["shell_quartets_per_s"] for x in r["rates"])
     line = {"metric": "served p50/p99 latency (submit to done) and quartets/s, requests vs serial plain launches",
             "value": best, "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": "f64",
@@ -727,8 +745,10 @@ def run_mixed(args):
         F.f12int_compute_class(ctx, bid, c, dq, o64, doff, stream)   # warm-up
         F.f12int_compute_class_mixed(ctx, bid, c, dq, o32, doff, split, stream)
         stream.synchronize()
-        ts = {}
+        ts, kst = {}, {}
         for name in ("fp64", "mixed"):
+            F.f12int_set_timing(ctx, True)
+            F.f12int_kernel_stats(ctx, reset=True)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             if name == "fp64":
@@ -738,6 +758,9 @@ def run_mixed(args):
             e1.record(stream)
             e1.synchronize()
             ts[name] = e0.elapsed_time(e1) / 1e3
+            st = F.f12int_kernel_stats(ctx, reset=True)
+            F.f12int_set_timing(ctx, False)
+            kst[name] = {"aux_ms": st["aux_ms"], "contract_ms": st["contract_ms"]}
         a = o64.cpu().numpy()
         b = o32.cpu().numpy()
         d = np.abs(a - b)
@@ -754,6 +777,7 @@ def run_mixed(args):
         per_class["I%d" % c] = {"shell_quartets": len(q), "prim_quartets": nprim,
                                 "fp32_quartets": int(np.sum(est < split)),
                                 "fp64_s": ts["fp64"], "mixed_s": ts["mixed"], "speedup": ts["fp64"] / ts["mixed"],
+                                "kernels_ms": kst,
                                 "max_abs_diff": float(d.max()),
                                 "max_rel_diff_where_abs_gt_1e-12": float((d[big] / np.abs(a[big])).max()) if big.any() else 0.0,
                                 "max_abs_diff_by_bound_decade": by_decade}

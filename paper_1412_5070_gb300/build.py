@@ -14,10 +14,13 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libf12int.so")
-SOURCES = [os.path.join(CSRC, f) for f in ("f12int.cu", "thin_l2.cu", "thin_l3.cu", "thin_i5.cu", "peak.cu",
-                                            "termlist.cpp")]
-DEPS = SOURCES + [os.path.join(CSRC, f) for f in ("aux.cuh", "auxtab.h", "engine.cuh", "termlist.h",
-                                                  "kernel_common.cuh", "thin.cuh")] + \
+# (source, extra nvcc flags): the thin contraction instances are one source
+# compiled in seven parts, so that they build in parallel
+SOURCES = [(os.path.join(CSRC, "f12int.cu"), ())] + \
+    [(os.path.join(CSRC, "thin_inst.cu"), ("-DF12_THIN_PART=%d" % p,)) for p in range(7)] + \
+    [(os.path.join(CSRC, "peak.cu"), ()), (os.path.join(CSRC, "termlist.cpp"), ())]
+DEPS = sorted({src for src, _ in SOURCES}) + [os.path.join(CSRC, f) for f in (
+    "aux.cuh", "auxtab.h", "engine.cuh", "termlist.h", "kernel_common.cuh", "thin.cuh")] + \
     [os.path.join(os.path.dirname(HERE), "include", "f12int.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -45,9 +48,10 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     nvcc = nvcc_path()
     tag = ".tmp%d" % os.getpid()
     objs, procs = [], []
-    for src in SOURCES:
-        obj = os.path.join(BUILD, os.path.basename(src) + tag + ".o")
-        cmd = [nvcc, "-O3", "-lineinfo", "-std=c++17", *ARCH, "-Xcompiler", "-fPIC", "-c", "-o", obj, src, *extra]
+    for k, (src, flags) in enumerate(SOURCES):
+        obj = os.path.join(BUILD, "%s.%d%s.o" % (os.path.basename(src), k, tag))
+        cmd = [nvcc, "-O3", "-lineinfo", "-std=c++17", *ARCH, "-Xcompiler", "-fPIC", *flags, "-c", "-o", obj, src,
+               *extra]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         objs.append(obj)

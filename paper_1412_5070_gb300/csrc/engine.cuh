@@ -20,6 +20,8 @@ constexpr int kTiers = 5;                // shared-memory tiers per precision
 constexpr size_t kTierCap[kTiers] = {32 * 1024, 64 * 1024, 112 * 1024, 200 * 1024, 200 * 1024};
 constexpr int kTierWarps[kTiers] = {4, 4, 4, 4, 2};   // the last for quartets that need fewer warps
 constexpr int kLaunches = 2 * kTiers;     // FP64 tiers, then FP32 tiers (mixed requests)
+constexpr int kThinSlot = kLaunches;      // then the thin contraction (total order <= 3, I5 <= 2), one
+constexpr int kSlots = kLaunches + kThinKeys;   // launch per (la, lb, lc, ld)
 
 struct EngineReq {
   uint64_t ticket = 0;
@@ -54,6 +56,12 @@ struct BatchPlan {
 static bool batch_plan(int la, int lb, int lc, int ld, int cls, int64_t nprimq, double target, BatchPlan *bp,
                        bool fp32 = false) {
   const int ncd = ncart(lc) * ncart(ld);
+  if (thin_quartet((la << 6) | (lb << 4) | (lc << 2) | ld, cls)) {   // one warp, FP64 (mixed requests too)
+    bp->tier = kThinSlot + thin_slot((la << 6) | (lb << 4) | (lc << 2) | ld, cls == 5);
+    bp->nsplit = 1;
+    bp->work = (double)nprimq * task_flops(la, lb, lc, ld, cls, ncd);
+    return true;
+  }
   const size_t esz = fp32 ? 4 : 8;
   // 4-warp tiers first; the 2-warp tier only for what no 4-warp tier holds
   for (int pass = 0; pass < 2; ++pass) {
@@ -87,7 +95,7 @@ struct ClassLists {
   PairView *views = nullptr;      // [scap]
   double **outs = nullptr;        // [scap]
 };
-constexpr int kCounts = 2 + 2 * kLaunches;
+constexpr int kCounts = 2 + 2 * kSlots;
 
 struct Engine {
   // limits
@@ -119,6 +127,7 @@ struct Engine {
   cudaGraphExec_t exec = nullptr;
   bool graph_dirty = true;
   int items_blocks = 0, quad_blocks = 0, classify_blocks = 0, tier_blocks[kLaunches] = {0};
+  int thin_blocks = 0;           // persistent thin contraction launches
   double fp32_below = 1e-5;           // mixed requests: FP32 below this screening estimate
   // per-class schedule (f12int_batch_autotune): work target of a contraction
   // task and the divisor of the auxiliary-stage grid
@@ -243,6 +252,14 @@ static int engine_capture(f12int_ctx *ctx, Engine &E) {
               none, QV, cls, nf, 0, L.tasks, 0, L.counts + 2 + 2 * t, E.keys[cls], E.part[cls], nullptr, L.offsets,
               E.status, nullptr);
       }
+      // one persistent launch per thin (la, lb, lc, ld) of the class kind
+      for (int k = 0; k < 256; ++k) {
+        const int slot = thin_quartet(k, cls) ? thin_slot(k, cls == 5) : -1;
+        if (slot < 0) continue;
+        thin_kernel(k, cls == 5)<<<E.thin_blocks, 32 * kThinWarps, 0, bs>>>(
+            none, QV, nf, 0, L.tasks, 0, L.counts + 2 + 2 * (kThinSlot + slot), E.keys[cls], E.part[cls], nullptr,
+            L.offsets, nullptr);
+      }
       cudaEventRecord(join[cls], bs);
       cudaStreamWaitEvent(cs, join[cls], 0);
     }
@@ -321,6 +338,7 @@ static int engine_init(f12int_ctx *ctx, Engine &E) {
                                                      kTierCap[t]));
     E.tier_blocks[kTiers + t] = nsm * std::max(per, 1);
   }
+  E.thin_blocks = nsm * 4;   // 16 warps per SM: the thin launches of a batch are mostly small
   E.ready = true;
   return F12INT_OK;
 }
@@ -414,7 +432,7 @@ static int engine_launch(f12int_ctx *ctx, Engine &E, const std::vector<EngineReq
     S.counts[0] = n;
     S.counts[1] = npq;
     int64_t i = 0;
-    for (int t = 0; t < kLaunches; ++t) {
+    for (int t = 0; t < kSlots; ++t) {
       S.counts[2 + 2 * t] = nt;
       for (; i < n && items[i].tier == t; ++i)
         for (int sp = 0; sp < items[i].nsplit; ++sp) S.tasks[nt++] = CTask{(int32_t)i, (int16_t)sp, (int16_t)items[i].nsplit};
@@ -763,7 +781,9 @@ int f12int_batch_autotune(f12int_ctx *ctx, int basis_id, const int32_t *quartets
     const auto t0 = std::chrono::steady_clock::now();
     int r = f12int_submit(ctx, basis_id, &rq, &t);
     int done = 0;
-    while (r == F12INT_OK && !done) r = f12int_poll(ctx, t, 100000, &done);
+    // wait until the request is done (a 100 ms wait that runs out returns
+    // F12INT_ETIMEOUT with done = 0: keep waiting)
+    while ((r == F12INT_OK || r == F12INT_ETIMEOUT) && !done) r = f12int_poll(ctx, t, 100000, &done);
     *sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return r;
   };
@@ -802,8 +822,15 @@ int f12int_batch_autotune(f12int_ctx *ctx, int basis_id, const int32_t *quartets
       report[3 * (c - 1) + 2] = best;
     }
   }
-  dfree(ctx, out, sizeof(double) * (size_t)tot);
-  return rc;
+  // the sample's output may be freed only once no batch writes it any more
+  // (an error above can leave one in flight): bounded wait, else keep it
+  bool idle = engine_idle(ctx);
+  for (int k = 0; k < 6000 && !idle; ++k) {
+    std::this_thread::sleep_for(std::chrono::milliseconds(10));
+    idle = engine_idle(ctx);
+  }
+  if (idle) dfree(ctx, out, sizeof(double) * (size_t)tot);
+  return idle ? rc : F12INT_ETIMEOUT;
 }
 
 int f12int_set_fp32_below(f12int_ctx *ctx, double bound) {

@@ -1693,7 +1693,7 @@ static int launch_chunk(f12int_ctx *ctx, const f12int_ctx::BasisData &B, int cls
       cudaEventRecord(ev.first, st);
     }
     kern<<<(unsigned)((nt + kThinWarps - 1) / kThinWarps), 32 * kThinWarps, 0, st>>>(
-        PV, QV, nf, pqa, ctx->d_tasks + t0, nt, ctx->d_keys, ctx->d_part, out_dev, offsets_dev,
+        PV, QV, nf, pqa, ctx->d_tasks + t0, nt, nullptr, ctx->d_keys, ctx->d_part, out_dev, offsets_dev,
         ctx->timing ? ctx->d_fma + 1 : nullptr);
     t0 += nt;
     if (ctx->timing) {
@@ -2350,7 +2350,7 @@ extern "C" int f12int_compute_class_static(f12int_ctx *ctx, int basis_id, int cl
           break;
         }
         kern<<<(unsigned)((nt + kThinWarps - 1) / kThinWarps), 32 * kThinWarps, 0, st>>>(
-            PV, QV, nf, pqa, d_tk + tfirst[ra], nt, d_keys, d_part, out_dev, d_o, nullptr);
+            PV, QV, nf, pqa, d_tk + tfirst[ra], nt, nullptr, d_keys, d_part, out_dev, d_o, nullptr);
         ctx->launches++;
         if (cudaGetLastError() != cudaSuccess) rc_launch = F12INT_ECUDA;
         ra = rb;

@@ -68,10 +68,14 @@ __device__ __forceinline__ double pair_sep(const double *ppP, int pab, int pcd, 
 // path too: there it is faster than the FP32 general kernel).
 constexpr int kThinL = 3, kThinL5 = 2;
 constexpr int kThinWarps = 4;
-using ThinKernel = void (*)(PairView, QuartetView, int, int64_t, const CTask *, int64_t, const int *, const double *,
-                            double *, const int64_t *, unsigned long long *);
+using ThinKernel = void (*)(PairView, QuartetView, int, int64_t, const CTask *, int64_t, const int64_t *, const int *,
+                            const double *, double *, const int64_t *, unsigned long long *);
 // The instance for class key (la << 6 | lb << 4 | lc << 2 | ld), or null.
 ThinKernel thin_kernel(int key, bool i5);
+// Index of a thin class key among the thin keys of its class kind (the batch
+// engine's launch slot), -1 if the key is not thin there.
+int thin_slot(int key, bool i5);
+constexpr int kThinKeys = 35;   // thin keys of the classes other than I5 (15 for I5)
 __host__ __device__ inline bool thin_quartet(int key, int cls) {
   const int L = ((key >> 6) & 3) + ((key >> 4) & 3) + ((key >> 2) & 3) + (key & 3);
   return L <= (cls == 5 ? kThinL5 : kThinL);

@@ -1,6 +1,6 @@
 // thin.cuh -- the thin contraction kernel template, instantiated by
-// thin_l2.cu, thin_l3.cu and thin_i5.cu (three translation units, so that
-// the fifty instances compile in parallel with the rest of the library).
+// thin_inst.cu in seven parts (seven objects compiled in parallel with the
+// rest of the library).
 #pragma once
 
 #include "kernel_common.cuh"
@@ -32,11 +32,12 @@ __host__ __device__ constexpr int cart_j(int l, int k) {   // y exponent
   return 0;
 }
 
+// One shell quartet q (index into the list) by the calling warp; its block
+// goes to o.
 template <int LA, int LB, int LC, int LD, bool I5>
-__global__ void __launch_bounds__(32 * kThinWarps)
-k_contract_thin(PairView PV, QuartetView QV, int nf, int64_t pq0, const CTask *tasks, int64_t ntask,
-                const int *keys, const double *part, double *out, const int64_t *offsets,
-                unsigned long long *flops_total) {
+__device__ __forceinline__ void thin_quartet_body(const PairView &PV, const QuartetView &QV, int nf, int64_t pq0,
+                                                  int64_t q, const int *keys, const double *part, double *out_q,
+                                                  unsigned long long *flops_total) {
   constexpr int EXT = I5 ? 2 : 0;
   constexpr int L = LA + LB + LC + LD + EXT;   // highest order of g_n and R
   constexpr int NA = (LA + 1) * (LA + 2) / 2, NB = (LB + 1) * (LB + 2) / 2;
@@ -46,9 +47,6 @@ k_contract_thin(PairView PV, QuartetView QV, int nf, int64_t pq0, const CTask *t
   constexpr int N1AB = (LA + 1) * (LB + 1) * NTAB, N1CD = (LC + 1) * (LD + 1) * NTCD;
   constexpr int NH = (L + 1) * (L + 2) * (L + 3) / 6;
   const int lane = threadIdx.x & 31;
-  const int64_t task = (int64_t)blockIdx.x * kThinWarps + (threadIdx.x >> 5);
-  if (task >= ntask) return;   // warp-uniform
-  const int64_t q = tasks[task].q;
   const int32_t *s = QV.quartets + 4 * q;
   const int ns = PV.nshell;
   const int ab = s[0] * ns + s[1], cd = s[2] * ns + s[3];
@@ -183,9 +181,8 @@ k_contract_thin(PairView PV, QuartetView QV, int nf, int64_t pq0, const CTask *t
     O[i] = v;
   }
   if (lane == 0) {
-    double *o = out + offsets[q];
 #pragma unroll
-    for (int i = 0; i < NE; ++i) o[i] = O[i];
+    for (int i = 0; i < NE; ++i) out_q[i] = O[i];
   }
   if (flops_total) {
     // the same algorithmic count per primitive quartet as the general kernel
@@ -201,22 +198,56 @@ k_contract_thin(PairView PV, QuartetView QV, int nf, int64_t pq0, const CTask *t
   }
 }
 
+// range == null: tasks [0, ntask), one warp each, pair data PV, blocks into
+// out.  range != null (the batch engine's persistent launch): the tasks
+// [range[0], range[1]) in grid-stride order, each quartet's pair data and
+// output array from its request's slot.
+template <int LA, int LB, int LC, int LD, bool I5>
+__global__ void __launch_bounds__(32 * kThinWarps)
+k_contract_thin(PairView PV, QuartetView QV, int nf, int64_t pq0, const CTask *tasks, int64_t ntask,
+                const int64_t *range, const int *keys, const double *part, double *out, const int64_t *offsets,
+                unsigned long long *flops_total) {
+  const int64_t warp = (int64_t)blockIdx.x * kThinWarps + (threadIdx.x >> 5);
+  if (!range) {
+    if (warp >= ntask) return;   // warp-uniform
+    const int64_t q = tasks[warp].q;
+    thin_quartet_body<LA, LB, LC, LD, I5>(PV, QV, nf, pq0, q, keys, part, out + offsets[q], flops_total);
+    return;
+  }
+  const int64_t t1 = range[1], stride = (int64_t)gridDim.x * kThinWarps;
+  for (int64_t tk = range[0] + warp; tk < t1; tk += stride) {
+    const int64_t q = tasks[tk].q;
+    const int slot = QV.qslot[q];
+    thin_quartet_body<LA, LB, LC, LD, I5>(QV.slot_view[slot], QV, nf, pq0, q, keys, part,
+                                          QV.slot_out[slot] + offsets[q], flops_total);
+  }
+}
+
 // Class keys (la << 6 | lb << 4 | lc << 2 | ld): every (la, lb, lc, ld) with
-// la + lb + lc + ld <= 2, and with la + lb + lc + ld = 3.
-#define F12_THIN_KEYS_2(X)                                                                                     \
-  X(0x00) X(0x01) X(0x04) X(0x10) X(0x40) X(0x02) X(0x08) X(0x20) X(0x80) X(0x05) X(0x11) X(0x41) X(0x14)   \
-  X(0x44) X(0x50)
-#define F12_THIN_KEYS_3(X)                                                                                     \
-  X(0x03) X(0x0C) X(0x30) X(0xC0) X(0x06) X(0x09) X(0x12) X(0x18) X(0x21) X(0x24) X(0x42) X(0x48) X(0x60)   \
-  X(0x81) X(0x84) X(0x90) X(0x15) X(0x45) X(0x51) X(0x54)
+// la + lb + lc + ld <= 2 (in two groups), and with la + lb + lc + ld = 3 (in
+// four): the instances are compiled in seven parts, in parallel.
+#define F12_THIN_KEYS_2A(X) X(0x00) X(0x01) X(0x04) X(0x10) X(0x40) X(0x02) X(0x08) X(0x20)
+#define F12_THIN_KEYS_2B(X) X(0x80) X(0x05) X(0x11) X(0x41) X(0x14) X(0x44) X(0x50)
+#define F12_THIN_KEYS_2(X) F12_THIN_KEYS_2A(X) F12_THIN_KEYS_2B(X)
+#define F12_THIN_KEYS_3A(X) X(0x03) X(0x0C) X(0x30) X(0xC0) X(0x06)
+#define F12_THIN_KEYS_3B(X) X(0x09) X(0x12) X(0x18) X(0x21) X(0x24)
+#define F12_THIN_KEYS_3C(X) X(0x42) X(0x48) X(0x60) X(0x81) X(0x84)
+#define F12_THIN_KEYS_3D(X) X(0x90) X(0x15) X(0x45) X(0x51) X(0x54)
+#define F12_THIN_KEYS_3(X) F12_THIN_KEYS_3A(X) F12_THIN_KEYS_3B(X) F12_THIN_KEYS_3C(X) F12_THIN_KEYS_3D(X)
 
 template <int K, bool I5>
 ThinKernel thin_entry() {
   return &k_contract_thin<(K >> 6) & 3, (K >> 4) & 3, (K >> 2) & 3, K & 3, I5>;
 }
 
-ThinKernel thin_kernel_l2(int key);   // thin_l2.cu: L <= 2, classes other than I5
-ThinKernel thin_kernel_l3(int key);   // thin_l3.cu: L = 3, classes other than I5
-ThinKernel thin_kernel_i5(int key);   // thin_i5.cu: I5 with L <= 2
+// Part p (thin_inst.cu compiled with F12_THIN_PART = p) of the instances: the
+// kernel for (key, i5) if the part holds it, else null.
+ThinKernel thin_part0(int key, bool i5);   // L <= 2, not I5
+ThinKernel thin_part1(int key, bool i5);   // L = 3, not I5 (four parts)
+ThinKernel thin_part2(int key, bool i5);
+ThinKernel thin_part3(int key, bool i5);
+ThinKernel thin_part4(int key, bool i5);
+ThinKernel thin_part5(int key, bool i5);   // I5, L <= 2 (two parts)
+ThinKernel thin_part6(int key, bool i5);
 
 }  // namespace f12k

@@ -83,7 +83,14 @@ XI_D_GRID = [(xi, D) for xi in (0.025, 0.1, 0.5, 2.0, 10.0, 50.0) for D in (0.0,
 @pytest.mark.parametrize("cls", [1, 2, 3, 4, 6])
 def test_aux_stage_against_oracle(ctx, cls):
     """hat g_n (n <= 10) from the auxiliary-function kernel against the
-    oracle's quadrature of Eq. bfinal."""
+    oracle's quadrature of Eq. bfinal.  Judged against the natural scale of
+    order n, (2 xi)^n |hat g_0| (or |hat g_n| if larger): D_Q^n of a smooth
+    function of width ~1/sqrt(xi) is of that size, and an order whose value is
+    accidentally far below it (a sum over the kernel's families that nearly
+    cancels) cannot be resolved relative to itself.  Bounds: 1e-13 of the
+    natural scale for I1-I4 (the CPU build of the stage reaches 3e-15), 2e-12
+    for I6 (3.3e-13), whose f_r f'_r families cancel most; and relative to the
+    value itself 1e-10 (I6: 2e-9)."""
     nmax = 10
     xi = torch.tensor([p[0] for p in XI_D_GRID], dtype=torch.float64, device="cuda")
     D = torch.tensor([p[1] for p in XI_D_GRID], dtype=torch.float64, device="cuda")
@@ -93,13 +100,15 @@ def test_aux_stage_against_oracle(ctx, cls):
     F.f12int_device_status(ctx)
     got = out.cpu().numpy().reshape(len(XI_D_GRID), nmax + 1)
     K = O.factor_kernel(M.P0)
-    worst = 0.0
+    worst, worst_nat = 0.0, 0.0
     for i, (x, d) in enumerate(XI_D_GRID):
         ref = O.radial(K, cls, x, d, nmax)
-        rel = np.abs(got[i] - ref) / np.abs(ref)
-        worst = max(worst, float(rel.max()))
-    print("class %d worst relative error of hat g_n: %.3g" % (cls, worst))
-    assert worst < 1e-8
+        nat = np.maximum(np.abs(ref), (2.0 * x) ** np.arange(nmax + 1) * abs(ref[0]))
+        worst = max(worst, float(np.max(np.abs(got[i] - ref) / np.abs(ref))))
+        worst_nat = max(worst_nat, float(np.max(np.abs(got[i] - ref) / nat)))
+    print("class %d worst error of hat g_n: %.3g relative, %.3g of the natural scale" % (cls, worst, worst_nat))
+    assert worst_nat < (2e-12 if cls == 6 else 1e-13)
+    assert worst < (2e-9 if cls == 6 else 1e-10)
 
 
 @pytest.mark.parametrize("cls", [1, 2, 3, 4, 5, 6])
