@@ -110,6 +110,7 @@ struct FamDev {
   int group;                  // index of its GroupDev (families evaluated together), -1 none
   int lead;                   // the group's first member, which evaluates the whole group
   int jtab;                   // offset of its start-value table in Tables::jtab, -1 none
+  int ktab;                   // 1: b = 0, integer alpha0 >= 0 and every a_j on the Kummer table's grid
   int ha_base;                // 2 alpha0 - 2: index of (alpha0 + m - 1)/2 in d_quarter is ha_base + 2m
   int ha_tab;                 // 1: that index stays inside d_quarter for every m of the series
   int jrow;                   // doubles per table row (JT_NK, or 2 JT_NK for a finite-part family)
@@ -170,6 +171,18 @@ F12_GLOBAL double d_vstep[KMAX];
 // for integer and half-integer alpha0, read instead of being accumulated
 constexpr int NQUARTER = 2 * (JMAX + 2 * KMAX) + 16;
 F12_GLOBAL double d_quarter[NQUARTER];
+// Families with b = 0 (Gaussian terms e^{-g r^2} x^alpha): S(alpha, 0, gamma) is
+// a Gamma function, and the series of each order sums to a confluent
+// hypergeometric (Kummer) function: with a_j = (alpha0 + j + 1)/2,
+//   sum_k c_{l,k} v^k Gamma(a_j + k) = Gamma(a_j) c_{l,0} M(a_j, l + 3/2, x),  x = v/4,
+// tabulated as T(a, l, x) = e^{-x} M(a, l + 3/2, x) on the grid x_i = i MT_DX,
+// a = (ia + 1)/2, with MT_NT Taylor coefficients per point:
+//   d^m T/dx^m = (-1)^m (b - a)_m / (b)_m  e^{-x} M(a, b + m, x),  b = l + 3/2.
+constexpr int MT_NA = 40;            // a = 1/2 .. 20
+constexpr int MT_NX = 201;           // x = 0 .. 100 (the series region: x < 36 + 4.5 l <= 99)
+constexpr double MT_DX = 0.5;
+constexpr int MT_NT = 14;            // Taylor terms: (DX/2)^14 / 14! < 1e-19
+F12_GLOBAL const double *d_mtab;     // [l][ia][ix][m], built on the host (fill_kummer_table)
 
 F12_DEV inline double threshold_z(int l) { return 36.0 + 4.5 * l; }
 // The peak quadrature's integrand is x^alpha0 P_l(x) e^{-z} j_l(z) about a
@@ -671,9 +684,12 @@ F12_DEV inline int family_eval(const Tables &T, const FamDev &F, double xi, doub
       return bad;
     }
   }
-  // orders l < ls use the quadrature about the peak, l >= ls the series
+  // orders l < ls use the quadrature about the peak, l >= ls the series (or,
+  // for a family on the Kummer table, the table wherever x = z lies in its
+  // range: it is exact there, with no r -> 0 argument to satisfy)
   int ls = 0;
-  if (!QUAD || beta > 0.0)       // beta <= 0 (b < 0): no peak inside (0, inf)
+  const bool ktab = !QUAD && F.ktab && z < (MT_NX - 1) * MT_DX;
+  if (!ktab && (!QUAD || beta > 0.0))   // beta <= 0 (b < 0): no peak inside (0, inf)
     while (ls <= L && z >= threshold_z(ls)) ++ls;
   double fct[LAUX + 1];
   fct[0] = 4.0 * xi;
@@ -683,6 +699,33 @@ F12_DEV inline int family_eval(const Tables &T, const FamDev &F, double xi, doub
 
   if constexpr (QUAD) {
     if (ls <= L) bad |= family_quad(T, F, xi, D, ls, L, fct, out, &nfma);
+  } else if (ktab) {
+    // b = 0: each order from the Kummer table,
+    //   sum_l = e^{-xi g D^2 / gamma} gamma^{-(alpha0+1)/2} c_{l,0}/2
+    //           sum_j P_lj gamma^{-j/2} Gamma(a_j) T(a_j, l, x),  x = z = xi^2 D^2 / gamma
+    const double rgam = rsqrt(gam);
+    double gpow0 = 1.0;                    // gamma^{-(alpha0+1)/2}, alpha0 = pow_int >= 0
+    for (int k = 0; k < F.pow_int + 1; ++k) gpow0 *= rgam;
+    const double E = exp(-xi * F.g * D * D / gam) * gpow0 * 0.5;
+    const double xt = z * (1.0 / MT_DX);
+    const double ri = rint(xt);
+    const double h = (xt - ri) * MT_DX;
+    const int ix = (int)ri;
+    const int ia0 = F.pow_int;             // a_j = (alpha0 + j + 1)/2 is grid point alpha0 + j
+    for (int l = ls; l <= L; ++l) {
+      const double *P = T.coef + F.coff[l];
+      const double *rowl = d_mtab + ((size_t)l * MT_NA * MT_NX + ix) * MT_NT;
+      double s = 0.0, gp = 1.0;
+      for (int j = 0; j < F.span[l]; ++j) {
+        const double *row = rowl + (size_t)(ia0 + j) * MT_NX * MT_NT;
+        double t = row[MT_NT - 1];
+        for (int m = MT_NT - 2; m >= 0; --m) t = fma(t, h, row[m]);
+        s = fma(P[j] * gp * F.gam_tab[j], t, s);
+        gp *= rgam;
+      }
+      out[l] += fct[l] * E * c_inv_dfact[l] * s;
+      nfma += (unsigned long long)F.span[l] * (MT_NT + 1);
+    }
   } else if (ls <= L) {
     const double y = F.b * rsqrt(gam);
     const double v = 4.0 * xi * xi * D * D / gam;

@@ -243,6 +243,7 @@ inline bool build_class_tables(const f12::TermList kernels[NCLASS], ClassTables 
       d.lead = 0;
       d.jtab = -1;
       d.jrow = 0;
+      d.ktab = 0;   // set once the spans are known (mark_kummer_families)
       d.ha_base = (int)std::lround(2.0 * d.alpha0) - 2;
       d.ha_tab = (d.pow_kind != 0 && d.ha_base >= -4 && d.ha_base + 2 * (JMAX + 2 * KMAX) < NQUARTER) ? 1 : 0;
       double as = d.fp_minus1 ? 0.0 : d.alpha0;
@@ -369,7 +370,52 @@ inline bool build_class_tables(const f12::TermList kernels[NCLASS], ClassTables 
     for (const FamDev &d : mine) ct.quad[cls] = ct.quad[cls] || d.quad;
   }
   build_start_tables(ct);
+  for (FamDev &d : ct.fams) {
+    // the Kummer table serves b = 0 series families with an integer alpha0 >= 0
+    // whose a_j = (alpha0 + j + 1)/2 stay on its grid for every order
+    int jmax = 0;
+    for (int l = 0; l <= LAUX; ++l) jmax = std::max(jmax, d.span[l]);
+    d.ktab = (!d.quad && d.b == 0.0 && d.group < 0 && !d.fp_minus1 && d.pow_kind == 1 && d.pow_int >= 0 &&
+              d.pow_int + jmax - 1 < MT_NA) ? 1 : 0;
+  }
   return true;
+}
+
+// Kummer M(a, b, x) e^{-x} for x >= 0, a > 0, b > 0, in long double: the
+// series sum_k (a)_k x^k / (k! (b)_k) (every term positive) times e^{-x}.
+inline long double kummer_scaled(long double a, long double b, long double x) {
+  long double t = 1.0L, s = 1.0L;
+  for (int k = 0; k < 5000; ++k) {
+    t *= (a + k) * x / ((b + k) * (k + 1));
+    s += t;
+    if (t <= 1e-21L * s && k > 2) break;
+  }
+  return s * std::exp(-x);
+}
+
+// The table d_mtab: for l <= LAUX, a = (ia + 1)/2 (ia < MT_NA), x_i = i MT_DX,
+// the Taylor coefficients (1/m!) d^m T/dx^m of T(a, l, x) = e^{-x} M(a, l + 3/2, x),
+//   d^m T/dx^m = (-1)^m (b - a)_m / (b)_m  e^{-x} M(a, b + m, x),  b = l + 3/2.
+inline void fill_kummer_table(std::vector<double> &tab) {
+  tab.assign((size_t)(LAUX + 1) * MT_NA * MT_NX * MT_NT, 0.0);
+  constexpr int NB = LAUX + MT_NT;   // b = 3/2 .. LAUX + MT_NT + 1/2
+  std::vector<long double> tb((size_t)NB);
+  for (int ia = 0; ia < MT_NA; ++ia) {
+    const long double a = 0.5L * (ia + 1);
+    for (int ix = 0; ix < MT_NX; ++ix) {
+      const long double x = (long double)ix * (long double)MT_DX;
+      for (int ib = 0; ib < NB; ++ib) tb[ib] = kummer_scaled(a, 1.5L + ib, x);
+      for (int l = 0; l <= LAUX; ++l) {
+        const long double b = 1.5L + l;
+        long double c = 1.0L;   // (-1)^m (b - a)_m / ((b)_m m!)
+        double *row = &tab[(((size_t)l * MT_NA + ia) * MT_NX + ix) * MT_NT];
+        for (int m = 0; m < MT_NT; ++m) {
+          row[m] = (double)(c * tb[l + m]);
+          c *= -(b - a + m) / ((b + m) * (m + 1));
+        }
+      }
+    }
+  }
 }
 
 // J_a(y) = int_0^inf t^a e^{y t - t^2} dt, a > -1, y >= 0, in long double from

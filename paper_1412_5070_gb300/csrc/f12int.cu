@@ -898,6 +898,16 @@ int upload_constants() {
   CK(cudaMemcpyToSymbol(d_cser, ac.cser, sizeof(ac.cser)));
   CK(cudaMemcpyToSymbol(d_vstep, ac.vstep, sizeof(ac.vstep)));
   CK(cudaMemcpyToSymbol(d_quarter, ac.quarter, sizeof(ac.quarter)));
+  {
+    // the Kummer table of the b = 0 families (13.5 MB), kept for the process
+    std::vector<double> kt;
+    fill_kummer_table(kt);
+    double *dk = nullptr;
+    CK(cudaMalloc(&dk, sizeof(double) * kt.size()));
+    CK(cudaMemcpy(dk, kt.data(), sizeof(double) * kt.size(), cudaMemcpyHostToDevice));
+    const double *dkc = dk;
+    CK(cudaMemcpyToSymbol(d_mtab, &dkc, sizeof(dkc)));
+  }
   CK(cudaMemcpyToSymbol(c_tuv, tuv, sizeof(tuv)));
   CK(cudaMemcpyToSymbol(c_cart, cart, sizeof(cart)));
   CK(cudaMemcpyToSymbol(c_gh_x, ac.gh_x, sizeof(ac.gh_x)));

@@ -8,6 +8,7 @@
 // the kernels.
 #include <cstdint>
 #include <cstring>
+#include <vector>
 
 #include "../paper_1412_5070_gb300/csrc/aux.cuh"
 #include "../paper_1412_5070_gb300/csrc/auxtab.h"
@@ -33,6 +34,9 @@ void load_constants() {
   std::memcpy(d_cser, ac.cser, sizeof(ac.cser));
   std::memcpy(d_vstep, ac.vstep, sizeof(ac.vstep));
   std::memcpy(d_quarter, ac.quarter, sizeof(ac.quarter));
+  static std::vector<double> kt;
+  fill_kummer_table(kt);
+  d_mtab = kt.data();
   done = true;
 }
 
