@@ -45,6 +45,10 @@ namespace {
 constexpr int LSH = 3;                 // highest shell angular momentum
 constexpr int NHMAX = 680;             // Hermite indices with t+u+v <= 14
 constexpr int BLOCK_CONTRACT = 128;
+// ket component order of a contraction task: 100 components at most (f f),
+// then the class starts (7 term counts at most for lc + ld <= 6)
+constexpr int KORD_CLS = 100;
+constexpr int KORD_SIZE = KORD_CLS + 16;
 constexpr int BLOCK_AUX = 64;
 
 __constant__ unsigned char c_tuv[NHMAX][3];   // Hermite index -> (t, u, v)
@@ -449,7 +453,7 @@ __device__ __forceinline__ void contract_task(const PairView &PV0, const Quartet
                                               int64_t pq0, const CTask task, const int *keys, const double *part,
                                               double *out,
                                               const int64_t *offsets, unsigned long long *flops_total,
-                                              T *smem, int *off_ab, int *off_cd) {
+                                              T *smem, int *off_ab, int *off_cd, int *kord) {
   const int64_t q = task.q;
   const int split = task.split, nsplit = task.nsplit;
   const PairView &PV = qv_view<BATCH>(PV0, QV, q);
@@ -476,6 +480,24 @@ __device__ __forceinline__ void contract_task(const PairView &PV0, const Quartet
       o += (ec[0] + ed[0] + 1) * (ec[1] + ed[1] + 1) * (ec[2] + ed[2] + 1);
     }
     off_cd[ncd] = o;
+    // ket components in order of increasing term count (the ket step's loop
+    // length), one class per count: kord[0..ncd) the components,
+    // kord[KORD_CLS + c] the first position of class c (ncd after the last).
+    // Lanes that take consecutive entries of the (class, bra index,
+    // component) order run loops of one length.
+    int nc_ = 0, pos = 0;
+    while (pos < ncd) {
+      int len = 1 << 30;
+      for (int j = 0; j < ncd; ++j) {
+        const int lj = off_cd[j + 1] - off_cd[j];
+        if (lj > (nc_ ? off_cd[kord[pos - 1] + 1] - off_cd[kord[pos - 1]] : 0) && lj < len) len = lj;
+      }
+      kord[KORD_CLS + nc_] = pos;
+      for (int j = 0; j < ncd; ++j)
+        if (off_cd[j + 1] - off_cd[j] == len) kord[pos++] = j;
+      ++nc_;
+    }
+    kord[KORD_CLS + nc_] = ncd;
     o = 0;
     for (int j = 0; j < nab; ++j) {
       off_ab[j] = o;
@@ -595,14 +617,19 @@ __device__ __forceinline__ void contract_task(const PairView &PV0, const Quartet
         cur = nxt;
         nxt = tmp;
       }
-      // inner (ket) sum of Eq. ii:  W[tuv][cd] += sum E^{cd}_{t'u'v'} R_{t+t',u+u',v+v'}
-      for (int i = lane; i < nhB * ncd; i += 32) {
-        const int bi = i / ncd, j = i - bi * ncd;
+      // inner (ket) sum of Eq. ii:  W[tuv][cd] += sum E^{cd}_{t'u'v'} R_{t+t',u+u',v+v'},
+      // entries taken in (term-count class, bra index, component) order
+      for (int r = lane, c = 0; r < nhB * ncd; r += 32) {
+        while (r >= nhB * kord[KORD_CLS + c + 1]) ++c;
+        const int c0 = kord[KORD_CLS + c], n_c = kord[KORD_CLS + c + 1] - c0;
+        const int rr = r - nhB * c0;
+        const int bi = rr / n_c;
+        const int j = kord[c0 + rr - bi * n_c];
         const int cb = (c_tuv[bi][0] * P + c_tuv[bi][1]) * P + c_tuv[bi][2];
         const int m0 = off_cd[j], m1 = off_cd[j + 1];
         T acc = 0;
         for (int m = m0; m < m1; ++m) acc = tfma(E3cd[m], Rc[cb + ck[m]], acc);
-        W[i] += acc;
+        W[bi * ncd + j] += acc;
       }
       __syncwarp();
     }
@@ -698,19 +725,19 @@ k_contract(PairView PV0, QuartetView QV, int cls, int nf, int64_t pq0, const CTa
            unsigned int *status, unsigned long long *flops_total) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *smem = reinterpret_cast<T *>(smem_raw);
-  __shared__ int off_ab[101], off_cd[101];
+  __shared__ int off_ab[101], off_cd[101], kord[KORD_SIZE];
   if constexpr (BATCH) {
     // ntask_dev = {first, end} of this launch's tasks
     const int64_t te = ntask_dev[1];
     for (int64_t tk = ntask_dev[0] + blockIdx.x; tk < te; tk += gridDim.x) {
       __syncthreads();   // the previous task's shared-memory reads are done
       contract_task<BATCH, T>(PV0, QV, cls, nf, pq0, tasks[tk], keys, part, out, offsets, flops_total, smem, off_ab,
-                              off_cd);
+                              off_cd, kord);
     }
   } else {
     if (blockIdx.x < ntask)
       contract_task<BATCH, T>(PV0, QV, cls, nf, pq0, tasks[blockIdx.x], keys, part, out, offsets, flops_total, smem,
-                              off_ab, off_cd);
+                              off_ab, off_cd, kord);
   }
 }
 // Derivation note for I5: with d/dA_x = (a/p) d/dP_x + d/dAB_x and
