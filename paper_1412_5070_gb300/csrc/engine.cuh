@@ -283,7 +283,7 @@ static int engine_init(f12int_ctx *ctx, Engine &E) {
     size_t free_b = 0, total_b = 0;
     CK(cudaMemGetInfo(&free_b, &total_b));
     if (ctx->budget) free_b = std::min(free_b, ctx->budget > ctx->used ? ctx->budget - ctx->used : (size_t)0);
-    const size_t per_item = sizeof(int) + sizeof(unsigned) + sizeof(double) * (LAUX + 1);
+    const size_t per_item = sizeof(int) + sizeof(unsigned) + sizeof(double) * kPartPitch;
     const int64_t fit = (int64_t)(free_b / 4 / (6 * per_item));
     E.icap = std::min<int64_t>((int64_t)1 << 26, fit);
     if (E.icap < ((int64_t)1 << 16)) return F12INT_ENOMEM;
@@ -298,7 +298,7 @@ static int engine_init(f12int_ctx *ctx, Engine &E) {
   for (int c = 1; c <= 6 && rc == F12INT_OK; ++c) {
     rc = engine_alloc(ctx, E, &E.keys[c], (size_t)E.icap);
     if (rc == F12INT_OK) rc = engine_alloc(ctx, E, &E.order[c], (size_t)E.icap);
-    if (rc == F12INT_OK) rc = engine_alloc(ctx, E, &E.part[c], (size_t)E.icap * (LAUX + 1));
+    if (rc == F12INT_OK) rc = engine_alloc(ctx, E, &E.part[c], (size_t)E.icap * kPartPitch);
     if (rc == F12INT_OK) rc = engine_alloc(ctx, E, &E.hist[c], (size_t)kNKeys);
     if (rc == F12INT_OK && cudaStreamCreateWithFlags(&E.branch[c], cudaStreamNonBlocking) != cudaSuccess)
       rc = F12INT_ECUDA;
@@ -613,7 +613,7 @@ static size_t prim_bounds_bytes(const f12int_ctx *ctx, const f12int_ctx::BasisDa
     }
   const size_t npairs = np * (np + 1) / 2;
   const size_t nf = (size_t)std::max(1, ctx->tables.nfam[cls == 5 ? 3 : cls]);
-  const size_t items = npairs * nf * (sizeof(int) + sizeof(unsigned) + sizeof(double) * (LAUX + 1));
+  const size_t items = npairs * nf * (sizeof(int) + sizeof(unsigned) + sizeof(double) * kPartPitch);
   return pair_data + diag + items;
 }
 

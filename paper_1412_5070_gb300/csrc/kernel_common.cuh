@@ -10,6 +10,7 @@
 namespace f12k {
 
 constexpr int kLaux = 14;                          // highest radial order (I5 of f shells)
+constexpr int kPartPitch = 16;                     // doubles per family-partial row (128 bytes, whole sectors)
 constexpr int kSkipKey = 24 * (kLaux + 1) * 34;    // work-item key of a primitive quartet the screen drops
 
 // Pair data of a basis as the kernels see it (shell-pair tables of Sec. 2.2).

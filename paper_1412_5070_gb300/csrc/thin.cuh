@@ -71,7 +71,7 @@ __device__ __forceinline__ void thin_quartet_body(const PairView &PV, const Quar
 #pragma unroll
     for (int n = 0; n <= L; ++n) g[n] = 0.0;
     for (int f = 0; f < nf; ++f) {
-      const double *pp = part + (pq * nf + f) * (kLaux + 1);
+      const double *pp = part + (pq * nf + f) * kPartPitch;
 #pragma unroll
       for (int n = 0; n <= L; ++n) g[n] += pp[n];
     }
