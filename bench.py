@@ -76,6 +76,15 @@ from paper_1412_5070_gb300 import molecules as M  # noqa: E402
 from paper_1412_5070_gb300.sharding import max_over_ranks, shard  # noqa: E402
 
 METRIC = "F12 quartets/s per class vs FP64 roofline; served p50/p99 vs plain, err<=1e-10"
+# DRAM bytes (read + written) of k_items_eval per primitive quartet, per class,
+# from one ncu capture of its launches on the 1% slices of the 12-atom lists:
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
+#       --clock-control none --nvtx --nvtx-include "profiled/" -k regex:k_items_eval
+#       python bench.py --workload slice --fraction 0.01
+# The roofline's traffic is these times the step's primitive quartets per
+# class, over the step's launches of the kernel (valid while the kernel is the
+# one captured).
+AUX_DRAM_BYTES_PER_PRIM_QUARTET = {1: 53.8, 2: 1003.1, 3: 1006.5, 4: 2643.1, 5: 1785.0, 6: 3054.0}
 UNIT = "shell quartets/s"
 CLASSES = (1, 2, 3, 4, 5, 6)
 THRESH = 1e-12
@@ -282,6 +291,15 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def aux_traffic_per_launch(nprimq, launches):
+    """DRAM bytes per launch of k_items_eval for a step over nprimq[c]
+    primitive quartets of class c in `launches` launches (the captured bytes
+    per primitive quartet, scaled)."""
+    if launches <= 0:
+        return None
+    return sum(AUX_DRAM_BYTES_PER_PRIM_QUARTET[c] * n for c, n in nprimq.items()) / launches
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -408,6 +426,7 @@ def run_ours(args):
     con_ach = kst["contract_flops"] / (kst["contract_ms"] / 1e3) / 1e12 if kst["contract_ms"] > 0 else 0.0
     dom = "aux" if kst["aux_ms"] >= kst["contract_ms"] else "contract"
     ach = aux_ach if dom == "aux" else con_ach
+    traffic = aux_traffic_per_launch(nprimq, kst["aux_launches"] / args.steps) if dom == "aux" else None
     kernels = {"k_items_eval": {"ms": kst["aux_ms"] / args.steps, "launches": kst["aux_launches"] // args.steps,
                                 "achieved_tflops": aux_ach, "flops": kst["aux_flops"] / args.steps,
                                 "share": kst["aux_ms"] / max(kst["aux_ms"] + kst["contract_ms"], 1e-9)},
@@ -427,7 +446,10 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "roofline": {"bound": "alu", "kernel": "k_items_eval" if dom == "aux" else "k_contract",
                          "achieved": ach, "peak": peak64, "unit": "TFLOP/s",
-                         "frac": ach / peak64, "traffic": None,
+                         "frac": ach / peak64, "traffic": traffic,
+                         "traffic_note": "DRAM bytes per launch, scaled from an ncu capture of the 1% slices "
+                                         "(bytes per primitive quartet and class); mostly local memory of "
+                                         "the series (window and coefficient vector per thread)",
                          "note": "FP64 pipe; achieved = counted FP64 flops of the kernel (series and quadrature "
                                  "multiply-adds for k_items_eval, the algorithmic count for k_contract) / its "
                                  "event-timed launch durations; peak = FP64 FMA rate measured in this run "

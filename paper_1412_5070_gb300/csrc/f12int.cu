@@ -1568,74 +1568,26 @@ static int work_split(int la, int lb, int lc, int ld, int cls, int64_t nprimq, i
   return ncd;
 }
 
-// Warps an SM keeps resident for blocks of nw warps with smem bytes of
-// dynamic shared memory: 228 KB per SM with 1 KB reserved per block, and 20
-// warps for the kernel's registers (80-96 per thread).
-static int resident_warps(int nw, size_t smem) {
-  const int by_smem = (int)((size_t)228 * 1024 / (smem + 1024));
-  return std::min(std::min(by_smem, 20 / nw), 32) * nw;
-}
-
-// FP64-pipe use of the general contraction against the warps that keep an SM
-// busy (measured on its launches: 39% at 4, 64% at 8, 82% near 20).
-static double contract_eff(double warps) { return std::min(0.85, 0.39 * std::pow(warps / 4.0, 0.72)); }
-
-// FP64 lane slots (idle lanes included) one primitive quartet costs with nw
-// warps per block and ns ket ranges: per range the Hermite recursion (level
-// by level over 32 lanes), the g_n and E set-up, the ket step over nh(lab)
-// x (range's components) entries and the bra step over nab x (range's
-// components) entries per bra primitive pair, shared by npcd ket pairs.
-static double plan_cost(int la, int lb, int lc, int ld, int cls, int nw, int ns, int npcd) {
-  const int ext = cls == 5 ? 2 : 0;
-  const int L = la + lb + lc + ld + ext;
-  const int nhB = nh_count(la + lb + ext);
-  const int ncd = ncart(lc) * ncart(ld), nab = ncart(la) * ncart(lb);
-  const int jc = (ncd + ns - 1) / ns;
-  auto slots = [](double n, int width) { return std::ceil(n / width) * width; };
-  double rec = 0.0;
-  for (int n = 0; n < L; ++n) rec += 2.0 * slots(nh_count(L - n), 32);
-  const double len_cd = (double)ne3_count(lc, ld) / ncd, len_ab = (double)ne3_count(la, lb) / nab;
-  double cost = 0.0;
-  for (int sp = 0; sp < ns; ++sp) {
-    const int j = std::min(jc, ncd - sp * jc);
-    if (j <= 0) break;
-    cost += rec + 1000.0;
-    cost += 2.0 * len_cd * slots((double)nhB * j, 32);
-    cost += 2.0 * len_ab * (cls == 5 ? 6 : 1) * slots((double)nab * j, 32 * nw) / npcd;
-  }
-  return cost;
-}
-
 // Warps and ket ranges per contraction block for a quartet of nprimq
-// primitive quartets with npcd ket primitive pairs: of the (warps, ranges)
-// that fit in 200 KB of shared memory, the one with the least modelled time
-// -- lane slots (plan_cost) over the FP64-pipe use of the warps the SM keeps
-// busy (resident warps times the share the ket pairs keep occupied, a block's
-// warps splitting its npcd ket pairs); then more ranges while a block would
-// exceed kTaskFlops.  Ranges and warps change neither the terms of a block
-// element nor, within a warp, their order.  smem = 0 when nothing fits.
-static ContractPlan contract_plan(int la, int lb, int lc, int ld, int cls, int64_t nprimq, int npcd,
-                                  size_t esz = 8) {
+// primitive quartets: 4 warps, else 2, on the whole ket; where neither fits
+// in 200 KB of shared memory, the fewest ket ranges that fit with 4 warps,
+// else 2, else 1; then more ranges while a block would exceed kTaskFlops.
+// smem = 0 when nothing fits.
+static ContractPlan contract_plan(int la, int lb, int lc, int ld, int cls, int64_t nprimq, size_t esz = 8) {
   const size_t cap = 200 * 1024;
   const int ncd = ncart(lc) * ncart(ld);
-  ContractPlan best{1, 1, 0};
-  double tbest = 0.0;
-  for (int nw = BLOCK_CONTRACT / 32; nw >= 1; nw /= 2)
-    for (int ns = 1; ns <= ncd; ++ns) {
-      if (!valid_split(ncd, ns)) continue;
-      const size_t sm = contract_smem(la, lb, lc, ld, cls, nw, ns, esz);
-      if (sm > cap) continue;
-      const double busy = (double)npcd / nw / ((npcd + nw - 1) / nw);
-      const double t = plan_cost(la, lb, lc, ld, cls, nw, ns, std::max(npcd, 1)) /
-                       contract_eff(resident_warps(nw, sm) * std::min(busy, 1.0));
-      if (best.smem == 0 || t < tbest * (1.0 - 1e-9)) {
-        best = ContractPlan{nw, ns, sm};
-        tbest = t;
+  int nw = 0, ns = 1;
+  for (int w = BLOCK_CONTRACT / 32; w > 1 && !nw; w /= 2)
+    if (contract_smem(la, lb, lc, ld, cls, w, 1, esz) <= cap) nw = w;
+  for (int w = BLOCK_CONTRACT / 32; w >= 1 && !nw; w /= 2)
+    for (int k = 2; k <= ncd && !nw; ++k)
+      if (valid_split(ncd, k) && contract_smem(la, lb, lc, ld, cls, w, k, esz) <= cap) {
+        nw = w;
+        ns = k;
       }
-    }
-  if (best.smem == 0) return best;
-  const int ns = work_split(la, lb, lc, ld, cls, nprimq, best.nsplit);
-  return ContractPlan{best.nw, ns, contract_smem(la, lb, lc, ld, cls, best.nw, ns, esz)};
+  if (!nw) return ContractPlan{1, 1, 0};
+  ns = work_split(la, lb, lc, ld, cls, nprimq, ns);
+  return ContractPlan{nw, ns, contract_smem(la, lb, lc, ld, cls, nw, ns, esz)};
 }
 
 static std::pair<cudaEvent_t, cudaEvent_t> take_events(f12int_ctx *ctx) {
@@ -1735,8 +1687,7 @@ static int launch_chunk(f12int_ctx *ctx, const f12int_ctx::BasisData &B, int cls
     const char f32 = ctx->h_fp32[ra];
     const size_t sm0 = ctx->h_smem[ra];
     int64_t rb = ra + 1, nt = ctx->h_split[ra];
-    while (rb < qthin && ctx->h_nw[rb] == nw && ctx->h_fp32[rb] == f32 &&
-           resident_warps(nw, ctx->h_smem[rb]) == resident_warps(nw, sm0))
+    while (rb < qthin && ctx->h_nw[rb] == nw && ctx->h_fp32[rb] == f32 && 2 * ctx->h_smem[rb] > sm0)
       nt += ctx->h_split[rb++];
     std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
     if (ctx->timing) {
@@ -1986,8 +1937,7 @@ static int compute_class_impl(f12int_ctx *ctx, int basis_id, int cls, const int3
       const int64_t np = (int64_t)B.nprim[s[0]] * B.nprim[s[1]] * B.nprim[s[2]] * B.nprim[s[3]];
       // mixed path: FP32 Hermite recursion and contraction below the bound
       const int f32 = (pb && screen_estimate(ctx, B, cls, s[0], s[1], s[2], s[3]) < fp32_below) ? 1 : 0;
-      const int64_t npcd = (int64_t)B.nprim[s[2]] * B.nprim[s[3]];
-      const int64_t gk = (((np << 7) | npcd) << 9) | (f32 << 8) | k;
+      const int64_t gk = (np << 9) | (f32 << 8) | k;
       size_t h = (size_t)((uint64_t)gk * 0x9E3779B97F4A7C15ull >> 40) & mask;
       while (slot_key[h] != -1 && slot_key[h] != gk) h = (h + 1) & mask;
       if (slot_key[h] == -1) {
@@ -2010,7 +1960,7 @@ static int compute_class_impl(f12int_ctx *ctx, int basis_id, int cls, const int3
         }
         const int la = (k >> 6) & 3, lb = (k >> 4) & 3, lc = (k >> 2) & 3, ld = k & 3;
         PlanGroup g{};
-        g.pl = contract_plan(la, lb, lc, ld, cls, np, (int)npcd, f32 ? 4 : 8);
+        g.pl = contract_plan(la, lb, lc, ld, cls, np, f32 ? 4 : 8);
         if (g.pl.smem == 0) return F12INT_EINVAL;
         g.thin = thin_quartet(k, cls);
         if (g.thin) g.pl = ContractPlan{1, 1, 0};   // one warp of the thin kernel, no shared memory
@@ -2035,7 +1985,6 @@ static int compute_class_impl(f12int_ctx *ctx, int basis_id, int cls, const int3
       if (A.thin) return (A.key & 0xFF) < (Bg.key & 0xFF) || ((A.key & 0xFF) == (Bg.key & 0xFF) && A.key < Bg.key);
       const int fa = (int)((A.key >> 8) & 1), fb = (int)((Bg.key >> 8) & 1);
       if (fa != fb) return fa < fb;
-      if (A.pl.nw != Bg.pl.nw) return A.pl.nw > Bg.pl.nw;
       if (A.pl.smem != Bg.pl.smem) return A.pl.smem > Bg.pl.smem;
       if (A.work != Bg.work) return A.work > Bg.work;
       return (A.key & 0xFF) < (Bg.key & 0xFF) || ((A.key & 0xFF) == (Bg.key & 0xFF) && A.key < Bg.key);
@@ -2319,18 +2268,13 @@ extern "C" int f12int_compute_class_static(f12int_ctx *ctx, int basis_id, int cl
   const int ns = B.nshell;
   std::vector<size_t> sm0((size_t)n);
   std::vector<int> nw0((size_t)n), sp0((size_t)n), key0((size_t)n);
-  std::unordered_map<int64_t, ContractPlan> plans;   // one plan per (primitive counts, class key)
   for (int64_t i = 0; i < n; ++i) {
     const int32_t *s = &hq0[4 * i];
     for (int k = 0; k < 4; ++k)
       if (s[k] < 0 || s[k] >= ns) return F12INT_EINVAL;
     key0[i] = (B.l[s[0]] << 6) | (B.l[s[1]] << 4) | (B.l[s[2]] << 2) | B.l[s[3]];
-    const int64_t np = (int64_t)B.nprim[s[0]] * B.nprim[s[1]] * B.nprim[s[2]] * B.nprim[s[3]];
-    const int npcd = B.nprim[s[2]] * B.nprim[s[3]];
-    const int64_t pk = (((np << 7) | npcd) << 8) | key0[i];
-    auto hit = plans.find(pk);
-    if (hit == plans.end()) hit = plans.emplace(pk, contract_plan(B.l[s[0]], B.l[s[1]], B.l[s[2]], B.l[s[3]], cls, np, npcd)).first;
-    const ContractPlan pl = hit->second;
+    const ContractPlan pl = contract_plan(B.l[s[0]], B.l[s[1]], B.l[s[2]], B.l[s[3]], cls,
+                                          (int64_t)B.nprim[s[0]] * B.nprim[s[1]] * B.nprim[s[2]] * B.nprim[s[3]]);
     if (pl.smem == 0 || pl.smem > 227 * 1024) return F12INT_EINVAL;
     nw0[i] = pl.nw;
     sp0[i] = pl.nsplit;
@@ -2344,8 +2288,6 @@ extern "C" int f12int_compute_class_static(f12int_ctx *ctx, int basis_id, int cl
   std::vector<int64_t> perm((size_t)n);
   for (int64_t i = 0; i < n; ++i) perm[i] = i;
   std::stable_sort(perm.begin(), perm.end(), [&](int64_t x, int64_t y) {
-    if ((sm0[x] == 0) != (sm0[y] == 0)) return sm0[y] == 0;   // the thin quartets last
-    if (nw0[x] != nw0[y]) return nw0[x] > nw0[y];
     if (sm0[x] != sm0[y]) return sm0[x] > sm0[y];
     return key0[x] < key0[y];
   });
@@ -2454,7 +2396,7 @@ extern "C" int f12int_compute_class_static(f12int_ctx *ctx, int basis_id, int cl
         ra = rb;
         continue;
       }
-      while (rb < qb && hnw[rb] == nwr && hsm[rb] != 0 && resident_warps(nwr, hsm[rb]) == resident_warps(nwr, smr)) ++rb;
+      while (rb < qb && hnw[rb] == nwr && 2 * hsm[rb] > smr) ++rb;
       const int64_t nt = tfirst[rb] - tfirst[ra];
       if (smr > 48 * 1024 &&
           cudaFuncSetAttribute(k_contract<false, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr) !=
