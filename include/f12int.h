@@ -314,7 +314,7 @@ int f12int_poll(f12int_ctx *ctx, uint64_t ticket, int64_t timeout_us, int *done)
 
 /* Capacity of one batch, per class: max_quartets shell quartets and
  * max_items auxiliary work items (primitive quartets times the kernel's term
- * families); each class has its own item buffers (128 bytes per item).
+ * families); each class has its own item buffers (136 bytes per item).
  * Default 2^19 quartets; the default item capacity is set from free device
  * memory when the engine starts (the six classes' item buffers take at most
  * a quarter of it, 2^26 items per class at most).  Only before the first

@@ -252,3 +252,15 @@ def test_factor_classes_query_matches_gpu_test_rule(lib):
         fpp = fp if fp is not None else f
         for cls in (2, 3, 4, 5, 6):
             assert (flags[cls] != 0) == tg.supported(f, fpp, cls), (name, cls)
+
+
+def test_bench_traffic_scaling():
+    """The roofline's traffic of the auxiliary kernel: the captured DRAM
+    bytes per primitive quartet and class, times the step's primitive
+    quartets per class, over the step's launches of the kernel."""
+    import bench
+    assert sorted(bench.AUX_DRAM_BYTES_PER_PRIM_QUARTET) == [1, 2, 3, 4, 5, 6]
+    npq = {1: 1000, 3: 2000}
+    want = (bench.AUX_DRAM_BYTES_PER_PRIM_QUARTET[1] * 1000 + bench.AUX_DRAM_BYTES_PER_PRIM_QUARTET[3] * 2000) / 4
+    assert abs(bench.aux_traffic_per_launch(npq, 4) - want) <= 1e-9 * want
+    assert bench.aux_traffic_per_launch(npq, 0) is None
