@@ -422,3 +422,22 @@ def test_random_points_wide_range(lib, name):
             nat = np.max(np.abs(refs[i]) / sc) * sc
             err = np.abs(got[i] - refs[i]) / (np.abs(refs[i]) + 1e-3 * nat)
             assert err.max() < tol, (cls, x, d, float(err.max()))
+
+
+@pytest.mark.parametrize("cls", [1, 2, 3, 4])
+def test_gaussian_families_from_the_kummer_table(lib, cls):
+    """A Gaussian geminal's kernels have only b = 0 families, which the stage
+    takes from its table of e^{-x} M(a, l + 3/2, x) (x = xi^2 D^2 / gamma,
+    grid step 1/2, 14 Taylor terms) wherever x < 100.  Points at the largest
+    Taylor step (x half-way between grid points) and at the table's end
+    (x = 99.75), orders up to 14, against the oracle."""
+    gam = 0.7
+    t = [(1.0, 0, 0, gam)]
+    g = {1: 0.0, 2: gam, 3: gam, 4: 2 * gam}[cls]          # the family's Gaussian exponent
+    pts = []
+    for xi in (0.3, 2.0, 15.0):
+        for x in (0.25, 10.25, 49.75, 99.75):
+            pts.append((xi, float(np.sqrt(x * (g + xi)) / xi)))
+    rc, got = host_aux_terms(lib, t, t, cls, pts, 14)
+    assert rc == 0
+    assert worst_relative(got, O.factor_kernel_terms(t), cls, pts, 14) < 1e-12   # measured: 2.6e-13 at worst
