@@ -456,6 +456,8 @@ def run_ours(args):
                                  "(f12int_measure_peak), of measured"},
             "peaks_tflops": peaks,
             "kernels": kernels,
+            "streams": {"output_bytes_per_step": int(d2h), "output_gbs": d2h / (ms / 1e3) / 1e9,
+                        "note": "dense FP64 blocks the contraction writes per step, over the device step time"},
             "clocks": clk.summary()}
     if rank == 0 and not args.no_cpu_baseline:
         # the oracle samples from the canonical lists: its inputs never come from the CUDA path
