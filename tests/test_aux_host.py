@@ -441,3 +441,30 @@ def test_gaussian_families_from_the_kummer_table(lib, cls):
     rc, got = host_aux_terms(lib, t, t, cls, pts, 14)
     assert rc == 0
     assert worst_relative(got, O.factor_kernel_terms(t), cls, pts, 14) < 1e-12   # measured: 2.6e-13 at worst
+
+
+@pytest.mark.parametrize("cls", [2, 3, 4, 6])
+def test_series_start_values_from_the_y_table(lib, cls):
+    """The series families with b > 0 take their start values J_as, J_as+1
+    (and, for the finite-part family of I6, the S(-1) series) from a table in
+    y = b / sqrt(g + xi) by Taylor steps from the nearest grid point (step
+    1/16).  For every such family of the default factor, xi is chosen so that
+    y sits half-way between grid points (the largest step), from y = 0.28 to
+    19.03, where the series serves the high orders (z = y^2/4 at D = 0, and a
+    small D); orders up to 14 against the oracle."""
+    f = M.P0
+    b_g = {2: [(0.5, 0.0), (0.5, 1.0)], 3: [(0.5, 0.0), (0.5, 1.0)],
+           4: [(0.5, 1.0), (0.5, 2.0), (1.0, 0.0), (1.0, 1.0), (1.0, 2.0)],
+           6: [(0.5, 1.0), (0.5, 2.0), (1.0, 0.0), (1.0, 1.0), (1.0, 2.0)]}[cls]
+    pts = []
+    for b, g in b_g:
+        for i in (4, 40, 100, 200, 304):
+            y = (i + 0.5) / 16.0
+            xi = (b / y) ** 2 - g
+            if xi <= 1e-3:
+                continue
+            pts += [(xi, 0.0), (xi, 0.02 / np.sqrt(xi))]
+    rc, got = host_aux(lib, f, f, cls, pts, 14)
+    assert rc == 0
+    # measured: 2.3e-13 at worst (I2-I4), 6e-11 for I6 (its families cancel at order 14)
+    assert worst_relative(got, O.factor_kernel(f), cls, pts, 14) < (2e-10 if cls == 6 else 1e-12)
