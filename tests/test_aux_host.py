@@ -468,3 +468,33 @@ def test_series_start_values_from_the_y_table(lib, cls):
     assert rc == 0
     # measured: 2.3e-13 at worst (I2-I4), 6e-11 for I6 (its families cancel at order 14)
     assert worst_relative(got, O.factor_kernel(f), cls, pts, 14) < (2e-10 if cls == 6 else 1e-12)
+
+
+@pytest.mark.parametrize("cls", [1, 2, 3, 4, 6])
+def test_short_peak_rule_at_its_threshold(lib, cls):
+    """Far from r = 0 (z >= 60 + 12 l) orders l <= 3 take the 10-node
+    Gauss-Hermite rule about the peak instead of 16 nodes.  For every family
+    of the default factor, points just past the switch of each order 0..3
+    (z = 60.01 + 12 l at xi = 1), orders up to 14, against the oracle:
+    orders 0..3 relative to themselves, all orders against the natural scale
+    max(|g_n|, (2 xi)^n |g_0|) (far from r = 0 the high orders are sums over
+    the families that cancel to far below that scale)."""
+    f = M.P0
+    fam = {1: [(0.0, 0.0)], 2: [(0.0, 1.0), (0.5, 0.0), (0.5, 1.0)], 3: [(0.0, 1.0), (0.5, 0.0), (0.5, 1.0)],
+           4: [(0.0, 2.0), (0.5, 1.0), (0.5, 2.0), (1.0, 0.0), (1.0, 1.0), (1.0, 2.0)],
+           6: [(0.0, 2.0), (0.5, 1.0), (0.5, 2.0), (1.0, 0.0), (1.0, 1.0), (1.0, 2.0)]}[cls]
+    xi = 1.0
+    pts = []
+    for b, g in fam:
+        for l in range(4):
+            z = 60.01 + 12.0 * l
+            pts.append((xi, (np.sqrt(4.0 * z * (g + xi)) - b) / (2.0 * xi)))
+    rc, got = host_aux(lib, f, f, cls, pts, 14)
+    assert rc == 0
+    kern = O.factor_kernel(f)
+    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        refs = list(ex.map(lambda p: O.radial(kern, cls, p[0], p[1], 14), pts))
+    low = max(float(np.max(np.abs(got[i][:4] - r[:4]) / np.abs(r[:4]))) for i, r in enumerate(refs))
+    nat = max(float(np.max(np.abs(got[i] - r) / np.maximum(np.abs(r), (2 * xi) ** np.arange(15) * abs(r[0]))))
+              for i, r in enumerate(refs))
+    assert low < 1e-14 and nat < 1e-14, (low, nat)   # measured: 7.8e-16 and 7.4e-16 at worst
