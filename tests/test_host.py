@@ -264,3 +264,62 @@ def test_bench_traffic_scaling():
     want = (bench.AUX_DRAM_BYTES_PER_PRIM_QUARTET[1] * 1000 + bench.AUX_DRAM_BYTES_PER_PRIM_QUARTET[3] * 2000) / 4
     assert abs(bench.aux_traffic_per_launch(npq, 4) - want) <= 1e-9 * want
     assert bench.aux_traffic_per_launch(npq, 0) is None
+
+
+def _cart(l):
+    return [(i, j, l - i - j) for i in range(l, -1, -1) for j in range(l - i, -1, -1)]
+
+
+def test_ket_term_count_order_visits_every_entry_once():
+    """The general contraction's ket step takes its (bra Hermite index, ket
+    component) entries in order of the component's term count: a task builds
+    kord (the components by increasing count, then the class starts at
+    KORD_CLS) and lane r of the flat loop maps to (bi, j) through the class
+    it falls in.  Replayed here for every (lc, ld), ket-range split and bra
+    order the kernel serves: each entry is visited exactly once and the
+    indexes stay inside kord's 116 entries."""
+    KORD_CLS, KORD_SIZE = 100, 116
+    nh = lambda L: (L + 1) * (L + 2) * (L + 3) // 6
+    for lc in range(4):
+        for ld in range(4):
+            nd = len(_cart(ld))
+            ncd_all = len(_cart(lc)) * nd
+            for nsplit in range(1, ncd_all + 1):
+                jc = (ncd_all + nsplit - 1) // nsplit
+                if (ncd_all + jc - 1) // jc != nsplit:
+                    continue
+                for split in range(nsplit):
+                    j0 = split * jc
+                    ncd = min(jc, ncd_all - j0)
+                    off = [0]
+                    for j in range(ncd):
+                        ec, ed = _cart(lc)[(j0 + j) // nd], _cart(ld)[(j0 + j) % nd]
+                        off.append(off[-1] + (ec[0] + ed[0] + 1) * (ec[1] + ed[1] + 1) * (ec[2] + ed[2] + 1))
+                    kord = [None] * KORD_SIZE
+                    nc, pos = 0, 0
+                    while pos < ncd:
+                        prev = off[kord[pos - 1] + 1] - off[kord[pos - 1]] if nc else 0
+                        ln = min(off[j + 1] - off[j] for j in range(ncd) if off[j + 1] - off[j] > prev)
+                        kord[KORD_CLS + nc] = pos
+                        for j in range(ncd):
+                            if off[j + 1] - off[j] == ln:
+                                kord[pos] = j
+                                pos += 1
+                        nc += 1
+                    kord[KORD_CLS + nc] = ncd
+                    assert KORD_CLS + nc < KORD_SIZE
+                    for lb_ext in range(0, 9):
+                        nhB = nh(lb_ext)
+                        seen = set()
+                        for lane in range(32):
+                            c = 0
+                            for r in range(lane, nhB * ncd, 32):
+                                while r >= nhB * kord[KORD_CLS + c + 1]:
+                                    c += 1
+                                c0, n_c = kord[KORD_CLS + c], kord[KORD_CLS + c + 1] - kord[KORD_CLS + c]
+                                rr = r - nhB * c0
+                                bi = rr // n_c
+                                j = kord[c0 + rr - bi * n_c]
+                                assert 0 <= bi < nhB and 0 <= j < ncd
+                                seen.add((bi, j))
+                        assert len(seen) == nhB * ncd
